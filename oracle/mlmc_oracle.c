@@ -205,6 +205,8 @@ typedef struct {
     int64_t* r;      /* c_l drawn indices */
     double* Asel;    /* m x c_l: column t is A[:, r_t] of this realisation */
     double* Bsel;    /* c_l x p: row t is B[r_t, :] of this realisation */
+    double* Aabs;    /* m x c_l: |M| + |S| |Z| of the same entries */
+    double* Babs;    /* c_l x p: |M'| + |S'| |Z'| of the same entries */
 } realisation;
 
 static void quantise_e4m3_blocks(double* X, int64_t rows, int64_t cols, int along_rows)
@@ -236,20 +238,25 @@ static int draw_realisation(const orc_problem* pr, const orc_levels* lv, int l, 
     int64_t m = pr->m, n = pr->n, p = pr->p;
     int64_t c = orc_cl(lv, l);
     rz->c = c;
+    rz->r = NULL; rz->Asel = rz->Bsel = rz->Aabs = rz->Babs = NULL;
     rz->r = (int64_t*)malloc(sizeof(int64_t) * (size_t)c);
     rz->Asel = (double*)malloc(sizeof(double) * (size_t)(m * c));
     rz->Bsel = (double*)malloc(sizeof(double) * (size_t)(c * p));
-    if (!rz->r || !rz->Asel || !rz->Bsel) return -1;
+    rz->Aabs = (double*)malloc(sizeof(double) * (size_t)(m * c));
+    rz->Babs = (double*)malloc(sizeof(double) * (size_t)(c * p));
+    if (!rz->r || !rz->Asel || !rz->Bsel || !rz->Aabs || !rz->Babs) return -1;
     for (int64_t t = 0; t < c; ++t) rz->r[t] = orc_index(pr->seed_idx, pr->problem_id, l, s, t, n);
     for (int64_t t = 0; t < c; ++t) {
         int64_t k = rz->r[t];
         for (int64_t i = 0; i < m; ++i) {
             double z = orc_normal(pr->seed_A, pr->problem_id, l, s, i, k);
             rz->Asel[i * c + t] = pr->M[i * n + k] + pr->S[i * n + k] * z;
+            rz->Aabs[i * c + t] = fabs(pr->M[i * n + k]) + fabs(pr->S[i * n + k] * z);
         }
         for (int64_t j = 0; j < p; ++j) {
             double z = orc_normal(pr->seed_B, pr->problem_id, l, s, j, k);
             rz->Bsel[t * p + j] = pr->Mp[k * p + j] + pr->Sp[k * p + j] * z;
+            rz->Babs[t * p + j] = fabs(pr->Mp[k * p + j]) + fabs(pr->Sp[k * p + j] * z);
         }
     }
     if (quant == ORC_QUANT_BF16) {
@@ -267,10 +274,12 @@ static void free_realisation(realisation* rz)
     free(rz->r);
     free(rz->Asel);
     free(rz->Bsel);
+    free(rz->Aabs);
+    free(rz->Babs);
 }
 
 /* out = scale * sum_{slots t = first, first+stride, ...} Asel[:,t] Bsel[t,:];
- * if mag != NULL, mag += |scale| * sum |Asel[i,t] Bsel[t,j]| over the same t. */
+ * if mag != NULL, mag += |scale| * sum Aabs[i,t] Babs[t,j] over the same t. */
 static void sampled_sum(int64_t m, int64_t p, const realisation* rz, int64_t first, int64_t stride,
                         double scale, double* out, double* mag)
 {
@@ -282,7 +291,7 @@ static void sampled_sum(int64_t m, int64_t p, const realisation* rz, int64_t fir
             for (int64_t j = 0; j < p; ++j) {
                 double b = rz->Bsel[t * p + j];
                 out[i * p + j] += a * b;
-                if (mag) mag[i * p + j] += fabs(scale) * fabs(a * b);
+                if (mag) mag[i * p + j] += fabs(scale) * rz->Aabs[i * c + t] * rz->Babs[t * p + j];
             }
         }
     }
@@ -298,8 +307,10 @@ void orc_sample(const orc_problem* pr, const orc_levels* lv, int l, uint64_t s, 
     double* fine = (double*)malloc(sz);
     double* coarse = (double*)calloc((size_t)(m * p), sizeof(double));
     if (mag) memset(mag, 0, sz);
-    if (!fine || !coarse || draw_realisation(pr, lv, l, s, quant, &rz) != 0) {
+    int drawn = draw_realisation(pr, lv, l, s, quant, &rz);
+    if (!fine || !coarse || drawn != 0) {
         for (int64_t e = 0; e < m * p; ++e) D[e] = NAN;
+        free_realisation(&rz);
         free(fine);
         free(coarse);
         return;

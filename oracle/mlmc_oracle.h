@@ -100,8 +100,9 @@ void orc_sketch(int64_t m, int64_t n, int64_t p, const double* A, const double* 
  *   Pf  = fine estimate from all c_l draws,
  *   Pc  = coarse estimate from the draws r_{jR}, j = 1..c_{l-1} (zero at l = 0),
  *   D   = Pf - Pc,
- *   mag = sum over the products that enter D of |weight * A_it * B_tj|
- *         (the magnitude against which rounding error is measured).
+ *   mag = sum over the products that enter D of |weight| (|M_ik| + |S_ik Z_ik|)
+ *         (|M'_kj| + |S'_kj Z'_kj|) with k = r_t: the magnitude against which
+ *         rounding error, including that of the generated entries, is measured.
  * quant rounds every sampled A and B entry first (ORC_QUANT_*); for E4M3 the
  * scales are the power-of-two absmax block scales described in
  * orc_e4m3_block_scale. */

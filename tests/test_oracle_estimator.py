@@ -60,12 +60,16 @@ def test_bruteforce_sketch_and_coupled_difference(n, c, R):
     assert np.isclose(sum_D2 / N, (1.0 / cc - 1.0 / c) * _bracket(A, B), rtol=1e-10)
 
 
-def _realised(pr, l, s):
-    """The full realisation A, B of sample s at level l, entry by entry (tiny n only)."""
+def _realised(pr, l, s, magnitudes=False):
+    """The full realisation A, B of sample s at level l, entry by entry (tiny n only);
+    with magnitudes=True, also |M| + |S||Z| and |M'| + |S'||Z'|."""
     sA, sB, _, pid = pr.seeds
     ZA = np.array([[oracle.normal(sA, pid, l, s, i, k) for k in range(pr.n)] for i in range(pr.m)])
     ZB = np.array([[oracle.normal(sB, pid, l, s, j, k) for j in range(pr.p)] for k in range(pr.n)])
-    return pr.M + pr.S * ZA, pr.Mp + pr.Sp * ZB
+    A, B = pr.M + pr.S * ZA, pr.Mp + pr.Sp * ZB
+    if magnitudes:
+        return A, B, np.abs(pr.M) + np.abs(pr.S * ZA), np.abs(pr.Mp) + np.abs(pr.Sp * ZB)
+    return A, B
 
 
 @pytest.mark.parametrize("R", [2, 3])
@@ -77,7 +81,7 @@ def test_sample_is_the_coupled_pair_of_one_realisation(R):
         for s in (0, 3, 2**33 + 1):
             c = lv.cl(l)
             idx = np.array([oracle.index(6, 1, l, s, t, pr.n) for t in range(c)])
-            A, B = _realised(pr, l, s)
+            A, B, Aa, Ba = _realised(pr, l, s, magnitudes=True)
             D, Pf, Pc, mag = oracle.sample(pr, lv, l, s)
             np.testing.assert_allclose(Pf, oracle.sketch(A, B, idx), rtol=1e-13, atol=1e-13)
             if l == 0:
@@ -88,9 +92,10 @@ def test_sample_is_the_coupled_pair_of_one_realisation(R):
                 np.testing.assert_allclose(Pc, oracle.sketch(A, B, sel), rtol=1e-13, atol=1e-13)
             np.testing.assert_array_equal(D, Pf - Pc)
             w = pr.n / c
-            terms = np.abs(A[:, idx]) @ np.abs(B[idx, :]) * w
+            terms = Aa[:, idx] @ Ba[idx, :] * w
             if l > 0:
-                terms += np.abs(A[:, sel]) @ np.abs(B[sel, :]) * (pr.n / (c // R))
+                terms += Aa[:, sel] @ Ba[sel, :] * (pr.n / (c // R))
+            assert np.all(mag >= np.abs(Pf) + np.abs(Pc) - 1e-12 * mag)
             np.testing.assert_allclose(mag, terms, rtol=1e-12)
 
 
