@@ -1,0 +1,362 @@
+"""Benchmark: time-to-RMSE 1e-3 of the MLMC estimate of E[AB] on one GB300.
+
+Workload ("mlmc_256x65536x256"): A 256 x 65536, B 65536 x 256, A = M + S o Z, B = M' + S' o Z'
+with M ~ U[-1,1], S ~ U[0.1,1] (A from seed 0, B from seed 1), c_l = 64 * 2^l for l = 0..8,
+N_l from the variance-optimal allocation (Remark 3.6) of 256 pilot samples per level for an
+absolute Frobenius tolerance eps = 1e-3 * ||E[AB]||_F = 1e-3 * ||M M'||_F.
+
+A full run at that tolerance evaluates about 5e13 sampled outer products (hours on one GPU),
+so the benchmark measures the exact work mix instead: after the pilot and the allocation
+(untimed setup), every step evaluates B_l = ceil(f * N_l) fresh samples of every level l
+(f fixed, sample ids continue across steps) through ``mlmc_level_stats``, the per-level
+statistics included, followed by the telescoping sum.  Samples are independent and the
+estimator has no bias for f = identity, so the time of the full run is
+    T(1e-3) = sum_l N_l * t_l / B_l
+with t_l the measured device time of level l's batches (CUDA events on the plan's stream).
+``value`` is that projected time in seconds (lower is better).
+
+e2e: the same metric through the C ABI from pinned host buffers: each e2e step copies the
+four parameter matrices host->device, builds a plan (layout copy), runs the step's batches
+and reads the estimate back; T_e2e = (e2e step time - its sampling time) + sum_l N_l t_l / B_l.
+
+--impl reference: the FP64 CPU oracle (test infrastructure) timed on the host cores on one
+sample per level per step, projected the same way.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = dict(name="mlmc_256x65536x256", m=256, n=65536, p=256, c0=64, R=2, L=8, pilot=256, rel_rmse=1e-3)
+FRACTION = {"fp32": 2.0**-20, "fp64": 2.0**-26, "bf16": 2.0**-18, "fp8": 2.0**-18}
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # CUDA-core FMA lanes x 2 flop x max SM clock
+FP64_PEAK_TFLOPS = 1.25
+
+
+def read_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu_index = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu_index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def batch_sizes(Nl, frac):
+    return [max(8, int(math.ceil(frac * n))) for n in Nl]
+
+
+def run_reference(args):
+    """The oracle (test infrastructure) on the host cores: one sample per level per step."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1904_00429_gb300.inputs import make_params
+    W = WORKLOAD
+    pp = make_params(W["m"], W["n"], W["p"], seed_A=0, seed_B=1, dtype=np.float32)
+    orc = oracle.Problem(*pp.f64())
+    lv = oracle.Levels(W["c0"], W["R"], W["L"])
+    levels = list(range(W["L"] + 1))
+    # allocation from the closed-form level variances of this law would need no sampling, but the
+    # reference arm reuses the device arm's quantity: N_l for eps from per-level variances of the
+    # oracle's own pilot is out of reach on a CPU, so N_l comes from the closed form of V_l.
+    Nl = closed_form_allocation(pp, W)
+    per_level = {l: [] for l in levels}
+    step_times = []
+    s_next = 0
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        for l in levels:
+            t1 = time.perf_counter()
+            oracle.sample(orc, lv, l, s_next)
+            if it >= args.warmup:
+                per_level[l].append(time.perf_counter() - t1)
+        s_next += 1
+        if it >= args.warmup:
+            step_times.append(time.perf_counter() - t0)
+    t_l = [statistics.mean(per_level[l]) for l in levels]
+    T = sum(n * t for n, t in zip(Nl, t_l))
+    line = {"impl": "reference", "metric": "time-to-RMSE 1e-3 for E[AB] (projected from the measured per-level "
+            "sample rate)", "value": T, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.mean(step_times), "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": W["name"], "m": W["m"], "n": W["n"], "p": W["p"], "c0": W["c0"], "L": W["L"],
+                       "N_l": Nl, "sample": "one oracle sample per level per step"},
+            "cpu_baseline": {"value": T, "unit": "s", "cores": 1, "kind": "oracle",
+                             "sample": "one FP64 oracle sample per level 0..8 per step, single thread"},
+            "e2e": {"value": T, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def closed_form_allocation(pp, W):
+    """N_l for eps from the closed-form single-sample variances of the Gaussian law (used only
+    to size the CPU reference arm; the device arm allocates from its own pilot)."""
+    M, S, Mp, Sp = pp.f64()
+    n = W["n"]
+    Q = (M**2 + S**2) @ (Mp**2 + Sp**2)
+    Rr = (M**2) @ (Mp**2)
+    mu = M @ Mp
+    K = float((n * Q - Q + Rr - mu**2).sum())
+    c = [W["c0"] * W["R"]**l for l in range(W["L"] + 1)]
+    V = [float((((n * Q - Q + Rr - mu**2) / c[0]) + Q - Rr).sum())] + \
+        [(1.0 / c[l - 1] - 1.0 / c[l]) * K for l in range(1, W["L"] + 1)]
+    C = [c[0]] + [c[l] + c[l - 1] for l in range(1, W["L"] + 1)]
+    eps = W["rel_rmse"] * float(np.linalg.norm(mu))
+    root = sum(math.sqrt(v * cc) for v, cc in zip(V, C))
+    return [max(W["pilot"], int(math.ceil(2.0 / eps**2 * math.sqrt(v / cc) * root))) for v, cc in zip(V, C)]
+
+
+def cpu_baseline_sample(W, budget_s=20.0):
+    """The oracle timed on a bounded sample (one sample per level, levels 0..8) on one host core."""
+    import oracle
+    from paper_1904_00429_gb300.inputs import make_params
+    pp = make_params(W["m"], W["n"], W["p"], seed_A=0, seed_B=1, dtype=np.float32)
+    orc = oracle.Problem(*pp.f64())
+    lv = oracle.Levels(W["c0"], W["R"], W["L"])
+    t_l = []
+    start = time.perf_counter()
+    for l in range(W["L"] + 1):
+        t0 = time.perf_counter()
+        oracle.sample(orc, lv, l, 1 << 40)
+        t_l.append(time.perf_counter() - t0)
+        if time.perf_counter() - start > budget_s:
+            # extrapolate the remaining levels by the per-slot cost of the last one
+            per_slot = t_l[-1] / lv.cl(l)
+            t_l += [per_slot * lv.cl(k) for k in range(l + 1, W["L"] + 1)]
+            break
+    return t_l, pp
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1904_00429_gb300 import binding
+    from paper_1904_00429_gb300.inputs import make_params
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    W = WORKLOAD
+    prec = args.precision
+    pdtype = torch.float64 if prec == "fp64" else torch.float32
+    npdtype = np.float64 if prec == "fp64" else np.float32
+    pp = make_params(W["m"], W["n"], W["p"], seed_A=0, seed_B=1, dtype=npdtype)
+    host = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in (pp.M, pp.S, pp.Mp, pp.Sp)]
+    dev_params = [h.to(dev, non_blocking=True) for h in host]
+    torch.cuda.synchronize()
+    eps = W["rel_rmse"] * float(np.linalg.norm(pp.exact_mean()))
+    stream = torch.cuda.current_stream(dev)
+
+    def make_plan(tensors):
+        spec = binding.ProblemSpec(*tensors, seed_A=0, seed_B=1, seed_idx=2, problem_id=rank)
+        return binding.Plan([spec], c0=W["c0"], L=W["L"], ratio=W["R"], precision=prec, pilot_n=W["pilot"],
+                            stream=stream)
+
+    plan = make_plan(dev_params)
+    levels = list(range(W["L"] + 1))
+    for l in levels:
+        plan.level_stats(0, l, 0, W["pilot"])
+    Nl = plan.allocate([eps])[0]
+    B = batch_sizes(Nl, FRACTION[prec])
+    next_id = [W["pilot"]] * len(levels)
+
+    def step(p, timing):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(levels) + 1)]
+        ev[0].record(stream)
+        for i, l in enumerate(levels):
+            p.level_stats(0, l, next_id[l], B[l])
+            next_id[l] += B[l]
+            ev[i + 1].record(stream)
+        p.telescoping_sum()
+        timing.append(ev)
+
+    for _ in range(args.warmup):
+        step(plan, [])
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    launches0 = plan.launch_count()
+    timings = []
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        torch.cuda.synchronize()
+        t_start.record(stream)
+        for _ in range(args.steps):
+            step(plan, timings)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    launches = plan.launch_count() - launches0
+    total_ms = t_start.elapsed_time(t_end)
+    lvl_ms = [sum(ev[i].elapsed_time(ev[i + 1]) for ev in timings) for i in range(len(levels))]
+    t_l = [ms / 1e3 / (args.steps * B[l]) for l, ms in zip(levels, lvl_ms)]   # seconds per sample
+    T_proj = sum(n * t for n, t in zip(Nl, t_l))
+    if world > 1:
+        tt = torch.tensor([T_proj, total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        T_proj, total_ms = float(tt[0]) / world, float(tt[1])   # ranks split the samples (weak per-GPU work)
+
+    # roofline of the level kernel: algorithmic flops and gathered bytes per sampled outer product
+    m, n, p = W["m"], W["n"], W["p"]
+    outer = sum(args.steps * B[l] * plan.cl(l) for l in levels)
+    sample_s = sum(lvl_ms) / 1e3
+    flops = 2.0 * m * p * outer
+    elem = 8 if prec == "fp64" else 4
+    bytes_alg = 2.0 * (m + p) * elem * outer
+    peaks, peak_kind = read_peaks()
+    if prec in ("fp32", "fp64"):
+        peak = FP32_PEAK_TFLOPS if prec == "fp32" else FP64_PEAK_TFLOPS
+        achieved = flops / sample_s / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": None, "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)",
+                    "hbm_achieved_gbs": bytes_alg / sample_s / 1e9, "hbm_peak_gbs": peaks["hbm_gbs"],
+                    "kernel": f"level_cuda_core_kernel<{prec}>"}
+    else:
+        peak = peaks["bf16_tflops_sustained"] * (2.0 if prec == "fp8" else 1.0)
+        achieved = flops / sample_s / 1e12
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None, "peak_source": f"bf16 sustained ({peak_kind})"}
+
+    # e2e through the C ABI from pinned host buffers
+    e2e_ms, e2e_sample_ms = [], []
+    out_host = torch.empty(m * p, dtype=torch.float64).pin_memory()
+    for it in range(args.warmup + max(1, min(args.steps, 3))):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        tensors = [h.to(dev, non_blocking=True) for h in host]
+        p2 = make_plan(tensors)
+        tm = []
+        step(p2, tm)
+        y = p2.telescoping_sum()[0]
+        out_host.copy_(y.reshape(-1), non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        p2.close()
+        if it >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+            e2e_sample_ms.append(sum(tm[0][i].elapsed_time(tm[0][i + 1]) for i in range(len(levels))))
+    overhead_s = (statistics.mean(e2e_ms) - statistics.mean(e2e_sample_ms)) / 1e3
+    E = overhead_s + T_proj
+    h2d = sum(h.numel() * h.element_size() for h in host)
+
+    if rank != 0:
+        return
+    line = {
+        "metric": "time-to-RMSE 1e-3 for E[AB] (projected from the measured per-level sample rate)",
+        "value": T_proj, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64", "bf16": "bf16", "fp8": "e4m3"}[prec],
+        "data": "synthetic",
+        "config": {"workload": W["name"], "m": m, "n": n, "p": p, "c0": W["c0"], "ratio": W["R"], "L": W["L"],
+                   "pilot": W["pilot"], "eps_abs": eps, "N_l": Nl, "batch_per_step": B,
+                   "inputs": "parameters 256 MiB > L2 (random row gathers), no flush",
+                   "precision": prec},
+        "outer_products_per_s": outer / sample_s,
+        "per_level_us_per_sample": [1e6 * t for t in t_l],
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "clocks": clocks.summary(),
+        "e2e": {"value": E, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": m * p * 8,
+                "overhead_s": overhead_s},
+    }
+    if not args.no_cpu_baseline and world == 1:
+        t_cpu, _ = cpu_baseline_sample(W)
+        T_cpu = sum(nl * t for nl, t in zip(Nl, t_cpu))
+        line["cpu_baseline"] = {"value": T_cpu, "unit": "s", "cores": 1, "kind": "oracle",
+                                "sample": "one FP64 oracle sample per level 0..8 (about 20 s of CPU work), "
+                                          "projected with the same N_l"}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32", "fp64", "bf16", "fp8"], default="fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,261 @@
+/*
+ * mlmc.h -- C ABI of the GB300 (sm_103a) multilevel Monte Carlo estimator of
+ * E[AB] for random matrices (Wu & Polydorides, "A Multilevel Monte Carlo
+ * Estimator for Matrix Multiplication", arXiv:1904.00429).
+ *
+ * The problem (Sec. 3): A is a random m x n matrix and B a random n x p
+ * matrix with independent entries; the target is E[AB].  Entries follow the
+ * Gaussian reparameterisation
+ *     A_ik = M_ik + S_ik Z_ik,   B_kj = M'_kj + S'_kj Z'_kj,   Z, Z' ~ N(0,1),
+ * so the caller supplies the four parameter matrices M, S (m x n) and
+ * M', S' (n x p).  Level l draws c_l = c0 R^l indices r_t uniformly from
+ * {0..n-1} (Eq. unique) and forms, from one realisation of A and B, the fine
+ * sketch P_l = (n/c_l) sum_t A[:,r_t] B[r_t,:] (Eq. matrixsketch) and the
+ * coarse sketch P_{l-1} = (n/c_{l-1}) sum_j A[:,r_{jR}] B[r_{jR},:] from every
+ * R-th draw (Sec. 3.1, Alg. 1).  Sample s of level l is D = P_l - P_{l-1}
+ * (D = P_0 at l = 0).  The estimator is Yhat = sum_l Y_l with Y_l the mean of
+ * N_l samples of level l (Eq. hatYl, Eq. hatY); the N_l follow the
+ * variance-optimal allocation of Remark 3.6 from pilot variances (Alg. 2).
+ *
+ * Random numbers are counter-based (Philox4x32-10, Salmon et al., SC'11), so
+ * every draw is a pure function of (seed, problem, level, sample, entry):
+ *   Z of A entry (i, k): key (seed_A, problem_id), counter (i/4, k, s_lo, s_hi<<8 | l)
+ *   Z' of B entry (k, j): key (seed_B, problem_id), counter (j/4, k, s_lo, s_hi<<8 | l)
+ *   index of slot t:      key (seed_idx, problem_id), counter (t/2, 0xFFFFFFFF, s_lo, s_hi<<8 | l)
+ * with Box-Muller on word pairs (w0,w1), (w2,w3) (cosine branch for even
+ * i mod 4, sine for odd), uniforms (w + 1/2) 2^-32, and indices
+ * floor(word64 * n / 2^64) from (w1:w0) for even t and (w3:w2) for odd t.
+ * Results therefore do not depend on grid shapes, on how sample ranges are
+ * split across calls, or on the device.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named *_dev are device pointers (cudaMalloc'd or torch CUDA
+ *     storage) on the device that was current when the plan was made; every
+ *     other pointer is host memory.  The caller owns all memory it passes;
+ *     the plan owns only its internal scratch.
+ *   - Matrices are dense row-major with the stated leading dimension.
+ *   - No entry point aborts, throws or prints.  Each returns an mlmc_status;
+ *     the first error seen by a plan sticks and is returned by every later
+ *     call on that plan.  mlmc_last_error() gives a thread-local message.
+ *   - Work is enqueued on the plan's stream and is asynchronous unless the
+ *     function says otherwise.
+ */
+#ifndef MLMC_H
+#define MLMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MLMC_MAX_LEVELS 32
+
+#if defined(__GNUC__)
+#define MLMC_API __attribute__((visibility("default")))
+#else
+#define MLMC_API
+#endif
+
+typedef enum {
+    MLMC_OK = 0,
+    MLMC_ERR_INVALID_ARG = 1,  /* a size, pointer, level or option is out of range */
+    MLMC_ERR_CUDA = 2,         /* a CUDA runtime call or kernel launch failed */
+    MLMC_ERR_OOM = 3,          /* device allocation of the plan's scratch failed */
+    MLMC_ERR_TIMEOUT = 4,      /* a bounded device wait gave up */
+    MLMC_ERR_NUMERIC = 5,      /* a statistic became NaN or infinite */
+    MLMC_ERR_UNSUPPORTED = 6,  /* valid request this build does not implement */
+    MLMC_ERR_STATE = 7         /* call out of order (e.g. backward before estimate) */
+} mlmc_status;
+
+/* Arithmetic of the sampled entries and of the rank-c_l contraction.  The
+ * per-level statistics, the allocation and the telescoping sum are FP64 in
+ * every precision. */
+typedef enum {
+    MLMC_FP64 = 0,     /* FP64 entries, FP64 CUDA-core contraction */
+    MLMC_FP32 = 1,     /* FP32 entries, FP32 CUDA-core contraction */
+    MLMC_BF16 = 2,     /* FP32 entries rounded to bfloat16, tensor-core contraction, FP32 accumulation */
+    MLMC_FP8_E4M3 = 3  /* FP32 entries scaled per 32-slot block and rounded to E4M3, FP32 accumulation */
+} mlmc_precision;
+
+/* Element type of the caller's parameter matrices. */
+typedef enum { MLMC_DTYPE_F64 = 0, MLMC_DTYPE_F32 = 1 } mlmc_dtype;
+
+/* One problem.  M, S: m x n with leading dimension ldA >= n; Mp, Sp: n x p
+ * with leading dimension ldB >= p; all four of element type `dtype`, device
+ * memory.  The plan copies them once (mlmc_plan) into its own sample-major
+ * layout, so they may be freed or changed afterwards without affecting it.
+ * Limits: 1 <= m, p <= 65536, 1 <= n < 2^31. */
+typedef struct {
+    int64_t m, n, p;
+    const void* M_dev;
+    const void* S_dev;
+    int64_t ldA;
+    const void* Mp_dev;
+    const void* Sp_dev;
+    int64_t ldB;
+    int32_t dtype;       /* mlmc_dtype */
+    int32_t L;           /* finest level of this problem; < 0 means options.L */
+    uint32_t seed_A, seed_B, seed_idx, problem_id;
+} mlmc_problem;
+
+/* Level schedule and method options shared by the problems of a plan. */
+typedef struct {
+    int32_t c0;          /* c_0 >= 1 indices at level 0 */
+    int32_t ratio;       /* R >= 2: c_l = c0 R^l (the paper's base number M) */
+    int32_t L;           /* default finest level, 0 <= L < MLMC_MAX_LEVELS */
+    int32_t precision;   /* mlmc_precision */
+    int64_t pilot_n;     /* pilot samples per level used by mlmc_estimate (>= 2) */
+    double nl_scale;     /* factor on the allocated N_l (Remark 2.6 oversampling control), > 0 */
+    int64_t timeout_ns;  /* bound on any device-side wait; 0 = 2 s */
+    int32_t tile_override; /* 0 = automatic tile choice; otherwise an internal tile id */
+    int32_t reserved;
+} mlmc_options;
+
+/* Report of one problem after mlmc_estimate. */
+typedef struct {
+    int32_t L;
+    int32_t reserved;
+    int64_t N[MLMC_MAX_LEVELS];     /* samples per level */
+    double V[MLMC_MAX_LEVELS];      /* single-sample variance V_l (Remark 3.6) */
+    double cost[MLMC_MAX_LEVELS];   /* C_l of the allocation: c_0, then c_l + c_{l-1} */
+    double mean_norm[MLMC_MAX_LEVELS]; /* ||Y_l||_F */
+    double rmse_pred;               /* sqrt(sum_l V_l / N_l) */
+    double eps_abs;                 /* the requested tolerance */
+    double outer_products;          /* sum_l N_l c_l sampled outer products evaluated */
+} mlmc_report;
+
+typedef struct mlmc_plan_s mlmc_plan_t;
+
+/* ---- plan ---------------------------------------------------------------- */
+
+/* mlmc_plan: validate `nprob` problems and the options, allocate the plan's
+ * device scratch, and copy each problem's parameters into the plan's
+ * sample-major layout (one gathered column of [M|S] and one gathered row of
+ * [M'|S'] become contiguous).  `stream` is a cudaStream_t (NULL = legacy
+ * default stream) on which every later call enqueues its work.  Statistics
+ * of every (problem, level) start empty.  Synchronous with respect to the
+ * host only in that the layout copy has been enqueued on return.
+ * Problem statement: inputs L_A, L_B, the base number and the tolerance
+ * (Alg. 1, Alg. 2). */
+MLMC_API mlmc_status mlmc_plan(const mlmc_problem* problems, int32_t nprob, const mlmc_options* options,
+                      void* stream, mlmc_plan_t** plan_out);
+
+/* Release everything the plan owns (after draining its stream).  NULL is a no-op. */
+MLMC_API mlmc_status mlmc_plan_destroy(mlmc_plan_t* plan);
+
+/* ---- level statistics (Alg. 1, incremental) ---------------------------------------- */
+
+/* mlmc_level_stats: evaluate samples s = sample_begin .. sample_begin+count-1
+ * of level `level` of problem `prob` (Alg. 1, one loop iteration each) and
+ * fold them into that level's running statistics: the count, the FP64
+ * per-entry sum of D and the FP64 sum of ||D||_F^2.  Samples are pure
+ * functions of their ids, so disjoint ranges may be evaluated in any order
+ * and split across calls; the statistics are bit-identical for any split at
+ * multiples of 8 sample ids and in any case equal up to rounding.
+ * count = 0 is a no-op. */
+MLMC_API mlmc_status mlmc_level_stats(mlmc_plan_t* plan, int32_t prob, int32_t level, uint64_t sample_begin,
+                             uint64_t count);
+
+/* Read the statistics of one level (synchronises the plan's stream):
+ * N = samples folded so far; mean_dev (m x p FP64, device, may be NULL) =
+ * Y_l = mean of D (Eq. hatYl); M2 (host, may be NULL) = sum_s ||D_s - Y_l||_F^2,
+ * so V_l = M2 / (N - 1) (Remark 3.6). */
+MLMC_API mlmc_status mlmc_get_level_stats(mlmc_plan_t* plan, int32_t prob, int32_t level, uint64_t* N,
+                                 double* mean_dev, double* M2);
+
+/* Raw accumulator state of one level for checkpointing: N, the per-entry sum
+ * of D (m x p FP64, device) and the sum of ||D||_F^2.  Get synchronises the
+ * plan's stream; set replaces the state (resume continues at sample id N). */
+MLMC_API mlmc_status mlmc_get_level_state(mlmc_plan_t* plan, int32_t prob, int32_t level, uint64_t* N,
+                                 double* sum_dev, double* sumsq);
+MLMC_API mlmc_status mlmc_set_level_state(mlmc_plan_t* plan, int32_t prob, int32_t level, uint64_t N,
+                                 const double* sum_dev, double sumsq);
+
+/* Empty the statistics of one level (level < 0: every level of the problem). */
+MLMC_API mlmc_status mlmc_reset_level_stats(mlmc_plan_t* plan, int32_t prob, int32_t level);
+
+/* ---- estimator (Alg. 2 with the finest level fixed) ---------------------------------- */
+
+/* mlmc_estimate: for every problem, run pilot_n samples on every level not
+ * yet holding that many, take V_l, allocate N_l = ceil(nl_scale 2 eps^-2
+ * sqrt(V_l/C_l) sum_j sqrt(V_j C_j)) with C_0 = c_0, C_l = c_l + c_{l-1}
+ * (Remark 3.6; at least pilot_n), evaluate the missing samples pilot_n ..
+ * N_l - 1 (earlier samples are kept, as Alg. 2 reuses them), and write
+ * Yhat = sum_l Y_l (Eq. hatY).  eps_abs: host array of nprob absolute
+ * Frobenius tolerances (> 0).  yhat_dev: device FP64 buffer holding every
+ * problem's m x p estimate back to back in problem order.  reports: host
+ * array of nprob reports, or NULL.  Synchronises the plan's stream (the
+ * allocation needs the pilot variances on the host); the N_l are recorded in
+ * the plan for mlmc_backward. */
+MLMC_API mlmc_status mlmc_estimate(mlmc_plan_t* plan, const double* eps_abs, double* yhat_dev,
+                          mlmc_report* reports);
+
+/* The allocation step of Alg. 2 alone: from the statistics currently held
+ * (every level needs N >= 2 samples), N_l = max(ceil(nl_scale 2 eps^-2
+ * sqrt(V_l/C_l) sum_j sqrt(V_j C_j)), pilot_n) (Remark 3.6) for every problem,
+ * without evaluating any sample.  eps_abs: host array of nprob tolerances;
+ * Nl: host array of nprob x MLMC_MAX_LEVELS (row q holds problem q's levels
+ * 0..L, the rest zero).  Synchronises the plan's stream. */
+MLMC_API mlmc_status mlmc_allocate(mlmc_plan_t* plan, const double* eps_abs, int64_t* Nl);
+
+/* Yhat of the current statistics without new samples: yhat_dev as above. */
+MLMC_API mlmc_status mlmc_telescoping_sum(mlmc_plan_t* plan, double* yhat_dev);
+
+/* ---- reparameterised adjoint ---------------------------------------------------------- */
+
+/* mlmc_backward: gradient of <G, Yhat> with respect to the caller's M, S, M',
+ * S' of every problem, with the draws (indices and Z) held fixed as in the
+ * reparameterisation A = M + S o Z.  Replays samples 0 .. N_l - 1 of every
+ * level with the N_l recorded by the last mlmc_estimate (MLMC_ERR_STATE if
+ * none), recomputing indices and Z from Philox.  G_dev: device FP64, every
+ * problem's m x p upstream gradient back to back in problem order.
+ * dM_dev, dS_dev, dMp_dev, dSp_dev: host arrays of nprob device pointers, one
+ * per problem, to m x n (ldA) and n x p (ldB) buffers of the problem's
+ * parameter dtype.  Gradients are written, not accumulated.  In BF16/FP8
+ * precision the rounding of the entries is treated as the identity and the
+ * forward's rounded operands are used (straight-through). */
+MLMC_API mlmc_status mlmc_backward(mlmc_plan_t* plan, const double* G_dev, void* const* dM_dev,
+                          void* const* dS_dev, void* const* dMp_dev, void* const* dSp_dev);
+
+/* ---- status ------------------------------------------------------------------------ */
+
+/* Wait for the plan's stream and return its sticky status. */
+MLMC_API mlmc_status mlmc_synchronize(mlmc_plan_t* plan);
+
+/* Number of kernels the plan has launched so far (all entry points). */
+MLMC_API mlmc_status mlmc_launch_count(const mlmc_plan_t* plan, uint64_t* count);
+
+/* Thread-local description of the last error returned on this thread ("" if none). */
+MLMC_API const char* mlmc_last_error(void);
+
+/* ---- verification hooks ----------------------------------------------------------------
+ * The same device functions the kernels use, exposed so tests can compare
+ * them with an independent implementation.  All write device buffers. */
+
+/* Philox4x32-10 blocks: ctr_dev holds count counters of 4 words, key_dev
+ * count keys of 2 words; out_dev receives count blocks of 4 words. */
+MLMC_API mlmc_status mlmc_debug_philox(const uint32_t* ctr_dev, const uint32_t* key_dev, int64_t count,
+                              uint32_t* out_dev, void* stream);
+
+/* Indices r_t, t = t0 .. t0+count-1, of sample s at level l of problem prob. */
+MLMC_API mlmc_status mlmc_debug_indices(mlmc_plan_t* plan, int32_t prob, int32_t level, uint64_t sample,
+                               int64_t t0, int64_t count, int64_t* idx_dev);
+
+/* Normals Z (which = 0, for A: rows i = row0 .. row0+count-1 of column k) or
+ * Z' (which = 1, for B: columns j = row0 .. of row k), in the precision of
+ * the plan's arithmetic, widened to FP64. */
+MLMC_API mlmc_status mlmc_debug_normals(mlmc_plan_t* plan, int32_t prob, int32_t which, int32_t level,
+                               uint64_t sample, int64_t k, int64_t row0, int64_t count, double* z_dev);
+
+/* One sample D (m x p FP64) of level `level` computed by the same kernel
+ * mlmc_level_stats launches, without touching the level's statistics. */
+MLMC_API mlmc_status mlmc_debug_sample(mlmc_plan_t* plan, int32_t prob, int32_t level, uint64_t sample,
+                              double* D_dev);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MLMC_H */

@@ -1,0 +1,320 @@
+"""ctypes binding of ``libmlmc.so`` (the C ABI of include/mlmc.h).
+
+Argument marshalling only: every step of the estimator runs in the CUDA library.
+PyTorch provides device memory and streams.  There is no fallback of any kind:
+if the library is missing or was built for another machine, loading raises.
+
+Names follow the C entry points: ``Plan`` wraps ``mlmc_plan`` / ``mlmc_plan_destroy``
+and its methods ``level_stats``, ``get_level_stats``, ``estimate``, ``backward`` ... call
+the functions of the same name.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libmlmc.so")
+MAX_LEVELS = 32
+
+STATUS = {0: "MLMC_OK", 1: "MLMC_ERR_INVALID_ARG", 2: "MLMC_ERR_CUDA", 3: "MLMC_ERR_OOM",
+          4: "MLMC_ERR_TIMEOUT", 5: "MLMC_ERR_NUMERIC", 6: "MLMC_ERR_UNSUPPORTED", 7: "MLMC_ERR_STATE"}
+PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2, "fp8": 3, "fp8_e4m3": 3}
+DTYPE = {torch.float64: 0, torch.float32: 1}
+
+
+class MLMCError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("p", ctypes.c_int64),
+                ("M_dev", ctypes.c_void_p), ("S_dev", ctypes.c_void_p), ("ldA", ctypes.c_int64),
+                ("Mp_dev", ctypes.c_void_p), ("Sp_dev", ctypes.c_void_p), ("ldB", ctypes.c_int64),
+                ("dtype", ctypes.c_int32), ("L", ctypes.c_int32),
+                ("seed_A", ctypes.c_uint32), ("seed_B", ctypes.c_uint32),
+                ("seed_idx", ctypes.c_uint32), ("problem_id", ctypes.c_uint32)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("c0", ctypes.c_int32), ("ratio", ctypes.c_int32), ("L", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("pilot_n", ctypes.c_int64), ("nl_scale", ctypes.c_double),
+                ("timeout_ns", ctypes.c_int64), ("tile_override", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("N", ctypes.c_int64 * MAX_LEVELS), ("V", ctypes.c_double * MAX_LEVELS),
+                ("cost", ctypes.c_double * MAX_LEVELS), ("mean_norm", ctypes.c_double * MAX_LEVELS),
+                ("rmse_pred", ctypes.c_double), ("eps_abs", ctypes.c_double), ("outer_products", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        L = self.L
+        return {"L": L, "N": list(self.N[:L + 1]), "V": list(self.V[:L + 1]), "cost": list(self.cost[:L + 1]),
+                "mean_norm": list(self.mean_norm[:L + 1]), "rmse_pred": self.rmse_pred, "eps_abs": self.eps_abs,
+                "outer_products": self.outer_products}
+
+
+_lock = threading.Lock()
+_lib: Optional[ctypes.CDLL] = None
+
+
+def lib() -> ctypes.CDLL:
+    """Open libmlmc.so (raises if it has not been built: run ``__graft_entry__.build()``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first "
+                               "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I32, I64, U64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+        sig = {
+            "mlmc_plan": [P, I32, P, P, P],
+            "mlmc_plan_destroy": [P],
+            "mlmc_level_stats": [P, I32, I32, U64, U64],
+            "mlmc_get_level_stats": [P, I32, I32, P, P, P],
+            "mlmc_get_level_state": [P, I32, I32, P, P, P],
+            "mlmc_set_level_state": [P, I32, I32, U64, P, D],
+            "mlmc_reset_level_stats": [P, I32, I32],
+            "mlmc_estimate": [P, P, P, P],
+            "mlmc_telescoping_sum": [P, P],
+            "mlmc_allocate": [P, P, P],
+            "mlmc_launch_count": [P, P],
+            "mlmc_backward": [P, P, P, P, P, P],
+            "mlmc_synchronize": [P],
+            "mlmc_debug_philox": [P, P, I64, P, P],
+            "mlmc_debug_indices": [P, I32, I32, U64, I64, I64, P],
+            "mlmc_debug_normals": [P, I32, I32, I32, U64, I64, I64, I64, P],
+            "mlmc_debug_sample": [P, I32, I32, U64, P],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        L.mlmc_last_error.argtypes = []
+        L.mlmc_last_error.restype = ctypes.c_char_p
+        _lib = L
+        return L
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        msg = lib().mlmc_last_error().decode(errors="replace")
+        raise MLMCError(status, where, msg)
+
+
+def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+@dataclass
+class ProblemSpec:
+    """One problem: M, S (m x n) and Mp, Sp (n x p) as 2-D CUDA tensors (float32 or float64)."""
+    M: torch.Tensor
+    S: torch.Tensor
+    Mp: torch.Tensor
+    Sp: torch.Tensor
+    seed_A: int = 0
+    seed_B: int = 1
+    seed_idx: int = 2
+    problem_id: int = 0
+    L: int = -1
+
+    def shape(self):
+        return self.M.shape[0], self.M.shape[1], self.Mp.shape[1]
+
+
+class Plan:
+    """A plan over one or more problems sharing the level schedule c_l = c0 * ratio**l."""
+
+    def __init__(self, problems: Sequence[ProblemSpec], *, c0: int, L: int, ratio: int = 2,
+                 precision: str = "fp32", pilot_n: int = 256, nl_scale: float = 1.0,
+                 timeout_ns: int = 0, tile_override: int = 0, stream=None):
+        self.problems = list(problems)
+        self.device = self.problems[0].M.device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        arr = (Problem * len(self.problems))()
+        self.shapes = []
+        self.levels = []
+        for q, pr in enumerate(self.problems):
+            for t in (pr.M, pr.S, pr.Mp, pr.Sp):
+                if not t.is_cuda or t.dim() != 2 or t.dtype not in DTYPE or t.stride(1) != 1:
+                    raise ValueError("parameters must be 2-D row-major float32/float64 CUDA tensors")
+            if pr.S.shape != pr.M.shape or pr.Sp.shape != pr.Mp.shape or pr.M.shape[1] != pr.Mp.shape[0]:
+                raise ValueError("inconsistent parameter shapes")
+            dtypes = {pr.M.dtype, pr.S.dtype, pr.Mp.dtype, pr.Sp.dtype}
+            if len(dtypes) != 1:
+                raise ValueError("the four parameter matrices must share one dtype")
+            m, n, p = pr.shape()
+            if pr.M.stride(0) != pr.S.stride(0) or pr.Mp.stride(0) != pr.Sp.stride(0):
+                raise ValueError("M and S (and Mp and Sp) must share a leading dimension")
+            arr[q] = Problem(m, n, p, pr.M.data_ptr(), pr.S.data_ptr(), pr.M.stride(0),
+                             pr.Mp.data_ptr(), pr.Sp.data_ptr(), pr.Mp.stride(0), DTYPE[pr.M.dtype],
+                             pr.L, pr.seed_A, pr.seed_B, pr.seed_idx, pr.problem_id)
+            self.shapes.append((m, n, p))
+            self.levels.append(pr.L if pr.L >= 0 else L)
+        self.options = Options(c0, ratio, L, PRECISION[precision], pilot_n, nl_scale, timeout_ns, tile_override, 0)
+        self.precision = precision
+        self.c0, self.ratio, self.L = c0, ratio, L
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib().mlmc_plan(arr, len(self.problems), ctypes.byref(self.options),
+                                   _stream_handle(self.stream), ctypes.byref(h)), "mlmc_plan")
+        self._h = h
+
+    # -- lifetime ---------------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().mlmc_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def cl(self, l: int) -> int:
+        return self.c0 * self.ratio ** l
+
+    def _out(self, *shape, dtype=torch.float64):
+        return torch.empty(*shape, dtype=dtype, device=self.device)
+
+    # -- Alg. 1, incremental ------------------------------------------------------------------
+    def level_stats(self, prob: int, level: int, begin: int, count: int):
+        _check(lib().mlmc_level_stats(self._h, prob, level, begin, count), "mlmc_level_stats")
+
+    def get_level_stats(self, prob: int, level: int):
+        """(N, mean (m x p FP64 CUDA tensor), M2 = sum_s ||D_s - mean||_F^2)."""
+        m, _, p = self.shapes[prob]
+        mean = self._out(m, p)
+        N = ctypes.c_uint64()
+        M2 = ctypes.c_double()
+        _check(lib().mlmc_get_level_stats(self._h, prob, level, ctypes.byref(N), _ptr(mean), ctypes.byref(M2)),
+               "mlmc_get_level_stats")
+        return N.value, mean, M2.value
+
+    def get_level_state(self, prob: int, level: int):
+        m, _, p = self.shapes[prob]
+        s = self._out(m, p)
+        N = ctypes.c_uint64()
+        q = ctypes.c_double()
+        _check(lib().mlmc_get_level_state(self._h, prob, level, ctypes.byref(N), _ptr(s), ctypes.byref(q)),
+               "mlmc_get_level_state")
+        return N.value, s, q.value
+
+    def set_level_state(self, prob: int, level: int, N: int, sum_dev: torch.Tensor, sumsq: float):
+        _check(lib().mlmc_set_level_state(self._h, prob, level, N, _ptr(sum_dev.contiguous()), sumsq),
+               "mlmc_set_level_state")
+
+    def reset(self, prob: int, level: int = -1):
+        _check(lib().mlmc_reset_level_stats(self._h, prob, level), "mlmc_reset_level_stats")
+
+    # -- Alg. 2 ---------------------------------------------------------------------------------
+    def estimate(self, eps_abs):
+        """Returns (list of m x p FP64 estimates, list of report dicts)."""
+        nprob = len(self.problems)
+        if not hasattr(eps_abs, "__len__"):
+            eps_abs = [float(eps_abs)] * nprob
+        eps = (ctypes.c_double * nprob)(*[float(e) for e in eps_abs])
+        total = sum(m * p for m, _, p in self.shapes)
+        y = self._out(total)
+        reps = (Report * nprob)()
+        _check(lib().mlmc_estimate(self._h, eps, _ptr(y), reps), "mlmc_estimate")
+        return self._split(y), [r.as_dict() for r in reps]
+
+    def allocate(self, eps_abs):
+        """N_l of the allocation (Remark 3.6) from the statistics held now, per problem."""
+        nprob = len(self.problems)
+        if not hasattr(eps_abs, "__len__"):
+            eps_abs = [float(eps_abs)] * nprob
+        eps = (ctypes.c_double * nprob)(*[float(e) for e in eps_abs])
+        out = (ctypes.c_int64 * (nprob * MAX_LEVELS))()
+        _check(lib().mlmc_allocate(self._h, eps, out), "mlmc_allocate")
+        return [list(out[q * MAX_LEVELS:q * MAX_LEVELS + self.levels[q] + 1]) for q in range(nprob)]
+
+    def launch_count(self) -> int:
+        c = ctypes.c_uint64()
+        _check(lib().mlmc_launch_count(self._h, ctypes.byref(c)), "mlmc_launch_count")
+        return c.value
+
+    def telescoping_sum(self):
+        total = sum(m * p for m, _, p in self.shapes)
+        y = self._out(total)
+        _check(lib().mlmc_telescoping_sum(self._h, _ptr(y)), "mlmc_telescoping_sum")
+        return self._split(y)
+
+    def _split(self, flat: torch.Tensor):
+        out, off = [], 0
+        for m, _, p in self.shapes:
+            out.append(flat[off:off + m * p].view(m, p))
+            off += m * p
+        return out
+
+    # -- adjoint ---------------------------------------------------------------------------------
+    def backward(self, G: Sequence[torch.Tensor], grads: Optional[Sequence[Sequence[torch.Tensor]]] = None):
+        """Gradient of sum_q <G_q, Yhat_q> w.r.t. (M, S, Mp, Sp) of every problem."""
+        G_flat = torch.cat([g.reshape(-1).to(torch.float64) for g in G]).contiguous()
+        if grads is None:
+            grads = [tuple(torch.empty_like(t) for t in (pr.M, pr.S, pr.Mp, pr.Sp)) for pr in self.problems]
+        n = len(self.problems)
+        ptrs = [(ctypes.c_void_p * n)(*[g[i].data_ptr() for g in grads]) for i in range(4)]
+        _check(lib().mlmc_backward(self._h, _ptr(G_flat), *ptrs), "mlmc_backward")
+        return grads
+
+    def synchronize(self):
+        _check(lib().mlmc_synchronize(self._h), "mlmc_synchronize")
+
+    # -- verification hooks ------------------------------------------------------------------
+    def debug_indices(self, prob: int, level: int, sample: int, t0: int, count: int) -> torch.Tensor:
+        out = self._out(count, dtype=torch.int64)
+        _check(lib().mlmc_debug_indices(self._h, prob, level, sample, t0, count, _ptr(out)), "mlmc_debug_indices")
+        return out
+
+    def debug_normals(self, prob: int, which: int, level: int, sample: int, k: int, row0: int,
+                      count: int) -> torch.Tensor:
+        out = self._out(count)
+        _check(lib().mlmc_debug_normals(self._h, prob, which, level, sample, k, row0, count, _ptr(out)),
+               "mlmc_debug_normals")
+        return out
+
+    def debug_sample(self, prob: int, level: int, sample: int) -> torch.Tensor:
+        m, _, p = self.shapes[prob]
+        out = self._out(m, p)
+        _check(lib().mlmc_debug_sample(self._h, prob, level, sample, _ptr(out)), "mlmc_debug_sample")
+        return out
+
+
+def debug_philox(ctr: torch.Tensor, key: torch.Tensor, stream=None) -> torch.Tensor:
+    """Philox4x32-10 blocks on the device: ctr (count x 4) and key (count x 2) int32 CUDA tensors
+    holding the 32-bit words; returns count x 4 int32 words."""
+    count = ctr.shape[0]
+    out = torch.empty(count, 4, dtype=torch.int32, device=ctr.device)
+    _check(lib().mlmc_debug_philox(_ptr(ctr.contiguous()), _ptr(key.contiguous()), count, _ptr(out),
+                                   _stream_handle(stream)), "mlmc_debug_philox")
+    return out

@@ -1,0 +1,667 @@
+// api.cu -- host side of the C ABI declared in include/mlmc.h.
+//
+// The plan holds, per problem, the parameters in sample-major layout and the
+// FP64 state of every level; level_stats enqueues the fused level kernel over
+// bounded batches of sample chunks followed by the in-order merge; estimate
+// runs Alg. 2 with the finest level fixed: pilot samples, V_l, the allocation
+// of Remark 3.6 in FP64 on the host, top-ups from the next unused sample id,
+// and the telescoping sum of Eq. hatY.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "mlmc.h"
+
+using namespace mlmc;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+mlmc_status fail(mlmc_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+constexpr size_t kPartialBudget = size_t(64) << 20;  // bytes of chunk partials per launch
+constexpr int kMaxChunksPerLaunch = 4096;
+constexpr int64_t kMaxCl = int64_t(1) << 30;
+
+}  // namespace
+
+struct ProblemState {
+    mlmc_problem desc;
+    int L = 0;
+    int64_t m = 0, n = 0, p = 0, m_pad = 0, p_pad = 0;
+    void* PA = nullptr;
+    void* PB = nullptr;
+    double* sum = nullptr;    // (L+1) x m x p
+    double* sumsq = nullptr;  // (L+1)
+    LevelCounts N{};
+    int64_t Nl_est[MLMC_MAX_LEVELS] = {};
+    bool has_estimate = false;
+    int tiles_m = 1, tiles_p = 1;
+    int max_chunks = 1;
+};
+
+struct mlmc_plan_s {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    mlmc_options opt{};
+    bool f64 = false;
+    size_t elem = 4;
+    std::vector<ProblemState> probs;
+    void* partial_sum = nullptr;
+    double* partial_q = nullptr;
+    double* dbg_sum = nullptr;    // one level's state for debug_sample
+    double* dbg_sumsq = nullptr;
+    double* M2_dev = nullptr;     // MLMC_MAX_LEVELS scratch for finalize
+    mlmc_status sticky = MLMC_OK;
+    std::string sticky_msg;
+    uint64_t launches = 0;
+};
+
+namespace {
+
+// Makes the plan's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+mlmc_status set_sticky(mlmc_plan_t* plan, mlmc_status st)
+{
+    if (plan && plan->sticky == MLMC_OK && st != MLMC_OK) {
+        plan->sticky = st;
+        plan->sticky_msg = g_last_error;
+    }
+    return st;
+}
+
+mlmc_status check_cuda(mlmc_plan_t* plan, cudaError_t err, const char* what)
+{
+    if (err == cudaSuccess) return MLMC_OK;
+    fail(err == cudaErrorMemoryAllocation ? MLMC_ERR_OOM : MLMC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(err));
+    return set_sticky(plan, err == cudaErrorMemoryAllocation ? MLMC_ERR_OOM : MLMC_ERR_CUDA);
+}
+
+mlmc_status enter(mlmc_plan_t* plan)
+{
+    if (!plan) return fail(MLMC_ERR_INVALID_ARG, "null plan");
+    if (plan->sticky != MLMC_OK) {
+        g_last_error = plan->sticky_msg;
+        return plan->sticky;
+    }
+    return MLMC_OK;
+}
+
+int64_t level_c(const mlmc_options& o, int l)
+{
+    int64_t c = o.c0;
+    for (int i = 0; i < l; ++i) c *= o.ratio;
+    return c;
+}
+
+double level_cost(const mlmc_options& o, int l)
+{
+    return l == 0 ? double(level_c(o, 0)) : double(level_c(o, l)) + double(level_c(o, l - 1));
+}
+
+uint2 key(uint32_t seed, uint32_t pid) { return make_uint2(seed, pid); }
+
+mlmc_status validate(const mlmc_problem* problems, int32_t nprob, const mlmc_options* o)
+{
+    if (!problems || nprob < 1) return fail(MLMC_ERR_INVALID_ARG, "need at least one problem");
+    if (!o) return fail(MLMC_ERR_INVALID_ARG, "null options");
+    if (o->c0 < 1) return fail(MLMC_ERR_INVALID_ARG, "c0 must be >= 1 (got %d)", o->c0);
+    if (o->ratio < 2) return fail(MLMC_ERR_INVALID_ARG, "ratio must be >= 2 (got %d)", o->ratio);
+    if (o->precision < MLMC_FP64 || o->precision > MLMC_FP8_E4M3)
+        return fail(MLMC_ERR_INVALID_ARG, "unknown precision %d", o->precision);
+    if (o->pilot_n < 2) return fail(MLMC_ERR_INVALID_ARG, "pilot_n must be >= 2");
+    if (!(o->nl_scale > 0.0) || !std::isfinite(o->nl_scale)) return fail(MLMC_ERR_INVALID_ARG, "nl_scale must be > 0");
+    if (o->timeout_ns < 0) return fail(MLMC_ERR_INVALID_ARG, "timeout_ns must be >= 0");
+    for (int32_t q = 0; q < nprob; ++q) {
+        const mlmc_problem& pr = problems[q];
+        const int L = pr.L >= 0 ? pr.L : o->L;
+        if (L < 0 || L >= MLMC_MAX_LEVELS) return fail(MLMC_ERR_INVALID_ARG, "problem %d: L=%d out of range", q, L);
+        int64_t c = o->c0;
+        for (int l = 0; l < L; ++l) {
+            c *= o->ratio;
+            if (c > kMaxCl) return fail(MLMC_ERR_INVALID_ARG, "problem %d: c_L exceeds 2^30", q);
+        }
+        if (pr.m < 1 || pr.m > 65536 || pr.p < 1 || pr.p > 65536)
+            return fail(MLMC_ERR_INVALID_ARG, "problem %d: m, p must be in [1, 65536]", q);
+        if (pr.n < 1 || pr.n >= (int64_t(1) << 31)) return fail(MLMC_ERR_INVALID_ARG, "problem %d: n must be in [1, 2^31)", q);
+        if (pr.ldA < pr.n || pr.ldB < pr.p) return fail(MLMC_ERR_INVALID_ARG, "problem %d: leading dimension too small", q);
+        if (!pr.M_dev || !pr.S_dev || !pr.Mp_dev || !pr.Sp_dev)
+            return fail(MLMC_ERR_INVALID_ARG, "problem %d: null parameter pointer", q);
+        if (pr.dtype != MLMC_DTYPE_F64 && pr.dtype != MLMC_DTYPE_F32)
+            return fail(MLMC_ERR_INVALID_ARG, "problem %d: unknown dtype %d", q, pr.dtype);
+    }
+    return MLMC_OK;
+}
+
+void free_plan(mlmc_plan_t* plan)
+{
+    for (auto& ps : plan->probs) {
+        cudaFree(ps.PA);
+        cudaFree(ps.PB);
+        cudaFree(ps.sum);
+        cudaFree(ps.sumsq);
+    }
+    cudaFree(plan->partial_sum);
+    cudaFree(plan->partial_q);
+    cudaFree(plan->dbg_sum);
+    cudaFree(plan->dbg_sumsq);
+    cudaFree(plan->M2_dev);
+}
+
+mlmc_status check_prob_level(mlmc_plan_t* plan, int32_t prob, int32_t level)
+{
+    if (prob < 0 || prob >= int32_t(plan->probs.size()))
+        return fail(MLMC_ERR_INVALID_ARG, "problem %d out of range", prob);
+    if (level < 0 || level > plan->probs[prob].L)
+        return fail(MLMC_ERR_INVALID_ARG, "level %d out of range for problem %d", level, prob);
+    return MLMC_OK;
+}
+
+// Evaluate samples [s0, s0+count) of one level and fold them into (sum, sumsq).
+mlmc_status run_level(mlmc_plan_t* plan, ProblemState& ps, int level, uint64_t s0, uint64_t count, double* sum,
+                      double* sumsq)
+{
+    if (count == 0) return MLMC_OK;
+    const mlmc_options& o = plan->opt;
+    if (o.precision == MLMC_BF16 || o.precision == MLMC_FP8_E4M3)
+        return set_sticky(plan, fail(MLMC_ERR_UNSUPPORTED, "precision %d is not available in this build", o.precision));
+    const int64_t c = level_c(o, level);
+    LevelParams prm{};
+    prm.PA = ps.PA;
+    prm.PB = ps.PB;
+    prm.n = ps.n;
+    prm.m = int(ps.m);
+    prm.p = int(ps.p);
+    prm.m_pad = int(ps.m_pad);
+    prm.p_pad = int(ps.p_pad);
+    prm.l = level;
+    prm.c = int(c);
+    prm.R = o.ratio;
+    prm.w_fine = double(ps.n) / double(c);
+    prm.w_coarse = level > 0 ? double(ps.n) / double(c) - double(ps.n) / double(c / o.ratio) : 0.0;
+    prm.keyA = key(ps.desc.seed_A, ps.desc.problem_id);
+    prm.keyB = key(ps.desc.seed_B, ps.desc.problem_id);
+    prm.keyI = key(ps.desc.seed_idx, ps.desc.problem_id);
+    prm.tiles_m = ps.tiles_m;
+    prm.tiles_p = ps.tiles_p;
+    prm.partial_sum = plan->partial_sum;
+    prm.partial_q = plan->partial_q;
+    const uint64_t s_end = s0 + count;
+    const uint64_t chunk_first = s0 / kChunk;
+    const uint64_t chunk_last = (s_end - 1) / kChunk;
+    for (uint64_t cb = chunk_first; cb <= chunk_last; cb += uint64_t(ps.max_chunks)) {
+        const int nb = int(std::min<uint64_t>(uint64_t(ps.max_chunks), chunk_last - cb + 1));
+        prm.chunk0 = cb;
+        prm.nchunks = nb;
+        prm.s_begin = std::max<uint64_t>(s0, cb * kChunk);
+        prm.s_end = std::min<uint64_t>(s_end, (cb + nb) * kChunk);
+        cudaError_t err = plan->f64 ? launch_level_cuda_core_f64(prm, plan->stream)
+                                    : launch_level_cuda_core_f32(prm, plan->stream);
+        if (check_cuda(plan, err, "level kernel launch") != MLMC_OK) return plan->sticky;
+        plan->launches += 3;  // level kernel, merge of sums, merge of sums of squares
+        err = launch_merge_partials(plan->partial_sum, plan->f64, plan->partial_q, nb, ps.tiles_m * ps.tiles_p,
+                                    ps.m * ps.p, sum, sumsq, plan->stream);
+        if (check_cuda(plan, err, "merge kernel launch") != MLMC_OK) return plan->sticky;
+    }
+    return MLMC_OK;
+}
+
+// M2 of levels [0, count) of a problem into host array (synchronises).
+mlmc_status level_M2(mlmc_plan_t* plan, ProblemState& ps, int first, int count, double* M2_host)
+{
+    const int64_t mp = ps.m * ps.p;
+    cudaError_t err = launch_finalize(ps.sum + int64_t(first) * mp, ps.sumsq + first, ps.N, first, count, mp,
+                                      nullptr, plan->M2_dev, plan->stream);
+    if (check_cuda(plan, err, "finalize launch") != MLMC_OK) return plan->sticky;
+    plan->launches += 1;
+    err = cudaMemcpyAsync(M2_host, plan->M2_dev, sizeof(double) * size_t(count), cudaMemcpyDeviceToHost, plan->stream);
+    if (check_cuda(plan, err, "copy M2") != MLMC_OK) return plan->sticky;
+    err = cudaStreamSynchronize(plan->stream);
+    return check_cuda(plan, err, "stream synchronize");
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mlmc_last_error(void) { return g_last_error.c_str(); }
+
+mlmc_status mlmc_plan(const mlmc_problem* problems, int32_t nprob, const mlmc_options* options, void* stream,
+                      mlmc_plan_t** plan_out)
+{
+    if (!plan_out) return fail(MLMC_ERR_INVALID_ARG, "null plan_out");
+    *plan_out = nullptr;
+    mlmc_status st = validate(problems, nprob, options);
+    if (st != MLMC_OK) return st;
+    mlmc_plan_t* plan = new (std::nothrow) mlmc_plan_s();
+    if (!plan) return fail(MLMC_ERR_OOM, "host allocation failed");
+    if (cudaGetDevice(&plan->device) != cudaSuccess) {
+        delete plan;
+        return fail(MLMC_ERR_CUDA, "no CUDA device available");
+    }
+    plan->stream = static_cast<cudaStream_t>(stream);
+    plan->opt = *options;
+    plan->f64 = options->precision == MLMC_FP64;
+    plan->elem = plan->f64 ? 8 : 4;
+    plan->probs.resize(size_t(nprob));
+
+    size_t max_partial = 0, max_q = 0, max_mp = 0;
+    auto oom = [&](const char* what) {
+        free_plan(plan);
+        delete plan;
+        return fail(MLMC_ERR_OOM, "cudaMalloc of %s failed", what);
+    };
+    for (int32_t q = 0; q < nprob; ++q) {
+        ProblemState& ps = plan->probs[size_t(q)];
+        ps.desc = problems[q];
+        ps.L = problems[q].L >= 0 ? problems[q].L : options->L;
+        ps.m = problems[q].m;
+        ps.n = problems[q].n;
+        ps.p = problems[q].p;
+        ps.m_pad = (ps.m + 3) / 4 * 4;
+        ps.p_pad = (ps.p + 3) / 4 * 4;
+        const CudaCoreTile tile = cuda_core_tile(options->precision);
+        ps.tiles_m = int((ps.m + tile.tm - 1) / tile.tm);
+        ps.tiles_p = int((ps.p + tile.tp - 1) / tile.tp);
+        const size_t mp = size_t(ps.m * ps.p);
+        const size_t per_chunk = mp * plan->elem;
+        ps.max_chunks = int(std::clamp<size_t>(kPartialBudget / per_chunk, 1, kMaxChunksPerLaunch));
+        max_partial = std::max(max_partial, per_chunk * size_t(ps.max_chunks));
+        max_q = std::max(max_q, size_t(ps.max_chunks) * size_t(ps.tiles_m * ps.tiles_p));
+        max_mp = std::max(max_mp, mp);
+        if (cudaMalloc(&ps.PA, size_t(ps.n) * size_t(ps.m_pad) * 2 * plan->elem) != cudaSuccess) return oom("PA");
+        if (cudaMalloc(&ps.PB, size_t(ps.n) * size_t(ps.p_pad) * 2 * plan->elem) != cudaSuccess) return oom("PB");
+        if (cudaMalloc(&ps.sum, sizeof(double) * mp * size_t(ps.L + 1)) != cudaSuccess) return oom("level sums");
+        if (cudaMalloc(&ps.sumsq, sizeof(double) * size_t(ps.L + 1)) != cudaSuccess) return oom("level sumsq");
+        cudaMemsetAsync(ps.sum, 0, sizeof(double) * mp * size_t(ps.L + 1), plan->stream);
+        cudaMemsetAsync(ps.sumsq, 0, sizeof(double) * size_t(ps.L + 1), plan->stream);
+        cudaError_t err = launch_layout_A(ps.desc.M_dev, ps.desc.S_dev, ps.desc.dtype, ps.desc.ldA, ps.m, ps.n,
+                                          ps.m_pad, ps.PA, plan->f64, plan->stream);
+        if (err == cudaSuccess)
+            err = launch_layout_B(ps.desc.Mp_dev, ps.desc.Sp_dev, ps.desc.dtype, ps.desc.ldB, ps.n, ps.p, ps.p_pad,
+                                  ps.PB, plan->f64, plan->stream);
+        if (err != cudaSuccess) {
+            free_plan(plan);
+            delete plan;
+            return fail(MLMC_ERR_CUDA, "layout kernel: %s", cudaGetErrorString(err));
+        }
+    }
+    if (cudaMalloc(&plan->partial_sum, max_partial) != cudaSuccess) return oom("chunk partials");
+    if (cudaMalloc(reinterpret_cast<void**>(&plan->partial_q), sizeof(double) * max_q) != cudaSuccess)
+        return oom("chunk sums of squares");
+    if (cudaMalloc(reinterpret_cast<void**>(&plan->dbg_sum), sizeof(double) * max_mp) != cudaSuccess)
+        return oom("debug state");
+    if (cudaMalloc(reinterpret_cast<void**>(&plan->dbg_sumsq), sizeof(double)) != cudaSuccess) return oom("debug state");
+    if (cudaMalloc(reinterpret_cast<void**>(&plan->M2_dev), sizeof(double) * MLMC_MAX_LEVELS) != cudaSuccess)
+        return oom("M2 scratch");
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) {
+        free_plan(plan);
+        delete plan;
+        return fail(MLMC_ERR_CUDA, "plan setup: %s", cudaGetErrorString(err));
+    }
+    *plan_out = plan;
+    return MLMC_OK;
+}
+
+mlmc_status mlmc_plan_destroy(mlmc_plan_t* plan)
+{
+    if (!plan) return MLMC_OK;
+    DeviceGuard g(plan->device);
+    cudaStreamSynchronize(plan->stream);
+    free_plan(plan);
+    delete plan;
+    return MLMC_OK;
+}
+
+mlmc_status mlmc_synchronize(mlmc_plan_t* plan)
+{
+    mlmc_status st = enter(plan);
+    if (st != MLMC_OK) return st;
+    DeviceGuard g(plan->device);
+    return check_cuda(plan, cudaStreamSynchronize(plan->stream), "stream synchronize");
+}
+
+mlmc_status mlmc_level_stats(mlmc_plan_t* plan, int32_t prob, int32_t level, uint64_t sample_begin, uint64_t count)
+{
+    mlmc_status st = enter(plan);
+    if (st != MLMC_OK) return st;
+    if ((st = check_prob_level(plan, prob, level)) != MLMC_OK) return st;
+    if (count == 0) return MLMC_OK;
+    if (sample_begin + count < sample_begin || sample_begin + count > (uint64_t(1) << 56))
+        return fail(MLMC_ERR_INVALID_ARG, "sample ids must stay below 2^56");
+    DeviceGuard g(plan->device);
+    ProblemState& ps = plan->probs[size_t(prob)];
+    const int64_t mp = ps.m * ps.p;
+    st = run_level(plan, ps, level, sample_begin, count, ps.sum + int64_t(level) * mp, ps.sumsq + level);
+    if (st == MLMC_OK) ps.N.v[level] += count;
+    return st;
+}
+
+mlmc_status mlmc_get_level_stats(mlmc_plan_t* plan, int32_t prob, int32_t level, uint64_t* N, double* mean_dev,
+                                 double* M2)
+{
+    mlmc_status st = enter(plan);
+    if (st != MLMC_OK) return st;
+    if ((st = check_prob_level(plan, prob, level)) != MLMC_OK) return st;
+    DeviceGuard g(plan->device);
+    ProblemState& ps = plan->probs[size_t(prob)];
+    const int64_t mp = ps.m * ps.p;
+    cudaError_t err = launch_finalize(ps.sum + int64_t(level) * mp, ps.sumsq + level, ps.N, level, 1, mp, mean_dev,
+                                      plan->M2_dev, plan->stream);
+    if (check_cuda(plan, err, "finalize launch") != MLMC_OK) return plan->sticky;
+    plan->launches += 1;
+    double m2 = 0.0;
+    err = cudaMemcpyAsync(&m2, plan->M2_dev, sizeof(double), cudaMemcpyDeviceToHost, plan->stream);
+    if (check_cuda(plan, err, "copy M2") != MLMC_OK) return plan->sticky;
+    if (check_cuda(plan, cudaStreamSynchronize(plan->stream), "stream synchronize") != MLMC_OK) return plan->sticky;
+    if (N) *N = ps.N.v[level];
+    if (M2) *M2 = m2;
+    if (!std::isfinite(m2)) return fail(MLMC_ERR_NUMERIC, "level %d: non-finite second moment", level);
+    return MLMC_OK;
+}
+
+mlmc_status mlmc_get_level_state(mlmc_plan_t* plan, int32_t prob, int32_t level, uint64_t* N, double* sum_dev,
+                                 double* sumsq)
+{
+    mlmc_status st = enter(plan);
+    if (st != MLMC_OK) return st;
+    if ((st = check_prob_level(plan, prob, level)) != MLMC_OK) return st;
+    DeviceGuard g(plan->device);
+    ProblemState& ps = plan->probs[size_t(prob)];
+    const int64_t mp = ps.m * ps.p;
+    cudaError_t err = cudaSuccess;
+    if (sum_dev)
+        err = cudaMemcpyAsync(sum_dev, ps.sum + int64_t(level) * mp, sizeof(double) * size_t(mp),
+                              cudaMemcpyDeviceToDevice, plan->stream);
+    double q = 0.0;
+    if (err == cudaSuccess)
+        err = cudaMemcpyAsync(&q, ps.sumsq + level, sizeof(double), cudaMemcpyDeviceToHost, plan->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(plan->stream);
+    if (check_cuda(plan, err, "read level state") != MLMC_OK) return plan->sticky;
+    if (N) *N = ps.N.v[level];
+    if (sumsq) *sumsq = q;
+    return MLMC_OK;
+}
+
+mlmc_status mlmc_set_level_state(mlmc_plan_t* plan, int32_t prob, int32_t level, uint64_t N, const double* sum_dev,
+                                 double sumsq)
+{
+    mlmc_status st = enter(plan);
+    if (st != MLMC_OK) return st;
+    if ((st = check_prob_level(plan, prob, level)) != MLMC_OK) return st;
+    if (!sum_dev) return fail(MLMC_ERR_INVALID_ARG, "null sum_dev");
+    DeviceGuard g(plan->device);
+    ProblemState& ps = plan->probs[size_t(prob)];
+    const int64_t mp = ps.m * ps.p;
+    cudaError_t err = cudaMemcpyAsync(ps.sum + int64_t(level) * mp, sum_dev, sizeof(double) * size_t(mp),
+                                      cudaMemcpyDeviceToDevice, plan->stream);
+    if (err == cudaSuccess)
+        err = cudaMemcpyAsync(ps.sumsq + level, &sumsq, sizeof(double), cudaMemcpyHostToDevice, plan->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(plan->stream);
+    if (check_cuda(plan, err, "write level state") != MLMC_OK) return plan->sticky;
+    ps.N.v[level] = N;
+    ps.has_estimate = false;
+    return MLMC_OK;
+}
+
+mlmc_status mlmc_reset_level_stats(mlmc_plan_t* plan, int32_t prob, int32_t level)
+{
+    mlmc_status st = enter(plan);
+    if (st != MLMC_OK) return st;
+    if (prob < 0 || prob >= int32_t(plan->probs.size())) return fail(MLMC_ERR_INVALID_ARG, "problem out of range");
+    ProblemState& ps = plan->probs[size_t(prob)];
+    if (level > ps.L) return fail(MLMC_ERR_INVALID_ARG, "level out of range");
+    DeviceGuard g(plan->device);
+    const int64_t mp = ps.m * ps.p;
+    const int first = level < 0 ? 0 : level;
+    const int cnt = level < 0 ? ps.L + 1 : 1;
+    cudaError_t err = cudaMemsetAsync(ps.sum + int64_t(first) * mp, 0, sizeof(double) * size_t(mp) * size_t(cnt),
+                                      plan->stream);
+    if (err == cudaSuccess) err = cudaMemsetAsync(ps.sumsq + first, 0, sizeof(double) * size_t(cnt), plan->stream);
+    if (check_cuda(plan, err, "reset level state") != MLMC_OK) return plan->sticky;
+    for (int l = first; l < first + cnt; ++l) ps.N.v[l] = 0;
+    ps.has_estimate = false;
+    return MLMC_OK;
+}
+
+mlmc_status mlmc_telescoping_sum(mlmc_plan_t* plan, double* yhat_dev)
+{
+    mlmc_status st = enter(plan);
+    if (st != MLMC_OK) return st;
+    if (!yhat_dev) return fail(MLMC_ERR_INVALID_ARG, "null yhat_dev");
+    DeviceGuard g(plan->device);
+    int64_t off = 0;
+    for (auto& ps : plan->probs) {
+        const int64_t mp = ps.m * ps.p;
+        cudaError_t err = launch_telescoping(ps.sum, ps.N, ps.L + 1, mp, yhat_dev + off, plan->stream);
+        if (check_cuda(plan, err, "telescoping launch") != MLMC_OK) return plan->sticky;
+        plan->launches += 1;
+        off += mp;
+    }
+    return MLMC_OK;
+}
+
+mlmc_status mlmc_allocate(mlmc_plan_t* plan, const double* eps_abs, int64_t* Nl)
+{
+    mlmc_status st = enter(plan);
+    if (st != MLMC_OK) return st;
+    if (!eps_abs || !Nl) return fail(MLMC_ERR_INVALID_ARG, "null eps_abs or Nl");
+    DeviceGuard g(plan->device);
+    const mlmc_options& o = plan->opt;
+    for (size_t q = 0; q < plan->probs.size(); ++q) {
+        ProblemState& ps = plan->probs[q];
+        if (!(eps_abs[q] > 0.0) || !std::isfinite(eps_abs[q]))
+            return fail(MLMC_ERR_INVALID_ARG, "eps_abs[%zu] must be finite and > 0", q);
+        int64_t* row = Nl + q * MLMC_MAX_LEVELS;
+        std::fill(row, row + MLMC_MAX_LEVELS, int64_t(0));
+        for (int l = 0; l <= ps.L; ++l)
+            if (ps.N.v[l] < 2) return fail(MLMC_ERR_STATE, "problem %zu level %d holds fewer than 2 samples", q, l);
+        double M2[MLMC_MAX_LEVELS], V[MLMC_MAX_LEVELS], C[MLMC_MAX_LEVELS], root_sum = 0.0;
+        if ((st = level_M2(plan, ps, 0, ps.L + 1, M2)) != MLMC_OK) return st;
+        for (int l = 0; l <= ps.L; ++l) {
+            V[l] = std::max(0.0, M2[l] / double(ps.N.v[l] - 1));
+            C[l] = level_cost(o, l);
+            root_sum += std::sqrt(V[l] * C[l]);
+        }
+        for (int l = 0; l <= ps.L; ++l) {
+            const double target = o.nl_scale * 2.0 / (eps_abs[q] * eps_abs[q]) * std::sqrt(V[l] / C[l]) * root_sum;
+            if (!(target < 9.0e18)) return fail(MLMC_ERR_NUMERIC, "allocated N_l overflows");
+            row[l] = std::max<int64_t>(int64_t(std::ceil(target)), o.pilot_n);
+        }
+    }
+    return MLMC_OK;
+}
+
+mlmc_status mlmc_launch_count(const mlmc_plan_t* plan, uint64_t* count)
+{
+    if (!plan || !count) return fail(MLMC_ERR_INVALID_ARG, "null argument");
+    *count = plan->launches;
+    return MLMC_OK;
+}
+
+mlmc_status mlmc_estimate(mlmc_plan_t* plan, const double* eps_abs, double* yhat_dev, mlmc_report* reports)
+{
+    mlmc_status st = enter(plan);
+    if (st != MLMC_OK) return st;
+    if (!eps_abs || !yhat_dev) return fail(MLMC_ERR_INVALID_ARG, "null eps_abs or yhat_dev");
+    for (size_t q = 0; q < plan->probs.size(); ++q)
+        if (!(eps_abs[q] > 0.0) || !std::isfinite(eps_abs[q]))
+            return fail(MLMC_ERR_INVALID_ARG, "eps_abs[%zu] must be finite and > 0", q);
+    DeviceGuard g(plan->device);
+    const mlmc_options& o = plan->opt;
+    const uint64_t pilot = uint64_t(o.pilot_n);
+    // pilot run on every level of every problem
+    for (auto& ps : plan->probs) {
+        const int64_t mp = ps.m * ps.p;
+        for (int l = 0; l <= ps.L; ++l) {
+            if (ps.N.v[l] >= pilot) continue;
+            const uint64_t have = ps.N.v[l];
+            st = run_level(plan, ps, l, have, pilot - have, ps.sum + int64_t(l) * mp, ps.sumsq + l);
+            if (st != MLMC_OK) return st;
+            ps.N.v[l] = pilot;
+        }
+    }
+    // allocation from the pilot variances, then top-ups from the next unused sample id
+    for (size_t q = 0; q < plan->probs.size(); ++q) {
+        ProblemState& ps = plan->probs[q];
+        const int64_t mp = ps.m * ps.p;
+        double M2[MLMC_MAX_LEVELS];
+        if ((st = level_M2(plan, ps, 0, ps.L + 1, M2)) != MLMC_OK) return st;
+        double V[MLMC_MAX_LEVELS], C[MLMC_MAX_LEVELS], root_sum = 0.0;
+        for (int l = 0; l <= ps.L; ++l) {
+            V[l] = std::max(0.0, M2[l] / double(ps.N.v[l] - 1));
+            C[l] = level_cost(o, l);
+            if (!std::isfinite(V[l])) return set_sticky(plan, fail(MLMC_ERR_NUMERIC, "problem %zu level %d: V_l not finite", q, l));
+            root_sum += std::sqrt(V[l] * C[l]);
+        }
+        for (int l = 0; l <= ps.L; ++l) {
+            const double target = o.nl_scale * 2.0 / (eps_abs[q] * eps_abs[q]) * std::sqrt(V[l] / C[l]) * root_sum;
+            if (!(target < 9.0e18)) return set_sticky(plan, fail(MLMC_ERR_NUMERIC, "allocated N_l overflows"));
+            const uint64_t nl = std::max<uint64_t>(uint64_t(std::ceil(target)), pilot);
+            ps.Nl_est[l] = int64_t(std::max<uint64_t>(nl, ps.N.v[l]));
+            if (nl > ps.N.v[l]) {
+                const uint64_t have = ps.N.v[l];
+                st = run_level(plan, ps, l, have, nl - have, ps.sum + int64_t(l) * mp, ps.sumsq + l);
+                if (st != MLMC_OK) return st;
+                ps.N.v[l] = nl;
+            }
+        }
+    }
+    // telescoping sum and report
+    int64_t off = 0;
+    for (size_t q = 0; q < plan->probs.size(); ++q) {
+        ProblemState& ps = plan->probs[q];
+        const int64_t mp = ps.m * ps.p;
+        cudaError_t err = launch_telescoping(ps.sum, ps.N, ps.L + 1, mp, yhat_dev + off, plan->stream);
+        if (check_cuda(plan, err, "telescoping launch") != MLMC_OK) return plan->sticky;
+        plan->launches += 1;
+        off += mp;
+        ps.has_estimate = true;
+        if (reports) {
+            mlmc_report& r = reports[q];
+            std::memset(&r, 0, sizeof(r));
+            double M2[MLMC_MAX_LEVELS];
+            if ((st = level_M2(plan, ps, 0, ps.L + 1, M2)) != MLMC_OK) return st;
+            r.L = ps.L;
+            r.eps_abs = eps_abs[q];
+            double var = 0.0;
+            std::vector<double> sums(static_cast<size_t>(mp));
+            for (int l = 0; l <= ps.L; ++l) {
+                r.N[l] = int64_t(ps.N.v[l]);
+                r.V[l] = M2[l] / double(ps.N.v[l] - 1);
+                r.cost[l] = level_cost(o, l);
+                var += r.V[l] / double(ps.N.v[l]);
+                r.outer_products += double(ps.N.v[l]) * double(level_c(o, l));
+                err = cudaMemcpy(sums.data(), ps.sum + int64_t(l) * mp, sizeof(double) * size_t(mp),
+                                 cudaMemcpyDeviceToHost);
+                if (check_cuda(plan, err, "read level mean") != MLMC_OK) return plan->sticky;
+                double nrm = 0.0;
+                for (double v : sums) nrm += v * v;
+                r.mean_norm[l] = std::sqrt(nrm) / double(ps.N.v[l]);
+            }
+            r.rmse_pred = std::sqrt(var);
+        }
+    }
+    return MLMC_OK;
+}
+
+mlmc_status mlmc_backward(mlmc_plan_t* plan, const double* G_dev, void* const* dM_dev, void* const* dS_dev,
+                          void* const* dMp_dev, void* const* dSp_dev)
+{
+    mlmc_status st = enter(plan);
+    if (st != MLMC_OK) return st;
+    if (!G_dev || !dM_dev || !dS_dev || !dMp_dev || !dSp_dev) return fail(MLMC_ERR_INVALID_ARG, "null argument");
+    for (auto& ps : plan->probs)
+        if (!ps.has_estimate) return fail(MLMC_ERR_STATE, "mlmc_backward needs a preceding mlmc_estimate");
+    return fail(MLMC_ERR_UNSUPPORTED, "mlmc_backward is not available in this build");
+}
+
+mlmc_status mlmc_debug_philox(const uint32_t* ctr_dev, const uint32_t* key_dev, int64_t count, uint32_t* out_dev,
+                              void* stream)
+{
+    if (count < 0 || (count > 0 && (!ctr_dev || !key_dev || !out_dev))) return fail(MLMC_ERR_INVALID_ARG, "bad arguments");
+    cudaError_t err = launch_debug_philox(ctr_dev, key_dev, count, out_dev, static_cast<cudaStream_t>(stream));
+    if (err != cudaSuccess) return fail(MLMC_ERR_CUDA, "debug_philox: %s", cudaGetErrorString(err));
+    return MLMC_OK;
+}
+
+mlmc_status mlmc_debug_indices(mlmc_plan_t* plan, int32_t prob, int32_t level, uint64_t sample, int64_t t0,
+                               int64_t count, int64_t* idx_dev)
+{
+    mlmc_status st = enter(plan);
+    if (st != MLMC_OK) return st;
+    if ((st = check_prob_level(plan, prob, level)) != MLMC_OK) return st;
+    if (t0 < 0 || count < 0 || (count > 0 && !idx_dev)) return fail(MLMC_ERR_INVALID_ARG, "bad slot range");
+    DeviceGuard g(plan->device);
+    ProblemState& ps = plan->probs[size_t(prob)];
+    cudaError_t err = launch_debug_indices(key(ps.desc.seed_idx, ps.desc.problem_id), level, sample, ps.n, t0, count,
+                                           idx_dev, plan->stream);
+    return check_cuda(plan, err, "debug_indices");
+}
+
+mlmc_status mlmc_debug_normals(mlmc_plan_t* plan, int32_t prob, int32_t which, int32_t level, uint64_t sample,
+                               int64_t k, int64_t row0, int64_t count, double* z_dev)
+{
+    mlmc_status st = enter(plan);
+    if (st != MLMC_OK) return st;
+    if ((st = check_prob_level(plan, prob, level)) != MLMC_OK) return st;
+    if ((which != 0 && which != 1) || row0 < 0 || count < 0 || k < 0 || (count > 0 && !z_dev))
+        return fail(MLMC_ERR_INVALID_ARG, "bad arguments");
+    DeviceGuard g(plan->device);
+    ProblemState& ps = plan->probs[size_t(prob)];
+    const uint2 kk = key(which == 0 ? ps.desc.seed_A : ps.desc.seed_B, ps.desc.problem_id);
+    cudaError_t err = launch_debug_normals(kk, plan->f64, level, sample, k, row0, count, z_dev, plan->stream);
+    return check_cuda(plan, err, "debug_normals");
+}
+
+mlmc_status mlmc_debug_sample(mlmc_plan_t* plan, int32_t prob, int32_t level, uint64_t sample, double* D_dev)
+{
+    mlmc_status st = enter(plan);
+    if (st != MLMC_OK) return st;
+    if ((st = check_prob_level(plan, prob, level)) != MLMC_OK) return st;
+    if (!D_dev) return fail(MLMC_ERR_INVALID_ARG, "null D_dev");
+    DeviceGuard g(plan->device);
+    ProblemState& ps = plan->probs[size_t(prob)];
+    const int64_t mp = ps.m * ps.p;
+    cudaError_t err = cudaMemsetAsync(plan->dbg_sum, 0, sizeof(double) * size_t(mp), plan->stream);
+    if (err == cudaSuccess) err = cudaMemsetAsync(plan->dbg_sumsq, 0, sizeof(double), plan->stream);
+    if (check_cuda(plan, err, "debug state reset") != MLMC_OK) return plan->sticky;
+    st = run_level(plan, ps, level, sample, 1, plan->dbg_sum, plan->dbg_sumsq);
+    if (st != MLMC_OK) return st;
+    err = cudaMemcpyAsync(D_dev, plan->dbg_sum, sizeof(double) * size_t(mp), cudaMemcpyDeviceToDevice, plan->stream);
+    return check_cuda(plan, err, "debug sample copy");
+}
+
+}  // extern "C"

@@ -1,0 +1,82 @@
+// internal.h -- declarations shared by the CUDA sources of libmlmc (not part of the ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "mlmc.h"
+
+namespace mlmc {
+
+// Samples are grouped into fixed chunks of kChunk consecutive sample ids
+// (chunk c holds ids c*kChunk .. c*kChunk+kChunk-1).  Partial statistics are
+// produced per chunk and folded into a level in chunk order, so the result
+// does not depend on grid shapes or on how sample ranges are split at chunk
+// boundaries.
+constexpr int kChunk = 8;
+
+// Arguments of one level-kernel launch over samples [s_begin, s_end).
+struct LevelParams {
+    const void* PA;       // [n][m_pad][2] of T: (M_ik, S_ik) pairs, gathered column k contiguous
+    const void* PB;       // [n][p_pad][2] of T: (M'_kj, S'_kj) pairs, gathered row k contiguous
+    int64_t n;
+    int m, p, m_pad, p_pad;
+    int l;                // level
+    int c;                // c_l sampled indices
+    int R;                // ratio; slot t is also coarse iff t % R == R - 1 (and l > 0)
+    double w_fine;        // n / c_l
+    double w_coarse;      // n / c_l - n / c_{l-1}
+    uint2 keyA, keyB, keyI;
+    uint64_t s_begin, s_end;
+    uint64_t chunk0;      // absolute chunk id handled by blockIdx.y == 0
+    int nchunks;
+    int tiles_m, tiles_p;
+    void* partial_sum;    // [nchunks][m][p] of T
+    double* partial_q;    // [nchunks][tiles_m * tiles_p]
+};
+
+// Tile geometry of the CUDA-core level kernel.
+struct CudaCoreTile {
+    int tm, tp;
+};
+
+// Launchers (return the launch error, if any).
+cudaError_t launch_level_cuda_core_f64(const LevelParams& prm, cudaStream_t st);
+cudaError_t launch_level_cuda_core_f32(const LevelParams& prm, cudaStream_t st);
+CudaCoreTile cuda_core_tile(int precision);
+
+// Fold the partials of one launch into a level's FP64 state, in chunk order.
+cudaError_t launch_merge_partials(const void* partial_sum, bool partial_f64, const double* partial_q,
+                                  int nchunks, int tiles, int64_t mp, double* level_sum,
+                                  double* level_sumsq, cudaStream_t st);
+
+// Sample counts of the levels of one problem, passed by value to kernels.
+struct LevelCounts {
+    uint64_t v[MLMC_MAX_LEVELS];
+};
+
+// mean = sum / N and M2 = sumsq - ||sum||^2 / N for `count` levels laid out
+// back to back (sum: count x mp; sumsq, M2: count), N[l] = counts.v[first + l].
+// mean may be null.
+cudaError_t launch_finalize(const double* sum, const double* sumsq, LevelCounts counts, int first, int count,
+                            int64_t mp, double* mean, double* M2, cudaStream_t st);
+
+// yhat[e] = sum_l sum_l[e] / N_l over levels with N_l > 0.
+cudaError_t launch_telescoping(const double* sum, LevelCounts counts, int levels, int64_t mp, double* yhat,
+                               cudaStream_t st);
+
+// Copy row-major parameters into the sample-major pair layout.
+cudaError_t launch_layout_A(const void* M, const void* S, int src_dtype, int64_t ldA, int64_t m,
+                            int64_t n, int64_t m_pad, void* PA, bool dst_f64, cudaStream_t st);
+cudaError_t launch_layout_B(const void* Mp, const void* Sp, int src_dtype, int64_t ldB, int64_t n,
+                            int64_t p, int64_t p_pad, void* PB, bool dst_f64, cudaStream_t st);
+
+// Verification hooks.
+cudaError_t launch_debug_philox(const uint32_t* ctr, const uint32_t* key, int64_t count, uint32_t* out,
+                                cudaStream_t st);
+cudaError_t launch_debug_indices(uint2 keyI, int l, uint64_t s, int64_t n, int64_t t0, int64_t count,
+                                 int64_t* out, cudaStream_t st);
+cudaError_t launch_debug_normals(uint2 key, bool f64, int l, uint64_t s, int64_t k, int64_t row0,
+                                 int64_t count, double* out, cudaStream_t st);
+
+}  // namespace mlmc

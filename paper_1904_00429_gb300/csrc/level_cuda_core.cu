@@ -1,0 +1,244 @@
+// level_cuda_core.cu -- fused level kernel on the CUDA cores (FP64 and FP32).
+//
+// One CTA owns one TM x TP tile of the m x p output and one chunk of up to
+// kChunk samples of one level.  For every sample s it evaluates
+//     D_s = sum_t w_t A[:, r_t] B[r_t, :],   w_t = n/c_l - [t coarse] n/c_{l-1},
+// which is P_l - P_{l-1} of Alg. 1 written as one weighted sum: the coarse
+// estimate reuses the draws r_{jR} (0-based slots t = jR - 1) of the fine one,
+// so those slots carry both weights (Sec. 3.1).  Slots are processed in
+// chunks of TK: the CTA draws the TK indices, gathers the sampled (M, S)
+// pairs of its TM rows and (M', S') pairs of its TP columns (each gathered
+// column/row is contiguous in the plan's layout), generates the entries
+// A = M + S Z and w B = w (M' + S' Z') from Philox into shared memory, and
+// accumulates the outer products in a register tile.  After each sample the
+// tile is added to a running per-chunk sum and its squared Frobenius norm to
+// a running FP64 scalar; at the end of the chunk both are written as
+// partials, which the merge kernel folds into the level in chunk order.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "rng.cuh"
+
+namespace mlmc {
+namespace {
+
+template <typename T>
+struct Pair4;  // four (M, S) pairs: 8 consecutive values
+
+template <>
+struct Pair4<float> {
+    float v[8];
+    static __device__ __forceinline__ Pair4 load(const float* p)
+    {
+        Pair4 r;
+        const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+        const float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+        r.v[0] = a.x; r.v[1] = a.y; r.v[2] = a.z; r.v[3] = a.w;
+        r.v[4] = b.x; r.v[5] = b.y; r.v[6] = b.z; r.v[7] = b.w;
+        return r;
+    }
+};
+
+template <>
+struct Pair4<double> {
+    double v[8];
+    static __device__ __forceinline__ Pair4 load(const double* p)
+    {
+        Pair4 r;
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const double2 a = __ldg(reinterpret_cast<const double2*>(p) + h);
+            r.v[2 * h] = a.x;
+            r.v[2 * h + 1] = a.y;
+        }
+        return r;
+    }
+};
+
+template <typename T, int TM, int TP, int TK, int RM, int RP>
+__global__ void __launch_bounds__((TM / RM) * (TP / RP))
+level_cuda_core_kernel(const LevelParams prm)
+{
+    constexpr int NT = (TM / RM) * (TP / RP);
+    constexpr int TXN = TP / RP;
+    static_assert(TK % 2 == 0 && TM % 4 == 0 && TP % 4 == 0, "tile shape");
+
+    __shared__ __align__(16) T As[TK][TM];
+    __shared__ __align__(16) T Bs[TK][TP];
+    __shared__ int idx_s[TK];
+    __shared__ T w_s[TK];
+    __shared__ double red_s[NT / 32];
+
+    const int tid = threadIdx.x;
+    const int tile = blockIdx.x;
+    const int tm0 = (tile / prm.tiles_p) * TM;
+    const int tp0 = (tile % prm.tiles_p) * TP;
+    const int tx = tid % TXN;
+    const int ty = tid / TXN;
+
+    const uint64_t chunk = prm.chunk0 + blockIdx.y;
+    const uint64_t sa = max(prm.s_begin, chunk * kChunk);
+    const uint64_t sb = min(prm.s_end, (chunk + 1) * kChunk);
+
+    const T* PA = static_cast<const T*>(prm.PA);
+    const T* PB = static_cast<const T*>(prm.PB);
+    const T wf = static_cast<T>(prm.w_fine);
+    const T wc = static_cast<T>(prm.w_coarse);
+
+    T sum[RM][RP];
+#pragma unroll
+    for (int i = 0; i < RM; ++i)
+#pragma unroll
+        for (int j = 0; j < RP; ++j) sum[i][j] = T(0);
+    double q = 0.0;
+
+    for (uint64_t s = sa; s < sb; ++s) {
+        const uint32_t lsw = level_sample_word(prm.l, s);
+        const uint32_t s_lo = static_cast<uint32_t>(s);
+        T acc[RM][RP];
+#pragma unroll
+        for (int i = 0; i < RM; ++i)
+#pragma unroll
+            for (int j = 0; j < RP; ++j) acc[i][j] = T(0);
+
+        for (int k0 = 0; k0 < prm.c; k0 += TK) {
+            // 1. indices and weights of slots k0 .. k0 + TK - 1
+            for (int h = tid; h < TK / 2; h += NT) {
+                const int t = k0 + 2 * h;
+                if (t < prm.c) {
+                    int64_t r0, r1;
+                    index_pair(prm.keyI, lsw, s_lo, t >> 1, static_cast<uint64_t>(prm.n), r0, r1);
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        const int te = t + e;
+                        const bool valid = te < prm.c;
+                        const bool coarse = prm.l > 0 && (te % prm.R) == prm.R - 1;
+                        idx_s[2 * h + e] = valid ? static_cast<int>(e ? r1 : r0) : -1;
+                        w_s[2 * h + e] = valid ? (coarse ? wc : wf) : T(0);
+                    }
+                } else {
+                    idx_s[2 * h] = idx_s[2 * h + 1] = -1;
+                    w_s[2 * h] = w_s[2 * h + 1] = T(0);
+                }
+            }
+            __syncthreads();
+
+            // 2. sampled entries of A: TK slots x TM rows, four rows per Philox block
+            for (int it = tid; it < TK * (TM / 4); it += NT) {
+                const int tt = it / (TM / 4);
+                const int q4 = it % (TM / 4);
+                const int i = tm0 + 4 * q4;
+                const int k = idx_s[tt];
+                T a[4] = {T(0), T(0), T(0), T(0)};
+                if (k >= 0 && i < prm.m) {
+                    const uint4 w = philox4x32_10(make_uint4(static_cast<uint32_t>(i >> 2),
+                                                             static_cast<uint32_t>(k), s_lo, lsw),
+                                                  prm.keyA);
+                    T z[4];
+                    Normals<T>::four(w, z);
+                    const Pair4<T> ms = Pair4<T>::load(PA + (static_cast<int64_t>(k) * prm.m_pad + i) * 2);
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) a[r] = fma(ms.v[2 * r + 1], z[r], ms.v[2 * r]);
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r) As[tt][4 * q4 + r] = a[r];
+            }
+            // 3. sampled entries of B, weight folded in: TK slots x TP columns
+            for (int it = tid; it < TK * (TP / 4); it += NT) {
+                const int tt = it / (TP / 4);
+                const int q4 = it % (TP / 4);
+                const int j = tp0 + 4 * q4;
+                const int k = idx_s[tt];
+                T b[4] = {T(0), T(0), T(0), T(0)};
+                if (k >= 0 && j < prm.p) {
+                    const uint4 w = philox4x32_10(make_uint4(static_cast<uint32_t>(j >> 2),
+                                                             static_cast<uint32_t>(k), s_lo, lsw),
+                                                  prm.keyB);
+                    T z[4];
+                    Normals<T>::four(w, z);
+                    const Pair4<T> ms = Pair4<T>::load(PB + (static_cast<int64_t>(k) * prm.p_pad + j) * 2);
+                    const T wt = w_s[tt];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) b[r] = wt * fma(ms.v[2 * r + 1], z[r], ms.v[2 * r]);
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r) Bs[tt][4 * q4 + r] = b[r];
+            }
+            __syncthreads();
+
+            // 4. rank-TK update of the register tile
+            const int kt = min(TK, prm.c - k0);
+            for (int tt = 0; tt < kt; ++tt) {
+                T av[RM], bv[RP];
+#pragma unroll
+                for (int i = 0; i < RM; ++i) av[i] = As[tt][ty * RM + i];
+#pragma unroll
+                for (int j = 0; j < RP; ++j) bv[j] = Bs[tt][tx * RP + j];
+#pragma unroll
+                for (int i = 0; i < RM; ++i)
+#pragma unroll
+                    for (int j = 0; j < RP; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+            }
+            __syncthreads();
+        }
+
+        // per-sample statistics: running sum of D and of ||D||_F^2
+        T qs = T(0);
+#pragma unroll
+        for (int i = 0; i < RM; ++i)
+#pragma unroll
+            for (int j = 0; j < RP; ++j) {
+                qs = fma(acc[i][j], acc[i][j], qs);
+                sum[i][j] += acc[i][j];
+            }
+        q += static_cast<double>(qs);
+    }
+
+    // chunk partials: the tile's sum of D (rows/cols inside the problem only)
+    T* out = static_cast<T*>(prm.partial_sum) + static_cast<int64_t>(blockIdx.y) * prm.m * prm.p;
+#pragma unroll
+    for (int i = 0; i < RM; ++i) {
+        const int gi = tm0 + ty * RM + i;
+        if (gi >= prm.m) continue;
+#pragma unroll
+        for (int j = 0; j < RP; ++j) {
+            const int gj = tp0 + tx * RP + j;
+            if (gj < prm.p) out[static_cast<int64_t>(gi) * prm.p + gj] = sum[i][j];
+        }
+    }
+    // and its sum of squares, reduced over the CTA in a fixed order
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) q += __shfl_xor_sync(0xffffffffu, q, off);
+    if ((tid & 31) == 0) red_s[tid >> 5] = q;
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < NT / 32; ++w) t += red_s[w];
+        prm.partial_q[static_cast<int64_t>(blockIdx.y) * prm.tiles_m * prm.tiles_p + tile] = t;
+    }
+}
+
+template <typename T, int TM, int TP, int TK, int RM, int RP>
+cudaError_t launch(const LevelParams& prm, cudaStream_t st)
+{
+    constexpr int NT = (TM / RM) * (TP / RP);
+    dim3 grid(prm.tiles_m * prm.tiles_p, prm.nchunks);
+    level_cuda_core_kernel<T, TM, TP, TK, RM, RP><<<grid, NT, 0, st>>>(prm);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+CudaCoreTile cuda_core_tile(int /*precision*/) { return CudaCoreTile{64, 64}; }
+
+cudaError_t launch_level_cuda_core_f64(const LevelParams& prm, cudaStream_t st)
+{
+    return launch<double, 64, 64, 32, 4, 4>(prm, st);
+}
+
+cudaError_t launch_level_cuda_core_f32(const LevelParams& prm, cudaStream_t st)
+{
+    return launch<float, 64, 64, 32, 4, 4>(prm, st);
+}
+
+}  // namespace mlmc
