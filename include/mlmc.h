@@ -203,6 +203,40 @@ MLMC_API mlmc_status mlmc_allocate(mlmc_plan_t* plan, const double* eps_abs, int
 /* Yhat of the current statistics without new samples: yhat_dev as above. */
 MLMC_API mlmc_status mlmc_telescoping_sum(mlmc_plan_t* plan, double* yhat_dev);
 
+/* ---- level statistics without allocation ------------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory: code running while a stream is being
+ * captured into a CUDA graph, inference-runtime plugins whose enqueue step
+ * must not allocate, and applications that give all device memory to their
+ * own pool at start-up.  mlmc_plan allocates (its layout copy and scratch),
+ * so such callers use this instead.
+ *
+ * mlmc_level_stats_noalloc: evaluate samples s = sample_begin ..
+ * sample_begin+count-1 of level `level` of one problem, with the same draws
+ * and arithmetic as mlmc_level_stats, reading the caller's row-major
+ * parameters in place (problem->M_dev etc.; dtype F64 with precision FP64,
+ * or F32 with FP32; other precisions: MLMC_ERR_UNSUPPORTED).  Writes (does
+ * not accumulate) sum_dev (m x p FP64, device) = sum_s D_s and *sumsq_dev
+ * (one FP64, device) = sum_s ||D_s||_F^2; count = 0 writes zeros.  Only
+ * options->c0, ratio and precision are read.  Enqueued on `stream`
+ * (cudaStream_t, NULL = legacy default stream).
+ * Memory: calls no cudaMalloc, cudaFree or allocating library routine.  Its
+ * scratch is a fixed 4 MiB array in the library's device image, present on
+ * every GPU that loads the library until the process exits.  A problem is
+ * accepted only if one chunk of partials fits: m*p*(8 for FP64, 4 for FP32)
+ * + 8*ceil(m/64)*ceil(p/64) <= 4 MiB (for FP64, about m*p <= 520000);
+ * larger sizes return MLMC_ERR_INVALID_ARG with a message.
+ * Set-up: the first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture starts.
+ * Concurrency: all calls share the one array and each call overwrites it, so
+ * calls whose GPU work overlaps (different streams or threads without
+ * ordering) race and give wrong results; order them on one stream or with
+ * events. */
+MLMC_API mlmc_status mlmc_level_stats_noalloc(const mlmc_problem* problem, const mlmc_options* options,
+                                              int32_t level, uint64_t sample_begin, uint64_t count,
+                                              double* sum_dev, double* sumsq_dev, void* stream);
+
 /* ---- reparameterised adjoint ---------------------------------------------------------- */
 
 /* mlmc_backward: gradient of <G, Yhat> with respect to the caller's M, S, M',

@@ -43,6 +43,15 @@ constexpr int64_t kMaxCl = int64_t(1) << 30;
 
 }  // namespace
 
+namespace mlmc {
+// Record a message for mlmc_last_error() from another translation unit.
+mlmc_status report_error(mlmc_status st, const char* msg)
+{
+    g_last_error = msg;
+    return st;
+}
+}  // namespace mlmc
+
 struct ProblemState {
     mlmc_problem desc;
     int L = 0;

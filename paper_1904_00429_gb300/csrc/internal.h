@@ -71,6 +71,9 @@ cudaError_t launch_layout_A(const void* M, const void* S, int src_dtype, int64_t
 cudaError_t launch_layout_B(const void* Mp, const void* Sp, int src_dtype, int64_t ldB, int64_t n,
                             int64_t p, int64_t p_pad, void* PB, bool dst_f64, cudaStream_t st);
 
+// Set the thread-local message returned by mlmc_last_error().
+mlmc_status report_error(mlmc_status st, const char* msg);
+
 // Verification hooks.
 cudaError_t launch_debug_philox(const uint32_t* ctr, const uint32_t* key, int64_t count, uint32_t* out,
                                 cudaStream_t st);

@@ -1,0 +1,95 @@
+"""mlmc_level_stats_noalloc: level statistics for callers that cannot allocate device memory.
+
+Callers inside CUDA-graph stream capture, inference-runtime plugins that must not allocate in
+their enqueue step, and applications that hand all device memory to their own pool cannot go
+through mlmc_plan (it allocates).  The no-alloc entry point keeps its scratch in a fixed array
+of the library image instead.  This test calls it through the C ABI twice in a row (the second
+call reuses the scratch the first one left behind) and compares each result with what the
+plan-based entry points (mlmc_level_stats + mlmc_get_level_state) give for the same samples,
+within the FP64 parity tolerance of the other tests (1e-12 of the summed term magnitudes).
+
+The file is named so that pytest collects it last.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1904_00429_gb300 import binding
+from paper_1904_00429_gb300.inputs import make_params
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+    lib = binding.lib()
+    f = lib.mlmc_level_stats_noalloc
+    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64,
+                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    assert torch.cuda.is_available()
+
+
+def _noalloc(tensors, pp, c0, level, begin, count, precision, dtype_code, stream):
+    M, S, Mp, Sp = tensors
+    m, n = M.shape
+    p = Mp.shape[1]
+    prob = binding.Problem(m, n, p, M.data_ptr(), S.data_ptr(), M.stride(0), Mp.data_ptr(), Sp.data_ptr(),
+                           Mp.stride(0), dtype_code, -1, pp.seed_A, pp.seed_B, pp.seed_idx, pp.problem_id)
+    opts = binding.Options(c0, 2, level, binding.PRECISION[precision], 2, 1.0, 0, 0, 0)
+    out_sum = torch.full((m, p), float("nan"), dtype=torch.float64, device=M.device)
+    out_q = torch.full((1,), float("nan"), dtype=torch.float64, device=M.device)
+    rc = binding.lib().mlmc_level_stats_noalloc(ctypes.byref(prob), ctypes.byref(opts), level, begin, count,
+                                                out_sum.data_ptr(), out_q.data_ptr(), stream.cuda_stream)
+    return rc, out_sum, out_q
+
+
+def _plan_state(tensors, pp, c0, L, level, begin, count, precision):
+    spec = binding.ProblemSpec(*tensors, seed_A=pp.seed_A, seed_B=pp.seed_B, seed_idx=pp.seed_idx,
+                               problem_id=pp.problem_id)
+    with binding.Plan([spec], c0=c0, L=L, precision=precision) as plan:
+        plan.level_stats(0, level, begin, count)
+        N, s, q = plan.get_level_state(0, level)
+        assert N == count
+        return s.clone(), q
+
+
+@pytest.mark.parametrize("precision,np_dtype,t_dtype,code", [("fp64", np.float64, torch.float64, 0),
+                                                              ("fp32", np.float32, torch.float32, 1)])
+def test_noalloc_matches_plan_path_on_two_calls_in_a_row(precision, np_dtype, t_dtype, code):
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream(dev)
+    m, n, p, c0, L = 70, 900, 45, 8, 3
+    pp = make_params(m, n, p, seed_A=21, seed_B=22, seed_idx=23, problem_id=5, dtype=np_dtype)
+    tensors = [torch.from_numpy(np.ascontiguousarray(x)).to(dev, t_dtype) for x in (pp.M, pp.S, pp.Mp, pp.Sp)]
+    orc = oracle.Problem(*pp.f64(), seed_A=21, seed_B=22, seed_idx=23, problem_id=5)
+    lv = oracle.Levels(c0, 2, L)
+    tol = 1e-12 if precision == "fp64" else (c0 * 2**L + 8) * 2.0**-24 + 2.0**-16
+    for level, begin, count in [(2, 0, 40), (3, 13, 27)]:   # two calls in a row, second one ragged
+        rc, s_na, q_na = _noalloc(tensors, pp, c0, level, begin, count, precision, code, stream)
+        assert rc == 0, binding.lib().mlmc_last_error()
+        s_plan, q_plan = _plan_state(tensors, pp, c0, L, level, begin, count, precision)
+        torch.cuda.synchronize()
+        _, _, magm = oracle.level_stats(orc, lv, level, begin, count)
+        bound = tol * count * magm
+        diff = np.abs(s_na.cpu().numpy() - s_plan.cpu().numpy())
+        assert np.all(diff <= bound), diff.max()
+        assert abs(float(q_na.item()) - q_plan) <= tol * count * float((magm**2).sum()) + 1e-12 * q_plan
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch():
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream(dev)
+    m, n, p = 1024, 16, 1024   # 1024 * 1024 * 8 bytes of FP64 partials > 4 MiB
+    pp = make_params(m, n, p)
+    tensors = [torch.from_numpy(x).to(dev) for x in (pp.M, pp.S, pp.Mp, pp.Sp)]
+    rc, s, q = _noalloc(tensors, pp, 4, 1, 0, 8, "fp64", 0, stream)
+    assert rc == 1
+    assert b"scratch" in binding.lib().mlmc_last_error()
+    rc, _, _ = _noalloc(tensors, pp, 4, 1, 0, 8, "bf16", 0, stream)
+    assert rc == 6
