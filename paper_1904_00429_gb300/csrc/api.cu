@@ -37,7 +37,8 @@ mlmc_status fail(mlmc_status st, const char* fmt, ...)
     return st;
 }
 
-constexpr size_t kPartialBudget = size_t(64) << 20;  // bytes of chunk partials per launch
+constexpr size_t kPartialBudget = size_t(64) << 20;     // bytes of chunk partials per launch (CUDA cores)
+constexpr size_t kPartialBudgetTc = size_t(256) << 20;  // tensor-core path: more chunks per persistent launch
 constexpr int kMaxChunksPerLaunch = 4096;
 constexpr int64_t kMaxCl = int64_t(1) << 30;
 
@@ -79,6 +80,9 @@ struct mlmc_plan_s {
     double* dbg_sum = nullptr;    // one level's state for debug_sample
     double* dbg_sumsq = nullptr;
     double* M2_dev = nullptr;     // MLMC_MAX_LEVELS scratch for finalize
+    int* err_flag = nullptr;      // set by kernels whose bounded waits give up
+    int num_sms = 1;
+    uint64_t timeout_ns = 2000000000ull;
     mlmc_status sticky = MLMC_OK;
     std::string sticky_msg;
     uint64_t launches = 0;
@@ -150,6 +154,9 @@ mlmc_status validate(const mlmc_problem* problems, int32_t nprob, const mlmc_opt
     if (o->precision < MLMC_FP64 || o->precision > MLMC_FP8_E4M3)
         return fail(MLMC_ERR_INVALID_ARG, "unknown precision %d", o->precision);
     if (o->pilot_n < 2) return fail(MLMC_ERR_INVALID_ARG, "pilot_n must be >= 2");
+    if ((o->precision == MLMC_BF16 || o->precision == MLMC_FP8_E4M3) && o->ratio != 2)
+        return fail(MLMC_ERR_UNSUPPORTED, "the tensor-core precisions fold the coupling sign into B and need ratio 2");
+    if (o->precision == MLMC_FP8_E4M3) return fail(MLMC_ERR_UNSUPPORTED, "FP8 E4M3 is not available in this build");
     if (!(o->nl_scale > 0.0) || !std::isfinite(o->nl_scale)) return fail(MLMC_ERR_INVALID_ARG, "nl_scale must be > 0");
     if (o->timeout_ns < 0) return fail(MLMC_ERR_INVALID_ARG, "timeout_ns must be >= 0");
     for (int32_t q = 0; q < nprob; ++q) {
@@ -186,6 +193,21 @@ void free_plan(mlmc_plan_t* plan)
     cudaFree(plan->dbg_sum);
     cudaFree(plan->dbg_sumsq);
     cudaFree(plan->M2_dev);
+    cudaFree(plan->err_flag);
+}
+
+bool tensor_core_precision(int precision) { return precision == MLMC_BF16 || precision == MLMC_FP8_E4M3; }
+
+// Read the kernels' error word (synchronises the stream).
+mlmc_status check_device_flag(mlmc_plan_t* plan)
+{
+    int flag = 0;
+    cudaError_t err = cudaMemcpyAsync(&flag, plan->err_flag, sizeof(int), cudaMemcpyDeviceToHost, plan->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(plan->stream);
+    if (check_cuda(plan, err, "read device error flag") != MLMC_OK) return plan->sticky;
+    if (flag != 0)
+        return set_sticky(plan, fail(static_cast<mlmc_status>(flag), "a device-side wait gave up (status %d)", flag));
+    return MLMC_OK;
 }
 
 mlmc_status check_prob_level(mlmc_plan_t* plan, int32_t prob, int32_t level)
@@ -203,8 +225,6 @@ mlmc_status run_level(mlmc_plan_t* plan, ProblemState& ps, int level, uint64_t s
 {
     if (count == 0) return MLMC_OK;
     const mlmc_options& o = plan->opt;
-    if (o.precision == MLMC_BF16 || o.precision == MLMC_FP8_E4M3)
-        return set_sticky(plan, fail(MLMC_ERR_UNSUPPORTED, "precision %d is not available in this build", o.precision));
     const int64_t c = level_c(o, level);
     LevelParams prm{};
     prm.PA = ps.PA;
@@ -235,8 +255,14 @@ mlmc_status run_level(mlmc_plan_t* plan, ProblemState& ps, int level, uint64_t s
         prm.nchunks = nb;
         prm.s_begin = std::max<uint64_t>(s0, cb * kChunk);
         prm.s_end = std::min<uint64_t>(s_end, (cb + nb) * kChunk);
-        cudaError_t err = plan->f64 ? launch_level_cuda_core_f64(prm, plan->stream)
-                                    : launch_level_cuda_core_f32(prm, plan->stream);
+        cudaError_t err;
+        if (o.precision == MLMC_BF16) {
+            TcLaunch tl{plan->err_flag, plan->timeout_ns, static_cast<float>(double(ps.n) / double(c)), plan->num_sms};
+            err = launch_level_tc_bf16(prm, tl, plan->stream);
+        } else {
+            err = plan->f64 ? launch_level_cuda_core_f64(prm, plan->stream)
+                            : launch_level_cuda_core_f32(prm, plan->stream);
+        }
         if (check_cuda(plan, err, "level kernel launch") != MLMC_OK) return plan->sticky;
         plan->launches += 3;  // level kernel, merge of sums, merge of sums of squares
         err = launch_merge_partials(plan->partial_sum, plan->f64, plan->partial_q, nb, ps.tiles_m * ps.tiles_p,
@@ -257,7 +283,8 @@ mlmc_status level_M2(mlmc_plan_t* plan, ProblemState& ps, int first, int count, 
     err = cudaMemcpyAsync(M2_host, plan->M2_dev, sizeof(double) * size_t(count), cudaMemcpyDeviceToHost, plan->stream);
     if (check_cuda(plan, err, "copy M2") != MLMC_OK) return plan->sticky;
     err = cudaStreamSynchronize(plan->stream);
-    return check_cuda(plan, err, "stream synchronize");
+    if (check_cuda(plan, err, "stream synchronize") != MLMC_OK) return plan->sticky;
+    return check_device_flag(plan);
 }
 
 }  // namespace
@@ -300,12 +327,19 @@ mlmc_status mlmc_plan(const mlmc_problem* problems, int32_t nprob, const mlmc_op
         ps.p = problems[q].p;
         ps.m_pad = (ps.m + 3) / 4 * 4;
         ps.p_pad = (ps.p + 3) / 4 * 4;
-        const CudaCoreTile tile = cuda_core_tile(options->precision);
-        ps.tiles_m = int((ps.m + tile.tm - 1) / tile.tm);
-        ps.tiles_p = int((ps.p + tile.tp - 1) / tile.tp);
+        if (tensor_core_precision(options->precision)) {
+            const TcTile tile = tc_tile_for(ps.m, ps.p);
+            ps.tiles_m = int((ps.m + tile.rows - 1) / tile.rows);
+            ps.tiles_p = int((ps.p + tile.bn - 1) / tile.bn);
+        } else {
+            const CudaCoreTile tile = cuda_core_tile(options->precision);
+            ps.tiles_m = int((ps.m + tile.tm - 1) / tile.tm);
+            ps.tiles_p = int((ps.p + tile.tp - 1) / tile.tp);
+        }
         const size_t mp = size_t(ps.m * ps.p);
         const size_t per_chunk = mp * plan->elem;
-        ps.max_chunks = int(std::clamp<size_t>(kPartialBudget / per_chunk, 1, kMaxChunksPerLaunch));
+        const size_t budget = tensor_core_precision(options->precision) ? kPartialBudgetTc : kPartialBudget;
+        ps.max_chunks = int(std::clamp<size_t>(budget / per_chunk, 1, kMaxChunksPerLaunch));
         max_partial = std::max(max_partial, per_chunk * size_t(ps.max_chunks));
         max_q = std::max(max_q, size_t(ps.max_chunks) * size_t(ps.tiles_m * ps.tiles_p));
         max_mp = std::max(max_mp, mp);
@@ -334,6 +368,11 @@ mlmc_status mlmc_plan(const mlmc_problem* problems, int32_t nprob, const mlmc_op
     if (cudaMalloc(reinterpret_cast<void**>(&plan->dbg_sumsq), sizeof(double)) != cudaSuccess) return oom("debug state");
     if (cudaMalloc(reinterpret_cast<void**>(&plan->M2_dev), sizeof(double) * MLMC_MAX_LEVELS) != cudaSuccess)
         return oom("M2 scratch");
+    if (cudaMalloc(reinterpret_cast<void**>(&plan->err_flag), sizeof(int)) != cudaSuccess) return oom("error flag");
+    cudaMemsetAsync(plan->err_flag, 0, sizeof(int), plan->stream);
+    if (cudaDeviceGetAttribute(&plan->num_sms, cudaDevAttrMultiProcessorCount, plan->device) != cudaSuccess)
+        plan->num_sms = 1;
+    if (options->timeout_ns > 0) plan->timeout_ns = uint64_t(options->timeout_ns);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) {
         free_plan(plan);
@@ -359,7 +398,8 @@ mlmc_status mlmc_synchronize(mlmc_plan_t* plan)
     mlmc_status st = enter(plan);
     if (st != MLMC_OK) return st;
     DeviceGuard g(plan->device);
-    return check_cuda(plan, cudaStreamSynchronize(plan->stream), "stream synchronize");
+    if (check_cuda(plan, cudaStreamSynchronize(plan->stream), "stream synchronize") != MLMC_OK) return plan->sticky;
+    return check_device_flag(plan);
 }
 
 mlmc_status mlmc_level_stats(mlmc_plan_t* plan, int32_t prob, int32_t level, uint64_t sample_begin, uint64_t count)
@@ -395,6 +435,7 @@ mlmc_status mlmc_get_level_stats(mlmc_plan_t* plan, int32_t prob, int32_t level,
     err = cudaMemcpyAsync(&m2, plan->M2_dev, sizeof(double), cudaMemcpyDeviceToHost, plan->stream);
     if (check_cuda(plan, err, "copy M2") != MLMC_OK) return plan->sticky;
     if (check_cuda(plan, cudaStreamSynchronize(plan->stream), "stream synchronize") != MLMC_OK) return plan->sticky;
+    if ((st = check_device_flag(plan)) != MLMC_OK) return st;
     if (N) *N = ps.N.v[level];
     if (M2) *M2 = m2;
     if (!std::isfinite(m2)) return fail(MLMC_ERR_NUMERIC, "level %d: non-finite second moment", level);
@@ -419,6 +460,7 @@ mlmc_status mlmc_get_level_state(mlmc_plan_t* plan, int32_t prob, int32_t level,
         err = cudaMemcpyAsync(&q, ps.sumsq + level, sizeof(double), cudaMemcpyDeviceToHost, plan->stream);
     if (err == cudaSuccess) err = cudaStreamSynchronize(plan->stream);
     if (check_cuda(plan, err, "read level state") != MLMC_OK) return plan->sticky;
+    if ((st = check_device_flag(plan)) != MLMC_OK) return st;
     if (N) *N = ps.N.v[level];
     if (sumsq) *sumsq = q;
     return MLMC_OK;

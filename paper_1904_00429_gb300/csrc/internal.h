@@ -45,6 +45,19 @@ cudaError_t launch_level_cuda_core_f64(const LevelParams& prm, cudaStream_t st);
 cudaError_t launch_level_cuda_core_f32(const LevelParams& prm, cudaStream_t st);
 CudaCoreTile cuda_core_tile(int precision);
 
+// Tensor-core (BF16) level kernel: tile of (128 * mh) rows x bn columns per CTA.
+struct TcTile {
+    int mh, bn, rows;
+};
+struct TcLaunch {
+    int* err_flag;        // device word set to an mlmc_status when a bounded wait gives up
+    uint64_t timeout_ns;  // bound on every device-side wait
+    float scale;          // n / c_l, applied to the FP32 accumulator
+    int num_sms;
+};
+TcTile tc_tile_for(int64_t m, int64_t p);
+cudaError_t launch_level_tc_bf16(const LevelParams& prm, const TcLaunch& tl, cudaStream_t st);
+
 // Fold the partials of one launch into a level's FP64 state, in chunk order.
 cudaError_t launch_merge_partials(const void* partial_sum, bool partial_f64, const double* partial_q,
                                   int nchunks, int tiles, int64_t mp, double* level_sum,
