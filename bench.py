@@ -43,6 +43,14 @@ WORKLOAD = dict(name="mlmc_256x65536x256", m=256, n=65536, p=256, c0=64, R=2, L=
 FRACTION = {"fp32": 2.0**-20, "fp64": 2.0**-26, "bf16": 2.0**-18, "fp8": 2.0**-18}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # CUDA-core FMA lanes x 2 flop x max SM clock
 FP64_PEAK_TFLOPS = 1.25
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel from one ncu capture
+# (profiles/); None once the kernel changed after the capture
+TRAFFIC = {
+    "fp32": {"dram_bytes_per_launch": 473.5e6, "algorithmic_bytes_per_launch": 536.9e6,
+             "launch": "level 0, 2048 samples x 64 slots = 131072 outer products",
+             "source": "profiles/level_cuda_core_f32_mlmc_256x65536x256.md"},
+    "bf16": None,
+}
 
 
 def read_peaks():
@@ -197,39 +205,26 @@ def cpu_baseline_sample(W, budget_s=20.0):
     return t_l, pp
 
 
-def run_ours(args):
+def _measure(args, prec, W, host, dev, rank, stream, world, with_e2e):
+    """Pilot + allocation (untimed), then warm-up and exactly ``args.steps`` timed steps of the
+    allocation's work mix for one precision.  Returns a dict of measurements."""
     import torch
 
     from paper_1904_00429_gb300 import binding
-    from paper_1904_00429_gb300.inputs import make_params
-
-    world, rank, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    W = WORKLOAD
-    prec = args.precision
-    pdtype = torch.float64 if prec == "fp64" else torch.float32
-    npdtype = np.float64 if prec == "fp64" else np.float32
-    pp = make_params(W["m"], W["n"], W["p"], seed_A=0, seed_B=1, dtype=npdtype)
-    host = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in (pp.M, pp.S, pp.Mp, pp.Sp)]
-    dev_params = [h.to(dev, non_blocking=True) for h in host]
-    torch.cuda.synchronize()
-    eps = W["rel_rmse"] * float(np.linalg.norm(pp.exact_mean()))
-    stream = torch.cuda.current_stream(dev)
 
     def make_plan(tensors):
         spec = binding.ProblemSpec(*tensors, seed_A=0, seed_B=1, seed_idx=2, problem_id=rank)
         return binding.Plan([spec], c0=W["c0"], L=W["L"], ratio=W["R"], precision=prec, pilot_n=W["pilot"],
                             stream=stream)
 
+    pdtype = torch.float64 if prec == "fp64" else torch.float32
+    dev_params = [h.to(dev, pdtype, non_blocking=True) for h in host]
+    torch.cuda.synchronize()
     plan = make_plan(dev_params)
     levels = list(range(W["L"] + 1))
     for l in levels:
         plan.level_stats(0, l, 0, W["pilot"])
-    Nl = plan.allocate([eps])[0]
+    Nl = plan.allocate([W["eps"]])[0]
     B = batch_sizes(Nl, FRACTION[prec])
     next_id = [W["pilot"]] * len(levels)
 
@@ -251,7 +246,7 @@ def run_ours(args):
     launches0 = plan.launch_count()
     timings = []
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clocks:
+    with ClockSampler(torch.cuda.current_device()) as clocks:
         torch.cuda.synchronize()
         t_start.record(stream)
         for _ in range(args.steps):
@@ -260,83 +255,137 @@ def run_ours(args):
         torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
+    plan.synchronize()   # surfaces any device-side error of the timed launches
     launches = plan.launch_count() - launches0
     total_ms = t_start.elapsed_time(t_end)
     lvl_ms = [sum(ev[i].elapsed_time(ev[i + 1]) for ev in timings) for i in range(len(levels))]
     t_l = [ms / 1e3 / (args.steps * B[l]) for l, ms in zip(levels, lvl_ms)]   # seconds per sample
     T_proj = sum(n * t for n, t in zip(Nl, t_l))
-    if world > 1:
-        tt = torch.tensor([T_proj, total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        T_proj, total_ms = float(tt[0]) / world, float(tt[1])   # ranks split the samples (weak per-GPU work)
-
-    # roofline of the level kernel: algorithmic flops and gathered bytes per sampled outer product
-    m, n, p = W["m"], W["n"], W["p"]
     outer = sum(args.steps * B[l] * plan.cl(l) for l in levels)
-    sample_s = sum(lvl_ms) / 1e3
-    flops = 2.0 * m * p * outer
+    res = {"prec": prec, "Nl": Nl, "B": B, "t_l": t_l, "T": T_proj, "total_ms": total_ms,
+           "sample_s": sum(lvl_ms) / 1e3, "outer": outer, "launches": launches, "clocks": clocks.summary()}
+    plan.close()
+    del dev_params
+
+    if with_e2e:
+        e2e_ms, e2e_sample_ms = [], []
+        m, p = W["m"], W["p"]
+        out_host = torch.empty(m * p, dtype=torch.float64).pin_memory()
+        for it in range(args.warmup + max(1, min(args.steps, 3))):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            tensors = [h.to(dev, pdtype, non_blocking=True) for h in host]
+            p2 = make_plan(tensors)
+            tm = []
+            step(p2, tm)
+            y = p2.telescoping_sum()[0]
+            out_host.copy_(y.reshape(-1), non_blocking=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            p2.close()
+            if it >= args.warmup:
+                e2e_ms.append(e0.elapsed_time(e1))
+                e2e_sample_ms.append(sum(tm[0][i].elapsed_time(tm[0][i + 1]) for i in range(len(levels))))
+        res["e2e_overhead_s"] = (statistics.mean(e2e_ms) - statistics.mean(e2e_sample_ms)) / 1e3
+        res["h2d"] = sum(h.numel() * h.element_size() for h in host)
+        res["d2h"] = m * p * 8
+    return res
+
+
+def _roofline(res, W, peaks, peak_kind):
+    m, p = W["m"], W["p"]
+    prec = res["prec"]
+    flops = 2.0 * m * p * res["outer"]
     elem = 8 if prec == "fp64" else 4
-    bytes_alg = 2.0 * (m + p) * elem * outer
-    peaks, peak_kind = read_peaks()
+    bytes_alg = 2.0 * (m + p) * elem * res["outer"]
+    t = res["sample_s"]
     if prec in ("fp32", "fp64"):
         peak = FP32_PEAK_TFLOPS if prec == "fp32" else FP64_PEAK_TFLOPS
-        achieved = flops / sample_s / 1e12
-        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": None, "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)",
-                    "hbm_achieved_gbs": bytes_alg / sample_s / 1e9, "hbm_peak_gbs": peaks["hbm_gbs"],
-                    "kernel": f"level_cuda_core_kernel<{prec}>"}
-    else:
-        peak = peaks["bf16_tflops_sustained"] * (2.0 if prec == "fp8" else 1.0)
-        achieved = flops / sample_s / 1e12
-        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None, "peak_source": f"bf16 sustained ({peak_kind})"}
+        achieved = flops / t / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": TRAFFIC.get(prec), "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)",
+                "hbm_achieved_gbs": bytes_alg / t / 1e9, "hbm_peak_gbs": peaks["hbm_gbs"],
+                "kernel": f"level_cuda_core_kernel<{prec}>"}
+    # tensor-core path: the slower of gathered bytes at HBM bandwidth and FLOPs at the tensor peak
+    hbm = bytes_alg / t / 1e9
+    tflops = flops / t / 1e12
+    tpeak = peaks["bf16_tflops_sustained"] * (2.0 if prec == "fp8" else 1.0)
+    t_hbm = bytes_alg / (peaks["hbm_gbs"] * 1e9)
+    t_tc = flops / (tpeak * 1e12)
+    if t_hbm >= t_tc:
+        return {"bound": "hbm", "achieved": hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": hbm / peaks["hbm_gbs"], "traffic": TRAFFIC.get(prec),
+                "peak_source": f"hbm_gbs ({peak_kind})", "tensor_achieved_tflops": tflops,
+                "tensor_peak_tflops": tpeak, "tensor_frac": tflops / tpeak,
+                "kernel": f"level_tc_{prec}_kernel"}
+    return {"bound": "tensor", "achieved": tflops, "peak": tpeak, "unit": "TFLOP/s", "frac": tflops / tpeak,
+            "traffic": TRAFFIC.get(prec), "peak_source": f"bf16_tflops_sustained ({peak_kind})",
+            "hbm_achieved_gbs": hbm, "kernel": f"level_tc_{prec}_kernel"}
 
-    # e2e through the C ABI from pinned host buffers
-    e2e_ms, e2e_sample_ms = [], []
-    out_host = torch.empty(m * p, dtype=torch.float64).pin_memory()
-    for it in range(args.warmup + max(1, min(args.steps, 3))):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        tensors = [h.to(dev, non_blocking=True) for h in host]
-        p2 = make_plan(tensors)
-        tm = []
-        step(p2, tm)
-        y = p2.telescoping_sum()[0]
-        out_host.copy_(y.reshape(-1), non_blocking=True)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        p2.close()
-        if it >= args.warmup:
-            e2e_ms.append(e0.elapsed_time(e1))
-            e2e_sample_ms.append(sum(tm[0][i].elapsed_time(tm[0][i + 1]) for i in range(len(levels))))
-    overhead_s = (statistics.mean(e2e_ms) - statistics.mean(e2e_sample_ms)) / 1e3
-    E = overhead_s + T_proj
-    h2d = sum(h.numel() * h.element_size() for h in host)
 
+def run_ours(args):
+    import torch
+
+    from paper_1904_00429_gb300.inputs import make_params
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    W = dict(WORKLOAD)
+    pp = make_params(W["m"], W["n"], W["p"], seed_A=0, seed_B=1, dtype=np.float32)
+    host = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in (pp.M, pp.S, pp.Mp, pp.Sp)]
+    W["eps"] = W["rel_rmse"] * float(np.linalg.norm(pp.exact_mean()))
+    stream = torch.cuda.current_stream(dev)
+
+    head = _measure(args, args.precision, W, host, dev, rank, stream, world, with_e2e=True)
+    others = []
+    if not args.no_compare:
+        for prec in ("fp32",):
+            if prec != args.precision:
+                others.append(_measure(args, prec, W, host, dev, rank, stream, world, with_e2e=False))
+    T = head["T"]
+    if world > 1:
+        tt = torch.tensor([T, head["total_ms"]] + [o["T"] for o in others], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        # every rank evaluates its own sample ranges: the N_l are split across the ranks
+        T, head["total_ms"] = float(tt[0]) / world, float(tt[1])
+        for i, o in enumerate(others):
+            o["T"] = float(tt[2 + i]) / world
     if rank != 0:
         return
+    peaks, peak_kind = read_peaks()
+    m, n, p = W["m"], W["n"], W["p"]
+    prec = head["prec"]
     line = {
         "metric": "time-to-RMSE 1e-3 for E[AB] (projected from the measured per-level sample rate)",
-        "value": T_proj, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": total_ms / args.steps, "higher_is_better": False, "scaling": "weak",
+        "value": T, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": head["total_ms"] / args.steps, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64", "bf16": "bf16", "fp8": "e4m3"}[prec],
         "data": "synthetic",
         "config": {"workload": W["name"], "m": m, "n": n, "p": p, "c0": W["c0"], "ratio": W["R"], "L": W["L"],
-                   "pilot": W["pilot"], "eps_abs": eps, "N_l": Nl, "batch_per_step": B,
-                   "inputs": "parameters 256 MiB > L2 (random row gathers), no flush",
-                   "precision": prec},
-        "outer_products_per_s": outer / sample_s,
-        "per_level_us_per_sample": [1e6 * t for t in t_l],
-        "gpu_launches": launches,
-        "roofline": roofline,
-        "clocks": clocks.summary(),
-        "e2e": {"value": E, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": m * p * 8,
-                "overhead_s": overhead_s},
+                   "pilot": W["pilot"], "eps_abs": W["eps"], "N_l": head["Nl"], "batch_per_step": head["B"],
+                   "inputs": "parameters 256 MiB > L2 (random row gathers), no flush", "precision": prec},
+        "outer_products_per_s": head["outer"] / head["sample_s"],
+        "per_level_us_per_sample": [1e6 * t for t in head["t_l"]],
+        "gpu_launches": head["launches"],
+        "roofline": _roofline(head, W, peaks, peak_kind),
+        "clocks": head["clocks"],
+        "e2e": {"value": head["e2e_overhead_s"] + T, "unit": "s", "h2d_bytes_per_step": head["h2d"],
+                "d2h_bytes_per_step": head["d2h"], "overhead_s": head["e2e_overhead_s"]},
     }
+    if others:
+        line["compare"] = {o["prec"]: {"value": o["T"], "unit": "s",
+                                       "outer_products_per_s": o["outer"] / o["sample_s"],
+                                       "speedup_of_headline": o["T"] / T,
+                                       "roofline": _roofline(o, W, peaks, peak_kind), "clocks": o["clocks"]}
+                           for o in others}
     if not args.no_cpu_baseline and world == 1:
         t_cpu, _ = cpu_baseline_sample(W)
-        T_cpu = sum(nl * t for nl, t in zip(Nl, t_cpu))
+        T_cpu = sum(nl * t for nl, t in zip(head["Nl"], t_cpu))
         line["cpu_baseline"] = {"value": T_cpu, "unit": "s", "cores": 1, "kind": "oracle",
                                 "sample": "one FP64 oracle sample per level 0..8 (about 20 s of CPU work), "
                                           "projected with the same N_l"}
@@ -349,7 +398,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp32", "fp64", "bf16", "fp8"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "fp64", "bf16", "fp8"], default="bf16")
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP32 comparison measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

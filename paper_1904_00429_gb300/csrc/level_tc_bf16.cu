@@ -7,17 +7,22 @@
 // slots at l >= 1 (sigma = +1 at l = 0).  sigma is folded into the B operand before rounding
 // (exact); the magnitude n/c_l is applied to the FP32 accumulator.
 //
-// Persistent CTAs of 8 warps walk (chunk of samples, output tile) work items.  For each
-// 64-slot K-block of a sample, all warps draw the slot indices, gather the sampled (M, S) /
-// (M', S') pairs, generate A = M + S Z and sigma (M' + S' Z') from Philox, round them to bf16
-// and store them into a 128-byte-swizzled K-major tile of a 2- or 3-stage shared-memory ring;
-// one thread then issues tcgen05.mma (M = 128 per half, N = tile width, K = 16 steps) into
-// TMEM and commits to the stage's mbarrier, so the next stage is generated while the tensor
-// core works.  After the last K-block of a sample, the 8 warps drain the accumulator with
-// tcgen05.ld, add the sample's D to the chunk partial in global memory (the TMEM is fully
-// used by D for 256 x 256 tiles) and accumulate ||D||_F^2.  Every mbarrier wait is bounded by
-// a %globaltimer deadline; on timeout the kernel records MLMC_ERR_TIMEOUT and leaves after
-// freeing its tensor memory.
+// Persistent CTAs of 9 warps walk (chunk of samples, output tile) work items; a sample's slots
+// are processed in sub-blocks of 16 (one MMA K step):
+//   * producer warp (warp 8): draws the 16 slot indices of a sub-block from Philox and issues
+//     TMA bulk copies (cp.async.bulk) of the sampled (M, S) column and (M', S') row pairs of the
+//     tile into a double-buffered staging area, completing on the buffer's mbarrier;
+//   * generator warps (0-7): wait for the staged pairs, generate A = M + S Z and
+//     sigma (M' + S' Z') with Philox and a special-function-unit Box-Muller, round to bf16 and
+//     write them into one 16-slot slice of a 128-byte-swizzled K-major tile (four slices form
+//     one swizzle atom); thread 0 then issues tcgen05.mma (M = 128 per half, N = tile width,
+//     K = 16) into TMEM and commits to the slice's mbarrier;
+//   * after the last sub-block of a sample the generator warps drain the accumulator with
+//     tcgen05.ld, add the sample's D to the chunk partial in global memory (store for the first
+//     sample of the chunk, then red.global.add: each element has one owner thread, so the
+//     order is fixed) and accumulate ||D||_F^2.
+// Every mbarrier wait is bounded by a %globaltimer deadline; on timeout the kernel records
+// MLMC_ERR_TIMEOUT and leaves after freeing its tensor memory.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -28,25 +33,32 @@
 namespace mlmc {
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kKB = 64;  // slots per K-block: one 128-byte swizzle atom of bf16
+constexpr int kGenWarps = 8;
+constexpr int kGenThreads = kGenWarps * 32;
+constexpr int kThreads = kGenThreads + 32;  // + producer warp
+constexpr int kSub = 16;                    // slots per sub-block = one MMA K step
+constexpr int kSlices = 4;                  // sub-blocks per 128-byte swizzle atom (64 bf16)
+constexpr int kGenBarrier = 1;              // named barrier of the generator warps
 
 template <int MH, int BN>
 struct TcCfg {
-    static constexpr int kRows = 128 * MH;                  // output rows of a tile
-    static constexpr int kABytes = kRows * 128;             // kRows x 64 bf16
-    static constexpr int kBBytes = BN * 128;                // BN x 64 bf16 (B transposed, K-major)
-    static constexpr int kStageBytes = kABytes + kBBytes;
-    static constexpr int kStages = kStageBytes * 3 <= 200 * 1024 ? 3 : 2;
+    static constexpr int kRows = 128 * MH;                 // output rows of a tile
+    static constexpr int kABytes = kRows * 128;            // kRows x 64 bf16, 128-byte swizzled
+    static constexpr int kBBytes = BN * 128;               // BN x 64 bf16 (B transposed, K-major)
+    static constexpr int kTileBytes = kABytes + kBBytes;
+    static constexpr int kStageABytes = kSub * kRows * 8;  // FP32 (M, S) pairs of the sub-block
+    static constexpr int kStageBBytes = kSub * BN * 8;     // FP32 (M', S') pairs
+    static constexpr int kStageBytes = kStageABytes + kStageBBytes;
     static constexpr int kTileCols = MH * BN;
     static constexpr int kTmemCols = kTileCols <= 32 ? 32 : kTileCols <= 64 ? 64 : kTileCols <= 128 ? 128
                                      : kTileCols <= 256 ? 256 : 512;
-    // dynamic shared memory: stage tiles (1024-aligned), then bookkeeping
-    static constexpr int kBookBytes = kStages * kKB * 4 /*idx*/ + kStages * kKB * 4 /*sign*/ +
-                                      (kStages + 1) * 8 /*mbarriers*/ + 16 /*tmem addr, abort*/ + 8 * 8 /*red*/;
-    static constexpr int kSmemBytes = 1024 /*align slack*/ + kStages * kStageBytes + kBookBytes;
+    // barriers: full[2], empty[2], slice[4], done
+    static constexpr int kNumBars = 2 + 2 + kSlices + 1;
+    static constexpr int kBookBytes = 2 * kSub * 4 /*idx*/ + kNumBars * 8 + 16 /*tmem, abort*/ + kGenWarps * 8;
+    static constexpr int kSmemBytes = 1024 /*align slack*/ + kTileBytes + 2 * kStageBytes + kBookBytes;
     static_assert(kTileCols <= 512, "tile exceeds tensor memory");
     static_assert(BN % 16 == 0 && BN >= 32 && BN <= 256, "N of the MMA");
+    static_assert(kSmemBytes <= 227 * 1024, "shared memory");
 };
 
 struct TcExtra {
@@ -62,6 +74,41 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
     return *reinterpret_cast<const uint32_t*>(&v);
 }
 
+// Generate one block of (4 rows of A, or 4 columns of B) x (8 slots) entries from staged (M, S)
+// pairs and write them as bf16 into the swizzled tile: tile rows row0 .. row0+3, 16-byte chunk
+// `chunk`.  Staged pairs of slot u start at stage + u * stride (8 floats: (M,S) x 4).
+__device__ __forceinline__ void gen_block(const int* idx, int slot0, bool valid_rows, uint32_t rowgrp,
+                                          uint32_t s_lo, uint32_t lsw, uint2 key, const unsigned char* stage,
+                                          int stride, bool odd_negative, unsigned char* tile, int row0, int chunk)
+{
+    float v[4][8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int k = idx[slot0 + u];
+        if (k >= 0 && valid_rows) {
+            const uint4 w = philox4x32_10(make_uint4(rowgrp, static_cast<uint32_t>(k), s_lo, lsw), key);
+            float z[4];
+            normals4_mufu(w, z);
+            const float4* src = reinterpret_cast<const float4*>(stage + u * stride);
+            const float4 p0 = src[0];
+            const float4 p1 = src[1];
+            const float sg = (odd_negative && (u & 1)) ? -1.0f : 1.0f;
+            v[0][u] = sg * fmaf(p0.y, z[0], p0.x);
+            v[1][u] = sg * fmaf(p0.w, z[1], p0.z);
+            v[2][u] = sg * fmaf(p1.y, z[2], p1.x);
+            v[3][u] = sg * fmaf(p1.w, z[3], p1.z);
+        } else {
+            v[0][u] = v[1][u] = v[2][u] = v[3][u] = 0.0f;
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const uint4 packed = make_uint4(pack_bf16x2(v[r][0], v[r][1]), pack_bf16x2(v[r][2], v[r][3]),
+                                        pack_bf16x2(v[r][4], v[r][5]), pack_bf16x2(v[r][6], v[r][7]));
+        *reinterpret_cast<uint4*>(tile + tc::sw128_offset(row0 + r, chunk)) = packed;
+    }
+}
+
 template <int MH, int BN>
 __global__ void __launch_bounds__(kThreads, 1) level_tc_bf16_kernel(const LevelParams prm, const TcExtra ex)
 {
@@ -69,22 +116,32 @@ __global__ void __launch_bounds__(kThreads, 1) level_tc_bf16_kernel(const LevelP
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                            ~static_cast<uintptr_t>(1023));
-    unsigned char* tiles = smem;
-    int* idx_s = reinterpret_cast<int*>(smem + C::kStages * C::kStageBytes);
-    float* sgn_s = reinterpret_cast<float*>(idx_s + C::kStages * kKB);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sgn_s + C::kStages * kKB);  // [kStages] free + [1] done
-    uint32_t* tmem_s = reinterpret_cast<uint32_t*>(bars + C::kStages + 1);
-    int* abort_s = reinterpret_cast<int*>(tmem_s + 1);
+    unsigned char* a_tile = smem;
+    unsigned char* b_tile = smem + C::kABytes;
+    unsigned char* staging = smem + C::kTileBytes;  // [2][kStageBytes]
+    int* idx_s = reinterpret_cast<int*>(staging + 2 * C::kStageBytes);  // [2][kSub]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(idx_s + 2 * kSub);
+    uint32_t* tmem_s = reinterpret_cast<uint32_t*>(bars + C::kNumBars);
+    volatile int* abort_s = reinterpret_cast<volatile int*>(tmem_s + 1);
     double* red_s = reinterpret_cast<double*>(tmem_s + 4);
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
     const int lane = tid & 31;
-    const uint32_t bar_done = tc::smem_addr(&bars[C::kStages]);
+    const uint32_t bars0 = tc::smem_addr(bars);
+    const uint32_t bar_done = bars0 + 8 * (4 + kSlices);
+    auto bar_full = [&](int b) { return bars0 + 8 * b; };
+    auto bar_empty = [&](int b) { return bars0 + 8 * (2 + b); };
+    auto bar_slice = [&](int kk) { return bars0 + 8 * (4 + kk); };
 
     if (warp == 0) tc::tmem_alloc(tc::smem_addr(tmem_s), C::kTmemCols);
     if (tid == 0) {
-        for (int st = 0; st <= C::kStages; ++st) tc::mbar_init(tc::smem_addr(&bars[st]), 1);
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(bar_full(b), 1);
+            tc::mbar_init(bar_empty(b), kGenWarps);
+        }
+        for (int kk = 0; kk < kSlices; ++kk) tc::mbar_init(bar_slice(kk), 1);
+        tc::mbar_init(bar_done, 1);
         tc::mbar_init_fence();
         *abort_s = 0;
     }
@@ -96,228 +153,228 @@ __global__ void __launch_bounds__(kThreads, 1) level_tc_bf16_kernel(const LevelP
     const int tiles_n = prm.tiles_m * prm.tiles_p;
     const float* PA = static_cast<const float*>(prm.PA);
     const float* PB = static_cast<const float*>(prm.PB);
-    const int nkb = (prm.c + kKB - 1) / kKB;
-    constexpr uint32_t idesc = tc::idesc_bf16_f32(128, BN);
+    const int nsub = (prm.c + kSub - 1) / kSub;
 
-    uint32_t kb_count = 0;    // K-blocks issued by this CTA (ring position and phase)
-    uint32_t done_count = 0;  // samples completed by this CTA (phase of the done barrier)
-    bool aborted = false;
-
-    for (int item = blockIdx.x; item < ex.total_items && !aborted; item += gridDim.x) {
-        const int cy = item / tiles_n;
-        const int tile = item % tiles_n;
-        const int tm0 = (tile / prm.tiles_p) * C::kRows;
-        const int tp0 = (tile % prm.tiles_p) * BN;
-        const uint64_t chunk = prm.chunk0 + static_cast<uint64_t>(cy);
-        const uint64_t sa = max(prm.s_begin, chunk * kChunk);
-        const uint64_t sb = min(prm.s_end, (chunk + 1) * kChunk);
-        float* part = static_cast<float*>(prm.partial_sum) + static_cast<int64_t>(cy) * prm.m * prm.p;
-        double q = 0.0;
-
-        for (uint64_t s = sa; s < sb && !aborted; ++s) {
-            const uint32_t lsw = level_sample_word(prm.l, s);
-            const uint32_t s_lo = static_cast<uint32_t>(s);
-            for (int kb = 0; kb < nkb; ++kb, ++kb_count) {
-                const int stage = static_cast<int>(kb_count % C::kStages);
-                unsigned char* a_tile = tiles + stage * C::kStageBytes;
-                unsigned char* b_tile = a_tile + C::kABytes;
-                int* idx = idx_s + stage * kKB;
-                float* sgn = sgn_s + stage * kKB;
-                // the ring slot is free once the MMAs of K-block kb_count - kStages completed
-                if (kb_count >= static_cast<uint32_t>(C::kStages)) {
-                    const uint32_t use = kb_count / C::kStages - 1;
-                    if (!tc::mbar_wait_bounded(tc::smem_addr(&bars[stage]), use & 1,
-                                               tc::globaltimer() + ex.timeout_ns)) {
+    if (warp == kGenWarps) {
+        // ---------------- producer warp: indices + TMA bulk copies of the sampled pairs ----------
+        uint32_t g = 0;  // sub-blocks produced by this CTA
+        bool aborted = false;
+        for (int item = blockIdx.x; item < ex.total_items && !aborted; item += gridDim.x) {
+            const int cy = item / tiles_n;
+            const int tile = item % tiles_n;
+            const int tm0 = (tile / prm.tiles_p) * C::kRows;
+            const int tp0 = (tile % prm.tiles_p) * BN;
+            const uint32_t a_bytes = static_cast<uint32_t>(min(C::kRows, prm.m_pad - tm0)) * 8u;
+            const uint32_t b_bytes = static_cast<uint32_t>(min(BN, prm.p_pad - tp0)) * 8u;
+            const uint64_t chunk = prm.chunk0 + static_cast<uint64_t>(cy);
+            const uint64_t sa = max(prm.s_begin, chunk * kChunk);
+            const uint64_t sb = min(prm.s_end, (chunk + 1) * kChunk);
+            for (uint64_t s = sa; s < sb && !aborted; ++s) {
+                const uint32_t lsw = level_sample_word(prm.l, s);
+                const uint32_t s_lo = static_cast<uint32_t>(s);
+                for (int j = 0; j < nsub; ++j, ++g) {
+                    const int b = static_cast<int>(g & 1);
+                    if (g >= 2 && !tc::mbar_wait_bounded(bar_empty(b), ((g >> 1) - 1) & 1,
+                                                         tc::globaltimer() + ex.timeout_ns)) {
                         *abort_s = 1;
                         atomicExch(ex.err_flag, MLMC_ERR_TIMEOUT);
                     }
+                    if (__any_sync(0xffffffffu, *abort_s != 0)) {
+                        aborted = true;
+                        break;
+                    }
+                    int* idx = idx_s + b * kSub;
+                    const int t0 = j * kSub;
+                    if (lane < kSub / 2) {
+                        const int t = t0 + 2 * lane;
+                        int64_t r0 = -1, r1 = -1;
+                        if (t < prm.c) index_pair(prm.keyI, lsw, s_lo, t >> 1, static_cast<uint64_t>(prm.n), r0, r1);
+                        idx[2 * lane] = t < prm.c ? static_cast<int>(r0) : -1;
+                        idx[2 * lane + 1] = t + 1 < prm.c ? static_cast<int>(r1) : -1;
+                    }
+                    __syncwarp();
+                    const int nvalid = min(kSub, prm.c - t0);
+                    if (lane == 0)
+                        tc::mbar_arrive_expect_tx(bar_full(b), static_cast<uint32_t>(nvalid) * (a_bytes + b_bytes));
+                    __syncwarp();
+                    if (lane < nvalid) {
+                        const int k = idx[lane];
+                        unsigned char* st = staging + b * C::kStageBytes;
+                        tc::bulk_copy_g2s(tc::smem_addr(st + lane * (C::kRows * 8)),
+                                          PA + (static_cast<int64_t>(k) * prm.m_pad + tm0) * 2, a_bytes, bar_full(b));
+                        tc::bulk_copy_g2s(tc::smem_addr(st + C::kStageABytes + lane * (BN * 8)),
+                                          PB + (static_cast<int64_t>(k) * prm.p_pad + tp0) * 2, b_bytes, bar_full(b));
+                    }
+                    __syncwarp();
                 }
-                // slot indices and signs of this K-block
-                if (tid < kKB / 2) {
-                    const int t = kb * kKB + 2 * tid;
-                    int64_t r0 = -1, r1 = -1;
-                    if (t < prm.c) index_pair(prm.keyI, lsw, s_lo, t >> 1, static_cast<uint64_t>(prm.n), r0, r1);
-                    idx[2 * tid] = t < prm.c ? static_cast<int>(r0) : -1;
-                    idx[2 * tid + 1] = t + 1 < prm.c ? static_cast<int>(r1) : -1;
-                    // slot t is coarse iff t % 2 == 1 (ratio 2) and l > 0
-                    sgn[2 * tid] = 1.0f;
-                    sgn[2 * tid + 1] = prm.l > 0 ? -1.0f : 1.0f;
+            }
+        }
+    } else {
+        // ---------------- generator warps: entries, MMA issue, drain ----------------------------
+        constexpr uint32_t idesc = tc::idesc_bf16_f32(128, BN);
+        constexpr int kItemsA = (C::kRows / 4) * 2;
+        constexpr int kItemsB = (BN / 4) * 2;
+        uint32_t g = 0;  // sub-blocks consumed
+        uint32_t slice_uses[kSlices] = {0, 0, 0, 0};
+        uint32_t done_count = 0;
+        bool aborted = false;
+        const bool coarse_sign = prm.l > 0;
+        for (int item = blockIdx.x; item < ex.total_items && !aborted; item += gridDim.x) {
+            const int cy = item / tiles_n;
+            const int tile = item % tiles_n;
+            const int tm0 = (tile / prm.tiles_p) * C::kRows;
+            const int tp0 = (tile % prm.tiles_p) * BN;
+            const uint64_t chunk = prm.chunk0 + static_cast<uint64_t>(cy);
+            const uint64_t sa = max(prm.s_begin, chunk * kChunk);
+            const uint64_t sb = min(prm.s_end, (chunk + 1) * kChunk);
+            float* part = static_cast<float*>(prm.partial_sum) + static_cast<int64_t>(cy) * prm.m * prm.p;
+            double q = 0.0;
+            for (uint64_t s = sa; s < sb && !aborted; ++s) {
+                const uint32_t lsw = level_sample_word(prm.l, s);
+                const uint32_t s_lo = static_cast<uint32_t>(s);
+                for (int j = 0; j < nsub; ++j, ++g) {
+                    const int b = static_cast<int>(g & 1);
+                    const int kk = j % kSlices;
+                    bool ok = tc::mbar_wait_bounded(bar_full(b), (g >> 1) & 1, tc::globaltimer() + ex.timeout_ns);
+                    if (ok && slice_uses[kk] > 0)
+                        ok = tc::mbar_wait_bounded(bar_slice(kk), (slice_uses[kk] - 1) & 1,
+                                                   tc::globaltimer() + ex.timeout_ns);
+                    if (!ok) {
+                        *abort_s = 1;
+                        atomicExch(ex.err_flag, MLMC_ERR_TIMEOUT);
+                    }
+                    const int* idx = idx_s + b * kSub;
+                    const unsigned char* st = staging + b * C::kStageBytes;
+                    if (ok) {
+                        for (int it = tid; it < kItemsA + kItemsB; it += kGenThreads) {
+                            if (it < kItemsA) {
+                                // 4 rows of A x 8 slots
+                                const int g4 = it % (C::kRows / 4);
+                                const int sg = it / (C::kRows / 4);
+                                const int i = tm0 + 4 * g4;
+                                gen_block(idx, sg * 8, i < prm.m, static_cast<uint32_t>(i >> 2), s_lo, lsw, prm.keyA,
+                                          st + (sg * 8) * (C::kRows * 8) + g4 * 32, C::kRows * 8, false, a_tile,
+                                          4 * g4, 2 * kk + sg);
+                            } else {
+                                // 4 columns of B (rows of the transposed tile) x 8 slots, sign folded in
+                                const int it2 = it - kItemsA;
+                                const int g4 = it2 % (BN / 4);
+                                const int sg = it2 / (BN / 4);
+                                const int jc = tp0 + 4 * g4;
+                                gen_block(idx, sg * 8, jc < prm.p, static_cast<uint32_t>(jc >> 2), s_lo, lsw,
+                                          prm.keyB, st + C::kStageABytes + (sg * 8) * (BN * 8) + g4 * 32, BN * 8,
+                                          coarse_sign, b_tile, 4 * g4, 2 * kk + sg);
+                            }
+                        }
+                    }
+                    // staging buffer b fully read by this warp
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(bar_empty(b));
+                    tc::fence_proxy_async_smem();
+                    tc::named_barrier(kGenBarrier, kGenThreads);
+                    if (*abort_s) {
+                        aborted = true;
+                        break;
+                    }
+                    if (tid == 0) {
+                        tc::tc_fence_after_sync();
+#pragma unroll
+                        for (int h = 0; h < MH; ++h) {
+                            const uint64_t adesc =
+                                tc::sw128_kmajor_desc(tc::smem_addr(a_tile) + h * 128 * 128 + 32 * kk);
+                            const uint64_t bdesc = tc::sw128_kmajor_desc(tc::smem_addr(b_tile) + 32 * kk);
+                            tc::mma_bf16(tmem + h * BN, adesc, bdesc, idesc, j > 0 ? 1u : 0u);
+                        }
+                        tc::mma_commit(bar_slice(kk));
+                        if (j == nsub - 1) tc::mma_commit(bar_done);
+                    }
+                    ++slice_uses[kk];
                 }
-                __syncthreads();
+                if (aborted) break;
+                // sample epilogue: wait for the accumulator, then drain it
+                if (!tc::mbar_wait_bounded(bar_done, done_count & 1, tc::globaltimer() + ex.timeout_ns)) {
+                    *abort_s = 1;
+                    atomicExch(ex.err_flag, MLMC_ERR_TIMEOUT);
+                }
+                ++done_count;
+                tc::named_barrier(kGenBarrier, kGenThreads);
                 if (*abort_s) {
                     aborted = true;
                     break;
                 }
-                // A tile: kRows rows x 64 slots; item = (row group of 4, slot group of 8)
-                for (int it = tid; it < (C::kRows / 4) * 8; it += kThreads) {
-                    const int g4 = it % (C::kRows / 4);
-                    const int sg = it / (C::kRows / 4);
-                    const int i = tm0 + 4 * g4;
-                    float v[4][8];
+                tc::tc_fence_after_sync();
+                {
+                    const int quarter = warp & 3;
+                    const int hgrp = warp >> 2;
+                    // MH == 2: warp group h drains M-half h (all BN columns); MH == 1: the two warp
+                    // groups split the columns, or group 0 takes all of them when BN < 64.
+                    const bool split = MH == 1 && BN >= 64;
+                    const int row_local = (MH == 2 ? hgrp * 128 : 0) + quarter * 32 + lane;
+                    const int col_tm = MH == 2 ? hgrp * BN : (split ? hgrp * (BN / 2) : 0);
+                    const int col_d = MH == 2 ? 0 : col_tm;
+                    const int ncols = MH == 2 ? BN : (split ? BN / 2 : (hgrp == 0 ? BN : 0));
+                    const int gi = tm0 + row_local;
+                    const bool first = (s == sa);
+                    for (int cb = 0; cb < ncols; cb += 32) {
+                        float v[32];
+                        tc::tmem_ld_32x32b_x32(tmem + (static_cast<uint32_t>(quarter * 32) << 16) +
+                                                   static_cast<uint32_t>(col_tm + cb),
+                                               v);
+                        float qs = 0.0f;
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const int k = idx[sg * 8 + u];
-                        if (k >= 0 && i < prm.m) {
-                            const uint4 w = philox4x32_10(
-                                make_uint4(static_cast<uint32_t>(i >> 2), static_cast<uint32_t>(k), s_lo, lsw),
-                                prm.keyA);
-                            float z[4];
-                            normals4_f32(w, z);
-                            const float4* src = reinterpret_cast<const float4*>(
-                                PA + (static_cast<int64_t>(k) * prm.m_pad + i) * 2);
-                            const float4 p0 = __ldg(src);
-                            const float4 p1 = __ldg(src + 1);
-                            v[0][u] = fmaf(p0.y, z[0], p0.x);
-                            v[1][u] = fmaf(p0.w, z[1], p0.z);
-                            v[2][u] = fmaf(p1.y, z[2], p1.x);
-                            v[3][u] = fmaf(p1.w, z[3], p1.z);
-                        } else {
-                            v[0][u] = v[1][u] = v[2][u] = v[3][u] = 0.0f;
+                        for (int e = 0; e < 32; ++e) {
+                            v[e] *= ex.scale;
+                            qs = fmaf(v[e], v[e], qs);
+                        }
+                        q += static_cast<double>(qs);
+                        const int gj0 = tp0 + col_d + cb;
+                        if (gi < prm.m && gj0 < prm.p) {
+                            float* dst = part + static_cast<int64_t>(gi) * prm.p + gj0;
+                            const int valid = min(32, prm.p - gj0);
+                            if (valid == 32 && (prm.p & 3) == 0) {
+#pragma unroll
+                                for (int e4 = 0; e4 < 8; ++e4) {
+                                    if (first)
+                                        reinterpret_cast<float4*>(dst)[e4] =
+                                            make_float4(v[4 * e4], v[4 * e4 + 1], v[4 * e4 + 2], v[4 * e4 + 3]);
+                                    else
+                                        tc::red_add_v4(dst + 4 * e4, v[4 * e4], v[4 * e4 + 1], v[4 * e4 + 2],
+                                                       v[4 * e4 + 3]);
+                                }
+                            } else {
+#pragma unroll
+                                for (int e = 0; e < 32; ++e)
+                                    if (e < valid) {
+                                        if (first)
+                                            dst[e] = v[e];
+                                        else
+                                            atomicAdd(dst + e, v[e]);
+                                    }
+                            }
                         }
                     }
-#pragma unroll
-                    for (int r = 0; r < 4; ++r) {
-                        const uint4 packed = make_uint4(pack_bf16x2(v[r][0], v[r][1]), pack_bf16x2(v[r][2], v[r][3]),
-                                                        pack_bf16x2(v[r][4], v[r][5]), pack_bf16x2(v[r][6], v[r][7]));
-                        *reinterpret_cast<uint4*>(a_tile + tc::sw128_offset(4 * g4 + r, sg)) = packed;
-                    }
                 }
-                // B tile (transposed: BN rows j x 64 slots), sign folded in
-                for (int it = tid; it < (BN / 4) * 8; it += kThreads) {
-                    const int g4 = it % (BN / 4);
-                    const int sg = it / (BN / 4);
-                    const int j = tp0 + 4 * g4;
-                    float v[4][8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const int k = idx[sg * 8 + u];
-                        if (k >= 0 && j < prm.p) {
-                            const uint4 w = philox4x32_10(
-                                make_uint4(static_cast<uint32_t>(j >> 2), static_cast<uint32_t>(k), s_lo, lsw),
-                                prm.keyB);
-                            float z[4];
-                            normals4_f32(w, z);
-                            const float4* src = reinterpret_cast<const float4*>(
-                                PB + (static_cast<int64_t>(k) * prm.p_pad + j) * 2);
-                            const float4 p0 = __ldg(src);
-                            const float4 p1 = __ldg(src + 1);
-                            const float sg_t = sgn[sg * 8 + u];
-                            v[0][u] = sg_t * fmaf(p0.y, z[0], p0.x);
-                            v[1][u] = sg_t * fmaf(p0.w, z[1], p0.z);
-                            v[2][u] = sg_t * fmaf(p1.y, z[2], p1.x);
-                            v[3][u] = sg_t * fmaf(p1.w, z[3], p1.z);
-                        } else {
-                            v[0][u] = v[1][u] = v[2][u] = v[3][u] = 0.0f;
-                        }
-                    }
-#pragma unroll
-                    for (int r = 0; r < 4; ++r) {
-                        const uint4 packed = make_uint4(pack_bf16x2(v[r][0], v[r][1]), pack_bf16x2(v[r][2], v[r][3]),
-                                                        pack_bf16x2(v[r][4], v[r][5]), pack_bf16x2(v[r][6], v[r][7]));
-                        *reinterpret_cast<uint4*>(b_tile + tc::sw128_offset(4 * g4 + r, sg)) = packed;
-                    }
-                }
-                tc::fence_proxy_async_smem();
-                __syncthreads();
-                if (tid == 0) {
-                    tc::tc_fence_after_sync();
-                    const int kt = min(kKB, prm.c - kb * kKB);
-                    const int ksteps = (kt + 15) / 16;
-                    const uint32_t a_base = tc::smem_addr(a_tile);
-                    const uint32_t b_base = tc::smem_addr(b_tile);
-                    for (int kk = 0; kk < ksteps; ++kk) {
-                        const uint64_t bdesc = tc::sw128_kmajor_desc(b_base + 32 * kk);
-#pragma unroll
-                        for (int h = 0; h < MH; ++h) {
-                            const uint64_t adesc = tc::sw128_kmajor_desc(a_base + h * 128 * 128 + 32 * kk);
-                            tc::mma_bf16(tmem + h * BN, adesc, bdesc, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
-                        }
-                    }
-                    tc::mma_commit(tc::smem_addr(&bars[stage]));
-                    if (kb == nkb - 1) tc::mma_commit(bar_done);
-                }
+                tc::tc_fence_before_sync();
+                tc::named_barrier(kGenBarrier, kGenThreads);  // the accumulator may now be overwritten
             }
             if (aborted) break;
-            // sample epilogue: wait for the accumulator, then drain it
-            if (!tc::mbar_wait_bounded(bar_done, done_count & 1, tc::globaltimer() + ex.timeout_ns)) {
-                *abort_s = 1;
-                atomicExch(ex.err_flag, MLMC_ERR_TIMEOUT);
-            }
-            ++done_count;
-            __syncthreads();
-            if (*abort_s) {
-                aborted = true;
-                break;
-            }
-            tc::tc_fence_after_sync();
-            {
-                const int quarter = warp & 3;
-                const int hgrp = warp >> 2;
-                // MH == 2: warp group h drains M-half h (all BN columns); MH == 1: the two warp
-                // groups split the columns, or group 0 takes all of them when BN < 64.
-                const bool split = MH == 1 && BN >= 64;
-                const int row_local = (MH == 2 ? hgrp * 128 : 0) + quarter * 32 + lane;
-                const int col_tm = MH == 2 ? hgrp * BN : (split ? hgrp * (BN / 2) : 0);
-                const int col_d = MH == 2 ? 0 : col_tm;
-                const int ncols = MH == 2 ? BN : (split ? BN / 2 : (hgrp == 0 ? BN : 0));
-                const int gi = tm0 + row_local;
-                const bool first = (s == sa);
-                for (int cb = 0; cb < ncols; cb += 32) {
-                    float v[32];
-                    tc::tmem_ld_32x32b_x32(tmem + (static_cast<uint32_t>(quarter * 32) << 16) +
-                                               static_cast<uint32_t>(col_tm + cb),
-                                           v);
-                    float qs = 0.0f;
+            // work-item epilogue: sum of ||D||^2 of this tile over the chunk, fixed-order reduction
 #pragma unroll
-                    for (int e = 0; e < 32; ++e) {
-                        v[e] *= ex.scale;
-                        qs = fmaf(v[e], v[e], qs);
-                    }
-                    q += static_cast<double>(qs);
-                    const int gj0 = tp0 + col_d + cb;
-                    if (gi < prm.m && gj0 < prm.p) {
-                        float* dst = part + static_cast<int64_t>(gi) * prm.p + gj0;
-                        const int valid = min(32, prm.p - gj0);
-                        if (valid == 32 && (prm.p & 3) == 0) {
-                            float4* d4 = reinterpret_cast<float4*>(dst);
-#pragma unroll
-                            for (int e4 = 0; e4 < 8; ++e4) {
-                                float4 o = first ? make_float4(0.f, 0.f, 0.f, 0.f) : d4[e4];
-                                o.x += v[4 * e4];
-                                o.y += v[4 * e4 + 1];
-                                o.z += v[4 * e4 + 2];
-                                o.w += v[4 * e4 + 3];
-                                d4[e4] = o;
-                            }
-                        } else {
-#pragma unroll
-                            for (int e = 0; e < 32; ++e)
-                                if (e < valid) dst[e] = first ? v[e] : dst[e] + v[e];
-                        }
-                    }
-                }
+            for (int off = 16; off > 0; off >>= 1) q += __shfl_xor_sync(0xffffffffu, q, off);
+            if (lane == 0) red_s[warp] = q;
+            tc::named_barrier(kGenBarrier, kGenThreads);
+            if (tid == 0) {
+                double t = 0.0;
+                for (int w = 0; w < kGenWarps; ++w) t += red_s[w];
+                prm.partial_q[static_cast<int64_t>(cy) * tiles_n + tile] = t;
             }
-            tc::tc_fence_before_sync();
-            __syncthreads();  // the accumulator may be overwritten by the next sample
+            tc::named_barrier(kGenBarrier, kGenThreads);
         }
-        if (aborted) break;
-        // work-item epilogue: sum of ||D||^2 of this tile over the chunk, fixed-order reduction
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) q += __shfl_xor_sync(0xffffffffu, q, off);
-        if (lane == 0) red_s[warp] = q;
-        __syncthreads();
-        if (tid == 0) {
-            double t = 0.0;
-            for (int w = 0; w < kThreads / 32; ++w) t += red_s[w];
-            prm.partial_q[static_cast<int64_t>(cy) * tiles_n + tile] = t;
+        // after an abort make sure no MMA is still writing TMEM before it is freed
+        if (aborted && tid == 0) {
+            tc::mma_commit(bar_done);
+            tc::mbar_wait_bounded(bar_done, done_count & 1, tc::globaltimer() + ex.timeout_ns);
         }
-        __syncthreads();
-    }
-
-    // teardown: after an abort make sure no MMA is still writing TMEM before freeing it
-    if (aborted && tid == 0) {
-        tc::mma_commit(bar_done);
-        tc::mbar_wait_bounded(bar_done, done_count & 1, tc::globaltimer() + ex.timeout_ns);
     }
     tc::tc_fence_before_sync();
     __syncthreads();

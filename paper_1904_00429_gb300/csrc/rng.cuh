@@ -115,6 +115,36 @@ __device__ __forceinline__ void normals4_f32(uint4 w, float z[4])
     box_muller_f32(w.z, w.w, z[2], z[3]);
 }
 
+// ---- FP32 normals from the special-function units (reduced-precision paths) -----------
+//
+// For entries that are rounded to bfloat16 or FP8 right after generation, Box-Muller runs on
+// the MUFU approximations: -ln u = ln 2 * lg2(1 + v/u) with v = 1 - u (absolute error about
+// 2^-23, so the radius keeps full relative accuracy except for rho < 2^-8, probability 2^-17,
+// where its absolute error stays below 2^-11), and the angle 2 pi u = theta + pi with theta in
+// [-pi, pi) so that sin.approx / cos.approx run inside their accurate range
+// (absolute error about 2^-21); cos(theta + pi) = -cos(theta), sin(theta + pi) = -sin(theta).
+
+__device__ __forceinline__ void box_muller_mufu(uint32_t wr, uint32_t wa, float& zc, float& zs)
+{
+    const float u = fmaf(__uint2float_rn(wr), 0x1p-32f, 0x1p-33f);
+    const float v = fmaf(__uint2float_rn(~wr), 0x1p-32f, 0x1p-33f);
+    float l2, radius, s, c;
+    asm("lg2.approx.f32 %0, %1;" : "=f"(l2) : "f"(1.0f + __fdividef(v, u)));
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(radius) : "f"(1.3862943611198906f * l2));
+    const float theta = fmaf(__int2float_rn(static_cast<int>(wa ^ 0x80000000u)), 6.283185307179586f * 0x1p-32f,
+                             3.141592653589793f * 0x1p-32f);
+    asm("sin.approx.f32 %0, %1;" : "=f"(s) : "f"(theta));
+    asm("cos.approx.f32 %0, %1;" : "=f"(c) : "f"(theta));
+    zc = -radius * c;
+    zs = -radius * s;
+}
+
+__device__ __forceinline__ void normals4_mufu(uint4 w, float z[4])
+{
+    box_muller_mufu(w.x, w.y, z[0], z[1]);
+    box_muller_mufu(w.z, w.w, z[2], z[3]);
+}
+
 template <typename T>
 struct Normals;
 
