@@ -153,7 +153,7 @@ MLMC_API mlmc_status mlmc_plan_destroy(mlmc_plan_t* plan);
  * per-entry sum of D and the FP64 sum of ||D||_F^2.  Samples are pure
  * functions of their ids, so disjoint ranges may be evaluated in any order
  * and split across calls; the statistics are bit-identical for any split at
- * multiples of 8 sample ids and in any case equal up to rounding.
+ * multiples of 64 sample ids and in any case equal up to rounding.
  * count = 0 is a no-op. */
 MLMC_API mlmc_status mlmc_level_stats(mlmc_plan_t* plan, int32_t prob, int32_t level, uint64_t sample_begin,
                              uint64_t count);

@@ -247,14 +247,16 @@ mlmc_status run_level(mlmc_plan_t* plan, ProblemState& ps, int level, uint64_t s
     prm.partial_sum = plan->partial_sum;
     prm.partial_q = plan->partial_q;
     const uint64_t s_end = s0 + count;
-    const uint64_t chunk_first = s0 / kChunk;
-    const uint64_t chunk_last = (s_end - 1) / kChunk;
+    const uint64_t ch = uint64_t(chunk_samples(c));
+    prm.chunk = int(ch);
+    const uint64_t chunk_first = s0 / ch;
+    const uint64_t chunk_last = (s_end - 1) / ch;
     for (uint64_t cb = chunk_first; cb <= chunk_last; cb += uint64_t(ps.max_chunks)) {
         const int nb = int(std::min<uint64_t>(uint64_t(ps.max_chunks), chunk_last - cb + 1));
         prm.chunk0 = cb;
         prm.nchunks = nb;
-        prm.s_begin = std::max<uint64_t>(s0, cb * kChunk);
-        prm.s_end = std::min<uint64_t>(s_end, (cb + nb) * kChunk);
+        prm.s_begin = std::max<uint64_t>(s0, cb * ch);
+        prm.s_end = std::min<uint64_t>(s_end, (cb + nb) * ch);
         cudaError_t err;
         if (o.precision == MLMC_BF16) {
             TcLaunch tl{plan->err_flag, plan->timeout_ns, static_cast<float>(double(ps.n) / double(c)), plan->num_sms};

@@ -8,12 +8,20 @@
 
 namespace mlmc {
 
-// Samples are grouped into fixed chunks of kChunk consecutive sample ids
-// (chunk c holds ids c*kChunk .. c*kChunk+kChunk-1).  Partial statistics are
-// produced per chunk and folded into a level in chunk order, so the result
-// does not depend on grid shapes or on how sample ranges are split at chunk
-// boundaries.
+// Samples are grouped into fixed chunks of consecutive sample ids (chunk c of a
+// level holds ids c*chunk .. c*chunk+chunk-1).  Partial statistics are produced
+// per chunk and folded into a level in chunk order, so the result does not
+// depend on grid shapes or on how sample ranges are split at chunk boundaries.
+// The plan's kernels use chunk_samples(c_l) (8 to 64, a power of two: cheap
+// samples get longer chunks); the no-allocation entry point uses kChunk.
 constexpr int kChunk = 8;
+constexpr int kMaxChunkSamples = 64;
+inline int chunk_samples(int64_t c_l)
+{
+    int ch = 8;
+    while (ch < kMaxChunkSamples && int64_t(ch) * 2 * c_l <= 2048) ch *= 2;
+    return ch;
+}
 
 // Arguments of one level-kernel launch over samples [s_begin, s_end).
 struct LevelParams {
@@ -29,6 +37,7 @@ struct LevelParams {
     uint2 keyA, keyB, keyI;
     uint64_t s_begin, s_end;
     uint64_t chunk0;      // absolute chunk id handled by blockIdx.y == 0
+    int chunk;            // samples per chunk
     int nchunks;
     int tiles_m, tiles_p;
     void* partial_sum;    // [nchunks][m][p] of T

@@ -1,7 +1,7 @@
 // level_cuda_core.cu -- fused level kernel on the CUDA cores (FP64 and FP32).
 //
 // One CTA owns one TM x TP tile of the m x p output and one chunk of up to
-// kChunk samples of one level.  For every sample s it evaluates
+// prm.chunk samples of one level.  For every sample s it evaluates
 //     D_s = sum_t w_t A[:, r_t] B[r_t, :],   w_t = n/c_l - [t coarse] n/c_{l-1},
 // which is P_l - P_{l-1} of Alg. 1 written as one weighted sum: the coarse
 // estimate reuses the draws r_{jR} (0-based slots t = jR - 1) of the fine one,
@@ -77,8 +77,8 @@ level_cuda_core_kernel(const LevelParams prm)
     const int ty = tid / TXN;
 
     const uint64_t chunk = prm.chunk0 + blockIdx.y;
-    const uint64_t sa = max(prm.s_begin, chunk * kChunk);
-    const uint64_t sb = min(prm.s_end, (chunk + 1) * kChunk);
+    const uint64_t sa = max(prm.s_begin, chunk * static_cast<uint64_t>(prm.chunk));
+    const uint64_t sb = min(prm.s_end, (chunk + 1) * static_cast<uint64_t>(prm.chunk));
 
     const T* PA = static_cast<const T*>(prm.PA);
     const T* PB = static_cast<const T*>(prm.PB);

@@ -167,8 +167,8 @@ __global__ void __launch_bounds__(kThreads, 1) level_tc_bf16_kernel(const LevelP
             const uint32_t a_bytes = static_cast<uint32_t>(min(C::kRows, prm.m_pad - tm0)) * 8u;
             const uint32_t b_bytes = static_cast<uint32_t>(min(BN, prm.p_pad - tp0)) * 8u;
             const uint64_t chunk = prm.chunk0 + static_cast<uint64_t>(cy);
-            const uint64_t sa = max(prm.s_begin, chunk * kChunk);
-            const uint64_t sb = min(prm.s_end, (chunk + 1) * kChunk);
+            const uint64_t sa = max(prm.s_begin, chunk * static_cast<uint64_t>(prm.chunk));
+            const uint64_t sb = min(prm.s_end, (chunk + 1) * static_cast<uint64_t>(prm.chunk));
             for (uint64_t s = sa; s < sb && !aborted; ++s) {
                 const uint32_t lsw = level_sample_word(prm.l, s);
                 const uint32_t s_lo = static_cast<uint32_t>(s);
@@ -215,7 +215,8 @@ __global__ void __launch_bounds__(kThreads, 1) level_tc_bf16_kernel(const LevelP
         constexpr int kItemsA = (C::kRows / 4) * 2;
         constexpr int kItemsB = (BN / 4) * 2;
         uint32_t g = 0;  // sub-blocks consumed
-        uint32_t slice_uses[kSlices] = {0, 0, 0, 0};
+        uint32_t slice_par = 0;   // bit kk: parity of the MMAs issued on slice kk so far
+        uint32_t slice_seen = 0;  // bit kk: slice kk has been used
         uint32_t done_count = 0;
         bool aborted = false;
         const bool coarse_sign = prm.l > 0;
@@ -225,8 +226,8 @@ __global__ void __launch_bounds__(kThreads, 1) level_tc_bf16_kernel(const LevelP
             const int tm0 = (tile / prm.tiles_p) * C::kRows;
             const int tp0 = (tile % prm.tiles_p) * BN;
             const uint64_t chunk = prm.chunk0 + static_cast<uint64_t>(cy);
-            const uint64_t sa = max(prm.s_begin, chunk * kChunk);
-            const uint64_t sb = min(prm.s_end, (chunk + 1) * kChunk);
+            const uint64_t sa = max(prm.s_begin, chunk * static_cast<uint64_t>(prm.chunk));
+            const uint64_t sb = min(prm.s_end, (chunk + 1) * static_cast<uint64_t>(prm.chunk));
             float* part = static_cast<float*>(prm.partial_sum) + static_cast<int64_t>(cy) * prm.m * prm.p;
             double q = 0.0;
             for (uint64_t s = sa; s < sb && !aborted; ++s) {
@@ -236,8 +237,8 @@ __global__ void __launch_bounds__(kThreads, 1) level_tc_bf16_kernel(const LevelP
                     const int b = static_cast<int>(g & 1);
                     const int kk = j % kSlices;
                     bool ok = tc::mbar_wait_bounded(bar_full(b), (g >> 1) & 1, tc::globaltimer() + ex.timeout_ns);
-                    if (ok && slice_uses[kk] > 0)
-                        ok = tc::mbar_wait_bounded(bar_slice(kk), (slice_uses[kk] - 1) & 1,
+                    if (ok && ((slice_seen >> kk) & 1u))
+                        ok = tc::mbar_wait_bounded(bar_slice(kk), ((slice_par >> kk) & 1u) ^ 1u,
                                                    tc::globaltimer() + ex.timeout_ns);
                     if (!ok) {
                         *abort_s = 1;
@@ -288,7 +289,8 @@ __global__ void __launch_bounds__(kThreads, 1) level_tc_bf16_kernel(const LevelP
                         tc::mma_commit(bar_slice(kk));
                         if (j == nsub - 1) tc::mma_commit(bar_done);
                     }
-                    ++slice_uses[kk];
+                    slice_par ^= 1u << kk;
+                    slice_seen |= 1u << kk;
                 }
                 if (aborted) break;
                 // sample epilogue: wait for the accumulator, then drain it
@@ -315,40 +317,49 @@ __global__ void __launch_bounds__(kThreads, 1) level_tc_bf16_kernel(const LevelP
                     const int ncols = MH == 2 ? BN : (split ? BN / 2 : (hgrp == 0 ? BN : 0));
                     const int gi = tm0 + row_local;
                     const bool first = (s == sa);
-                    for (int cb = 0; cb < ncols; cb += 32) {
-                        float v[32];
-                        tc::tmem_ld_32x32b_x32(tmem + (static_cast<uint32_t>(quarter * 32) << 16) +
-                                                   static_cast<uint32_t>(col_tm + cb),
-                                               v);
+                    // two 32-column loads in flight per wait
+                    for (int cb = 0; cb < ncols; cb += 64) {
+                        float v[64];
+                        const uint32_t ta = tmem + (static_cast<uint32_t>(quarter * 32) << 16) +
+                                            static_cast<uint32_t>(col_tm + cb);
+                        tc::tmem_ld_32x32b_x32_nowait(ta, v);
+                        if (cb + 32 < ncols) tc::tmem_ld_32x32b_x32_nowait(ta + 32, v + 32);
+                        tc::tmem_ld_wait();
+                        const int nv = min(64, ncols - cb);
                         float qs = 0.0f;
 #pragma unroll
-                        for (int e = 0; e < 32; ++e) {
-                            v[e] *= ex.scale;
-                            qs = fmaf(v[e], v[e], qs);
+                        for (int e = 0; e < 64; ++e) {
+                            if (e < nv) {
+                                v[e] *= ex.scale;
+                                qs = fmaf(v[e], v[e], qs);
+                            }
                         }
                         q += static_cast<double>(qs);
-                        const int gj0 = tp0 + col_d + cb;
-                        if (gi < prm.m && gj0 < prm.p) {
+#pragma unroll
+                        for (int half = 0; half < 2; ++half) {
+                            const int gj0 = tp0 + col_d + cb + 32 * half;
+                            if (32 * half >= nv || gi >= prm.m || gj0 >= prm.p) continue;
                             float* dst = part + static_cast<int64_t>(gi) * prm.p + gj0;
+                            const float* w = v + 32 * half;
                             const int valid = min(32, prm.p - gj0);
                             if (valid == 32 && (prm.p & 3) == 0) {
 #pragma unroll
                                 for (int e4 = 0; e4 < 8; ++e4) {
                                     if (first)
                                         reinterpret_cast<float4*>(dst)[e4] =
-                                            make_float4(v[4 * e4], v[4 * e4 + 1], v[4 * e4 + 2], v[4 * e4 + 3]);
+                                            make_float4(w[4 * e4], w[4 * e4 + 1], w[4 * e4 + 2], w[4 * e4 + 3]);
                                     else
-                                        tc::red_add_v4(dst + 4 * e4, v[4 * e4], v[4 * e4 + 1], v[4 * e4 + 2],
-                                                       v[4 * e4 + 3]);
+                                        tc::red_add_v4(dst + 4 * e4, w[4 * e4], w[4 * e4 + 1], w[4 * e4 + 2],
+                                                       w[4 * e4 + 3]);
                                 }
                             } else {
 #pragma unroll
                                 for (int e = 0; e < 32; ++e)
                                     if (e < valid) {
                                         if (first)
-                                            dst[e] = v[e];
+                                            dst[e] = w[e];
                                         else
-                                            atomicAdd(dst + e, v[e]);
+                                            atomicAdd(dst + e, w[e]);
                                     }
                             }
                         }

@@ -24,7 +24,16 @@ __global__ void merge_sum_kernel(const T* __restrict__ partial, int nchunks, int
     const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (e >= mp) return;
     double acc = level_sum[e];
-    for (int c = 0; c < nchunks; ++c) acc += static_cast<double>(partial[static_cast<int64_t>(c) * mp + e]);
+    int c = 0;
+    // eight independent loads in flight, then the adds in chunk order
+    for (; c + 8 <= nchunks; c += 8) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = static_cast<double>(partial[static_cast<int64_t>(c + u) * mp + e]);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc += v[u];
+    }
+    for (; c < nchunks; ++c) acc += static_cast<double>(partial[static_cast<int64_t>(c) * mp + e]);
     level_sum[e] = acc;
 }
 

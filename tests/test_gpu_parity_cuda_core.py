@@ -179,21 +179,21 @@ def test_n_equal_one_differences_vanish():
 def test_split_calls_and_checkpoint_resume_are_bit_identical():
     pp = make_params(64, 1024, 64, seed_A=3, seed_B=4)
     with _plan(pp, "fp64", 16, 2) as one, _plan(pp, "fp64", 16, 2) as two, _plan(pp, "fp64", 16, 2) as three:
-        one.level_stats(0, 2, 0, 64)
-        two.level_stats(0, 2, 0, 24)
-        two.level_stats(0, 2, 24, 40)
+        one.level_stats(0, 2, 0, 192)
+        two.level_stats(0, 2, 0, 64)
+        two.level_stats(0, 2, 64, 128)
         N, s, q = two.get_level_state(0, 2)
         three.set_level_state(0, 2, N, s, q)   # resume in another plan from the checkpoint
         three.reset(0, 1)
         N1, s1, q1 = one.get_level_state(0, 2)
         N2, s2, q2 = two.get_level_state(0, 2)
-        assert N1 == N2 == 64 and q1 == q2 and torch.equal(s1, s2)
+        assert N1 == N2 == 192 and q1 == q2 and torch.equal(s1, s2)
         N3, s3, q3 = three.get_level_state(0, 2)
-        assert N3 == 64 and q3 == q1 and torch.equal(s3, s1)
+        assert N3 == 192 and q3 == q1 and torch.equal(s3, s1)
         # a split that is not at a multiple of 8 agrees up to rounding
         four = _plan(pp, "fp64", 16, 2)
         four.level_stats(0, 2, 0, 13)
-        four.level_stats(0, 2, 13, 51)
+        four.level_stats(0, 2, 13, 179)
         _, s4, q4 = four.get_level_state(0, 2)
         torch.testing.assert_close(s4, s1, rtol=1e-13, atol=1e-10)
         assert abs(q4 - q1) <= 1e-13 * q1

@@ -109,12 +109,12 @@ def test_bf16_level_means_against_fp64_oracle_precision_workload():
 def test_bf16_split_calls_are_bit_identical():
     pp = make_params(96, 2048, 80, seed_A=8, seed_B=9, dtype=np.float32)
     with _plan(pp, 32, 3) as one, _plan(pp, 32, 3) as two:
-        one.level_stats(0, 2, 0, 48)
-        two.level_stats(0, 2, 0, 16)
-        two.level_stats(0, 2, 16, 32)
+        one.level_stats(0, 2, 0, 192)
+        two.level_stats(0, 2, 0, 64)
+        two.level_stats(0, 2, 64, 128)
         N1, s1, q1 = one.get_level_state(0, 2)
         N2, s2, q2 = two.get_level_state(0, 2)
-        assert N1 == N2 == 48 and q1 == q2 and torch.equal(s1, s2)
+        assert N1 == N2 == 192 and q1 == q2 and torch.equal(s1, s2)
 
 
 def test_bf16_estimate_runs_algorithm_2():
