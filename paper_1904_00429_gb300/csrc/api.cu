@@ -57,8 +57,8 @@ struct ProblemState {
     mlmc_problem desc;
     int L = 0;
     int64_t m = 0, n = 0, p = 0, m_pad = 0, p_pad = 0;
-    void* PA = nullptr;
-    void* PB = nullptr;
+    void* PAB = nullptr;   // row k: [(M_ik, S_ik) for i < m_pad | (M'_kj, S'_kj) for j < p_pad]
+    int64_t ld = 0;        // elements per row of PAB
     double* sum = nullptr;    // (L+1) x m x p
     double* sumsq = nullptr;  // (L+1)
     LevelCounts N{};
@@ -183,8 +183,7 @@ mlmc_status validate(const mlmc_problem* problems, int32_t nprob, const mlmc_opt
 void free_plan(mlmc_plan_t* plan)
 {
     for (auto& ps : plan->probs) {
-        cudaFree(ps.PA);
-        cudaFree(ps.PB);
+        cudaFree(ps.PAB);
         cudaFree(ps.sum);
         cudaFree(ps.sumsq);
     }
@@ -227,8 +226,10 @@ mlmc_status run_level(mlmc_plan_t* plan, ProblemState& ps, int level, uint64_t s
     const mlmc_options& o = plan->opt;
     const int64_t c = level_c(o, level);
     LevelParams prm{};
-    prm.PA = ps.PA;
-    prm.PB = ps.PB;
+    prm.PA = ps.PAB;
+    prm.PB = static_cast<const unsigned char*>(ps.PAB) + size_t(2 * ps.m_pad) * plan->elem;
+    prm.ldPA = ps.ld;
+    prm.ldPB = ps.ld;
     prm.n = ps.n;
     prm.m = int(ps.m);
     prm.p = int(ps.p);
@@ -242,6 +243,8 @@ mlmc_status run_level(mlmc_plan_t* plan, ProblemState& ps, int level, uint64_t s
     prm.keyA = key(ps.desc.seed_A, ps.desc.problem_id);
     prm.keyB = key(ps.desc.seed_B, ps.desc.problem_id);
     prm.keyI = key(ps.desc.seed_idx, ps.desc.problem_id);
+    prm.rkA = philox_round_keys(prm.keyA);
+    prm.rkB = philox_round_keys(prm.keyB);
     prm.tiles_m = ps.tiles_m;
     prm.tiles_p = ps.tiles_p;
     prm.partial_sum = plan->partial_sum;
@@ -345,17 +348,20 @@ mlmc_status mlmc_plan(const mlmc_problem* problems, int32_t nprob, const mlmc_op
         max_partial = std::max(max_partial, per_chunk * size_t(ps.max_chunks));
         max_q = std::max(max_q, size_t(ps.max_chunks) * size_t(ps.tiles_m * ps.tiles_p));
         max_mp = std::max(max_mp, mp);
-        if (cudaMalloc(&ps.PA, size_t(ps.n) * size_t(ps.m_pad) * 2 * plan->elem) != cudaSuccess) return oom("PA");
-        if (cudaMalloc(&ps.PB, size_t(ps.n) * size_t(ps.p_pad) * 2 * plan->elem) != cudaSuccess) return oom("PB");
+        // one row per inner index k holds both gathered vectors, so a sampled index is one
+        // contiguous read of 2 (m_pad + p_pad) elements
+        ps.ld = 2 * (ps.m_pad + ps.p_pad);
+        if (cudaMalloc(&ps.PAB, size_t(ps.n) * size_t(ps.ld) * plan->elem) != cudaSuccess) return oom("parameters");
         if (cudaMalloc(&ps.sum, sizeof(double) * mp * size_t(ps.L + 1)) != cudaSuccess) return oom("level sums");
         if (cudaMalloc(&ps.sumsq, sizeof(double) * size_t(ps.L + 1)) != cudaSuccess) return oom("level sumsq");
         cudaMemsetAsync(ps.sum, 0, sizeof(double) * mp * size_t(ps.L + 1), plan->stream);
         cudaMemsetAsync(ps.sumsq, 0, sizeof(double) * size_t(ps.L + 1), plan->stream);
         cudaError_t err = launch_layout_A(ps.desc.M_dev, ps.desc.S_dev, ps.desc.dtype, ps.desc.ldA, ps.m, ps.n,
-                                          ps.m_pad, ps.PA, plan->f64, plan->stream);
+                                          ps.m_pad, ps.PAB, ps.ld, plan->f64, plan->stream);
         if (err == cudaSuccess)
             err = launch_layout_B(ps.desc.Mp_dev, ps.desc.Sp_dev, ps.desc.dtype, ps.desc.ldB, ps.n, ps.p, ps.p_pad,
-                                  ps.PB, plan->f64, plan->stream);
+                                  static_cast<unsigned char*>(ps.PAB) + size_t(2 * ps.m_pad) * plan->elem, ps.ld,
+                                  plan->f64, plan->stream);
         if (err != cudaSuccess) {
             free_plan(plan);
             delete plan;

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "mlmc.h"
+#include "rng.cuh"
 
 namespace mlmc {
 
@@ -25,8 +26,9 @@ inline int chunk_samples(int64_t c_l)
 
 // Arguments of one level-kernel launch over samples [s_begin, s_end).
 struct LevelParams {
-    const void* PA;       // [n][m_pad][2] of T: (M_ik, S_ik) pairs, gathered column k contiguous
-    const void* PB;       // [n][p_pad][2] of T: (M'_kj, S'_kj) pairs, gathered row k contiguous
+    const void* PA;       // row k: (M_ik, S_ik) pairs, i < m_pad (gathered column k of [M|S])
+    const void* PB;       // row k: (M'_kj, S'_kj) pairs, j < p_pad (gathered row k of [M'|S'])
+    int64_t ldPA, ldPB;   // elements between consecutive rows k of PA / PB
     int64_t n;
     int m, p, m_pad, p_pad;
     int l;                // level
@@ -35,6 +37,7 @@ struct LevelParams {
     double w_fine;        // n / c_l
     double w_coarse;      // n / c_l - n / c_{l-1}
     uint2 keyA, keyB, keyI;
+    PhiloxRoundKeys rkA, rkB;  // round keys of keyA and keyB
     uint64_t s_begin, s_end;
     uint64_t chunk0;      // absolute chunk id handled by blockIdx.y == 0
     int chunk;            // samples per chunk
@@ -87,11 +90,12 @@ cudaError_t launch_finalize(const double* sum, const double* sumsq, LevelCounts 
 cudaError_t launch_telescoping(const double* sum, LevelCounts counts, int levels, int64_t mp, double* yhat,
                                cudaStream_t st);
 
-// Copy row-major parameters into the sample-major pair layout.
+// Copy row-major parameters into the sample-major pair layout: element (k, i) of [M|S] goes to
+// PA[k * ld_dst + 2 i + {0, 1}], element (k, j) of [M'|S'] to PB[k * ld_dst + 2 j + {0, 1}].
 cudaError_t launch_layout_A(const void* M, const void* S, int src_dtype, int64_t ldA, int64_t m,
-                            int64_t n, int64_t m_pad, void* PA, bool dst_f64, cudaStream_t st);
+                            int64_t n, int64_t m_pad, void* PA, int64_t ld_dst, bool dst_f64, cudaStream_t st);
 cudaError_t launch_layout_B(const void* Mp, const void* Sp, int src_dtype, int64_t ldB, int64_t n,
-                            int64_t p, int64_t p_pad, void* PB, bool dst_f64, cudaStream_t st);
+                            int64_t p, int64_t p_pad, void* PB, int64_t ld_dst, bool dst_f64, cudaStream_t st);
 
 // Set the thread-local message returned by mlmc_last_error().
 mlmc_status report_error(mlmc_status st, const char* msg);

@@ -136,7 +136,7 @@ level_cuda_core_kernel(const LevelParams prm)
                                                   prm.keyA);
                     T z[4];
                     Normals<T>::four(w, z);
-                    const Pair4<T> ms = Pair4<T>::load(PA + (static_cast<int64_t>(k) * prm.m_pad + i) * 2);
+                    const Pair4<T> ms = Pair4<T>::load(PA + static_cast<int64_t>(k) * prm.ldPA + 2 * i);
 #pragma unroll
                     for (int r = 0; r < 4; ++r) a[r] = fma(ms.v[2 * r + 1], z[r], ms.v[2 * r]);
                 }
@@ -156,7 +156,7 @@ level_cuda_core_kernel(const LevelParams prm)
                                                   prm.keyB);
                     T z[4];
                     Normals<T>::four(w, z);
-                    const Pair4<T> ms = Pair4<T>::load(PB + (static_cast<int64_t>(k) * prm.p_pad + j) * 2);
+                    const Pair4<T> ms = Pair4<T>::load(PB + static_cast<int64_t>(k) * prm.ldPB + 2 * j);
                     const T wt = w_s[tt];
 #pragma unroll
                     for (int r = 0; r < 4; ++r) b[r] = wt * fma(ms.v[2 * r + 1], z[r], ms.v[2 * r]);

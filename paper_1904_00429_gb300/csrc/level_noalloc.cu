@@ -315,6 +315,8 @@ extern "C" mlmc_status mlmc_level_stats_noalloc(const mlmc_problem* problem, con
     prm.tiles_m = tiles_m;
     prm.tiles_p = tiles_p;
     prm.chunk = kChunk;
+    prm.ldPA = pr.ldA;
+    prm.ldPB = pr.ldB;
     prm.partial_sum = partial_sum;
     prm.partial_q = partial_q;
     const RowMajorParams src{pr.M_dev, pr.S_dev, pr.ldA, pr.Mp_dev, pr.Sp_dev, pr.ldB};

@@ -46,9 +46,8 @@ struct TcCfg {
     static constexpr int kABytes = kRows * 128;            // kRows x 64 bf16, 128-byte swizzled
     static constexpr int kBBytes = BN * 128;               // BN x 64 bf16 (B transposed, K-major)
     static constexpr int kTileBytes = kABytes + kBBytes;
-    static constexpr int kStageABytes = kSub * kRows * 8;  // FP32 (M, S) pairs of the sub-block
-    static constexpr int kStageBBytes = kSub * BN * 8;     // FP32 (M', S') pairs
-    static constexpr int kStageBytes = kStageABytes + kStageBBytes;
+    static constexpr int kSlotBytes = (kRows + BN) * 8;     // staged FP32 (M, S) pairs of A, then of B
+    static constexpr int kStageBytes = kSub * kSlotBytes;
     static constexpr int kTileCols = MH * BN;
     static constexpr int kTmemCols = kTileCols <= 32 ? 32 : kTileCols <= 64 ? 64 : kTileCols <= 128 ? 128
                                      : kTileCols <= 256 ? 256 : 512;
@@ -78,28 +77,33 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
 // pairs and write them as bf16 into the swizzled tile: tile rows row0 .. row0+3, 16-byte chunk
 // `chunk`.  Staged pairs of slot u start at stage + u * stride (8 floats: (M,S) x 4).
 __device__ __forceinline__ void gen_block(const int* idx, int slot0, bool valid_rows, uint32_t rowgrp,
-                                          uint32_t s_lo, uint32_t lsw, uint2 key, const unsigned char* stage,
+                                          uint32_t s_lo, uint32_t lsw, const PhiloxRoundKeys& rk,
+                                          const unsigned char* stage,
                                           int stride, bool odd_negative, unsigned char* tile, int row0, int chunk)
 {
+    // Branch-free: the eight Philox blocks are independent dependency chains, computed for every
+    // slot (a missing slot uses k = 0) and zeroed afterwards, so they can interleave.
+    int ks[8];
+    uint4 w[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        ks[u] = idx[slot0 + u];
+        w[u] = philox4x32_10_rk(make_uint4(rowgrp, static_cast<uint32_t>(max(ks[u], 0)), s_lo, lsw), rk);
+    }
     float v[4][8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-        const int k = idx[slot0 + u];
-        if (k >= 0 && valid_rows) {
-            const uint4 w = philox4x32_10(make_uint4(rowgrp, static_cast<uint32_t>(k), s_lo, lsw), key);
-            float z[4];
-            normals4_mufu(w, z);
-            const float4* src = reinterpret_cast<const float4*>(stage + u * stride);
-            const float4 p0 = src[0];
-            const float4 p1 = src[1];
-            const float sg = (odd_negative && (u & 1)) ? -1.0f : 1.0f;
-            v[0][u] = sg * fmaf(p0.y, z[0], p0.x);
-            v[1][u] = sg * fmaf(p0.w, z[1], p0.z);
-            v[2][u] = sg * fmaf(p1.y, z[2], p1.x);
-            v[3][u] = sg * fmaf(p1.w, z[3], p1.z);
-        } else {
-            v[0][u] = v[1][u] = v[2][u] = v[3][u] = 0.0f;
-        }
+        float z[4];
+        normals4_mufu(w[u], z);
+        const float4* src = reinterpret_cast<const float4*>(stage + u * stride);
+        const float4 p0 = src[0];
+        const float4 p1 = src[1];
+        const bool use = ks[u] >= 0 && valid_rows;
+        const float sg = (odd_negative && (u & 1)) ? -1.0f : 1.0f;
+        v[0][u] = use ? sg * fmaf(p0.y, z[0], p0.x) : 0.0f;
+        v[1][u] = use ? sg * fmaf(p0.w, z[1], p0.z) : 0.0f;
+        v[2][u] = use ? sg * fmaf(p1.y, z[2], p1.x) : 0.0f;
+        v[3][u] = use ? sg * fmaf(p1.w, z[3], p1.z) : 0.0f;
     }
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
@@ -166,6 +170,8 @@ __global__ void __launch_bounds__(kThreads, 1) level_tc_bf16_kernel(const LevelP
             const int tp0 = (tile % prm.tiles_p) * BN;
             const uint32_t a_bytes = static_cast<uint32_t>(min(C::kRows, prm.m_pad - tm0)) * 8u;
             const uint32_t b_bytes = static_cast<uint32_t>(min(BN, prm.p_pad - tp0)) * 8u;
+            // PB rows start right after PA's in the plan's interleaved layout
+            const bool whole_row = tiles_n == 1 && PB == PA + 2 * prm.m_pad && prm.ldPA == prm.ldPB;
             const uint64_t chunk = prm.chunk0 + static_cast<uint64_t>(cy);
             const uint64_t sa = max(prm.s_begin, chunk * static_cast<uint64_t>(prm.chunk));
             const uint64_t sb = min(prm.s_end, (chunk + 1) * static_cast<uint64_t>(prm.chunk));
@@ -199,11 +205,16 @@ __global__ void __launch_bounds__(kThreads, 1) level_tc_bf16_kernel(const LevelP
                     __syncwarp();
                     if (lane < nvalid) {
                         const int k = idx[lane];
-                        unsigned char* st = staging + b * C::kStageBytes;
-                        tc::bulk_copy_g2s(tc::smem_addr(st + lane * (C::kRows * 8)),
-                                          PA + (static_cast<int64_t>(k) * prm.m_pad + tm0) * 2, a_bytes, bar_full(b));
-                        tc::bulk_copy_g2s(tc::smem_addr(st + C::kStageABytes + lane * (BN * 8)),
-                                          PB + (static_cast<int64_t>(k) * prm.p_pad + tp0) * 2, b_bytes, bar_full(b));
+                        unsigned char* dst = staging + b * C::kStageBytes + lane * C::kSlotBytes;
+                        const float* row = PA + static_cast<int64_t>(k) * prm.ldPA;
+                        if (whole_row) {
+                            // one tile covers every row and column: A and B pairs are one contiguous run
+                            tc::bulk_copy_g2s(tc::smem_addr(dst), row, a_bytes + b_bytes, bar_full(b));
+                        } else {
+                            tc::bulk_copy_g2s(tc::smem_addr(dst), row + 2 * tm0, a_bytes, bar_full(b));
+                            tc::bulk_copy_g2s(tc::smem_addr(dst + a_bytes),
+                                              PB + static_cast<int64_t>(k) * prm.ldPB + 2 * tp0, b_bytes, bar_full(b));
+                        }
                     }
                     __syncwarp();
                 }
@@ -229,6 +240,7 @@ __global__ void __launch_bounds__(kThreads, 1) level_tc_bf16_kernel(const LevelP
             const uint64_t sa = max(prm.s_begin, chunk * static_cast<uint64_t>(prm.chunk));
             const uint64_t sb = min(prm.s_end, (chunk + 1) * static_cast<uint64_t>(prm.chunk));
             float* part = static_cast<float*>(prm.partial_sum) + static_cast<int64_t>(cy) * prm.m * prm.p;
+            const int a_bytes = min(C::kRows, prm.m_pad - tm0) * 8;  // B pairs follow A's in a staged slot
             double q = 0.0;
             for (uint64_t s = sa; s < sb && !aborted; ++s) {
                 const uint32_t lsw = level_sample_word(prm.l, s);
@@ -253,8 +265,8 @@ __global__ void __launch_bounds__(kThreads, 1) level_tc_bf16_kernel(const LevelP
                                 const int g4 = it % (C::kRows / 4);
                                 const int sg = it / (C::kRows / 4);
                                 const int i = tm0 + 4 * g4;
-                                gen_block(idx, sg * 8, i < prm.m, static_cast<uint32_t>(i >> 2), s_lo, lsw, prm.keyA,
-                                          st + (sg * 8) * (C::kRows * 8) + g4 * 32, C::kRows * 8, false, a_tile,
+                                gen_block(idx, sg * 8, i < prm.m, static_cast<uint32_t>(i >> 2), s_lo, lsw, prm.rkA,
+                                          st + (sg * 8) * C::kSlotBytes + g4 * 32, C::kSlotBytes, false, a_tile,
                                           4 * g4, 2 * kk + sg);
                             } else {
                                 // 4 columns of B (rows of the transposed tile) x 8 slots, sign folded in
@@ -263,8 +275,8 @@ __global__ void __launch_bounds__(kThreads, 1) level_tc_bf16_kernel(const LevelP
                                 const int sg = it2 / (BN / 4);
                                 const int jc = tp0 + 4 * g4;
                                 gen_block(idx, sg * 8, jc < prm.p, static_cast<uint32_t>(jc >> 2), s_lo, lsw,
-                                          prm.keyB, st + C::kStageABytes + (sg * 8) * (BN * 8) + g4 * 32, BN * 8,
-                                          coarse_sign, b_tile, 4 * g4, 2 * kk + sg);
+                                          prm.rkB, st + (sg * 8) * C::kSlotBytes + a_bytes + g4 * 32,
+                                          C::kSlotBytes, coarse_sign, b_tile, 4 * g4, 2 * kk + sg);
                             }
                         }
                     }

@@ -47,6 +47,34 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
     return c;
 }
 
+// Round keys of Philox4x32-10: k_r = key + r (W0, W1), r = 0..9 (the schedule above, precomputed
+// once per launch so that the rounds read them as kernel-parameter operands).
+struct PhiloxRoundKeys {
+    uint2 k[10];
+};
+
+__host__ __device__ inline PhiloxRoundKeys philox_round_keys(uint2 key)
+{
+    PhiloxRoundKeys rk;
+    for (int r = 0; r < 10; ++r) {
+        rk.k[r] = make_uint2(key.x + static_cast<uint32_t>(r) * kPhiloxW0, key.y + static_cast<uint32_t>(r) * kPhiloxW1);
+    }
+    return rk;
+}
+
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const PhiloxRoundKeys& rk)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t hi0 = __umulhi(kPhiloxM0, c.x);
+        const uint32_t lo0 = kPhiloxM0 * c.x;
+        const uint32_t hi1 = __umulhi(kPhiloxM1, c.z);
+        const uint32_t lo1 = kPhiloxM1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ rk.k[round].x, lo1, hi0 ^ c.w ^ rk.k[round].y, lo0);
+    }
+    return c;
+}
+
 __host__ __device__ __forceinline__ uint32_t level_sample_word(int l, uint64_t s)
 {
     return static_cast<uint32_t>(((s >> 32) << 8) | static_cast<uint64_t>(l & 0xFF));
@@ -118,19 +146,19 @@ __device__ __forceinline__ void normals4_f32(uint4 w, float z[4])
 // ---- FP32 normals from the special-function units (reduced-precision paths) -----------
 //
 // For entries that are rounded to bfloat16 or FP8 right after generation, Box-Muller runs on
-// the MUFU approximations: -ln u = ln 2 * lg2(1 + v/u) with v = 1 - u (absolute error about
-// 2^-23, so the radius keeps full relative accuracy except for rho < 2^-8, probability 2^-17,
-// where its absolute error stays below 2^-11), and the angle 2 pi u = theta + pi with theta in
-// [-pi, pi) so that sin.approx / cos.approx run inside their accurate range
-// (absolute error about 2^-21); cos(theta + pi) = -cos(theta), sin(theta + pi) = -sin(theta).
+// the MUFU approximations: rho^2 = -2 ln 2 lg2(u) (absolute error of lg2 about 2^-22, so the
+// radius keeps full relative accuracy except for rho < 2^-6, probability 2^-13, where its
+// absolute error stays below 2^-11; u rounded to 1 for w >= 2^32 - 2^7 gives rho = 0 instead of
+// at most 2^-12), and the angle 2 pi u = theta + pi with theta in [-pi, pi) so that
+// sin.approx / cos.approx run inside their accurate range (absolute error about 2^-21);
+// cos(theta + pi) = -cos(theta), sin(theta + pi) = -sin(theta).
 
 __device__ __forceinline__ void box_muller_mufu(uint32_t wr, uint32_t wa, float& zc, float& zs)
 {
     const float u = fmaf(__uint2float_rn(wr), 0x1p-32f, 0x1p-33f);
-    const float v = fmaf(__uint2float_rn(~wr), 0x1p-32f, 0x1p-33f);
     float l2, radius, s, c;
-    asm("lg2.approx.f32 %0, %1;" : "=f"(l2) : "f"(1.0f + __fdividef(v, u)));
-    asm("sqrt.approx.f32 %0, %1;" : "=f"(radius) : "f"(1.3862943611198906f * l2));
+    asm("lg2.approx.f32 %0, %1;" : "=f"(l2) : "f"(u));
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(radius) : "f"(-1.3862943611198906f * l2));
     const float theta = fmaf(__int2float_rn(static_cast<int>(wa ^ 0x80000000u)), 6.283185307179586f * 0x1p-32f,
                              3.141592653589793f * 0x1p-32f);
     asm("sin.approx.f32 %0, %1;" : "=f"(s) : "f"(theta));

@@ -104,7 +104,7 @@ __device__ __forceinline__ double load_param(const void* p, int64_t off)
 // [M|S] (m x n, row-major, ldA) -> PA[k][i][2] through a 32 x 32 shared tile.
 template <typename S, typename D>
 __global__ void layout_A_kernel(const void* M, const void* Sg, int64_t ldA, int64_t m, int64_t n,
-                                int64_t m_pad, D* PA)
+                                int64_t m_pad, D* PA, int64_t ld_dst)
 {
     __shared__ double tm[32][33];
     __shared__ double ts[32][33];
@@ -120,8 +120,8 @@ __global__ void layout_A_kernel(const void* M, const void* Sg, int64_t ldA, int6
     for (int y = threadIdx.y; y < 32; y += blockDim.y) {
         const int64_t k = k0 + y, i = i0 + threadIdx.x;
         if (k < n && i < m_pad) {
-            PA[(k * m_pad + i) * 2] = static_cast<D>(tm[threadIdx.x][y]);
-            PA[(k * m_pad + i) * 2 + 1] = static_cast<D>(ts[threadIdx.x][y]);
+            PA[k * ld_dst + 2 * i] = static_cast<D>(tm[threadIdx.x][y]);
+            PA[k * ld_dst + 2 * i + 1] = static_cast<D>(ts[threadIdx.x][y]);
         }
     }
 }
@@ -129,15 +129,15 @@ __global__ void layout_A_kernel(const void* M, const void* Sg, int64_t ldA, int6
 // [M'|S'] (n x p, row-major, ldB) -> PB[k][j][2] (already row-contiguous: interleave only).
 template <typename S, typename D>
 __global__ void layout_B_kernel(const void* Mp, const void* Sp, int64_t ldB, int64_t n, int64_t p,
-                                int64_t p_pad, D* PB)
+                                int64_t p_pad, D* PB, int64_t ld_dst)
 {
     const int64_t total = n * p_pad;
     for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
          e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int64_t k = e / p_pad, j = e % p_pad;
         const bool ok = j < p;
-        PB[2 * e] = static_cast<D>(ok ? load_param<S>(Mp, k * ldB + j) : 0.0);
-        PB[2 * e + 1] = static_cast<D>(ok ? load_param<S>(Sp, k * ldB + j) : 0.0);
+        PB[k * ld_dst + 2 * j] = static_cast<D>(ok ? load_param<S>(Mp, k * ldB + j) : 0.0);
+        PB[k * ld_dst + 2 * j + 1] = static_cast<D>(ok ? load_param<S>(Sp, k * ldB + j) : 0.0);
     }
 }
 
@@ -217,35 +217,35 @@ cudaError_t launch_telescoping(const double* sum, LevelCounts counts, int levels
 }
 
 cudaError_t launch_layout_A(const void* M, const void* S, int src_dtype, int64_t ldA, int64_t m, int64_t n,
-                            int64_t m_pad, void* PA, bool dst_f64, cudaStream_t st)
+                            int64_t m_pad, void* PA, int64_t ld_dst, bool dst_f64, cudaStream_t st)
 {
     dim3 block(32, 8);
     dim3 grid(static_cast<unsigned>((n + 31) / 32), static_cast<unsigned>((m_pad + 31) / 32));
     const bool src_f64 = src_dtype == MLMC_DTYPE_F64;
     if (src_f64 && dst_f64)
-        layout_A_kernel<double, double><<<grid, block, 0, st>>>(M, S, ldA, m, n, m_pad, static_cast<double*>(PA));
+        layout_A_kernel<double, double><<<grid, block, 0, st>>>(M, S, ldA, m, n, m_pad, static_cast<double*>(PA), ld_dst);
     else if (src_f64)
-        layout_A_kernel<double, float><<<grid, block, 0, st>>>(M, S, ldA, m, n, m_pad, static_cast<float*>(PA));
+        layout_A_kernel<double, float><<<grid, block, 0, st>>>(M, S, ldA, m, n, m_pad, static_cast<float*>(PA), ld_dst);
     else if (dst_f64)
-        layout_A_kernel<float, double><<<grid, block, 0, st>>>(M, S, ldA, m, n, m_pad, static_cast<double*>(PA));
+        layout_A_kernel<float, double><<<grid, block, 0, st>>>(M, S, ldA, m, n, m_pad, static_cast<double*>(PA), ld_dst);
     else
-        layout_A_kernel<float, float><<<grid, block, 0, st>>>(M, S, ldA, m, n, m_pad, static_cast<float*>(PA));
+        layout_A_kernel<float, float><<<grid, block, 0, st>>>(M, S, ldA, m, n, m_pad, static_cast<float*>(PA), ld_dst);
     return cudaGetLastError();
 }
 
 cudaError_t launch_layout_B(const void* Mp, const void* Sp, int src_dtype, int64_t ldB, int64_t n, int64_t p,
-                            int64_t p_pad, void* PB, bool dst_f64, cudaStream_t st)
+                            int64_t p_pad, void* PB, int64_t ld_dst, bool dst_f64, cudaStream_t st)
 {
     const unsigned g = static_cast<unsigned>(std::min<int64_t>(blocks_for(n * p_pad, 256), 152 * 32));
     const bool src_f64 = src_dtype == MLMC_DTYPE_F64;
     if (src_f64 && dst_f64)
-        layout_B_kernel<double, double><<<g, 256, 0, st>>>(Mp, Sp, ldB, n, p, p_pad, static_cast<double*>(PB));
+        layout_B_kernel<double, double><<<g, 256, 0, st>>>(Mp, Sp, ldB, n, p, p_pad, static_cast<double*>(PB), ld_dst);
     else if (src_f64)
-        layout_B_kernel<double, float><<<g, 256, 0, st>>>(Mp, Sp, ldB, n, p, p_pad, static_cast<float*>(PB));
+        layout_B_kernel<double, float><<<g, 256, 0, st>>>(Mp, Sp, ldB, n, p, p_pad, static_cast<float*>(PB), ld_dst);
     else if (dst_f64)
-        layout_B_kernel<float, double><<<g, 256, 0, st>>>(Mp, Sp, ldB, n, p, p_pad, static_cast<double*>(PB));
+        layout_B_kernel<float, double><<<g, 256, 0, st>>>(Mp, Sp, ldB, n, p, p_pad, static_cast<double*>(PB), ld_dst);
     else
-        layout_B_kernel<float, float><<<g, 256, 0, st>>>(Mp, Sp, ldB, n, p, p_pad, static_cast<float*>(PB));
+        layout_B_kernel<float, float><<<g, 256, 0, st>>>(Mp, Sp, ldB, n, p, p_pad, static_cast<float*>(PB), ld_dst);
     return cudaGetLastError();
 }
 
