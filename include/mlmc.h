@@ -110,7 +110,8 @@ typedef struct {
     double nl_scale;     /* factor on the allocated N_l (Remark 2.6 oversampling control), > 0 */
     int64_t timeout_ns;  /* bound on any device-side wait; 0 = 2 s */
     int32_t tile_override; /* 0 = automatic tile choice; otherwise an internal tile id */
-    int32_t reserved;
+    int32_t adjoint_batch_log2; /* mlmc_backward replays at most 2^this sampled products per batch
+                                   (0 = 26; at least c_L + 1 are always taken); scratch is 8 B each */
 } mlmc_options;
 
 /* Report of one problem after mlmc_estimate. */
@@ -241,15 +242,31 @@ MLMC_API mlmc_status mlmc_level_stats_noalloc(const mlmc_problem* problem, const
 
 /* mlmc_backward: gradient of <G, Yhat> with respect to the caller's M, S, M',
  * S' of every problem, with the draws (indices and Z) held fixed as in the
- * reparameterisation A = M + S o Z.  Replays samples 0 .. N_l - 1 of every
- * level with the N_l recorded by the last mlmc_estimate (MLMC_ERR_STATE if
- * none), recomputing indices and Z from Philox.  G_dev: device FP64, every
- * problem's m x p upstream gradient back to back in problem order.
- * dM_dev, dS_dev, dMp_dev, dSp_dev: host arrays of nprob device pointers, one
- * per problem, to m x n (ldA) and n x p (ldB) buffers of the problem's
- * parameter dtype.  Gradients are written, not accumulated.  In BF16/FP8
- * precision the rounding of the entries is treated as the identity and the
- * forward's rounded operands are used (straight-through). */
+ * reparameterisation A = M + S o Z (the estimator is bilinear in (A, B), so
+ * for omega_t = w_t / N_l and k = r_t the sampled product a_t b_t^T gives
+ * dM[:, k] += omega G b_t, dS[:, k] += omega z_t o G b_t and the mirrored
+ * terms for M', S'; Eq. matrixsketch, Eq. hatYl, Eq. hatY).  Yhat here is the
+ * estimate of the statistics the plan holds, sum_l (sum of D) / N_l over the
+ * levels with N_l > 0; the samples are replayed (indices and Z recomputed from
+ * Philox, nothing stored by the forward), so every level must hold exactly
+ * the sample ids 0 .. N_l - 1 (true after mlmc_estimate, and after
+ * mlmc_level_stats calls that each start at the level's current N), else
+ * MLMC_ERR_STATE; a problem with no samples at all is MLMC_ERR_STATE too.
+ * G_dev: device FP64, every problem's m x p upstream gradient (row-major)
+ * back to back in problem order.  dM_dev, dS_dev, dMp_dev, dSp_dev: host
+ * arrays of nprob device pointers, one per problem, to m x n (leading
+ * dimension ldA) and n x p (ldB) buffers of the problem's parameter dtype.
+ * Gradients are written, not accumulated.  In BF16 precision the rounding of
+ * the entries to bfloat16 is treated as the identity and the rounded
+ * operands are used (straight-through).  Limits: n <= 2^30; the CUDA-core
+ * contraction keeps a block of G with all p columns (A side) or all m rows
+ * (B side) in shared memory, so m, p <= 1204 (FP64) or 2414 (FP32, BF16),
+ * else MLMC_ERR_UNSUPPORTED.  Scratch: the plan grows a device buffer to
+ * 20n + 8 (2nm + 2np) bytes + 8 B per record of a batch (options
+ * adjoint_batch_log2, default 2^26 records = 512 MiB) and keeps it until
+ * mlmc_plan_destroy.  Enqueued on the plan's stream; within a problem the
+ * records of one sampled column are summed in an order the sort leaves
+ * unspecified, so repeated calls agree to FP64 rounding, not bitwise. */
 MLMC_API mlmc_status mlmc_backward(mlmc_plan_t* plan, const double* G_dev, void* const* dM_dev,
                           void* const* dS_dev, void* const* dMp_dev, void* const* dSp_dev);
 

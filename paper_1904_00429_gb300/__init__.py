@@ -7,4 +7,4 @@ package loads nothing: the library is opened on first use of the binding, and ev
 entry point fails loudly when it is missing.
 """
 
-__all__ = ["binding", "inputs"]
+__all__ = ["autograd", "binding", "inputs"]

@@ -46,7 +46,7 @@ class Problem(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("c0", ctypes.c_int32), ("ratio", ctypes.c_int32), ("L", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("pilot_n", ctypes.c_int64), ("nl_scale", ctypes.c_double),
-                ("timeout_ns", ctypes.c_int64), ("tile_override", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("timeout_ns", ctypes.c_int64), ("tile_override", ctypes.c_int32), ("adjoint_batch_log2", ctypes.c_int32)]
 
 
 class Report(ctypes.Structure):
@@ -144,7 +144,7 @@ class Plan:
 
     def __init__(self, problems: Sequence[ProblemSpec], *, c0: int, L: int, ratio: int = 2,
                  precision: str = "fp32", pilot_n: int = 256, nl_scale: float = 1.0,
-                 timeout_ns: int = 0, tile_override: int = 0, stream=None):
+                 timeout_ns: int = 0, tile_override: int = 0, adjoint_batch_log2: int = 0, stream=None):
         self.problems = list(problems)
         self.device = self.problems[0].M.device
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -168,7 +168,8 @@ class Plan:
                              pr.L, pr.seed_A, pr.seed_B, pr.seed_idx, pr.problem_id)
             self.shapes.append((m, n, p))
             self.levels.append(pr.L if pr.L >= 0 else L)
-        self.options = Options(c0, ratio, L, PRECISION[precision], pilot_n, nl_scale, timeout_ns, tile_override, 0)
+        self.options = Options(c0, ratio, L, PRECISION[precision], pilot_n, nl_scale, timeout_ns, tile_override,
+                               adjoint_batch_log2)
         self.precision = precision
         self.c0, self.ratio, self.L = c0, ratio, L
         h = ctypes.c_void_p()
@@ -278,10 +279,24 @@ class Plan:
 
     # -- adjoint ---------------------------------------------------------------------------------
     def backward(self, G: Sequence[torch.Tensor], grads: Optional[Sequence[Sequence[torch.Tensor]]] = None):
-        """Gradient of sum_q <G_q, Yhat_q> w.r.t. (M, S, Mp, Sp) of every problem."""
+        """Gradient of sum_q <G_q, Yhat_q> w.r.t. (M, S, Mp, Sp) of every problem.
+
+        Returns one (dM, dS, dMp, dSp) tuple per problem, shaped and strided like the
+        problem's parameters (or written into ``grads`` when given)."""
+        if len(G) != len(self.problems):
+            raise ValueError("one upstream gradient per problem")
+        for g, (m, _, p) in zip(G, self.shapes):
+            if tuple(g.shape) != (m, p) or g.device != self.device:
+                raise ValueError("each G must be an m x p tensor on the plan's device")
         G_flat = torch.cat([g.reshape(-1).to(torch.float64) for g in G]).contiguous()
         if grads is None:
-            grads = [tuple(torch.empty_like(t) for t in (pr.M, pr.S, pr.Mp, pr.Sp)) for pr in self.problems]
+            grads = [tuple(torch.empty_strided(t.shape, t.stride(), dtype=t.dtype, device=t.device)
+                           for t in (pr.M, pr.S, pr.Mp, pr.Sp)) for pr in self.problems]
+        else:
+            for gr, pr in zip(grads, self.problems):
+                for d, t in zip(gr, (pr.M, pr.S, pr.Mp, pr.Sp)):
+                    if d.shape != t.shape or d.stride() != t.stride() or d.dtype != t.dtype:
+                        raise ValueError("gradient buffers must match the parameters' shape, strides and dtype")
         n = len(self.problems)
         ptrs = [(ctypes.c_void_p * n)(*[g[i].data_ptr() for g in grads]) for i in range(4)]
         _check(lib().mlmc_backward(self._h, _ptr(G_flat), *ptrs), "mlmc_backward")

@@ -63,7 +63,9 @@ struct ProblemState {
     double* sumsq = nullptr;  // (L+1)
     LevelCounts N{};
     int64_t Nl_est[MLMC_MAX_LEVELS] = {};
+    bool prefix[MLMC_MAX_LEVELS];   // level l holds exactly the samples 0 .. N_l - 1
     bool has_estimate = false;
+    ProblemState() { std::fill(prefix, prefix + MLMC_MAX_LEVELS, true); }
     int tiles_m = 1, tiles_p = 1;
     int max_chunks = 1;
 };
@@ -86,6 +88,9 @@ struct mlmc_plan_s {
     mlmc_status sticky = MLMC_OK;
     std::string sticky_msg;
     uint64_t launches = 0;
+    // adjoint scratch, grown on demand
+    void* adj_buf = nullptr;
+    size_t adj_bytes = 0;
 };
 
 namespace {
@@ -159,6 +164,8 @@ mlmc_status validate(const mlmc_problem* problems, int32_t nprob, const mlmc_opt
     if (o->precision == MLMC_FP8_E4M3) return fail(MLMC_ERR_UNSUPPORTED, "FP8 E4M3 is not available in this build");
     if (!(o->nl_scale > 0.0) || !std::isfinite(o->nl_scale)) return fail(MLMC_ERR_INVALID_ARG, "nl_scale must be > 0");
     if (o->timeout_ns < 0) return fail(MLMC_ERR_INVALID_ARG, "timeout_ns must be >= 0");
+    if (o->adjoint_batch_log2 < 0 || o->adjoint_batch_log2 > 40)
+        return fail(MLMC_ERR_INVALID_ARG, "adjoint_batch_log2 must be in [0, 40]");
     for (int32_t q = 0; q < nprob; ++q) {
         const mlmc_problem& pr = problems[q];
         const int L = pr.L >= 0 ? pr.L : o->L;
@@ -193,6 +200,7 @@ void free_plan(mlmc_plan_t* plan)
     cudaFree(plan->dbg_sumsq);
     cudaFree(plan->M2_dev);
     cudaFree(plan->err_flag);
+    cudaFree(plan->adj_buf);
 }
 
 bool tensor_core_precision(int precision) { return precision == MLMC_BF16 || precision == MLMC_FP8_E4M3; }
@@ -421,8 +429,12 @@ mlmc_status mlmc_level_stats(mlmc_plan_t* plan, int32_t prob, int32_t level, uin
     DeviceGuard g(plan->device);
     ProblemState& ps = plan->probs[size_t(prob)];
     const int64_t mp = ps.m * ps.p;
+    const bool continues = sample_begin == ps.N.v[level];
     st = run_level(plan, ps, level, sample_begin, count, ps.sum + int64_t(level) * mp, ps.sumsq + level);
-    if (st == MLMC_OK) ps.N.v[level] += count;
+    if (st == MLMC_OK) {
+        ps.N.v[level] += count;
+        ps.prefix[level] = ps.prefix[level] && continues;
+    }
     return st;
 }
 
@@ -491,6 +503,7 @@ mlmc_status mlmc_set_level_state(mlmc_plan_t* plan, int32_t prob, int32_t level,
     if (err == cudaSuccess) err = cudaStreamSynchronize(plan->stream);
     if (check_cuda(plan, err, "write level state") != MLMC_OK) return plan->sticky;
     ps.N.v[level] = N;
+    ps.prefix[level] = true;
     ps.has_estimate = false;
     return MLMC_OK;
 }
@@ -510,7 +523,10 @@ mlmc_status mlmc_reset_level_stats(mlmc_plan_t* plan, int32_t prob, int32_t leve
                                       plan->stream);
     if (err == cudaSuccess) err = cudaMemsetAsync(ps.sumsq + first, 0, sizeof(double) * size_t(cnt), plan->stream);
     if (check_cuda(plan, err, "reset level state") != MLMC_OK) return plan->sticky;
-    for (int l = first; l < first + cnt; ++l) ps.N.v[l] = 0;
+    for (int l = first; l < first + cnt; ++l) {
+        ps.N.v[l] = 0;
+        ps.prefix[l] = true;
+    }
     ps.has_estimate = false;
     return MLMC_OK;
 }
@@ -656,15 +672,169 @@ mlmc_status mlmc_estimate(mlmc_plan_t* plan, const double* eps_abs, double* yhat
     return MLMC_OK;
 }
 
+namespace {
+
+constexpr int64_t kAdjRecordBudget = int64_t(1) << 26;   // default records per replay batch (512 MiB)
+constexpr size_t kAdjSmemLimit = 227 * 1024;
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// Grow the plan's adjoint scratch to at least `bytes`.
+mlmc_status adj_reserve(mlmc_plan_t* plan, size_t bytes)
+{
+    if (bytes <= plan->adj_bytes) return MLMC_OK;
+    cudaError_t err = cudaStreamSynchronize(plan->stream);
+    if (check_cuda(plan, err, "adjoint scratch") != MLMC_OK) return plan->sticky;
+    cudaFree(plan->adj_buf);
+    plan->adj_buf = nullptr;
+    plan->adj_bytes = 0;
+    err = cudaMalloc(&plan->adj_buf, bytes);
+    if (err != cudaSuccess) return check_cuda(plan, err, "adjoint scratch");
+    plan->adj_bytes = bytes;
+    return MLMC_OK;
+}
+
+// Replay of one problem: batches of (level, sample range) entries whose records fit the budget.
+mlmc_status backward_problem(mlmc_plan_t* plan, ProblemState& ps, const double* G, void* dM, void* dS, void* dMp,
+                             void* dSp)
+{
+    const mlmc_options& o = plan->opt;
+    const bool f64 = plan->f64;
+    int64_t cmax = 1;
+    for (int l = 0; l <= ps.L; ++l) cmax = std::max(cmax, level_c(o, l));
+    const int64_t want = o.adjoint_batch_log2 > 0 ? int64_t(1) << o.adjoint_batch_log2 : kAdjRecordBudget;
+    const int64_t budget = std::max(want, cmax + 1);
+    // scratch layout
+    const int64_t n = ps.n, m = ps.m, p = ps.p;
+    size_t off = 0;
+    const size_t o_counts = off;  off = align256(off + sizeof(int) * size_t(n));
+    const size_t o_offsets = off; off = align256(off + sizeof(int64_t) * size_t(n));
+    const size_t o_cursor = off;  off = align256(off + sizeof(int64_t) * size_t(n));
+    const size_t o_scan = off;    off = align256(off + sizeof(int64_t) * size_t(adjoint_scan_scratch(n)));
+    const size_t o_rec = off;     off = align256(off + sizeof(uint64_t) * size_t(budget));
+    const size_t o_stage = off;   off = align256(off + sizeof(double) * size_t(2 * n * m + 2 * n * p));
+    mlmc_status st = adj_reserve(plan, off);
+    if (st != MLMC_OK) return st;
+    unsigned char* base = static_cast<unsigned char*>(plan->adj_buf);
+    int* counts = reinterpret_cast<int*>(base + o_counts);
+    int64_t* offsets = reinterpret_cast<int64_t*>(base + o_offsets);
+    int64_t* cursor = reinterpret_cast<int64_t*>(base + o_cursor);
+    int64_t* scan = reinterpret_cast<int64_t*>(base + o_scan);
+    uint64_t* records = reinterpret_cast<uint64_t*>(base + o_rec);
+    double* stage = reinterpret_cast<double*>(base + o_stage);
+
+    AdjSegmentParams sp{};
+    sp.PAB = ps.PAB;
+    sp.ld = ps.ld;
+    sp.m = int(m);
+    sp.p = int(p);
+    sp.m_pad = int(ps.m_pad);
+    sp.n = n;
+    sp.rkA = philox_round_keys(key(ps.desc.seed_A, ps.desc.problem_id));
+    sp.rkB = philox_round_keys(key(ps.desc.seed_B, ps.desc.problem_id));
+    sp.G = G;
+    sp.offsets = offsets;
+    sp.records = records;
+    sp.bf16 = o.precision == MLMC_BF16 ? 1 : 0;
+    sp.gM_t = stage;
+    sp.gS_t = stage + n * m;
+    sp.gMp = stage + 2 * n * m;
+    sp.gSp = stage + 2 * n * m + n * p;
+    for (int l = 0; l <= ps.L; ++l) {
+        const double c = double(level_c(o, l));
+        sp.w_fine[l] = double(n) / c;
+        sp.w_coarse_extra[l] = l > 0 ? -double(n) / double(level_c(o, l - 1)) : 0.0;
+        sp.inv_N[l] = ps.N.v[l] > 0 ? 1.0 / double(ps.N.v[l]) : 0.0;
+    }
+    const uint2 keyI = key(ps.desc.seed_idx, ps.desc.problem_id);
+    cudaError_t err = cudaMemsetAsync(stage, 0, sizeof(double) * size_t(2 * n * m + 2 * n * p), plan->stream);
+    if (check_cuda(plan, err, "adjoint staging") != MLMC_OK) return plan->sticky;
+
+    int l = 0;
+    uint64_t s_next = 0;
+    for (;;) {
+        // next batch
+        AdjLevels lv{};
+        int64_t recs = 0;
+        while (l <= ps.L && lv.count < MLMC_MAX_LEVELS) {
+            if (s_next >= ps.N.v[l]) {
+                ++l;
+                s_next = 0;
+                continue;
+            }
+            const int64_t c = level_c(o, l);
+            const uint64_t room = uint64_t((budget - recs) / c);
+            if (room == 0) break;
+            const uint64_t take = std::min<uint64_t>(room, ps.N.v[l] - s_next);
+            lv.lev[lv.count] = l;
+            lv.c[lv.count] = c;
+            lv.s0[lv.count] = s_next;
+            lv.pair_begin[lv.count] = lv.total_pairs;
+            lv.total_pairs += int64_t(take) * ((c + 1) / 2);
+            lv.count += 1;
+            recs += int64_t(take) * c;
+            s_next += take;
+        }
+        if (lv.count == 0) break;
+        err = cudaMemsetAsync(counts, 0, sizeof(int) * size_t(n), plan->stream);
+        if (err == cudaSuccess) err = adjoint_count(lv, keyI, n, o.ratio, counts, plan->stream);
+        if (err == cudaSuccess) err = adjoint_scan(counts, n, offsets, scan, plan->stream);
+        if (err == cudaSuccess)
+            err = cudaMemcpyAsync(cursor, offsets, sizeof(int64_t) * size_t(n), cudaMemcpyDeviceToDevice, plan->stream);
+        if (err == cudaSuccess) err = adjoint_scatter(lv, keyI, n, o.ratio, cursor, records, plan->stream);
+        sp.total = recs;
+        for (int side = 0; side < 2 && err == cudaSuccess; ++side) {
+            sp.ob = adjoint_output_block(side == 0 ? int(p) : int(m), f64);
+            err = adjoint_segments(sp, f64, side, plan->num_sms, plan->stream);
+        }
+        if (check_cuda(plan, err, "adjoint batch") != MLMC_OK) return plan->sticky;
+        plan->launches += 9;   // count, five scan passes, scatter, two segment reductions
+    }
+    err = adjoint_write_A(sp.gM_t, n, m, dM, ps.desc.ldA, ps.desc.dtype, plan->stream);
+    if (err == cudaSuccess) err = adjoint_write_A(sp.gS_t, n, m, dS, ps.desc.ldA, ps.desc.dtype, plan->stream);
+    if (err == cudaSuccess) err = adjoint_write_B(sp.gMp, n, p, dMp, ps.desc.ldB, ps.desc.dtype, plan->stream);
+    if (err == cudaSuccess) err = adjoint_write_B(sp.gSp, n, p, dSp, ps.desc.ldB, ps.desc.dtype, plan->stream);
+    if (check_cuda(plan, err, "adjoint write-out") != MLMC_OK) return plan->sticky;
+    plan->launches += 4;
+    return MLMC_OK;
+}
+
+}  // namespace
+
 mlmc_status mlmc_backward(mlmc_plan_t* plan, const double* G_dev, void* const* dM_dev, void* const* dS_dev,
                           void* const* dMp_dev, void* const* dSp_dev)
 {
     mlmc_status st = enter(plan);
     if (st != MLMC_OK) return st;
     if (!G_dev || !dM_dev || !dS_dev || !dMp_dev || !dSp_dev) return fail(MLMC_ERR_INVALID_ARG, "null argument");
-    for (auto& ps : plan->probs)
-        if (!ps.has_estimate) return fail(MLMC_ERR_STATE, "mlmc_backward needs a preceding mlmc_estimate");
-    return fail(MLMC_ERR_UNSUPPORTED, "mlmc_backward is not available in this build");
+    for (size_t q = 0; q < plan->probs.size(); ++q) {
+        const ProblemState& ps = plan->probs[q];
+        if (!dM_dev[q] || !dS_dev[q] || !dMp_dev[q] || !dSp_dev[q])
+            return fail(MLMC_ERR_INVALID_ARG, "problem %zu: null gradient pointer", q);
+        uint64_t total = 0;
+        for (int l = 0; l <= ps.L; ++l) {
+            if (!ps.prefix[l])
+                return fail(MLMC_ERR_STATE, "problem %zu level %d: held samples are not the ids 0 .. N_l - 1", q, l);
+            total += ps.N.v[l];
+        }
+        if (total == 0) return fail(MLMC_ERR_STATE, "mlmc_backward: problem %zu holds no samples", q);
+        for (int side = 0; side < 2; ++side) {
+            const int kin = int(side == 0 ? ps.p : ps.m);
+            if (adjoint_segment_smem(kin, adjoint_output_block(kin, plan->f64), plan->f64) > kAdjSmemLimit)
+                return fail(MLMC_ERR_UNSUPPORTED, "problem %zu: the adjoint keeps a block of G with all %d %s on chip; "
+                            "at most %d fit", q, kin, side == 0 ? "columns" : "rows", plan->f64 ? 1204 : 2414);
+        }
+        if (ps.n > (int64_t(1) << 30)) return fail(MLMC_ERR_UNSUPPORTED, "problem %zu: the adjoint needs n <= 2^30", q);
+    }
+    DeviceGuard g(plan->device);
+    int64_t goff = 0;
+    for (size_t q = 0; q < plan->probs.size(); ++q) {
+        ProblemState& ps = plan->probs[q];
+        st = backward_problem(plan, ps, G_dev + goff, dM_dev[q], dS_dev[q], dMp_dev[q], dSp_dev[q]);
+        if (st != MLMC_OK) return st;
+        goff += ps.m * ps.p;
+    }
+    return MLMC_OK;
 }
 
 mlmc_status mlmc_debug_philox(const uint32_t* ctr_dev, const uint32_t* key_dev, int64_t count, uint32_t* out_dev,

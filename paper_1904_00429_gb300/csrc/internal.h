@@ -97,6 +97,51 @@ cudaError_t launch_layout_A(const void* M, const void* S, int src_dtype, int64_t
 cudaError_t launch_layout_B(const void* Mp, const void* Sp, int src_dtype, int64_t ldB, int64_t n,
                             int64_t p, int64_t p_pad, void* PB, int64_t ld_dst, bool dst_f64, cudaStream_t st);
 
+// ---- adjoint ----------------------------------------------------------------------------
+// One batch of the adjoint's replay: entry e covers samples s0[e] .. s0[e] + (pairs of the entry)
+// / ceil(c[e] / 2) - 1 of level lev[e]; pair_begin[e] is the entry's first Philox block (two
+// slots) in the batch's flattened enumeration.
+struct AdjLevels {
+    int count;
+    int lev[MLMC_MAX_LEVELS];
+    int64_t c[MLMC_MAX_LEVELS];
+    uint64_t s0[MLMC_MAX_LEVELS];
+    int64_t pair_begin[MLMC_MAX_LEVELS];
+    int64_t total_pairs;
+};
+
+struct AdjSegmentParams {
+    const void* PAB;        // plan layout: row k = [(M, S) pairs of A | (M', S') pairs of B]
+    int64_t ld;             // elements per row
+    int m, p, m_pad;
+    int64_t n;
+    PhiloxRoundKeys rkA, rkB;
+    const double* G;        // m x p upstream gradient
+    const int64_t* offsets; // segment starts (n)
+    int64_t total;          // number of records
+    const uint64_t* records;
+    double w_fine[MLMC_MAX_LEVELS];        // n / c_l
+    double w_coarse_extra[MLMC_MAX_LEVELS];  // -n / c_{l-1} (l > 0), added on coarse slots
+    double inv_N[MLMC_MAX_LEVELS];
+    int bf16;               // round the regenerated operands to bfloat16 (straight-through)
+    int ob;                 // outputs per CTA block
+    double* gM_t;           // n x m staging of dM (the kernels add to the staging)
+    double* gS_t;           // n x m staging of dS
+    double* gMp;            // n x p
+    double* gSp;            // n x p
+};
+
+cudaError_t adjoint_count(const AdjLevels& lv, uint2 keyI, int64_t n, int R, int* counts, cudaStream_t st);
+cudaError_t adjoint_scatter(const AdjLevels& lv, uint2 keyI, int64_t n, int R, int64_t* cursor, uint64_t* records,
+                            cudaStream_t st);
+int64_t adjoint_scan_scratch(int64_t n);
+cudaError_t adjoint_scan(const int* counts, int64_t n, int64_t* offsets, int64_t* scratch, cudaStream_t st);
+size_t adjoint_segment_smem(int kin, int ob, bool f64);
+int adjoint_output_block(int kin, bool f64);
+cudaError_t adjoint_segments(const AdjSegmentParams& prm, bool f64, int side, int num_sms, cudaStream_t st);
+cudaError_t adjoint_write_A(const double* src, int64_t n, int64_t m, void* dst, int64_t ld, int dtype, cudaStream_t st);
+cudaError_t adjoint_write_B(const double* src, int64_t n, int64_t p, void* dst, int64_t ld, int dtype, cudaStream_t st);
+
 // Set the thread-local message returned by mlmc_last_error().
 mlmc_status report_error(mlmc_status st, const char* msg);
 
