@@ -324,6 +324,56 @@ def _roofline(res, W, peaks, peak_kind):
             "hbm_achieved_gbs": hbm, "kernel": f"level_tc_{prec}_kernel"}
 
 
+ADJOINT = dict(name="adjoint_256x65536x256", m=256, n=65536, p=256, c0=64, R=2, L=8, N=256, precision="bf16")
+
+
+def _measure_adjoint(args, host, dev, stream):
+    """Backward of the loss ||Yhat - T||_F^2 through mlmc_backward: A 256 x 65536, B 65536 x 256,
+    c_l = 64 * 2^l for l = 0..8, N_l = 256 samples per level, BF16 forward (straight-through
+    adjoint).  Times exactly ``args.steps`` backward calls after ``args.warmup`` untimed ones."""
+    import torch
+
+    from paper_1904_00429_gb300 import binding
+    from paper_1904_00429_gb300.inputs import make_target
+
+    A = ADJOINT
+    tensors = [h.to(dev, torch.float32, non_blocking=True) for h in host]
+    spec = binding.ProblemSpec(*tensors, seed_A=0, seed_B=1, seed_idx=2, problem_id=0)
+    plan = binding.Plan([spec], c0=A["c0"], L=A["L"], ratio=A["R"], precision=A["precision"], stream=stream)
+    for l in range(A["L"] + 1):
+        plan.level_stats(0, l, 0, A["N"])
+    (Y,) = plan.telescoping_sum()
+    T = torch.from_numpy(make_target(A["m"], A["p"])).to(dev)
+    G = (2.0 * (Y - T)).contiguous()
+    grads = [tuple(torch.empty_like(t) for t in tensors)]
+    for _ in range(args.warmup):
+        plan.backward([G], grads)
+    torch.cuda.synchronize()
+    launches0 = plan.launch_count()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
+    for i in range(args.steps):
+        plan.backward([G], grads)
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    plan.synchronize()
+    launches = plan.launch_count() - launches0
+    ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    records = A["N"] * sum(A["c0"] * A["R"]**l for l in range(A["L"] + 1))
+    # two contractions (G b and G^T a) of m x p FMAs per sampled product
+    flops = 2.0 * 2.0 * A["m"] * A["p"] * records
+    t = statistics.mean(ms) / 1e3
+    plan.close()
+    achieved = flops / t / 1e12
+    return {"workload": A["name"], "metric": "backward time (mlmc_backward, all four gradients)",
+            "value": t, "unit": "s", "ms_per_backward": [round(x, 4) for x in ms], "records": records,
+            "N_l": [A["N"]] * (A["L"] + 1), "precision": A["precision"], "gpu_launches": launches,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)",
+                         "kernel": "segment_kernel<float>"}}
+
+
 def run_ours(args):
     import torch
 
@@ -383,6 +433,8 @@ def run_ours(args):
                                        "speedup_of_headline": o["T"] / T,
                                        "roofline": _roofline(o, W, peaks, peak_kind), "clocks": o["clocks"]}
                            for o in others}
+    if not args.no_adjoint and world == 1:
+        line["adjoint"] = _measure_adjoint(args, host, dev, stream)
     if not args.no_cpu_baseline and world == 1:
         t_cpu, _ = cpu_baseline_sample(W)
         T_cpu = sum(nl * t for nl, t in zip(head["Nl"], t_cpu))
@@ -401,6 +453,7 @@ def main():
     ap.add_argument("--precision", choices=["fp32", "fp64", "bf16", "fp8"], default="bf16")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP32 comparison measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the backward measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
