@@ -260,7 +260,7 @@ MLMC_API mlmc_status mlmc_level_stats_noalloc(const mlmc_problem* problem, const
  * the entries to bfloat16 is treated as the identity and the rounded
  * operands are used (straight-through).  Limits: n <= 2^30; the CUDA-core
  * contraction keeps a block of G with all p columns (A side) or all m rows
- * (B side) in shared memory, so m, p <= 1204 (FP64) or 2414 (FP32, BF16),
+ * (B side) in shared memory, so m, p <= 696 (FP64) or 1584 (FP32, BF16),
  * else MLMC_ERR_UNSUPPORTED.  Scratch: the plan grows a device buffer to
  * 20n + 8 (2nm + 2np) bytes + 8 B per record of a batch (options
  * adjoint_batch_log2, default 2^26 records = 512 MiB) and keeps it until

@@ -27,7 +27,7 @@ namespace {
 
 constexpr int kScanBlock = 1024;   // entries per block of the prefix sum
 constexpr int kAdjThreads = 256;
-constexpr int kAdjChunk = 16;      // contributions per smem chunk in the segment kernel
+constexpr size_t kAdjSmemMax = 227 * 1024;
 
 __device__ __forceinline__ uint64_t pack_record(int l, bool coarse, uint64_t s)
 {
@@ -128,112 +128,217 @@ __device__ __forceinline__ T round_operand(T x, bool bf16)
     return bf16 ? static_cast<T>(__bfloat162float(__float2bfloat16_rn(static_cast<float>(x)))) : x;
 }
 
+template <typename T>
+struct Vec4;
+template <>
+struct Vec4<float> {
+    static __device__ __forceinline__ void load(const float* p, float v[4])
+    {
+        const float4 a = *reinterpret_cast<const float4*>(p);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    }
+};
+template <>
+struct Vec4<double> {
+    static __device__ __forceinline__ void load(const double* p, double v[4])
+    {
+        const double2 a = reinterpret_cast<const double2*>(p)[0];
+        const double2 b = reinterpret_cast<const double2*>(p)[1];
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+};
+
+constexpr int kAdjNJ = 8;                    // records per warp per chunk
+constexpr int kAdjRec = kAdjNJ * (kAdjThreads / 32);   // records per chunk (64)
+constexpr int kAdjSlab = 64;                 // contracted entries regenerated per slab
+
+// Shared-memory layout of the segment kernel (bytes from the base), for kin contracted
+// entries, OB = 32 * opt outputs and element size e.
+struct SegSmem {
+    size_t g, vin, zo, omega, red, rec, total;
+    __host__ __device__ SegSmem(int kin, int opt, int e)
+    {
+        const size_t OB = size_t(32) * opt;
+        const size_t kin4 = (size_t(kin) + 3) / 4 * 4;
+        g = 0;
+        vin = g + kin4 * OB * e;
+        zo = vin + size_t(kAdjRec) * kAdjSlab * e;
+        omega = zo + size_t(kAdjRec) * OB * e;
+        red = (omega + size_t(kAdjRec) * e + 15) / 16 * 16;
+        rec = red + size_t(2) * (kAdjThreads / 32) * OB * 8;
+        total = rec + size_t(kAdjRec) * 8;
+    }
+};
+
 // Segment reduction for one side.  A side (side == 0): outputs o index rows of A (o < m), the
 // contracted vector is b_j = B[k, :] (x < p) and u_j[o] = sum_x G[o, x] b_j[x].  B side
 // (side == 1): outputs o index columns of B (o < p), the vector is a_j = A[:, k] (x < m) and
-// u_j[o] = sum_x G[x, o] a_j[x].  A CTA owns an OB-wide block of outputs (blockIdx.y) and keeps
-// that block of G resident in shared memory, transposed as Gs[x][o]; it walks a batch of
-// segments k (blockIdx.x, grid-stride), regenerating each contribution's vector (all x) and
-// the normals of its own outputs, and accumulates in FP64
-//     gM[k, o] = sum_j omega_j u_j[o],   gS[k, o] = sum_j omega_j z_j[o] u_j[o].
-template <typename T>
-__global__ void __launch_bounds__(kAdjThreads) segment_kernel(AdjSegmentParams prm, int side)
+// u_j[o] = sum_x G[x, o] a_j[x].  A CTA owns OB = 32 * OPT outputs (blockIdx.y) and keeps that
+// block of G resident in shared memory, transposed as Gs[x][o]; it walks a batch of segments k
+// (blockIdx.x, grid-stride).  The records of a segment are taken 64 at a time: warp w owns
+// records 8w .. 8w + 7 of the chunk and lane t the outputs t, t + 32, ..., so every thread
+// carries an OPT x 8 register tile of u.  The contracted vectors are regenerated from Philox in
+// slabs of 64 entries (all records of the chunk), the normals of the CTA's outputs once per
+// chunk.  Per chunk each thread folds its 8 records in the working precision, then adds the
+// result to FP64 accumulators
+//     gM[k, o] += sum_j omega_j u_j[o],   gS[k, o] += sum_j omega_j z_j[o] u_j[o];
+// at the end of the segment the 8 warps' accumulators are summed in warp order.
+template <typename T, int OPT, int side>
+__global__ void __launch_bounds__(kAdjThreads, 1) segment_kernel(const AdjSegmentParams prm)
 {
+    constexpr int OB = 32 * OPT;
+    constexpr int NW = kAdjThreads / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int kin = side == 0 ? prm.p : prm.m;
+    const int kin4 = (kin + 3) & ~3;
     const int kout = side == 0 ? prm.m : prm.p;
-    const int OB = prm.ob;
     const int o0 = blockIdx.y * OB;
     const int ob = min(OB, kout - o0);
-    T* Gs = reinterpret_cast<T*>(smem_raw);                               // [kin][OB]
-    T* vin = Gs + static_cast<int64_t>(kin) * OB;                           // [kAdjChunk][kin]
-    T* zo = vin + static_cast<int64_t>(kAdjChunk) * kin;                    // [kAdjChunk][OB]
-    double* omega = reinterpret_cast<double*>(zo + static_cast<int64_t>(kAdjChunk) * OB);  // [kAdjChunk]
-    __shared__ uint64_t rec_s[kAdjChunk];
+    const SegSmem L(kin, OPT, int(sizeof(T)));
+    T* Gs = reinterpret_cast<T*>(smem_raw + L.g);          // [kin4][OB]
+    T* vin = reinterpret_cast<T*>(smem_raw + L.vin);       // [kAdjRec][kAdjSlab]
+    T* zo = reinterpret_cast<T*>(smem_raw + L.zo);         // [kAdjRec][OB]
+    T* omega = reinterpret_cast<T*>(smem_raw + L.omega);   // [kAdjRec]
+    double* red = reinterpret_cast<double*>(smem_raw + L.red);   // [2][NW][OB]
+    uint64_t* rec_s = reinterpret_cast<uint64_t*>(smem_raw + L.rec);
 
-    // resident block of G, transposed
-    for (int64_t e = threadIdx.x; e < static_cast<int64_t>(kin) * OB; e += blockDim.x) {
-        const int x = static_cast<int>(e / OB), oo = static_cast<int>(e % OB);
+    for (int e = threadIdx.x; e < kin4 * OB; e += kAdjThreads) {
+        const int x = e / OB, oo = e % OB;
         const int o = o0 + oo;
         double g = 0.0;
-        if (oo < ob) g = side == 0 ? prm.G[static_cast<int64_t>(o) * prm.p + x] : prm.G[static_cast<int64_t>(x) * prm.p + o];
+        if (oo < ob && x < kin)
+            g = side == 0 ? prm.G[static_cast<int64_t>(o) * prm.p + x] : prm.G[static_cast<int64_t>(x) * prm.p + o];
         Gs[e] = static_cast<T>(g);
     }
     const T* P = static_cast<const T*>(prm.PAB);
-    const int64_t in_off = side == 0 ? 2 * static_cast<int64_t>(prm.m_pad) : 0;   // pairs of the contracted vector
+    const int64_t in_off = side == 0 ? 2 * static_cast<int64_t>(prm.m_pad) : 0;
     const PhiloxRoundKeys& rk_in = side == 0 ? prm.rkB : prm.rkA;
     const PhiloxRoundKeys& rk_out = side == 0 ? prm.rkA : prm.rkB;
-    const int groups = blockDim.x / OB;   // contributions handled in parallel per output
-    const int oo = threadIdx.x % OB;
-    const int grp = threadIdx.x / OB;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
     __syncthreads();
 
     for (int64_t k = blockIdx.x; k < prm.n; k += gridDim.x) {
         const int64_t seg0 = prm.offsets[k];
         const int64_t seg1 = k + 1 < prm.n ? prm.offsets[k + 1] : prm.total;
-        double accM = 0.0, accS = 0.0;
-        const T* row = P + k * prm.ld;
-        for (int64_t c0 = seg0; c0 < seg1; c0 += kAdjChunk) {
-            const int nc = static_cast<int>(seg1 - c0 < kAdjChunk ? seg1 - c0 : kAdjChunk);
-            if (threadIdx.x < nc) rec_s[threadIdx.x] = prm.records[c0 + threadIdx.x];
-            __syncthreads();
-            // regenerate the contracted vectors (all x) and the normals of this output block
-            const int nin4 = (kin + 3) / 4, nout4 = (ob + 3) / 4;
-            for (int e = threadIdx.x; e < nc * (nin4 + nout4); e += blockDim.x) {
-                const int j = e / (nin4 + nout4);
-                const int r = e % (nin4 + nout4);
-                const uint64_t rec = rec_s[j];
-                const int l = static_cast<int>(rec & 31);
-                const uint64_t s = rec >> 6;
-                const bool is_in = r < nin4;
-                const int g4 = is_in ? r : (o0 >> 2) + (r - nin4);   // block of four rows/columns
-                const uint4 w = philox4x32_10_rk(make_uint4(static_cast<uint32_t>(g4), static_cast<uint32_t>(k),
-                                                            static_cast<uint32_t>(s), level_sample_word(l, s)),
-                                                 is_in ? rk_in : rk_out);
-                T z[4];
-                Normals<T>::four(w, z);
+        if (seg0 == seg1) continue;   // uniform across the CTA
+        double accM[OPT], accS[OPT];
 #pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const int x = 4 * g4 + h;
-                    if (is_in) {
-                        if (x < kin) {
-                            const T val = fma(row[in_off + 2 * x + 1], z[h], row[in_off + 2 * x]);
-                            vin[static_cast<int64_t>(j) * kin + x] = round_operand(val, prm.bf16);
+        for (int q = 0; q < OPT; ++q) accM[q] = accS[q] = 0.0;
+        const T* row = P + k * prm.ld + in_off;
+        for (int64_t c0 = seg0; c0 < seg1; c0 += kAdjRec) {
+            const int nc = static_cast<int>(seg1 - c0 < kAdjRec ? seg1 - c0 : kAdjRec);
+            // records, weights and the normals of this CTA's outputs
+            if (threadIdx.x < kAdjRec) {
+                uint64_t rec = 0;
+                T om = T(0);
+                if (threadIdx.x < nc) {
+                    rec = prm.records[c0 + threadIdx.x];
+                    const int l = static_cast<int>(rec & 31);
+                    const bool coarse = (rec >> 5) & 1;
+                    om = static_cast<T>((prm.w_fine[l] + (coarse ? prm.w_coarse_extra[l] : 0.0)) * prm.inv_N[l]);
+                }
+                rec_s[threadIdx.x] = rec;
+                omega[threadIdx.x] = om;
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < kAdjRec * (OB / 4); e += kAdjThreads) {
+                const int j = e / (OB / 4), g4 = e % (OB / 4);
+                T z[4] = {T(0), T(0), T(0), T(0)};
+                if (j < nc && 4 * g4 < ob) {
+                    const uint64_t rec = rec_s[j];
+                    const uint64_t s = rec >> 6;
+                    const uint4 w = philox4x32_10_rk(
+                        make_uint4(static_cast<uint32_t>((o0 >> 2) + g4), static_cast<uint32_t>(k),
+                                   static_cast<uint32_t>(s), level_sample_word(static_cast<int>(rec & 31), s)),
+                        rk_out);
+                    Normals<T>::four(w, z);
+                }
+#pragma unroll
+                for (int h = 0; h < 4; ++h) zo[j * OB + 4 * g4 + h] = z[h];
+            }
+            T u[OPT][kAdjNJ];
+#pragma unroll
+            for (int q = 0; q < OPT; ++q)
+#pragma unroll
+                for (int j = 0; j < kAdjNJ; ++j) u[q][j] = T(0);
+
+            for (int x0 = 0; x0 < kin4; x0 += kAdjSlab) {
+                const int len = min(kAdjSlab, kin4 - x0);
+                __syncthreads();   // previous slab consumed
+                for (int e = threadIdx.x; e < kAdjRec * (kAdjSlab / 4); e += kAdjThreads) {
+                    const int j = e / (kAdjSlab / 4), g4 = e % (kAdjSlab / 4);
+                    const int x = x0 + 4 * g4;
+                    T v[4] = {T(0), T(0), T(0), T(0)};
+                    if (j < nc && x < kin) {
+                        const uint64_t rec = rec_s[j];
+                        const uint64_t s = rec >> 6;
+                        const uint4 w = philox4x32_10_rk(
+                            make_uint4(static_cast<uint32_t>(x >> 2), static_cast<uint32_t>(k), static_cast<uint32_t>(s),
+                                       level_sample_word(static_cast<int>(rec & 31), s)),
+                            rk_in);
+                        T z[4];
+                        Normals<T>::four(w, z);
+#pragma unroll
+                        for (int h = 0; h < 4; ++h)
+                            if (x + h < kin) v[h] = round_operand(fma(row[2 * (x + h) + 1], z[h], row[2 * (x + h)]), prm.bf16);
+                    }
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) vin[j * kAdjSlab + 4 * g4 + h] = v[h];
+                }
+                __syncthreads();
+                const T* vw = vin + warp * kAdjNJ * kAdjSlab;
+                const T* gx = Gs + static_cast<int64_t>(x0) * OB + lane;
+                for (int xx = 0; xx < len; xx += 4) {
+                    T g[4][OPT];
+#pragma unroll
+                    for (int h = 0; h < 4; ++h)
+#pragma unroll
+                        for (int q = 0; q < OPT; ++q) g[h][q] = gx[(xx + h) * OB + 32 * q];
+#pragma unroll
+                    for (int j = 0; j < kAdjNJ; ++j) {
+                        T v[4];
+                        Vec4<T>::load(vw + j * kAdjSlab + xx, v);
+#pragma unroll
+                        for (int q = 0; q < OPT; ++q) {
+                            T a = u[q][j];
+                            a = fma(g[0][q], v[0], a);
+                            a = fma(g[1][q], v[1], a);
+                            a = fma(g[2][q], v[2], a);
+                            a = fma(g[3][q], v[3], a);
+                            u[q][j] = a;
                         }
-                    } else if (x - o0 < ob) {
-                        zo[static_cast<int64_t>(j) * OB + (x - o0)] = z[h];
                     }
                 }
             }
-            if (threadIdx.x < nc) {
-                const uint64_t rec = rec_s[threadIdx.x];
-                const int l = static_cast<int>(rec & 31);
-                const bool coarse = (rec >> 5) & 1;
-                omega[threadIdx.x] = (prm.w_fine[l] + (coarse ? prm.w_coarse_extra[l] : 0.0)) * prm.inv_N[l];
-            }
-            __syncthreads();
-            if (oo < ob) {
-                for (int j = grp; j < nc; j += groups) {
-                    const T* v = vin + static_cast<int64_t>(j) * kin;
-                    T u = T(0);
-                    for (int x = 0; x < kin; ++x) u = fma(Gs[static_cast<int64_t>(x) * OB + oo], v[x], u);
-                    const double wu = omega[j] * static_cast<double>(u);
-                    accM += wu;
-                    accS += wu * static_cast<double>(zo[static_cast<int64_t>(j) * OB + oo]);
+            // fold this chunk's records (working precision), then into the FP64 accumulators
+#pragma unroll
+            for (int q = 0; q < OPT; ++q) {
+                const int oo = lane + 32 * q;
+                T sm = T(0), ss = T(0);
+#pragma unroll
+                for (int j = 0; j < kAdjNJ; ++j) {
+                    const int jj = warp * kAdjNJ + j;
+                    const T wu = omega[jj] * u[q][j];
+                    sm += wu;
+                    ss = fma(wu, zo[jj * OB + oo], ss);
                 }
+                accM[q] += static_cast<double>(sm);
+                accS[q] += static_cast<double>(ss);
             }
-            __syncthreads();
+            __syncthreads();   // records, weights and normals of the chunk consumed
         }
-        // combine the contribution groups of each output in a fixed order, then write
-        double* red = reinterpret_cast<double*>(vin);   // reuse: [groups][OB] x 2
-        red[grp * OB + oo] = accM;
-        red[(groups + grp) * OB + oo] = accS;
+#pragma unroll
+        for (int q = 0; q < OPT; ++q) {
+            red[warp * OB + lane + 32 * q] = accM[q];
+            red[(NW + warp) * OB + lane + 32 * q] = accS[q];
+        }
         __syncthreads();
-        if (grp == 0 && oo < ob) {
+        for (int oo = threadIdx.x; oo < ob; oo += kAdjThreads) {
             double tm = 0.0, ts = 0.0;
-            for (int g = 0; g < groups; ++g) {
-                tm += red[g * OB + oo];
-                ts += red[(groups + g) * OB + oo];
+            for (int w = 0; w < NW; ++w) {
+                tm += red[w * OB + oo];
+                ts += red[(NW + w) * OB + oo];
             }
             const int o = o0 + oo;
             if (side == 0) {
@@ -320,46 +425,49 @@ cudaError_t adjoint_scan(const int* counts, int64_t n, int64_t* offsets, int64_t
     return cudaGetLastError();
 }
 
-size_t adjoint_segment_smem(int kin, int ob, bool f64)
-{
-    const size_t e = f64 ? 8 : 4;
-    const size_t body = size_t(kin) * ob * e + size_t(kAdjChunk) * kin * e + size_t(kAdjChunk) * ob * e +
-                        size_t(kAdjChunk) * 8;
-    // the FP64 group reduction reuses the vector area: 2 * (threads / ob) * ob doubles
-    const size_t red = size_t(2) * kAdjThreads * 8;
-    const size_t vin_area = size_t(kAdjChunk) * kin * e;
-    return body + (red > vin_area ? red - vin_area : 0);
-}
+size_t adjoint_segment_smem(int kin, int opt, bool f64) { return SegSmem(kin, opt, f64 ? 8 : 4).total; }
 
 int adjoint_output_block(int kin, bool f64)
 {
-    // largest power of two <= 64 whose G block (kin x ob) stays within 96 KB
-    const size_t e = f64 ? 8 : 4;
-    int ob = 64;
-    while (ob > 8 && size_t(kin) * ob * e > 96 * 1024) ob /= 2;
-    return ob;
+    // widest register tile whose resident block of G fits next to the slab buffers
+    for (int opt = 4; opt >= 1; opt /= 2)
+        if (adjoint_segment_smem(kin, opt, f64) <= kAdjSmemMax) return opt;
+    return 0;
+}
+
+template <typename T, int OPT, int side>
+cudaError_t launch_segments(const AdjSegmentParams& prm, int num_sms, cudaStream_t st)
+{
+    const int kin = side == 0 ? prm.p : prm.m;
+    const int kout = side == 0 ? prm.m : prm.p;
+    const size_t smem = adjoint_segment_smem(kin, OPT, sizeof(T) == 8);
+    const int oblocks = (kout + 32 * OPT - 1) / (32 * OPT);
+    const int64_t want = (int64_t(2) * num_sms + oblocks - 1) / oblocks;
+    const unsigned batches = static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(prm.n, want)));
+    cudaError_t e = cudaFuncSetAttribute(segment_kernel<T, OPT, side>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    segment_kernel<T, OPT, side><<<dim3(batches, static_cast<unsigned>(oblocks)), kAdjThreads, smem, st>>>(prm);
+    return cudaGetLastError();
 }
 
 cudaError_t adjoint_segments(const AdjSegmentParams& prm, bool f64, int side, int num_sms, cudaStream_t st)
 {
-    const int kin = side == 0 ? prm.p : prm.m;
-    const int kout = side == 0 ? prm.m : prm.p;
-    const size_t smem = adjoint_segment_smem(kin, prm.ob, f64);
-    const int oblocks = (kout + prm.ob - 1) / prm.ob;
-    const int batches = std::max(1, std::min<int>(static_cast<int>(std::min<int64_t>(prm.n, 1 << 20)),
-                                                  (2 * num_sms + oblocks - 1) / oblocks));
-    dim3 grid(static_cast<unsigned>(batches), static_cast<unsigned>(oblocks));
-    cudaError_t e;
-    if (f64) {
-        e = cudaFuncSetAttribute(segment_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-        if (e != cudaSuccess) return e;
-        segment_kernel<double><<<grid, kAdjThreads, smem, st>>>(prm, side);
-    } else {
-        e = cudaFuncSetAttribute(segment_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-        if (e != cudaSuccess) return e;
-        segment_kernel<float><<<grid, kAdjThreads, smem, st>>>(prm, side);
+    switch ((f64 ? 16 : 0) + (side ? 8 : 0) + prm.ob) {
+    case 1: return launch_segments<float, 1, 0>(prm, num_sms, st);
+    case 2: return launch_segments<float, 2, 0>(prm, num_sms, st);
+    case 4: return launch_segments<float, 4, 0>(prm, num_sms, st);
+    case 9: return launch_segments<float, 1, 1>(prm, num_sms, st);
+    case 10: return launch_segments<float, 2, 1>(prm, num_sms, st);
+    case 12: return launch_segments<float, 4, 1>(prm, num_sms, st);
+    case 17: return launch_segments<double, 1, 0>(prm, num_sms, st);
+    case 18: return launch_segments<double, 2, 0>(prm, num_sms, st);
+    case 20: return launch_segments<double, 4, 0>(prm, num_sms, st);
+    case 25: return launch_segments<double, 1, 1>(prm, num_sms, st);
+    case 26: return launch_segments<double, 2, 1>(prm, num_sms, st);
+    case 28: return launch_segments<double, 4, 1>(prm, num_sms, st);
+    default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 cudaError_t adjoint_write_A(const double* src, int64_t n, int64_t m, void* dst, int64_t ld, int dtype, cudaStream_t st)

@@ -675,7 +675,7 @@ mlmc_status mlmc_estimate(mlmc_plan_t* plan, const double* eps_abs, double* yhat
 namespace {
 
 constexpr int64_t kAdjRecordBudget = int64_t(1) << 26;   // default records per replay batch (512 MiB)
-constexpr size_t kAdjSmemLimit = 227 * 1024;
+constexpr int kAdjMaxKin32 = 1584, kAdjMaxKin64 = 696;   // largest m, p the adjoint accepts (FP32, FP64)
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
@@ -820,9 +820,9 @@ mlmc_status mlmc_backward(mlmc_plan_t* plan, const double* G_dev, void* const* d
         if (total == 0) return fail(MLMC_ERR_STATE, "mlmc_backward: problem %zu holds no samples", q);
         for (int side = 0; side < 2; ++side) {
             const int kin = int(side == 0 ? ps.p : ps.m);
-            if (adjoint_segment_smem(kin, adjoint_output_block(kin, plan->f64), plan->f64) > kAdjSmemLimit)
+            if (adjoint_output_block(kin, plan->f64) == 0)
                 return fail(MLMC_ERR_UNSUPPORTED, "problem %zu: the adjoint keeps a block of G with all %d %s on chip; "
-                            "at most %d fit", q, kin, side == 0 ? "columns" : "rows", plan->f64 ? 1204 : 2414);
+                            "at most %d fit", q, kin, side == 0 ? "columns" : "rows", plan->f64 ? kAdjMaxKin64 : kAdjMaxKin32);
         }
         if (ps.n > (int64_t(1) << 30)) return fail(MLMC_ERR_UNSUPPORTED, "problem %zu: the adjoint needs n <= 2^30", q);
     }

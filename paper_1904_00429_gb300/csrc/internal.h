@@ -124,7 +124,7 @@ struct AdjSegmentParams {
     double w_coarse_extra[MLMC_MAX_LEVELS];  // -n / c_{l-1} (l > 0), added on coarse slots
     double inv_N[MLMC_MAX_LEVELS];
     int bf16;               // round the regenerated operands to bfloat16 (straight-through)
-    int ob;                 // outputs per CTA block
+    int ob;                 // register-tile width: the CTA owns 32 * ob outputs (adjoint_output_block)
     double* gM_t;           // n x m staging of dM (the kernels add to the staging)
     double* gS_t;           // n x m staging of dS
     double* gMp;            // n x p
@@ -136,7 +136,8 @@ cudaError_t adjoint_scatter(const AdjLevels& lv, uint2 keyI, int64_t n, int R, i
                             cudaStream_t st);
 int64_t adjoint_scan_scratch(int64_t n);
 cudaError_t adjoint_scan(const int* counts, int64_t n, int64_t* offsets, int64_t* scratch, cudaStream_t st);
-size_t adjoint_segment_smem(int kin, int ob, bool f64);
+size_t adjoint_segment_smem(int kin, int opt, bool f64);
+// Register-tile width (1, 2 or 4) for kin contracted entries; 0 if none fits in shared memory.
 int adjoint_output_block(int kin, bool f64);
 cudaError_t adjoint_segments(const AdjSegmentParams& prm, bool f64, int side, int num_sms, cudaStream_t st);
 cudaError_t adjoint_write_A(const double* src, int64_t n, int64_t m, void* dst, int64_t ld, int dtype, cudaStream_t st);
