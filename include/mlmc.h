@@ -109,7 +109,8 @@ typedef struct {
     int64_t pilot_n;     /* pilot samples per level used by mlmc_estimate (>= 2) */
     double nl_scale;     /* factor on the allocated N_l (Remark 2.6 oversampling control), > 0 */
     int64_t timeout_ns;  /* bound on any device-side wait; 0 = 2 s */
-    int32_t tile_override; /* 0 = automatic tile choice; otherwise an internal tile id */
+    int32_t tile_override; /* BF16 tile: 0 = automatic; else 1000 * (rows / 128) + columns, one of
+                              1032 1064 1128 1256 2032 2064 2128 2256 (e.g. 2128 = 256 x 128) */
     int32_t adjoint_batch_log2; /* mlmc_backward replays at most 2^this sampled products per batch
                                    (0 = 26; at least c_L + 1 are always taken); scratch is 8 B each */
 } mlmc_options;
@@ -176,6 +177,41 @@ MLMC_API mlmc_status mlmc_set_level_state(mlmc_plan_t* plan, int32_t prob, int32
 
 /* Empty the statistics of one level (level < 0: every level of the problem). */
 MLMC_API mlmc_status mlmc_reset_level_stats(mlmc_plan_t* plan, int32_t prob, int32_t level);
+
+/* ---- batched form: many problems and levels in one persistent launch ------------------ */
+
+typedef struct {
+    int32_t prob;
+    int32_t level;
+    uint64_t sample_begin;
+    uint64_t count;
+} mlmc_range;
+
+/* mlmc_level_stats_batch: evaluate every range (samples sample_begin ..
+ * sample_begin+count-1 of level `level` of problem `prob`) and fold it into
+ * that level's statistics, as mlmc_level_stats on the ranges one by one in the
+ * given order would.  BF16: the ranges are cut into (problem, level, chunk of
+ * samples, output tile) work items, packed into waves (at most 1 GiB of chunk
+ * partials, 4096 (problem, level) runs and 2^20 items each), balanced over
+ * persistent CTAs longest item first, and each wave runs as one persistent
+ * kernel launch plus one merge launch; up to four waves are captured in one
+ * CUDA graph, which is replayed while the tile, the CTA count and the number of
+ * waves stay the same.  The tile is options->tile_override if set, else the
+ * autotuner's: the first call times every candidate tile on the first chunk
+ * of each range and keeps the fastest for the plan (mlmc_get_batch_tile).
+ * The per-level sums of D do not depend on the tile; the sums of ||D||^2 are
+ * grouped by output tile, so they agree across tiles up to rounding.  Other
+ * precisions: one launch sequence per range, as mlmc_level_stats.  Problems
+ * whose m x p FP32 partial exceeds 1 GiB: MLMC_ERR_UNSUPPORTED.
+ * Scratch: the first BF16 call allocates 1 GiB of partials and about 40 MiB
+ * of device tables (plus the same in pinned host memory) for the plan. */
+MLMC_API mlmc_status mlmc_level_stats_batch(mlmc_plan_t* plan, const mlmc_range* ranges, int32_t count);
+
+/* Tile of the batched BF16 launches as a tile id (see mlmc_options), 0 before
+ * the first batched call.  timings_ms (host array of 8, may be NULL) receives
+ * the autotuner's time in ms of each candidate in the order 1032 1064 1128
+ * 1256 2032 2064 2128 2256 (negative: not tried). */
+MLMC_API mlmc_status mlmc_get_batch_tile(const mlmc_plan_t* plan, int32_t* tile_id, double* timings_ms);
 
 /* ---- estimator (Alg. 2 with the finest level fixed) ---------------------------------- */
 

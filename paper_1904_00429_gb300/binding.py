@@ -49,6 +49,11 @@ class Options(ctypes.Structure):
                 ("timeout_ns", ctypes.c_int64), ("tile_override", ctypes.c_int32), ("adjoint_batch_log2", ctypes.c_int32)]
 
 
+class Range(ctypes.Structure):
+    _fields_ = [("prob", ctypes.c_int32), ("level", ctypes.c_int32), ("sample_begin", ctypes.c_uint64),
+                ("count", ctypes.c_uint64)]
+
+
 class Report(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("N", ctypes.c_int64 * MAX_LEVELS), ("V", ctypes.c_double * MAX_LEVELS),
@@ -81,6 +86,8 @@ def lib() -> ctypes.CDLL:
             "mlmc_plan": [P, I32, P, P, P],
             "mlmc_plan_destroy": [P],
             "mlmc_level_stats": [P, I32, I32, U64, U64],
+            "mlmc_level_stats_batch": [P, P, I32],
+            "mlmc_get_batch_tile": [P, P, P],
             "mlmc_get_level_stats": [P, I32, I32, P, P, P],
             "mlmc_get_level_state": [P, I32, I32, P, P, P],
             "mlmc_set_level_state": [P, I32, I32, U64, P, D],
@@ -209,6 +216,20 @@ class Plan:
     # -- Alg. 1, incremental ------------------------------------------------------------------
     def level_stats(self, prob: int, level: int, begin: int, count: int):
         _check(lib().mlmc_level_stats(self._h, prob, level, begin, count), "mlmc_level_stats")
+
+    def level_stats_batch(self, ranges):
+        """``ranges``: iterable of (prob, level, begin, count); one batched launch sequence."""
+        ranges = list(ranges)
+        arr = (Range * max(1, len(ranges)))(*[Range(int(q), int(l), int(b), int(c)) for q, l, b, c in ranges])
+        _check(lib().mlmc_level_stats_batch(self._h, arr, len(ranges)), "mlmc_level_stats_batch")
+
+    def batch_tile(self):
+        """(tile id of the batched launches, autotuner ms per candidate tile id)."""
+        tid = ctypes.c_int32()
+        ms = (ctypes.c_double * 8)()
+        _check(lib().mlmc_get_batch_tile(self._h, ctypes.byref(tid), ms), "mlmc_get_batch_tile")
+        ids = (1032, 1064, 1128, 1256, 2032, 2064, 2128, 2256)
+        return tid.value, {i: ms[k] for k, i in enumerate(ids) if ms[k] >= 0}
 
     def get_level_stats(self, prob: int, level: int):
         """(N, mean (m x p FP64 CUDA tensor), M2 = sum_s ||D_s - mean||_F^2)."""

@@ -67,6 +67,7 @@ struct ProblemState {
     bool has_estimate = false;
     ProblemState() { std::fill(prefix, prefix + MLMC_MAX_LEVELS, true); }
     int tiles_m = 1, tiles_p = 1;
+    TcTile tile{0, 0, 0};   // tensor-core tile of the single-problem launches
     int max_chunks = 1;
 };
 
@@ -91,6 +92,18 @@ struct mlmc_plan_s {
     // adjoint scratch, grown on demand
     void* adj_buf = nullptr;
     size_t adj_bytes = 0;
+    // batched launches (created on the first mlmc_level_stats_batch)
+    TcTile batch_tile{0, 0, 0};
+    double tune_ms[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
+    int batch_grid = 0;
+    float* batch_partial = nullptr;
+    double* batch_q = nullptr;
+    unsigned char* batch_dev = nullptr;    // tables of kBatchMaxWaves waves
+    unsigned char* batch_host = nullptr;   // pinned staging of the same
+    cudaEvent_t batch_copied = nullptr;    // recorded after the last table upload
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t batch_exec = nullptr;
+    std::vector<int64_t> batch_key;
 };
 
 namespace {
@@ -150,6 +163,17 @@ double level_cost(const mlmc_options& o, int l)
 
 uint2 key(uint32_t seed, uint32_t pid) { return make_uint2(seed, pid); }
 
+// Tile ids: 1000 * (rows / 128) + columns, e.g. 2128 = 256 rows x 128 columns.
+TcTile decode_tile(int32_t id)
+{
+    TcTile t{id / 1000, id % 1000, 128 * (id / 1000)};
+    return t;
+}
+
+int32_t encode_tile(const TcTile& t) { return t.mh > 0 ? 1000 * t.mh + t.bn : 0; }
+
+const int32_t kTileIds[8] = {1032, 1064, 1128, 1256, 2032, 2064, 2128, 2256};
+
 mlmc_status validate(const mlmc_problem* problems, int32_t nprob, const mlmc_options* o)
 {
     if (!problems || nprob < 1) return fail(MLMC_ERR_INVALID_ARG, "need at least one problem");
@@ -164,6 +188,8 @@ mlmc_status validate(const mlmc_problem* problems, int32_t nprob, const mlmc_opt
     if (o->precision == MLMC_FP8_E4M3) return fail(MLMC_ERR_UNSUPPORTED, "FP8 E4M3 is not available in this build");
     if (!(o->nl_scale > 0.0) || !std::isfinite(o->nl_scale)) return fail(MLMC_ERR_INVALID_ARG, "nl_scale must be > 0");
     if (o->timeout_ns < 0) return fail(MLMC_ERR_INVALID_ARG, "timeout_ns must be >= 0");
+    if (o->tile_override != 0 && !tc_tile_valid(decode_tile(o->tile_override)))
+        return fail(MLMC_ERR_INVALID_ARG, "tile_override %d is not a tile id (1032 .. 2256)", o->tile_override);
     if (o->adjoint_batch_log2 < 0 || o->adjoint_batch_log2 > 40)
         return fail(MLMC_ERR_INVALID_ARG, "adjoint_batch_log2 must be in [0, 40]");
     for (int32_t q = 0; q < nprob; ++q) {
@@ -201,6 +227,13 @@ void free_plan(mlmc_plan_t* plan)
     cudaFree(plan->M2_dev);
     cudaFree(plan->err_flag);
     cudaFree(plan->adj_buf);
+    cudaFree(plan->batch_partial);
+    cudaFree(plan->batch_q);
+    cudaFree(plan->batch_dev);
+    if (plan->batch_host) cudaFreeHost(plan->batch_host);
+    if (plan->batch_copied) cudaEventDestroy(plan->batch_copied);
+    if (plan->batch_exec) cudaGraphExecDestroy(plan->batch_exec);
+    if (plan->capture_stream) cudaStreamDestroy(plan->capture_stream);
 }
 
 bool tensor_core_precision(int precision) { return precision == MLMC_BF16 || precision == MLMC_FP8_E4M3; }
@@ -271,7 +304,7 @@ mlmc_status run_level(mlmc_plan_t* plan, ProblemState& ps, int level, uint64_t s
         cudaError_t err;
         if (o.precision == MLMC_BF16) {
             TcLaunch tl{plan->err_flag, plan->timeout_ns, static_cast<float>(double(ps.n) / double(c)), plan->num_sms};
-            err = launch_level_tc_bf16(prm, tl, plan->stream);
+            err = launch_level_tc_bf16(prm, ps.tile, tl, plan->stream);
         } else {
             err = plan->f64 ? launch_level_cuda_core_f64(prm, plan->stream)
                             : launch_level_cuda_core_f32(prm, plan->stream);
@@ -281,6 +314,355 @@ mlmc_status run_level(mlmc_plan_t* plan, ProblemState& ps, int level, uint64_t s
         err = launch_merge_partials(plan->partial_sum, plan->f64, plan->partial_q, nb, ps.tiles_m * ps.tiles_p,
                                     ps.m * ps.p, sum, sumsq, plan->stream);
         if (check_cuda(plan, err, "merge kernel launch") != MLMC_OK) return plan->sticky;
+    }
+    return MLMC_OK;
+}
+
+// ---- batched form ---------------------------------------------------------------------
+
+constexpr size_t kBatchPartialBytes = size_t(1) << 30;  // FP32 chunk partials of one wave
+constexpr int kBatchMaxJobs = 4096;                     // jobs (problem, level, chunk run) per wave
+constexpr int kBatchMaxItems = 1 << 20;                 // (job, chunk, tile) items per wave
+constexpr int kBatchMaxWaves = 4;                       // waves per graph launch
+constexpr int kBatchMaxGrid = 4096;
+constexpr int kMergeMaxChunks = 4096;
+
+struct BatchRange {
+    int prob, level;
+    uint64_t s0, count;
+};
+
+struct BatchWave {
+    std::vector<LevelParams> jobs;
+    std::vector<MergeJob> merges;
+    std::vector<std::pair<double, uint64_t>> items;   // (cost, packed item)
+    std::vector<uint64_t> packed;                      // items grouped by CTA
+    std::vector<int> cta_begin;                        // grid + 1
+};
+
+// Byte layout of one wave's device tables.
+struct WaveLayout {
+    size_t jobs, merges, njobs, cta, items, stride;
+    WaveLayout()
+    {
+        jobs = 0;
+        merges = jobs + sizeof(LevelParams) * kBatchMaxJobs;
+        njobs = merges + sizeof(MergeJob) * kBatchMaxJobs;
+        cta = njobs + 256;
+        items = cta + ((sizeof(int) * (kBatchMaxGrid + 1) + 255) & ~size_t(255));
+        stride = items + sizeof(uint64_t) * kBatchMaxItems;
+    }
+};
+
+LevelParams base_params(const mlmc_plan_t* plan, const ProblemState& ps, int level)
+{
+    const mlmc_options& o = plan->opt;
+    const int64_t c = level_c(o, level);
+    LevelParams prm{};
+    prm.PA = ps.PAB;
+    prm.PB = static_cast<const unsigned char*>(ps.PAB) + size_t(2 * ps.m_pad) * plan->elem;
+    prm.ldPA = ps.ld;
+    prm.ldPB = ps.ld;
+    prm.n = ps.n;
+    prm.m = int(ps.m);
+    prm.p = int(ps.p);
+    prm.m_pad = int(ps.m_pad);
+    prm.p_pad = int(ps.p_pad);
+    prm.l = level;
+    prm.c = int(c);
+    prm.R = o.ratio;
+    prm.w_fine = double(ps.n) / double(c);
+    prm.w_coarse = level > 0 ? double(ps.n) / double(c) - double(ps.n) / double(c / o.ratio) : 0.0;
+    prm.keyA = key(ps.desc.seed_A, ps.desc.problem_id);
+    prm.keyB = key(ps.desc.seed_B, ps.desc.problem_id);
+    prm.keyI = key(ps.desc.seed_idx, ps.desc.problem_id);
+    prm.rkA = philox_round_keys(prm.keyA);
+    prm.rkB = philox_round_keys(prm.keyB);
+    prm.chunk = chunk_samples(c);
+    return prm;
+}
+
+// Cut the ranges into waves of (problem, level, chunk run) jobs and their (chunk, tile) items,
+// then balance each wave's items over `grid` persistent CTAs, longest first.
+mlmc_status build_waves(mlmc_plan_t* plan, const std::vector<BatchRange>& ranges, const TcTile& tile, int grid,
+                        std::vector<BatchWave>& waves)
+{
+    waves.clear();
+    size_t part_off = 0, q_off = 0;
+    std::vector<int64_t> in_wave;   // prob * MLMC_MAX_LEVELS + level of the open wave's jobs
+    auto open_wave = [&]() {
+        waves.emplace_back();
+        part_off = q_off = 0;
+        in_wave.clear();
+    };
+    open_wave();
+    for (const BatchRange& r : ranges) {
+        if (r.count == 0) continue;
+        ProblemState& ps = plan->probs[size_t(r.prob)];
+        const int64_t mp = ps.m * ps.p;
+        const int tm = int((ps.m + tile.rows - 1) / tile.rows), tp = int((ps.p + tile.bn - 1) / tile.bn);
+        const int tiles = tm * tp;
+        if (size_t(mp) * 4 > kBatchPartialBytes || tiles > 65535)
+            return fail(MLMC_ERR_UNSUPPORTED, "problem %d is too large for the batched launch", r.prob);
+        LevelParams base = base_params(plan, ps, r.level);
+        base.tiles_m = tm;
+        base.tiles_p = tp;
+        const uint64_t ch = uint64_t(base.chunk);
+        const uint64_t s_end = r.s0 + r.count;
+        uint64_t cb = r.s0 / ch;
+        const uint64_t last = (s_end - 1) / ch;
+        const int nsub = (base.c + 15) / 16;
+        const double per_sample = double(nsub) * 16.0 * double(tile.rows + tile.bn) + double(tile.rows) * tile.bn / 4.0;
+        const int64_t lvkey = int64_t(r.prob) * MLMC_MAX_LEVELS + r.level;
+        while (cb <= last) {
+            BatchWave* w = &waves.back();
+            if (std::find(in_wave.begin(), in_wave.end(), lvkey) != in_wave.end() ||
+                int(w->jobs.size()) >= kBatchMaxJobs) {
+                open_wave();
+                continue;
+            }
+            const size_t cap = kBatchPartialBytes / 4;
+            const uint64_t by_part = part_off < cap ? (cap - part_off) / uint64_t(mp) : 0;
+            const uint64_t by_items = uint64_t(kBatchMaxItems - int(w->items.size())) / uint64_t(tiles);
+            const uint64_t room = std::min<uint64_t>({by_part, by_items, uint64_t(kMergeMaxChunks)});
+            if (room == 0) {
+                if (w->jobs.empty()) return fail(MLMC_ERR_UNSUPPORTED, "batched wave cannot hold one chunk");
+                open_wave();
+                continue;
+            }
+            const uint64_t nb = std::min<uint64_t>(room, last - cb + 1);
+            LevelParams prm = base;
+            prm.chunk0 = cb;
+            prm.nchunks = int(nb);
+            prm.s_begin = std::max<uint64_t>(r.s0, cb * ch);
+            prm.s_end = std::min<uint64_t>(s_end, (cb + nb) * ch);
+            prm.partial_sum = plan->batch_partial + part_off;
+            prm.partial_q = plan->batch_q + q_off;
+            const int job = int(w->jobs.size());
+            w->jobs.push_back(prm);
+            MergeJob mj{plan->batch_partial + part_off, plan->batch_q + q_off, ps.sum + int64_t(r.level) * mp,
+                        ps.sumsq + r.level, mp, int(nb), tiles};
+            w->merges.push_back(mj);
+            for (uint64_t cy = 0; cy < nb; ++cy) {
+                const uint64_t a = std::max<uint64_t>(prm.s_begin, (cb + cy) * ch);
+                const uint64_t b = std::min<uint64_t>(prm.s_end, (cb + cy + 1) * ch);
+                const double cost = double(b - a) * per_sample;
+                for (int t = 0; t < tiles; ++t)
+                    w->items.emplace_back(cost, uint64_t(job) | (cy << 16) | (uint64_t(t) << 48));
+            }
+            // every job's partials start on a 256-byte boundary: the drain stores float4 vectors
+            part_off = (part_off + size_t(nb) * size_t(mp) + 63) & ~size_t(63);
+            q_off += size_t(nb) * size_t(tiles);
+            in_wave.push_back(lvkey);
+            cb += nb;
+        }
+    }
+    if (waves.back().jobs.empty()) waves.pop_back();
+    // longest processing time first onto the least loaded CTA
+    for (BatchWave& w : waves) {
+        std::stable_sort(w.items.begin(), w.items.end(),
+                         [](const auto& x, const auto& y) { return x.first > y.first; });
+        std::vector<std::vector<uint64_t>> per(static_cast<size_t>(grid));
+        std::vector<std::pair<double, int>> heap;
+        for (int b = 0; b < grid; ++b) heap.emplace_back(0.0, b);
+        auto cmp = [](const std::pair<double, int>& x, const std::pair<double, int>& y) {
+            return x.first > y.first || (x.first == y.first && x.second > y.second);
+        };
+        std::make_heap(heap.begin(), heap.end(), cmp);
+        for (const auto& it : w.items) {
+            std::pop_heap(heap.begin(), heap.end(), cmp);
+            auto& top = heap.back();
+            per[size_t(top.second)].push_back(it.second);
+            top.first += it.first;
+            std::push_heap(heap.begin(), heap.end(), cmp);
+        }
+        w.packed.clear();
+        w.cta_begin.assign(size_t(grid) + 1, 0);
+        for (int b = 0; b < grid; ++b) {
+            w.cta_begin[size_t(b)] = int(w.packed.size());
+            w.packed.insert(w.packed.end(), per[size_t(b)].begin(), per[size_t(b)].end());
+        }
+        w.cta_begin[size_t(grid)] = int(w.packed.size());
+    }
+    return MLMC_OK;
+}
+
+mlmc_status batch_setup(mlmc_plan_t* plan)
+{
+    if (plan->batch_dev) return MLMC_OK;
+    cudaError_t err = cudaMalloc(reinterpret_cast<void**>(&plan->batch_partial), kBatchPartialBytes + 256);
+    if (err == cudaSuccess) err = cudaMalloc(reinterpret_cast<void**>(&plan->batch_q), sizeof(double) * kBatchMaxItems);
+    const size_t bytes = WaveLayout().stride * kBatchMaxWaves;
+    if (err == cudaSuccess) err = cudaMalloc(reinterpret_cast<void**>(&plan->batch_dev), bytes);
+    if (err == cudaSuccess) err = cudaMallocHost(reinterpret_cast<void**>(&plan->batch_host), bytes);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&plan->batch_copied, cudaEventDisableTiming);
+    if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&plan->capture_stream, cudaStreamNonBlocking);
+    return check_cuda(plan, err, "batched-launch setup");
+}
+
+// Stage waves [first, first + count) into table slots 0.. and upload them on the plan's stream.
+mlmc_status upload_waves(mlmc_plan_t* plan, const std::vector<BatchWave>& waves, size_t first, size_t count)
+{
+    const WaveLayout L;
+    cudaError_t err = cudaEventSynchronize(plan->batch_copied);   // the pinned slots are free again
+    if (check_cuda(plan, err, "batched table staging") != MLMC_OK) return plan->sticky;
+    for (size_t i = 0; i < count; ++i) {
+        const BatchWave& w = waves[first + i];
+        unsigned char* h = plan->batch_host + i * L.stride;
+        unsigned char* d = plan->batch_dev + i * L.stride;
+        const int nj = int(w.jobs.size());
+        std::memcpy(h + L.jobs, w.jobs.data(), sizeof(LevelParams) * size_t(nj));
+        std::memcpy(h + L.merges, w.merges.data(), sizeof(MergeJob) * size_t(nj));
+        std::memcpy(h + L.njobs, &nj, sizeof(int));
+        std::memcpy(h + L.cta, w.cta_begin.data(), sizeof(int) * w.cta_begin.size());
+        std::memcpy(h + L.items, w.packed.data(), sizeof(uint64_t) * w.packed.size());
+        // one copy per table region actually used
+        const std::pair<size_t, size_t> parts[] = {{L.jobs, sizeof(LevelParams) * size_t(nj)},
+                                                   {L.merges, sizeof(MergeJob) * size_t(nj)},
+                                                   {L.njobs, sizeof(int)},
+                                                   {L.cta, sizeof(int) * w.cta_begin.size()},
+                                                   {L.items, sizeof(uint64_t) * w.packed.size()}};
+        for (const auto& pr : parts) {
+            if (pr.second == 0) continue;
+            err = cudaMemcpyAsync(d + pr.first, h + pr.first, pr.second, cudaMemcpyHostToDevice, plan->stream);
+            if (check_cuda(plan, err, "batched table upload") != MLMC_OK) return plan->sticky;
+        }
+    }
+    err = cudaEventRecord(plan->batch_copied, plan->stream);
+    return check_cuda(plan, err, "batched table upload");
+}
+
+TcBatch wave_tables(const mlmc_plan_t* plan, size_t slot)
+{
+    const WaveLayout L;
+    unsigned char* d = plan->batch_dev + slot * L.stride;
+    return TcBatch{reinterpret_cast<const LevelParams*>(d + L.jobs), reinterpret_cast<const uint64_t*>(d + L.items),
+                   reinterpret_cast<const int*>(d + L.cta)};
+}
+
+// Kernel launches of `count` staged waves on stream `st` (captured into the graph).
+cudaError_t enqueue_waves(mlmc_plan_t* plan, size_t count, bool merge, cudaStream_t st)
+{
+    const WaveLayout L;
+    TcLaunch tl{plan->err_flag, plan->timeout_ns, 0.0f, plan->num_sms};
+    for (size_t i = 0; i < count; ++i) {
+        cudaError_t err = launch_level_tc_bf16_batch(wave_tables(plan, i), plan->batch_tile, plan->batch_grid, tl, st);
+        if (err != cudaSuccess) return err;
+        if (merge) {
+            unsigned char* d = plan->batch_dev + i * L.stride;
+            err = launch_merge_batch(reinterpret_cast<const MergeJob*>(d + L.merges),
+                                     reinterpret_cast<const int*>(d + L.njobs), st);
+            if (err != cudaSuccess) return err;
+        }
+    }
+    return cudaSuccess;
+}
+
+// Autotuner: time every candidate tile on the first chunk of each range and keep the fastest.
+mlmc_status autotune_batch_tile(mlmc_plan_t* plan, const std::vector<BatchRange>& ranges)
+{
+    int64_t mmax = 1, pmax = 1;
+    for (const auto& ps : plan->probs) {
+        mmax = std::max(mmax, ps.m);
+        pmax = std::max(pmax, ps.p);
+    }
+    std::vector<BatchRange> probe;
+    for (const BatchRange& r : ranges) {
+        if (r.count == 0) continue;
+        const uint64_t ch = uint64_t(chunk_samples(level_c(plan->opt, r.level)));
+        const uint64_t end = std::min<uint64_t>(r.s0 + r.count, (r.s0 / ch + 1) * ch);
+        probe.push_back(BatchRange{r.prob, r.level, r.s0, end - r.s0});
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t err = cudaEventCreate(&e0);
+    if (err == cudaSuccess) err = cudaEventCreate(&e1);
+    if (check_cuda(plan, err, "autotuner events") != MLMC_OK) return plan->sticky;
+    double best = 1e300;
+    TcTile best_tile = tc_tile_for(mmax, pmax);
+    mlmc_status st = MLMC_OK;
+    for (int c = 0; c < 8 && st == MLMC_OK; ++c) {
+        const TcTile t = decode_tile(kTileIds[c]);
+        plan->tune_ms[c] = -1.0;
+        // skip tiles far wider or taller than every problem
+        if ((t.mh == 2 && mmax <= 128) || (t.bn > 32 && pmax <= t.bn / 2)) continue;
+        const int grid = std::min(tc_batch_grid(t, plan->num_sms), kBatchMaxGrid);
+        if (grid <= 0) continue;
+        std::vector<BatchWave> waves;
+        if ((st = build_waves(plan, probe, t, grid, waves)) != MLMC_OK) break;
+        if (waves.empty()) break;
+        if ((st = upload_waves(plan, waves, 0, 1)) != MLMC_OK) break;
+        plan->batch_tile = t;
+        plan->batch_grid = grid;
+        float ms = 0.0f;
+        err = enqueue_waves(plan, 1, false, plan->stream);   // warm-up (partials only, no merge)
+        if (err == cudaSuccess) err = cudaEventRecord(e0, plan->stream);
+        if (err == cudaSuccess) err = enqueue_waves(plan, 1, false, plan->stream);
+        if (err == cudaSuccess) err = cudaEventRecord(e1, plan->stream);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        if ((st = check_cuda(plan, err, "autotuner launch")) != MLMC_OK) break;
+        if ((st = check_device_flag(plan)) != MLMC_OK) break;
+        plan->launches += 2;
+        plan->tune_ms[c] = ms;
+        if (ms < best) {
+            best = ms;
+            best_tile = t;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != MLMC_OK) return st;
+    plan->batch_tile = best_tile;
+    plan->batch_grid = std::min(tc_batch_grid(best_tile, plan->num_sms), kBatchMaxGrid);
+    return plan->batch_grid > 0 ? MLMC_OK : set_sticky(plan, fail(MLMC_ERR_CUDA, "batched grid query failed"));
+}
+
+mlmc_status run_batch(mlmc_plan_t* plan, const std::vector<BatchRange>& ranges)
+{
+    mlmc_status st = batch_setup(plan);
+    if (st != MLMC_OK) return st;
+    if (plan->batch_tile.mh == 0) {
+        if (plan->opt.tile_override) {
+            plan->batch_tile = decode_tile(plan->opt.tile_override);
+            plan->batch_grid = std::min(tc_batch_grid(plan->batch_tile, plan->num_sms), kBatchMaxGrid);
+            if (plan->batch_grid <= 0) return set_sticky(plan, fail(MLMC_ERR_CUDA, "batched grid query failed"));
+        } else if ((st = autotune_batch_tile(plan, ranges)) != MLMC_OK) {
+            return st;
+        }
+    }
+    std::vector<BatchWave> waves;
+    if ((st = build_waves(plan, ranges, plan->batch_tile, plan->batch_grid, waves)) != MLMC_OK) return st;
+    for (size_t w0 = 0; w0 < waves.size(); w0 += kBatchMaxWaves) {
+        const size_t cnt = std::min<size_t>(kBatchMaxWaves, waves.size() - w0);
+        if ((st = upload_waves(plan, waves, w0, cnt)) != MLMC_OK) return st;
+        // the graph depends only on the tile, the grid and the number of waves
+        const std::vector<int64_t> key = {encode_tile(plan->batch_tile), plan->batch_grid, int64_t(cnt)};
+        if (!plan->batch_exec || key != plan->batch_key) {
+            if (plan->batch_exec) {
+                cudaGraphExecDestroy(plan->batch_exec);
+                plan->batch_exec = nullptr;
+            }
+            cudaGraph_t graph = nullptr;
+            cudaError_t err = cudaStreamBeginCapture(plan->capture_stream, cudaStreamCaptureModeThreadLocal);
+            if (err == cudaSuccess) {
+                const cudaError_t lerr = enqueue_waves(plan, cnt, true, plan->capture_stream);
+                err = cudaStreamEndCapture(plan->capture_stream, &graph);
+                if (lerr != cudaSuccess) err = lerr;
+            }
+            if (err == cudaSuccess) err = cudaGraphInstantiate(&plan->batch_exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (check_cuda(plan, err, "batched graph capture") != MLMC_OK) return plan->sticky;
+            plan->batch_key = key;
+        }
+        cudaError_t err = cudaGraphLaunch(plan->batch_exec, plan->stream);
+        if (check_cuda(plan, err, "batched graph launch") != MLMC_OK) return plan->sticky;
+        plan->launches += 2 * cnt;
+    }
+    for (const BatchRange& r : ranges) {
+        if (r.count == 0) continue;
+        ProblemState& ps = plan->probs[size_t(r.prob)];
+        ps.prefix[r.level] = ps.prefix[r.level] && r.s0 == ps.N.v[r.level];
+        ps.N.v[r.level] += r.count;
     }
     return MLMC_OK;
 }
@@ -341,7 +723,8 @@ mlmc_status mlmc_plan(const mlmc_problem* problems, int32_t nprob, const mlmc_op
         ps.m_pad = (ps.m + 3) / 4 * 4;
         ps.p_pad = (ps.p + 3) / 4 * 4;
         if (tensor_core_precision(options->precision)) {
-            const TcTile tile = tc_tile_for(ps.m, ps.p);
+            const TcTile tile = options->tile_override ? decode_tile(options->tile_override) : tc_tile_for(ps.m, ps.p);
+            ps.tile = tile;
             ps.tiles_m = int((ps.m + tile.rows - 1) / tile.rows);
             ps.tiles_p = int((ps.p + tile.bn - 1) / tile.bn);
         } else {
@@ -436,6 +819,45 @@ mlmc_status mlmc_level_stats(mlmc_plan_t* plan, int32_t prob, int32_t level, uin
         ps.prefix[level] = ps.prefix[level] && continues;
     }
     return st;
+}
+
+mlmc_status mlmc_level_stats_batch(mlmc_plan_t* plan, const mlmc_range* ranges, int32_t count)
+{
+    mlmc_status st = enter(plan);
+    if (st != MLMC_OK) return st;
+    if (count < 0 || (count > 0 && !ranges)) return fail(MLMC_ERR_INVALID_ARG, "bad range list");
+    std::vector<BatchRange> rs;
+    for (int32_t i = 0; i < count; ++i) {
+        const mlmc_range& r = ranges[i];
+        if ((st = check_prob_level(plan, r.prob, r.level)) != MLMC_OK) return st;
+        if (r.sample_begin + r.count < r.sample_begin || r.sample_begin + r.count > (uint64_t(1) << 56))
+            return fail(MLMC_ERR_INVALID_ARG, "range %d: sample ids must stay below 2^56", i);
+        if (r.count > 0) rs.push_back(BatchRange{r.prob, r.level, r.sample_begin, r.count});
+    }
+    if (rs.empty()) return MLMC_OK;
+    DeviceGuard g(plan->device);
+    if (plan->opt.precision != MLMC_BF16) {
+        for (const BatchRange& r : rs) {
+            ProblemState& ps = plan->probs[size_t(r.prob)];
+            const int64_t mp = ps.m * ps.p;
+            const bool continues = r.s0 == ps.N.v[r.level];
+            st = run_level(plan, ps, r.level, r.s0, r.count, ps.sum + int64_t(r.level) * mp, ps.sumsq + r.level);
+            if (st != MLMC_OK) return st;
+            ps.N.v[r.level] += r.count;
+            ps.prefix[r.level] = ps.prefix[r.level] && continues;
+        }
+        return MLMC_OK;
+    }
+    return run_batch(plan, rs);
+}
+
+mlmc_status mlmc_get_batch_tile(const mlmc_plan_t* plan, int32_t* tile_id, double* timings_ms)
+{
+    if (!plan || !tile_id) return fail(MLMC_ERR_INVALID_ARG, "null argument");
+    *tile_id = encode_tile(plan->batch_tile);
+    if (timings_ms)
+        for (int c = 0; c < 8; ++c) timings_ms[c] = plan->tune_ms[c];
+    return MLMC_OK;
 }
 
 mlmc_status mlmc_get_level_stats(mlmc_plan_t* plan, int32_t prob, int32_t level, uint64_t* N, double* mean_dev,
@@ -597,21 +1019,34 @@ mlmc_status mlmc_estimate(mlmc_plan_t* plan, const double* eps_abs, double* yhat
     DeviceGuard g(plan->device);
     const mlmc_options& o = plan->opt;
     const uint64_t pilot = uint64_t(o.pilot_n);
-    // pilot run on every level of every problem
-    for (auto& ps : plan->probs) {
-        const int64_t mp = ps.m * ps.p;
-        for (int l = 0; l <= ps.L; ++l) {
-            if (ps.N.v[l] >= pilot) continue;
-            const uint64_t have = ps.N.v[l];
-            st = run_level(plan, ps, l, have, pilot - have, ps.sum + int64_t(l) * mp, ps.sumsq + l);
-            if (st != MLMC_OK) return st;
-            ps.N.v[l] = pilot;
+    // several problems in BF16 go through the batched persistent launch
+    const bool batched = o.precision == MLMC_BF16 && plan->probs.size() > 1;
+    auto run_ranges = [&](const std::vector<BatchRange>& rs) -> mlmc_status {
+        if (batched) return run_batch(plan, rs);
+        for (const BatchRange& r : rs) {
+            ProblemState& ps = plan->probs[size_t(r.prob)];
+            const int64_t mp = ps.m * ps.p;
+            const bool continues = r.s0 == ps.N.v[r.level];
+            mlmc_status s2 = run_level(plan, ps, r.level, r.s0, r.count, ps.sum + int64_t(r.level) * mp,
+                                       ps.sumsq + r.level);
+            if (s2 != MLMC_OK) return s2;
+            ps.N.v[r.level] += r.count;
+            ps.prefix[r.level] = ps.prefix[r.level] && continues;
         }
+        return MLMC_OK;
+    };
+    // pilot run on every level of every problem
+    std::vector<BatchRange> todo;
+    for (size_t q = 0; q < plan->probs.size(); ++q) {
+        const ProblemState& ps = plan->probs[q];
+        for (int l = 0; l <= ps.L; ++l)
+            if (ps.N.v[l] < pilot) todo.push_back(BatchRange{int(q), l, ps.N.v[l], pilot - ps.N.v[l]});
     }
+    if ((st = run_ranges(todo)) != MLMC_OK) return st;
     // allocation from the pilot variances, then top-ups from the next unused sample id
+    todo.clear();
     for (size_t q = 0; q < plan->probs.size(); ++q) {
         ProblemState& ps = plan->probs[q];
-        const int64_t mp = ps.m * ps.p;
         double M2[MLMC_MAX_LEVELS];
         if ((st = level_M2(plan, ps, 0, ps.L + 1, M2)) != MLMC_OK) return st;
         double V[MLMC_MAX_LEVELS], C[MLMC_MAX_LEVELS], root_sum = 0.0;
@@ -626,14 +1061,10 @@ mlmc_status mlmc_estimate(mlmc_plan_t* plan, const double* eps_abs, double* yhat
             if (!(target < 9.0e18)) return set_sticky(plan, fail(MLMC_ERR_NUMERIC, "allocated N_l overflows"));
             const uint64_t nl = std::max<uint64_t>(uint64_t(std::ceil(target)), pilot);
             ps.Nl_est[l] = int64_t(std::max<uint64_t>(nl, ps.N.v[l]));
-            if (nl > ps.N.v[l]) {
-                const uint64_t have = ps.N.v[l];
-                st = run_level(plan, ps, l, have, nl - have, ps.sum + int64_t(l) * mp, ps.sumsq + l);
-                if (st != MLMC_OK) return st;
-                ps.N.v[l] = nl;
-            }
+            if (nl > ps.N.v[l]) todo.push_back(BatchRange{int(q), l, ps.N.v[l], nl - ps.N.v[l]});
         }
     }
+    if ((st = run_ranges(todo)) != MLMC_OK) return st;
     // telescoping sum and report
     int64_t off = 0;
     for (size_t q = 0; q < plan->probs.size(); ++q) {

@@ -67,8 +67,35 @@ struct TcLaunch {
     float scale;          // n / c_l, applied to the FP32 accumulator
     int num_sms;
 };
+// Batched launch: CTA b processes items[cta_begin[b] .. cta_begin[b+1]); an item packs
+// job (bits 0-15, index into jobs), chunk cy (bits 16-47) and output tile (bits 48-63).
+struct TcBatch {
+    const LevelParams* jobs;
+    const uint64_t* items;
+    const int* cta_begin;
+};
+
 TcTile tc_tile_for(int64_t m, int64_t p);
-cudaError_t launch_level_tc_bf16(const LevelParams& prm, const TcLaunch& tl, cudaStream_t st);
+bool tc_tile_valid(const TcTile& t);
+cudaError_t launch_level_tc_bf16(const LevelParams& prm, const TcTile& tile, const TcLaunch& tl, cudaStream_t st);
+// CTAs of a batched launch for this tile (resident CTAs per SM x SMs); 0 on error.  Also sets
+// the kernel's shared-memory attribute, which launch_level_tc_bf16_batch relies on.
+int tc_batch_grid(const TcTile& tile, int num_sms);
+cudaError_t launch_level_tc_bf16_batch(const TcBatch& bt, const TcTile& tile, int grid, const TcLaunch& tl,
+                                       cudaStream_t st);
+
+// One job of a batched merge: nchunks FP32 chunk partials of an m x p level (mp elements) and
+// their per-tile sums of squares, folded into the level's FP64 sum and sumsq.
+struct MergeJob {
+    const float* partial;
+    const double* partial_q;
+    double* sum;
+    double* sumsq;
+    int64_t mp;
+    int nchunks;   // <= 4096
+    int tiles;
+};
+cudaError_t launch_merge_batch(const MergeJob* jobs, const int* njobs_dev, cudaStream_t st);
 
 // Fold the partials of one launch into a level's FP64 state, in chunk order.
 cudaError_t launch_merge_partials(const void* partial_sum, bool partial_f64, const double* partial_q,

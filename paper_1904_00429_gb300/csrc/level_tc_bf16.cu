@@ -53,7 +53,8 @@ struct TcCfg {
                                      : kTileCols <= 256 ? 256 : 512;
     // barriers: full[2], empty[2], slice[4], done
     static constexpr int kNumBars = 2 + 2 + kSlices + 1;
-    static constexpr int kBookBytes = 2 * kSub * 4 /*idx*/ + kNumBars * 8 + 16 /*tmem, abort*/ + kGenWarps * 8;
+    static constexpr int kBookBytes = 2 * kSub * 4 /*idx*/ + kNumBars * 8 + 16 /*tmem, abort*/ + kGenWarps * 8 +
+                                      2 * static_cast<int>(sizeof(LevelParams)) /*job copies*/;
     static constexpr int kSmemBytes = 1024 /*align slack*/ + kTileBytes + 2 * kStageBytes + kBookBytes;
     static_assert(kTileCols <= 512, "tile exceeds tensor memory");
     static_assert(BN % 16 == 0 && BN >= 32 && BN <= 256, "N of the MMA");
@@ -113,8 +114,9 @@ __device__ __forceinline__ void gen_block(const int* idx, int slot0, bool valid_
     }
 }
 
-template <int MH, int BN>
-__global__ void __launch_bounds__(kThreads, 1) level_tc_bf16_kernel(const LevelParams prm, const TcExtra ex)
+template <int MH, int BN, bool kBatch>
+__global__ void __launch_bounds__(kThreads, 1)
+level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra ex, const TcBatch bt)
 {
     using C = TcCfg<MH, BN>;
     extern __shared__ unsigned char smem_raw[];
@@ -128,6 +130,9 @@ __global__ void __launch_bounds__(kThreads, 1) level_tc_bf16_kernel(const LevelP
     uint32_t* tmem_s = reinterpret_cast<uint32_t*>(bars + C::kNumBars);
     volatile int* abort_s = reinterpret_cast<volatile int*>(tmem_s + 1);
     double* red_s = reinterpret_cast<double*>(tmem_s + 4);
+    // batched launches: each role keeps its own copy of the current job's parameters
+    LevelParams* job_prod = reinterpret_cast<LevelParams*>(red_s + kGenWarps);
+    LevelParams* job_gen = job_prod + 1;
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
@@ -154,18 +159,46 @@ __global__ void __launch_bounds__(kThreads, 1) level_tc_bf16_kernel(const LevelP
     tc::tc_fence_after_sync();
     const uint32_t tmem = *tmem_s;
 
-    const int tiles_n = prm.tiles_m * prm.tiles_p;
-    const float* PA = static_cast<const float*>(prm.PA);
-    const float* PB = static_cast<const float*>(prm.PB);
-    const int nsub = (prm.c + kSub - 1) / kSub;
+    // Work items: (chunk cy, output tile) of the launch's level, or, in a batched launch, the
+    // CTA's list of (job, chunk, tile) items prepared by the host.
+    auto for_each_item = [&](LevelParams* copy, auto&& body_fn, bool whole_cta) {
+        if constexpr (kBatch) {
+            int cur = -1;
+            const int i0 = bt.cta_begin[blockIdx.x], i1 = bt.cta_begin[blockIdx.x + 1];
+            for (int i = i0; i < i1; ++i) {
+                const uint64_t it = bt.items[i];
+                const int job = static_cast<int>(it & 0xFFFFu);
+                if (job != cur) {
+                    const uint32_t* src = reinterpret_cast<const uint32_t*>(bt.jobs + job);
+                    uint32_t* dst = reinterpret_cast<uint32_t*>(copy);
+                    const int nthr = whole_cta ? kGenThreads : 32;
+                    const int me = whole_cta ? tid : lane;
+                    for (int w = me; w < static_cast<int>(sizeof(LevelParams) / 4); w += nthr) dst[w] = src[w];
+                    if (whole_cta)
+                        tc::named_barrier(kGenBarrier, kGenThreads);
+                    else
+                        __syncwarp();
+                    cur = job;
+                }
+                if (!body_fn(*copy, static_cast<int>((it >> 16) & 0xFFFFFFFFu), static_cast<int>(it >> 48))) break;
+            }
+        } else {
+            const int tiles_n = prm_arg.tiles_m * prm_arg.tiles_p;
+            const int total = prm_arg.nchunks * tiles_n;
+            for (int item = blockIdx.x; item < total; item += gridDim.x)
+                if (!body_fn(prm_arg, item / tiles_n, item % tiles_n)) break;
+        }
+    };
 
     if (warp == kGenWarps) {
         // ---------------- producer warp: indices + TMA bulk copies of the sampled pairs ----------
         uint32_t g = 0;  // sub-blocks produced by this CTA
         bool aborted = false;
-        for (int item = blockIdx.x; item < ex.total_items && !aborted; item += gridDim.x) {
-            const int cy = item / tiles_n;
-            const int tile = item % tiles_n;
+        for_each_item(job_prod, [&](const LevelParams& prm, int cy, int tile) -> bool {
+            const int tiles_n = prm.tiles_m * prm.tiles_p;
+            const float* PA = static_cast<const float*>(prm.PA);
+            const float* PB = static_cast<const float*>(prm.PB);
+            const int nsub = (prm.c + kSub - 1) / kSub;
             const int tm0 = (tile / prm.tiles_p) * C::kRows;
             const int tp0 = (tile % prm.tiles_p) * BN;
             const uint32_t a_bytes = static_cast<uint32_t>(min(C::kRows, prm.m_pad - tm0)) * 8u;
@@ -219,7 +252,8 @@ __global__ void __launch_bounds__(kThreads, 1) level_tc_bf16_kernel(const LevelP
                     __syncwarp();
                 }
             }
-        }
+            return !aborted;
+        }, false);
     } else {
         // ---------------- generator warps: entries, MMA issue, drain ----------------------------
         constexpr uint32_t idesc = tc::idesc_bf16_f32(128, BN);
@@ -230,10 +264,11 @@ __global__ void __launch_bounds__(kThreads, 1) level_tc_bf16_kernel(const LevelP
         uint32_t slice_seen = 0;  // bit kk: slice kk has been used
         uint32_t done_count = 0;
         bool aborted = false;
-        const bool coarse_sign = prm.l > 0;
-        for (int item = blockIdx.x; item < ex.total_items && !aborted; item += gridDim.x) {
-            const int cy = item / tiles_n;
-            const int tile = item % tiles_n;
+        for_each_item(job_gen, [&](const LevelParams& prm, int cy, int tile) -> bool {
+            const int tiles_n = prm.tiles_m * prm.tiles_p;
+            const int nsub = (prm.c + kSub - 1) / kSub;
+            const bool coarse_sign = prm.l > 0;
+            const float scale = static_cast<float>(prm.w_fine);
             const int tm0 = (tile / prm.tiles_p) * C::kRows;
             const int tp0 = (tile % prm.tiles_p) * BN;
             const uint64_t chunk = prm.chunk0 + static_cast<uint64_t>(cy);
@@ -342,7 +377,7 @@ __global__ void __launch_bounds__(kThreads, 1) level_tc_bf16_kernel(const LevelP
 #pragma unroll
                         for (int e = 0; e < 64; ++e) {
                             if (e < nv) {
-                                v[e] *= ex.scale;
+                                v[e] *= scale;
                                 qs = fmaf(v[e], v[e], qs);
                             }
                         }
@@ -380,7 +415,7 @@ __global__ void __launch_bounds__(kThreads, 1) level_tc_bf16_kernel(const LevelP
                 tc::tc_fence_before_sync();
                 tc::named_barrier(kGenBarrier, kGenThreads);  // the accumulator may now be overwritten
             }
-            if (aborted) break;
+            if (aborted) return false;
             // work-item epilogue: sum of ||D||^2 of this tile over the chunk, fixed-order reduction
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) q += __shfl_xor_sync(0xffffffffu, q, off);
@@ -392,7 +427,8 @@ __global__ void __launch_bounds__(kThreads, 1) level_tc_bf16_kernel(const LevelP
                 prm.partial_q[static_cast<int64_t>(cy) * tiles_n + tile] = t;
             }
             tc::named_barrier(kGenBarrier, kGenThreads);
-        }
+            return true;
+        }, true);
         // after an abort make sure no MMA is still writing TMEM before it is freed
         if (aborted && tid == 0) {
             tc::mma_commit(bar_done);
@@ -404,28 +440,92 @@ __global__ void __launch_bounds__(kThreads, 1) level_tc_bf16_kernel(const LevelP
     if (warp == 0) tc::tmem_dealloc(tmem, C::kTmemCols);
 }
 
+template <int MH, int BN, bool kBatch>
+cudaError_t prepare(int* per_sm)
+{
+    using C = TcCfg<MH, BN>;
+    // the attribute is per function and device; setting it again is cheap
+    cudaError_t e = cudaFuncSetAttribute(level_tc_bf16_kernel<MH, BN, kBatch>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, level_tc_bf16_kernel<MH, BN, kBatch>, kThreads,
+                                                      C::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    *per_sm = max(1, min(occ, 512 / C::kTmemCols));
+    return cudaSuccess;
+}
+
 template <int MH, int BN>
 cudaError_t launch_cfg(const LevelParams& prm, const TcLaunch& tl, cudaStream_t st)
 {
     using C = TcCfg<MH, BN>;
-    static bool attr_set = false;  // per process; the attribute is per function
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(level_tc_bf16_kernel<MH, BN>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
-    const int items = prm.nchunks * prm.tiles_m * prm.tiles_p;
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, level_tc_bf16_kernel<MH, BN>, kThreads,
-                                                                  C::kSmemBytes);
+    int per_sm = 1;
+    cudaError_t e = prepare<MH, BN, false>(&per_sm);
     if (e != cudaSuccess) return e;
-    per_sm = max(1, min(per_sm, 512 / C::kTmemCols));
+    const int items = prm.nchunks * prm.tiles_m * prm.tiles_p;
     const int grid = max(1, min(items, per_sm * tl.num_sms));
     TcExtra ex{tl.err_flag, tl.timeout_ns, items, tl.scale};
-    level_tc_bf16_kernel<MH, BN><<<grid, kThreads, C::kSmemBytes, st>>>(prm, ex);
+    level_tc_bf16_kernel<MH, BN, false><<<grid, kThreads, C::kSmemBytes, st>>>(prm, ex, TcBatch{});
     return cudaGetLastError();
 }
+
+template <int MH, int BN>
+cudaError_t launch_batch_cfg(const TcBatch& bt, int grid, const TcLaunch& tl, cudaStream_t st)
+{
+    using C = TcCfg<MH, BN>;
+    // the function attributes were set by tc_batch_grid (no attribute calls while a graph is captured)
+    TcExtra ex{tl.err_flag, tl.timeout_ns, 0, 0.0f};
+    LevelParams none{};
+    level_tc_bf16_kernel<MH, BN, true><<<grid, kThreads, C::kSmemBytes, st>>>(none, ex, bt);
+    return cudaGetLastError();
+}
+
+template <int MH, int BN>
+int batch_grid(int num_sms)
+{
+    int per_sm = 1;
+    if (prepare<MH, BN, true>(&per_sm) != cudaSuccess) return 0;
+    return per_sm * num_sms;
+}
+
+template <template <int, int> class F, typename... Args>
+auto dispatch_tile(const TcTile& t, Args&&... args)
+{
+    if (t.mh == 1) {
+        switch (t.bn) {
+            case 32: return F<1, 32>::run(args...);
+            case 64: return F<1, 64>::run(args...);
+            case 128: return F<1, 128>::run(args...);
+            default: return F<1, 256>::run(args...);
+        }
+    }
+    switch (t.bn) {
+        case 32: return F<2, 32>::run(args...);
+        case 64: return F<2, 64>::run(args...);
+        case 128: return F<2, 128>::run(args...);
+        default: return F<2, 256>::run(args...);
+    }
+}
+
+template <int MH, int BN>
+struct SingleF {
+    static cudaError_t run(const LevelParams& prm, const TcLaunch& tl, cudaStream_t st)
+    {
+        return launch_cfg<MH, BN>(prm, tl, st);
+    }
+};
+template <int MH, int BN>
+struct BatchF {
+    static cudaError_t run(const TcBatch& bt, int grid, const TcLaunch& tl, cudaStream_t st)
+    {
+        return launch_batch_cfg<MH, BN>(bt, grid, tl, st);
+    }
+};
+template <int MH, int BN>
+struct GridF {
+    static int run(int num_sms) { return batch_grid<MH, BN>(num_sms); }
+};
 
 }  // namespace
 
@@ -438,23 +538,28 @@ TcTile tc_tile_for(int64_t m, int64_t p)
     return t;
 }
 
-cudaError_t launch_level_tc_bf16(const LevelParams& prm, const TcLaunch& tl, cudaStream_t st)
+bool tc_tile_valid(const TcTile& t)
 {
-    const TcTile t = tc_tile_for(prm.m, prm.p);
-    if (t.mh == 1) {
-        switch (t.bn) {
-            case 32: return launch_cfg<1, 32>(prm, tl, st);
-            case 64: return launch_cfg<1, 64>(prm, tl, st);
-            case 128: return launch_cfg<1, 128>(prm, tl, st);
-            default: return launch_cfg<1, 256>(prm, tl, st);
-        }
-    }
-    switch (t.bn) {
-        case 32: return launch_cfg<2, 32>(prm, tl, st);
-        case 64: return launch_cfg<2, 64>(prm, tl, st);
-        case 128: return launch_cfg<2, 128>(prm, tl, st);
-        default: return launch_cfg<2, 256>(prm, tl, st);
-    }
+    return (t.mh == 1 || t.mh == 2) && (t.bn == 32 || t.bn == 64 || t.bn == 128 || t.bn == 256);
+}
+
+cudaError_t launch_level_tc_bf16(const LevelParams& prm, const TcTile& tile, const TcLaunch& tl, cudaStream_t st)
+{
+    if (!tc_tile_valid(tile)) return cudaErrorInvalidValue;
+    return dispatch_tile<SingleF>(tile, prm, tl, st);
+}
+
+int tc_batch_grid(const TcTile& tile, int num_sms)
+{
+    if (!tc_tile_valid(tile)) return 0;
+    return dispatch_tile<GridF>(tile, num_sms);
+}
+
+cudaError_t launch_level_tc_bf16_batch(const TcBatch& bt, const TcTile& tile, int grid, const TcLaunch& tl,
+                                       cudaStream_t st)
+{
+    if (!tc_tile_valid(tile)) return cudaErrorInvalidValue;
+    return dispatch_tile<BatchF>(tile, bt, grid, tl, st);
 }
 
 }  // namespace mlmc

@@ -56,6 +56,47 @@ __global__ void merge_sumsq_kernel(const double* __restrict__ partial_q, int nch
     }
 }
 
+// Batched merge: the jobs of one wave (count read from the device), each folded into its
+// level's FP64 state in chunk order exactly as merge_sum_kernel / merge_sumsq_kernel do.  The
+// grid is fixed (grid-stride over jobs in y and elements in x) so that a captured graph stays
+// valid when the wave's contents change; a wave holds at most one job per (problem, level).
+__global__ void merge_batch_kernel(const MergeJob* __restrict__ jobs, const int* __restrict__ njobs_dev)
+{
+    __shared__ double chunk_q[kMaxMergeChunks];
+    const int njobs = *njobs_dev;
+    for (int j = blockIdx.y; j < njobs; j += gridDim.y) {
+        const MergeJob jb = jobs[j];
+        for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < jb.mp;
+             e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+            double acc = jb.sum[e];
+            int c = 0;
+            for (; c + 8 <= jb.nchunks; c += 8) {
+                float v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = jb.partial[static_cast<int64_t>(c + u) * jb.mp + e];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc += static_cast<double>(v[u]);
+            }
+            for (; c < jb.nchunks; ++c) acc += static_cast<double>(jb.partial[static_cast<int64_t>(c) * jb.mp + e]);
+            jb.sum[e] = acc;
+        }
+        if (blockIdx.x == 0) {
+            for (int c = threadIdx.x; c < jb.nchunks; c += blockDim.x) {
+                double t = 0.0;
+                for (int x = 0; x < jb.tiles; ++x) t += jb.partial_q[static_cast<int64_t>(c) * jb.tiles + x];
+                chunk_q[c] = t;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double acc = *jb.sumsq;
+                for (int c = 0; c < jb.nchunks; ++c) acc += chunk_q[c];
+                *jb.sumsq = acc;
+            }
+            __syncthreads();
+        }
+    }
+}
+
 // One block per level: ||sum||^2 by a fixed-shape reduction, then M2.
 __global__ void finalize_kernel(const double* __restrict__ sum, const double* __restrict__ sumsq,
                                 const LevelCounts counts, int first, int64_t mp, double* mean, double* M2)
@@ -198,6 +239,12 @@ cudaError_t launch_merge_partials(const void* partial_sum, bool partial_f64, con
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     merge_sumsq_kernel<<<1, kMergeThreads, 0, st>>>(partial_q, nchunks, tiles, level_sumsq);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_merge_batch(const MergeJob* jobs, const int* njobs_dev, cudaStream_t st)
+{
+    merge_batch_kernel<<<dim3(64, 256), kMergeThreads, 0, st>>>(jobs, njobs_dev);
     return cudaGetLastError();
 }
 

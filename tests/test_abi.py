@@ -54,3 +54,8 @@ def test_struct_layouts_match_the_header():
     assert ctypes.sizeof(binding.Problem) == 3 * 8 + 2 * 8 + 8 + 2 * 8 + 8 + 2 * 4 + 4 * 4
     assert ctypes.sizeof(binding.Options) == 4 * 4 + 8 + 8 + 8 + 4 + 4
     assert ctypes.sizeof(binding.Report) == 8 + 32 * 8 * 4 + 3 * 8
+
+
+def test_range_layout():
+    # int32 prob, level; uint64 sample_begin, count
+    assert ctypes.sizeof(binding.Range) == 24
