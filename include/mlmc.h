@@ -199,7 +199,10 @@ typedef struct {
  * waves stay the same.  The tile is options->tile_override if set, else the
  * autotuner's: the first call times every candidate tile on the first chunk
  * of each range and keeps the fastest for the plan (mlmc_get_batch_tile).
- * The per-level sums of D do not depend on the tile; the sums of ||D||^2 are
+ * Tiles of at most 256 accumulator columns (all but 2256) keep each chunk's
+ * running sum of D in tensor memory, so with any of them the per-level sums
+ * of D are the same bit for bit; the 2256 tile adds scaled samples in global
+ * memory and agrees with them up to FP32 rounding.  The sums of ||D||^2 are
  * grouped by output tile, so they agree across tiles up to rounding.  Other
  * precisions: one launch sequence per range, as mlmc_level_stats.  Problems
  * whose m x p FP32 partial exceeds 1 GiB: MLMC_ERR_UNSUPPORTED.

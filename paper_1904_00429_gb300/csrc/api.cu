@@ -320,9 +320,9 @@ mlmc_status run_level(mlmc_plan_t* plan, ProblemState& ps, int level, uint64_t s
 
 // ---- batched form ---------------------------------------------------------------------
 
-constexpr size_t kBatchPartialBytes = size_t(1) << 30;  // FP32 chunk partials of one wave
+constexpr size_t kBatchPartialBytes = size_t(4) << 30;  // FP32 chunk partials of one wave
 constexpr int kBatchMaxJobs = 4096;                     // jobs (problem, level, chunk run) per wave
-constexpr int kBatchMaxItems = 1 << 20;                 // (job, chunk, tile) items per wave
+constexpr int kBatchMaxItems = 1 << 20;                 // (job, chunk, tile) units per wave
 constexpr int kBatchMaxWaves = 4;                       // waves per graph launch
 constexpr int kBatchMaxGrid = 4096;
 constexpr int kMergeMaxChunks = 4096;
@@ -338,6 +338,7 @@ struct BatchWave {
     std::vector<std::pair<double, uint64_t>> items;   // (cost, packed item)
     std::vector<uint64_t> packed;                      // items grouped by CTA
     std::vector<int> cta_begin;                        // grid + 1
+    int64_t units = 0;                                 // (chunk, tile) pairs: entries of the q partials
 };
 
 // Byte layout of one wave's device tables.
@@ -423,7 +424,7 @@ mlmc_status build_waves(mlmc_plan_t* plan, const std::vector<BatchRange>& ranges
             }
             const size_t cap = kBatchPartialBytes / 4;
             const uint64_t by_part = part_off < cap ? (cap - part_off) / uint64_t(mp) : 0;
-            const uint64_t by_items = uint64_t(kBatchMaxItems - int(w->items.size())) / uint64_t(tiles);
+            const uint64_t by_items = uint64_t(kBatchMaxItems - w->units) / uint64_t(tiles);
             const uint64_t room = std::min<uint64_t>({by_part, by_items, uint64_t(kMergeMaxChunks)});
             if (room == 0) {
                 if (w->jobs.empty()) return fail(MLMC_ERR_UNSUPPORTED, "batched wave cannot hold one chunk");
@@ -443,13 +444,17 @@ mlmc_status build_waves(mlmc_plan_t* plan, const std::vector<BatchRange>& ranges
             MergeJob mj{plan->batch_partial + part_off, plan->batch_q + q_off, ps.sum + int64_t(r.level) * mp,
                         ps.sumsq + r.level, mp, int(nb), tiles};
             w->merges.push_back(mj);
-            for (uint64_t cy = 0; cy < nb; ++cy) {
+            // items: runs of up to `run` chunks of one tile (fewer, larger items on long ranges)
+            const uint64_t run = std::clamp<uint64_t>(nb / 64, 1, 255);
+            for (uint64_t cy = 0; cy < nb; cy += run) {
+                const uint64_t len = std::min<uint64_t>(run, nb - cy);
                 const uint64_t a = std::max<uint64_t>(prm.s_begin, (cb + cy) * ch);
-                const uint64_t b = std::min<uint64_t>(prm.s_end, (cb + cy + 1) * ch);
+                const uint64_t b = std::min<uint64_t>(prm.s_end, (cb + cy + len) * ch);
                 const double cost = double(b - a) * per_sample;
                 for (int t = 0; t < tiles; ++t)
-                    w->items.emplace_back(cost, uint64_t(job) | (cy << 16) | (uint64_t(t) << 48));
+                    w->items.emplace_back(cost, uint64_t(job) | (cy << 16) | (len << 40) | (uint64_t(t) << 48));
             }
+            w->units += int64_t(nb) * tiles;
             // every job's partials start on a 256-byte boundary: the drain stores float4 vectors
             part_off = (part_off + size_t(nb) * size_t(mp) + 63) & ~size_t(63);
             q_off += size_t(nb) * size_t(tiles);

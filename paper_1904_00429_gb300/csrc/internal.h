@@ -68,7 +68,8 @@ struct TcLaunch {
     int num_sms;
 };
 // Batched launch: CTA b processes items[cta_begin[b] .. cta_begin[b+1]); an item packs
-// job (bits 0-15, index into jobs), chunk cy (bits 16-47) and output tile (bits 48-63).
+// job (bits 0-15, index into jobs), the first chunk cy of a run (bits 16-39), the run length
+// (bits 40-47, 1..255 chunks) and the output tile (bits 48-63).
 struct TcBatch {
     const LevelParams* jobs;
     const uint64_t* items;

@@ -49,14 +49,18 @@ struct TcCfg {
     static constexpr int kSlotBytes = (kRows + BN) * 8;     // staged FP32 (M, S) pairs of A, then of B
     static constexpr int kStageBytes = kSub * kSlotBytes;
     static constexpr int kTileCols = MH * BN;
-    static constexpr int kTmemCols = kTileCols <= 32 ? 32 : kTileCols <= 64 ? 64 : kTileCols <= 128 ? 128
-                                     : kTileCols <= 256 ? 256 : 512;
+    // Tiles of at most 256 accumulator columns also keep the chunk's running sum of D in tensor
+    // memory (a second accumulator S after D); the 256 x 256 tile adds each D to global memory.
+    static constexpr bool kAccS = kTileCols <= 256;
+    static constexpr int kAccCols = kAccS ? 2 * kTileCols : kTileCols;
+    static constexpr int kTmemCols = kAccCols <= 32 ? 32 : kAccCols <= 64 ? 64 : kAccCols <= 128 ? 128
+                                     : kAccCols <= 256 ? 256 : 512;
     // barriers: full[2], empty[2], slice[4], done
     static constexpr int kNumBars = 2 + 2 + kSlices + 1;
     static constexpr int kBookBytes = 2 * kSub * 4 /*idx*/ + kNumBars * 8 + 16 /*tmem, abort*/ + kGenWarps * 8 +
                                       2 * static_cast<int>(sizeof(LevelParams)) /*job copies*/;
     static constexpr int kSmemBytes = 1024 /*align slack*/ + kTileBytes + 2 * kStageBytes + kBookBytes;
-    static_assert(kTileCols <= 512, "tile exceeds tensor memory");
+    static_assert(kAccCols <= 512, "tile exceeds tensor memory");
     static_assert(BN % 16 == 0 && BN >= 32 && BN <= 256, "N of the MMA");
     static_assert(kSmemBytes <= 227 * 1024, "shared memory");
 };
@@ -82,6 +86,12 @@ __device__ __forceinline__ void gen_block(const int* idx, int slot0, bool valid_
                                           const unsigned char* stage,
                                           int stride, bool odd_negative, unsigned char* tile, int row0, int chunk)
 {
+    if (!valid_rows) {
+        // padding rows (or columns) of the tile: zeros, no random numbers needed
+#pragma unroll
+        for (int r = 0; r < 4; ++r) *reinterpret_cast<uint4*>(tile + tc::sw128_offset(row0 + r, chunk)) = make_uint4(0, 0, 0, 0);
+        return;
+    }
     // Branch-free: the eight Philox blocks are independent dependency chains, computed for every
     // slot (a missing slot uses k = 0) and zeroed afterwards, so they can interleave.
     int ks[8];
@@ -99,7 +109,7 @@ __device__ __forceinline__ void gen_block(const int* idx, int slot0, bool valid_
         const float4* src = reinterpret_cast<const float4*>(stage + u * stride);
         const float4 p0 = src[0];
         const float4 p1 = src[1];
-        const bool use = ks[u] >= 0 && valid_rows;
+        const bool use = ks[u] >= 0;
         const float sg = (odd_negative && (u & 1)) ? -1.0f : 1.0f;
         v[0][u] = use ? sg * fmaf(p0.y, z[0], p0.x) : 0.0f;
         v[1][u] = use ? sg * fmaf(p0.w, z[1], p0.z) : 0.0f;
@@ -180,7 +190,13 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                         __syncwarp();
                     cur = job;
                 }
-                if (!body_fn(*copy, static_cast<int>((it >> 16) & 0xFFFFFFFFu), static_cast<int>(it >> 48))) break;
+                // chunk run: first chunk in bits 16-39, run length in bits 40-47
+                const int cy0 = static_cast<int>((it >> 16) & 0xFFFFFFu);
+                const int ncy = static_cast<int>((it >> 40) & 0xFFu);
+                const int tile = static_cast<int>(it >> 48);
+                bool go = true;
+                for (int cy = cy0; cy < cy0 + ncy && go; ++cy) go = body_fn(*copy, cy, tile);
+                if (!go) break;
             }
         } else {
             const int tiles_n = prm_arg.tiles_m * prm_arg.tiles_p;
@@ -277,6 +293,55 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
             float* part = static_cast<float*>(prm.partial_sum) + static_cast<int64_t>(cy) * prm.m * prm.p;
             const int a_bytes = min(C::kRows, prm.m_pad - tm0) * 8;  // B pairs follow A's in a staged slot
             double q = 0.0;
+            const double scale_sq = static_cast<double>(scale) * static_cast<double>(scale);
+            // Drain mapping.  MH == 2: warp group h reads M-half h (all BN columns); MH == 1: the two
+            // warp groups split the columns, or group 0 takes all of them when BN < 64.
+            struct Drain {
+                int quarter, col_tm, col_d, ncols, gi;
+                __device__ uint32_t taddr(uint32_t base, int cb) const
+                {
+                    return base + (static_cast<uint32_t>(quarter * 32) << 16) + static_cast<uint32_t>(col_tm + cb);
+                }
+            } dr;
+            {
+                const int hgrp = warp >> 2;
+                const bool split = MH == 1 && BN >= 64;
+                dr.quarter = warp & 3;
+                dr.col_tm = MH == 2 ? hgrp * BN : (split ? hgrp * (BN / 2) : 0);
+                dr.col_d = MH == 2 ? 0 : dr.col_tm;
+                dr.ncols = MH == 2 ? BN : (split ? BN / 2 : (hgrp == 0 ? BN : 0));
+                dr.gi = tm0 + (MH == 2 ? hgrp * 128 : 0) + dr.quarter * 32 + lane;
+            }
+            // Write (first) or add 64 drained columns starting at column cb of this thread's row.
+            auto store_cols = [&](const float* v, int cb, int nv, bool first) {
+#pragma unroll
+                for (int half = 0; half < 2; ++half) {
+                    const int gj0 = tp0 + dr.col_d + cb + 32 * half;
+                    if (32 * half >= nv || dr.gi >= prm.m || gj0 >= prm.p) continue;
+                    float* dst = part + static_cast<int64_t>(dr.gi) * prm.p + gj0;
+                    const float* w = v + 32 * half;
+                    const int valid = min(32, prm.p - gj0);
+                    if (valid == 32 && (prm.p & 3) == 0) {
+#pragma unroll
+                        for (int e4 = 0; e4 < 8; ++e4) {
+                            if (first)
+                                reinterpret_cast<float4*>(dst)[e4] =
+                                    make_float4(w[4 * e4], w[4 * e4 + 1], w[4 * e4 + 2], w[4 * e4 + 3]);
+                            else
+                                tc::red_add_v4(dst + 4 * e4, w[4 * e4], w[4 * e4 + 1], w[4 * e4 + 2], w[4 * e4 + 3]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 32; ++e)
+                            if (e < valid) {
+                                if (first)
+                                    dst[e] = w[e];
+                                else
+                                    atomicAdd(dst + e, w[e]);
+                            }
+                    }
+                }
+            };
             for (uint64_t s = sa; s < sb && !aborted; ++s) {
                 const uint32_t lsw = level_sample_word(prm.l, s);
                 const uint32_t s_lo = static_cast<uint32_t>(s);
@@ -332,6 +397,9 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                                 tc::sw128_kmajor_desc(tc::smem_addr(a_tile) + h * 128 * 128 + 32 * kk);
                             const uint64_t bdesc = tc::sw128_kmajor_desc(tc::smem_addr(b_tile) + 32 * kk);
                             tc::mma_bf16(tmem + h * BN, adesc, bdesc, idesc, j > 0 ? 1u : 0u);
+                            if constexpr (C::kAccS)   // running sum of the chunk's samples
+                                tc::mma_bf16(tmem + C::kTileCols + h * BN, adesc, bdesc, idesc,
+                                             (j > 0 || s != sa) ? 1u : 0u);
                         }
                         tc::mma_commit(bar_slice(kk));
                         if (j == nsub - 1) tc::mma_commit(bar_done);
@@ -352,27 +420,31 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                     break;
                 }
                 tc::tc_fence_after_sync();
-                {
-                    const int quarter = warp & 3;
-                    const int hgrp = warp >> 2;
-                    // MH == 2: warp group h drains M-half h (all BN columns); MH == 1: the two warp
-                    // groups split the columns, or group 0 takes all of them when BN < 64.
-                    const bool split = MH == 1 && BN >= 64;
-                    const int row_local = (MH == 2 ? hgrp * 128 : 0) + quarter * 32 + lane;
-                    const int col_tm = MH == 2 ? hgrp * BN : (split ? hgrp * (BN / 2) : 0);
-                    const int col_d = MH == 2 ? 0 : col_tm;
-                    const int ncols = MH == 2 ? BN : (split ? BN / 2 : (hgrp == 0 ? BN : 0));
-                    const int gi = tm0 + row_local;
+                if constexpr (C::kAccS) {
+                    // ||D||^2 of the sample from its accumulator; the sum stays in tensor memory
+                    for (int cb = 0; cb < dr.ncols; cb += 64) {
+                        float v[64];
+                        const uint32_t ta = dr.taddr(tmem, cb);
+                        tc::tmem_ld_32x32b_x32_nowait(ta, v);
+                        if (cb + 32 < dr.ncols) tc::tmem_ld_32x32b_x32_nowait(ta + 32, v + 32);
+                        tc::tmem_ld_wait();
+                        const int nv = min(64, dr.ncols - cb);
+                        float qs = 0.0f;
+#pragma unroll
+                        for (int e = 0; e < 64; ++e)
+                            if (e < nv) qs = fmaf(v[e], v[e], qs);
+                        q += static_cast<double>(qs) * scale_sq;
+                    }
+                } else {
                     const bool first = (s == sa);
                     // two 32-column loads in flight per wait
-                    for (int cb = 0; cb < ncols; cb += 64) {
+                    for (int cb = 0; cb < dr.ncols; cb += 64) {
                         float v[64];
-                        const uint32_t ta = tmem + (static_cast<uint32_t>(quarter * 32) << 16) +
-                                            static_cast<uint32_t>(col_tm + cb);
+                        const uint32_t ta = dr.taddr(tmem, cb);
                         tc::tmem_ld_32x32b_x32_nowait(ta, v);
-                        if (cb + 32 < ncols) tc::tmem_ld_32x32b_x32_nowait(ta + 32, v + 32);
+                        if (cb + 32 < dr.ncols) tc::tmem_ld_32x32b_x32_nowait(ta + 32, v + 32);
                         tc::tmem_ld_wait();
-                        const int nv = min(64, ncols - cb);
+                        const int nv = min(64, dr.ncols - cb);
                         float qs = 0.0f;
 #pragma unroll
                         for (int e = 0; e < 64; ++e) {
@@ -382,38 +454,28 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                             }
                         }
                         q += static_cast<double>(qs);
-#pragma unroll
-                        for (int half = 0; half < 2; ++half) {
-                            const int gj0 = tp0 + col_d + cb + 32 * half;
-                            if (32 * half >= nv || gi >= prm.m || gj0 >= prm.p) continue;
-                            float* dst = part + static_cast<int64_t>(gi) * prm.p + gj0;
-                            const float* w = v + 32 * half;
-                            const int valid = min(32, prm.p - gj0);
-                            if (valid == 32 && (prm.p & 3) == 0) {
-#pragma unroll
-                                for (int e4 = 0; e4 < 8; ++e4) {
-                                    if (first)
-                                        reinterpret_cast<float4*>(dst)[e4] =
-                                            make_float4(w[4 * e4], w[4 * e4 + 1], w[4 * e4 + 2], w[4 * e4 + 3]);
-                                    else
-                                        tc::red_add_v4(dst + 4 * e4, w[4 * e4], w[4 * e4 + 1], w[4 * e4 + 2],
-                                                       w[4 * e4 + 3]);
-                                }
-                            } else {
-#pragma unroll
-                                for (int e = 0; e < 32; ++e)
-                                    if (e < valid) {
-                                        if (first)
-                                            dst[e] = w[e];
-                                        else
-                                            atomicAdd(dst + e, w[e]);
-                                    }
-                            }
-                        }
+                        store_cols(v, cb, nv, first);
                     }
                 }
                 tc::tc_fence_before_sync();
                 tc::named_barrier(kGenBarrier, kGenThreads);  // the accumulator may now be overwritten
+            }
+            if (aborted) return false;
+            if constexpr (C::kAccS) {
+                // the chunk's sum of D: one store per element of the tile
+                tc::tc_fence_after_sync();
+                for (int cb = 0; cb < dr.ncols; cb += 64) {
+                    float v[64];
+                    const uint32_t ta = dr.taddr(tmem + C::kTileCols, cb);
+                    tc::tmem_ld_32x32b_x32_nowait(ta, v);
+                    if (cb + 32 < dr.ncols) tc::tmem_ld_32x32b_x32_nowait(ta + 32, v + 32);
+                    tc::tmem_ld_wait();
+                    const int nv = min(64, dr.ncols - cb);
+#pragma unroll
+                    for (int e = 0; e < 64; ++e) v[e] *= scale;
+                    store_cols(v, cb, nv, true);
+                }
+                tc::tc_fence_before_sync();
             }
             if (aborted) return false;
             // work-item epilogue: sum of ||D||^2 of this tile over the chunk, fixed-order reduction

@@ -1,10 +1,12 @@
 """Batched persistent launch (BF16): parity with one-by-one launches and with the FP64 oracle.
 
-The per-level sums of D are sums over samples of FP32 tensor-memory accumulators, added per
-output element in sample order and folded per chunk in chunk order; none of that depends on
-the output tile or on how work items are spread over CTAs, so batched and one-by-one runs
-agree bit for bit.  The sums of ||D||^2 are grouped by output tile, so they agree bit for bit
-for the same tile and up to FP32 rounding of the per-tile partial sums otherwise.
+The per-level sums of D are sums over samples of FP32 tensor-memory accumulators folded per
+chunk in chunk order.  Tiles of at most 256 accumulator columns keep the chunk's running sum
+in tensor memory (one MMA chain per element, independent of the tile's shape and of how items
+are spread over CTAs), so batched and one-by-one runs with such tiles agree bit for bit.  The
+256 x 256 tile adds each scaled sample to the chunk partial in global memory instead, which
+rounds differently: against it the sums agree up to FP32 rounding.  The sums of ||D||^2 are
+grouped by output tile: bit-identical for the same tile, equal up to rounding otherwise.
 """
 import numpy as np
 import pytest
@@ -37,6 +39,17 @@ def _specs(shapes, seed0=0):
                                          problem_id=q))
         pps.append(pp)
     return specs, pps
+
+
+def _single_tile(m, p):
+    # the single-problem launch's tile for an m x p output: 128 or 256 rows, 32..256 columns
+    mh = 1 if m <= 128 else 2
+    bn = 32 if p <= 32 else 64 if p <= 64 else 128 if p <= 128 else 256
+    return 1000 * mh + bn
+
+
+def _sum_in_tmem(tile_id):
+    return (tile_id // 1000) * (tile_id % 1000) <= 256
 
 
 def _states(plan, nprob, L):
@@ -74,10 +87,15 @@ def test_batched_autotuned_matches_one_by_one_sums():
             b.level_stats(q, l, s0, cnt)
         tile, timings = a.batch_tile()
         assert tile in timings and timings[tile] == min(timings.values())
-        for ra, rb in zip(_states(a, len(SHAPES), L), _states(b, len(SHAPES), L)):
+        for (m, _, p), ra, rb in zip(SHAPES, _states(a, len(SHAPES), L), _states(b, len(SHAPES), L)):
+            same_scheme = _sum_in_tmem(tile) and _sum_in_tmem(_single_tile(m, p))
             for (na, sa, qa), (nb, sb, qb) in zip(ra, rb):
                 assert na == nb
-                assert torch.equal(sa, sb)
+                if same_scheme:
+                    assert torch.equal(sa, sb)
+                else:
+                    # FP32 accumulation of at most 64 samples in two orders
+                    assert float((sa - sb).abs().max()) <= 64 * 2.0**-23 * float(sb.abs().max())
                 assert abs(qa - qb) <= 1e-6 * qb
 
 
