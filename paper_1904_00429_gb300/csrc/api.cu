@@ -185,11 +185,11 @@ mlmc_status validate(const mlmc_problem* problems, int32_t nprob, const mlmc_opt
     if (o->pilot_n < 2) return fail(MLMC_ERR_INVALID_ARG, "pilot_n must be >= 2");
     if ((o->precision == MLMC_BF16 || o->precision == MLMC_FP8_E4M3) && o->ratio != 2)
         return fail(MLMC_ERR_UNSUPPORTED, "the tensor-core precisions fold the coupling sign into B and need ratio 2");
-    if (o->precision == MLMC_FP8_E4M3) return fail(MLMC_ERR_UNSUPPORTED, "FP8 E4M3 is not available in this build");
     if (!(o->nl_scale > 0.0) || !std::isfinite(o->nl_scale)) return fail(MLMC_ERR_INVALID_ARG, "nl_scale must be > 0");
     if (o->timeout_ns < 0) return fail(MLMC_ERR_INVALID_ARG, "timeout_ns must be >= 0");
-    if (o->tile_override != 0 && !tc_tile_valid(decode_tile(o->tile_override)))
-        return fail(MLMC_ERR_INVALID_ARG, "tile_override %d is not a tile id (1032 .. 2256)", o->tile_override);
+    if (o->tile_override != 0 && !tc_tile_valid(decode_tile(o->tile_override), o->precision == MLMC_FP8_E4M3 ? 1 : 0))
+        return fail(MLMC_ERR_INVALID_ARG, "tile_override %d is not a tile id of this precision (1032 .. 2256; "
+                    "E4M3: 1032 1064 1128 2032 2064)", o->tile_override);
     if (o->adjoint_batch_log2 < 0 || o->adjoint_batch_log2 > 40)
         return fail(MLMC_ERR_INVALID_ARG, "adjoint_batch_log2 must be in [0, 40]");
     for (int32_t q = 0; q < nprob; ++q) {
@@ -237,6 +237,9 @@ void free_plan(mlmc_plan_t* plan)
 }
 
 bool tensor_core_precision(int precision) { return precision == MLMC_BF16 || precision == MLMC_FP8_E4M3; }
+
+// Operand format of the tensor-core kernel: 0 = bfloat16, 1 = FP8 E4M3 block-scaled.
+int tc_format(const mlmc_options& o) { return o.precision == MLMC_FP8_E4M3 ? 1 : 0; }
 
 // Read the kernels' error word (synchronises the stream).
 mlmc_status check_device_flag(mlmc_plan_t* plan)
@@ -302,9 +305,9 @@ mlmc_status run_level(mlmc_plan_t* plan, ProblemState& ps, int level, uint64_t s
         prm.s_begin = std::max<uint64_t>(s0, cb * ch);
         prm.s_end = std::min<uint64_t>(s_end, (cb + nb) * ch);
         cudaError_t err;
-        if (o.precision == MLMC_BF16) {
+        if (tensor_core_precision(o.precision)) {
             TcLaunch tl{plan->err_flag, plan->timeout_ns, static_cast<float>(double(ps.n) / double(c)), plan->num_sms};
-            err = launch_level_tc_bf16(prm, ps.tile, tl, plan->stream);
+            err = launch_level_tc(prm, ps.tile, tc_format(o), tl, plan->stream);
         } else {
             err = plan->f64 ? launch_level_cuda_core_f64(prm, plan->stream)
                             : launch_level_cuda_core_f32(prm, plan->stream);
@@ -551,7 +554,8 @@ cudaError_t enqueue_waves(mlmc_plan_t* plan, size_t count, bool merge, cudaStrea
     const WaveLayout L;
     TcLaunch tl{plan->err_flag, plan->timeout_ns, 0.0f, plan->num_sms};
     for (size_t i = 0; i < count; ++i) {
-        cudaError_t err = launch_level_tc_bf16_batch(wave_tables(plan, i), plan->batch_tile, plan->batch_grid, tl, st);
+        cudaError_t err = launch_level_tc_batch(wave_tables(plan, i), plan->batch_tile, tc_format(plan->opt),
+                                                plan->batch_grid, tl, st);
         if (err != cudaSuccess) return err;
         if (merge) {
             unsigned char* d = plan->batch_dev + i * L.stride;
@@ -583,14 +587,15 @@ mlmc_status autotune_batch_tile(mlmc_plan_t* plan, const std::vector<BatchRange>
     if (err == cudaSuccess) err = cudaEventCreate(&e1);
     if (check_cuda(plan, err, "autotuner events") != MLMC_OK) return plan->sticky;
     double best = 1e300;
-    TcTile best_tile = tc_tile_for(mmax, pmax);
+    TcTile best_tile = tc_tile_for(mmax, pmax, tc_format(plan->opt));
     mlmc_status st = MLMC_OK;
     for (int c = 0; c < 8 && st == MLMC_OK; ++c) {
         const TcTile t = decode_tile(kTileIds[c]);
         plan->tune_ms[c] = -1.0;
         // skip tiles far wider or taller than every problem
         if ((t.mh == 2 && mmax <= 128) || (t.bn > 32 && pmax <= t.bn / 2)) continue;
-        const int grid = std::min(tc_batch_grid(t, plan->num_sms), kBatchMaxGrid);
+        if (!tc_tile_valid(t, tc_format(plan->opt))) continue;
+        const int grid = std::min(tc_batch_grid(t, tc_format(plan->opt), plan->num_sms), kBatchMaxGrid);
         if (grid <= 0) continue;
         std::vector<BatchWave> waves;
         if ((st = build_waves(plan, probe, t, grid, waves)) != MLMC_OK) break;
@@ -618,7 +623,7 @@ mlmc_status autotune_batch_tile(mlmc_plan_t* plan, const std::vector<BatchRange>
     cudaEventDestroy(e1);
     if (st != MLMC_OK) return st;
     plan->batch_tile = best_tile;
-    plan->batch_grid = std::min(tc_batch_grid(best_tile, plan->num_sms), kBatchMaxGrid);
+    plan->batch_grid = std::min(tc_batch_grid(best_tile, tc_format(plan->opt), plan->num_sms), kBatchMaxGrid);
     return plan->batch_grid > 0 ? MLMC_OK : set_sticky(plan, fail(MLMC_ERR_CUDA, "batched grid query failed"));
 }
 
@@ -629,7 +634,8 @@ mlmc_status run_batch(mlmc_plan_t* plan, const std::vector<BatchRange>& ranges)
     if (plan->batch_tile.mh == 0) {
         if (plan->opt.tile_override) {
             plan->batch_tile = decode_tile(plan->opt.tile_override);
-            plan->batch_grid = std::min(tc_batch_grid(plan->batch_tile, plan->num_sms), kBatchMaxGrid);
+            plan->batch_grid =
+                std::min(tc_batch_grid(plan->batch_tile, tc_format(plan->opt), plan->num_sms), kBatchMaxGrid);
             if (plan->batch_grid <= 0) return set_sticky(plan, fail(MLMC_ERR_CUDA, "batched grid query failed"));
         } else if ((st = autotune_batch_tile(plan, ranges)) != MLMC_OK) {
             return st;
@@ -728,7 +734,8 @@ mlmc_status mlmc_plan(const mlmc_problem* problems, int32_t nprob, const mlmc_op
         ps.m_pad = (ps.m + 3) / 4 * 4;
         ps.p_pad = (ps.p + 3) / 4 * 4;
         if (tensor_core_precision(options->precision)) {
-            const TcTile tile = options->tile_override ? decode_tile(options->tile_override) : tc_tile_for(ps.m, ps.p);
+            const TcTile tile = options->tile_override ? decode_tile(options->tile_override)
+                                                       : tc_tile_for(ps.m, ps.p, options->precision == MLMC_FP8_E4M3 ? 1 : 0);
             ps.tile = tile;
             ps.tiles_m = int((ps.m + tile.rows - 1) / tile.rows);
             ps.tiles_p = int((ps.p + tile.bn - 1) / tile.bn);
@@ -841,7 +848,7 @@ mlmc_status mlmc_level_stats_batch(mlmc_plan_t* plan, const mlmc_range* ranges, 
     }
     if (rs.empty()) return MLMC_OK;
     DeviceGuard g(plan->device);
-    if (plan->opt.precision != MLMC_BF16) {
+    if (!tensor_core_precision(plan->opt.precision)) {
         for (const BatchRange& r : rs) {
             ProblemState& ps = plan->probs[size_t(r.prob)];
             const int64_t mp = ps.m * ps.p;
@@ -1025,7 +1032,7 @@ mlmc_status mlmc_estimate(mlmc_plan_t* plan, const double* eps_abs, double* yhat
     const mlmc_options& o = plan->opt;
     const uint64_t pilot = uint64_t(o.pilot_n);
     // several problems in BF16 go through the batched persistent launch
-    const bool batched = o.precision == MLMC_BF16 && plan->probs.size() > 1;
+    const bool batched = tensor_core_precision(o.precision) && plan->probs.size() > 1;
     auto run_ranges = [&](const std::vector<BatchRange>& rs) -> mlmc_status {
         if (batched) return run_batch(plan, rs);
         for (const BatchRange& r : rs) {
@@ -1243,6 +1250,9 @@ mlmc_status mlmc_backward(mlmc_plan_t* plan, const double* G_dev, void* const* d
     mlmc_status st = enter(plan);
     if (st != MLMC_OK) return st;
     if (!G_dev || !dM_dev || !dS_dev || !dMp_dev || !dSp_dev) return fail(MLMC_ERR_INVALID_ARG, "null argument");
+    if (plan->opt.precision == MLMC_FP8_E4M3)
+        return fail(MLMC_ERR_UNSUPPORTED, "mlmc_backward: the E4M3 block scales couple the slots of a sample; "
+                    "use an FP32 or BF16 plan for gradients");
     for (size_t q = 0; q < plan->probs.size(); ++q) {
         const ProblemState& ps = plan->probs[q];
         if (!dM_dev[q] || !dS_dev[q] || !dMp_dev[q] || !dSp_dev[q])

@@ -76,14 +76,16 @@ struct TcBatch {
     const int* cta_begin;
 };
 
-TcTile tc_tile_for(int64_t m, int64_t p);
-bool tc_tile_valid(const TcTile& t);
-cudaError_t launch_level_tc_bf16(const LevelParams& prm, const TcTile& tile, const TcLaunch& tl, cudaStream_t st);
+// Tensor-core level kernel.  q selects the operand format: 0 = bfloat16, 1 = FP8 E4M3 with
+// per-(row, 32-slot block) power-of-two scales (dequantised into the same bf16 MMA).
+TcTile tc_tile_for(int64_t m, int64_t p, int q);
+bool tc_tile_valid(const TcTile& t, int q);
+cudaError_t launch_level_tc(const LevelParams& prm, const TcTile& tile, int q, const TcLaunch& tl, cudaStream_t st);
 // CTAs of a batched launch for this tile (resident CTAs per SM x SMs); 0 on error.  Also sets
-// the kernel's shared-memory attribute, which launch_level_tc_bf16_batch relies on.
-int tc_batch_grid(const TcTile& tile, int num_sms);
-cudaError_t launch_level_tc_bf16_batch(const TcBatch& bt, const TcTile& tile, int grid, const TcLaunch& tl,
-                                       cudaStream_t st);
+// the kernel's shared-memory attribute, which launch_level_tc_batch relies on.
+int tc_batch_grid(const TcTile& tile, int q, int num_sms);
+cudaError_t launch_level_tc_batch(const TcBatch& bt, const TcTile& tile, int q, int grid, const TcLaunch& tl,
+                                  cudaStream_t st);
 
 // One job of a batched merge: nchunks FP32 chunk partials of an m x p level (mp elements) and
 // their per-tile sums of squares, folded into the level's FP64 sum and sumsq.

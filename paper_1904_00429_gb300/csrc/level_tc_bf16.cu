@@ -24,6 +24,8 @@
 // Every mbarrier wait is bounded by a %globaltimer deadline; on timeout the kernel records
 // MLMC_ERR_TIMEOUT and leaves after freeing its tensor memory.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -36,12 +38,16 @@ namespace {
 constexpr int kGenWarps = 8;
 constexpr int kGenThreads = kGenWarps * 32;
 constexpr int kThreads = kGenThreads + 32;  // + producer warp
-constexpr int kSub = 16;                    // slots per sub-block = one MMA K step
-constexpr int kSlices = 4;                  // sub-blocks per 128-byte swizzle atom (64 bf16)
 constexpr int kGenBarrier = 1;              // named barrier of the generator warps
 
-template <int MH, int BN>
+// Operand formats: Q = 0 rounds the generated entries to bfloat16; Q = 1 quantises them to FP8
+// E4M3 with a power-of-two scale per (row of A or column of B, 32-slot block) and feeds the
+// dequantised values (exact in bfloat16) to the same MMA.
+template <int MH, int BN, int Q>
 struct TcCfg {
+    static constexpr int kSub = Q ? 32 : 16;               // slots per sub-block (one E4M3 scale block)
+    static constexpr int kKSteps = kSub / 16;              // MMA K steps per sub-block
+    static constexpr int kSlices = 64 / kSub;              // sub-blocks per 128-byte swizzle atom (64 bf16)
     static constexpr int kRows = 128 * MH;                 // output rows of a tile
     static constexpr int kABytes = kRows * 128;            // kRows x 64 bf16, 128-byte swizzled
     static constexpr int kBBytes = BN * 128;               // BN x 64 bf16 (B transposed, K-major)
@@ -62,7 +68,7 @@ struct TcCfg {
     static constexpr int kSmemBytes = 1024 /*align slack*/ + kTileBytes + 2 * kStageBytes + kBookBytes;
     static_assert(kAccCols <= 512, "tile exceeds tensor memory");
     static_assert(BN % 16 == 0 && BN >= 32 && BN <= 256, "N of the MMA");
-    static_assert(kSmemBytes <= 227 * 1024, "shared memory");
+    static constexpr bool kFits = kSmemBytes <= 227 * 1024;   // E4M3's 32-slot staging rules out wide tiles
 };
 
 struct TcExtra {
@@ -124,11 +130,85 @@ __device__ __forceinline__ void gen_block(const int* idx, int slot0, bool valid_
     }
 }
 
-template <int MH, int BN, bool kBatch>
+// E4M3 form of gen_block for 32-slot sub-blocks: the four adjacent lanes of one row group hold
+// the row's 32 slots (8 each).  Each row's block maximum |x| gives the scale 2^e, e the
+// smallest integer with max <= 448 * 2^e (1 for an all-zero block); x / 2^e is rounded to E4M3
+// (nearest even, saturating at 448) and the dequantised value, exact in bfloat16, is stored.
+// Every lane of the warp must call this together (shuffles).
+__device__ __forceinline__ float e4m3_block_scale(float absmax)
+{
+    if (!(absmax > 0.0f)) return 1.0f;
+    int e = ((__float_as_uint(absmax) >> 23) & 0xFF) - 127 - 9;   // absmax is a normal float here
+    while (absmax > ldexpf(448.0f, e)) ++e;
+    return ldexpf(1.0f, e);
+}
+
+__device__ __forceinline__ void gen_block_e4m3(const int* idx, int slot0, bool valid_rows, uint32_t rowgrp,
+                                               uint32_t s_lo, uint32_t lsw, const PhiloxRoundKeys& rk,
+                                               const unsigned char* stage, int stride, bool odd_negative,
+                                               unsigned char* tile, int row0, int chunk)
+{
+    float v[4][8];
+    if (valid_rows) {
+        int ks[8];
+        uint4 w[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            ks[u] = idx[slot0 + u];
+            w[u] = philox4x32_10_rk(make_uint4(rowgrp, static_cast<uint32_t>(max(ks[u], 0)), s_lo, lsw), rk);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            float z[4];
+            normals4_mufu(w[u], z);
+            const float4* src = reinterpret_cast<const float4*>(stage + u * stride);
+            const float4 p0 = src[0];
+            const float4 p1 = src[1];
+            const bool use = ks[u] >= 0;
+            const float sg = (odd_negative && (u & 1)) ? -1.0f : 1.0f;
+            v[0][u] = use ? sg * fmaf(p0.y, z[0], p0.x) : 0.0f;
+            v[1][u] = use ? sg * fmaf(p0.w, z[1], p0.z) : 0.0f;
+            v[2][u] = use ? sg * fmaf(p1.y, z[2], p1.x) : 0.0f;
+            v[3][u] = use ? sg * fmaf(p1.w, z[3], p1.z) : 0.0f;
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[r][u] = 0.0f;
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        float am = 0.0f;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) am = fmaxf(am, fabsf(v[r][u]));
+        am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, 1));
+        am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, 2));
+        const float sc = e4m3_block_scale(am);
+        const float inv = 1.0f / sc;   // exact: a power of two
+        uint32_t packed[4];
+#pragma unroll
+        for (int u2 = 0; u2 < 4; ++u2) {
+            const __nv_fp8x2_storage_t q =
+                __nv_cvt_float2_to_fp8x2(make_float2(v[r][2 * u2] * inv, v[r][2 * u2 + 1] * inv), __NV_SATFINITE,
+                                         __NV_E4M3);
+            const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(q, __NV_E4M3);
+            const float2 d = __half22float2(*reinterpret_cast<const __half2*>(&hr));
+            packed[u2] = pack_bf16x2(d.x * sc, d.y * sc);
+        }
+        *reinterpret_cast<uint4*>(tile + tc::sw128_offset(row0 + r, chunk)) =
+            make_uint4(packed[0], packed[1], packed[2], packed[3]);
+    }
+}
+
+template <int MH, int BN, int Q, bool kBatch>
 __global__ void __launch_bounds__(kThreads, 1)
 level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra ex, const TcBatch bt)
 {
-    using C = TcCfg<MH, BN>;
+    using C = TcCfg<MH, BN, Q>;
+    static_assert(C::kFits, "shared memory");
+    constexpr int kSub = C::kSub;
+    constexpr int kSlices = C::kSlices;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                            ~static_cast<uintptr_t>(1023));
@@ -273,8 +353,8 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
     } else {
         // ---------------- generator warps: entries, MMA issue, drain ----------------------------
         constexpr uint32_t idesc = tc::idesc_bf16_f32(128, BN);
-        constexpr int kItemsA = (C::kRows / 4) * 2;
-        constexpr int kItemsB = (BN / 4) * 2;
+        constexpr int kItemsA = (C::kRows / 4) * (kSub / 8);
+        constexpr int kItemsB = (BN / 4) * (kSub / 8);
         uint32_t g = 0;  // sub-blocks consumed
         uint32_t slice_par = 0;   // bit kk: parity of the MMAs issued on slice kk so far
         uint32_t slice_seen = 0;  // bit kk: slice kk has been used
@@ -358,25 +438,47 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                     }
                     const int* idx = idx_s + b * kSub;
                     const unsigned char* st = staging + b * C::kStageBytes;
+                    ok = __all_sync(0xffffffffu, ok);   // whole warps generate or skip (E4M3 uses shuffles)
                     if (ok) {
+                        constexpr int kGroups = kSub / 8;   // 8-slot groups per sub-block
                         for (int it = tid; it < kItemsA + kItemsB; it += kGenThreads) {
-                            if (it < kItemsA) {
-                                // 4 rows of A x 8 slots
-                                const int g4 = it % (C::kRows / 4);
-                                const int sg = it / (C::kRows / 4);
-                                const int i = tm0 + 4 * g4;
-                                gen_block(idx, sg * 8, i < prm.m, static_cast<uint32_t>(i >> 2), s_lo, lsw, prm.rkA,
-                                          st + (sg * 8) * C::kSlotBytes + g4 * 32, C::kSlotBytes, false, a_tile,
-                                          4 * g4, 2 * kk + sg);
+                            if constexpr (Q == 0) {
+                                // consecutive threads take consecutive row groups
+                                if (it < kItemsA) {
+                                    // 4 rows of A x 8 slots
+                                    const int g4 = it % (C::kRows / 4);
+                                    const int sg = it / (C::kRows / 4);
+                                    const int i = tm0 + 4 * g4;
+                                    gen_block(idx, sg * 8, i < prm.m, static_cast<uint32_t>(i >> 2), s_lo, lsw,
+                                              prm.rkA, st + (sg * 8) * C::kSlotBytes + g4 * 32, C::kSlotBytes, false,
+                                              a_tile, 4 * g4, kGroups * kk + sg);
+                                } else {
+                                    // 4 columns of B (rows of the transposed tile) x 8 slots, sign folded in
+                                    const int it2 = it - kItemsA;
+                                    const int g4 = it2 % (BN / 4);
+                                    const int sg = it2 / (BN / 4);
+                                    const int jc = tp0 + 4 * g4;
+                                    gen_block(idx, sg * 8, jc < prm.p, static_cast<uint32_t>(jc >> 2), s_lo, lsw,
+                                              prm.rkB, st + (sg * 8) * C::kSlotBytes + a_bytes + g4 * 32,
+                                              C::kSlotBytes, coarse_sign, b_tile, 4 * g4, kGroups * kk + sg);
+                                }
                             } else {
-                                // 4 columns of B (rows of the transposed tile) x 8 slots, sign folded in
-                                const int it2 = it - kItemsA;
-                                const int g4 = it2 % (BN / 4);
-                                const int sg = it2 / (BN / 4);
-                                const int jc = tp0 + 4 * g4;
-                                gen_block(idx, sg * 8, jc < prm.p, static_cast<uint32_t>(jc >> 2), s_lo, lsw,
-                                          prm.rkB, st + (sg * 8) * C::kSlotBytes + a_bytes + g4 * 32,
-                                          C::kSlotBytes, coarse_sign, b_tile, 4 * g4, 2 * kk + sg);
+                                // E4M3: the kGroups threads of one row group are adjacent lanes, so the
+                                // block maximum is a shuffle; a warp is all-A or all-B (kItemsA % 32 == 0)
+                                if (it < kItemsA) {
+                                    const int g4 = it / kGroups, sg = it % kGroups;
+                                    const int i = tm0 + 4 * g4;
+                                    gen_block_e4m3(idx, sg * 8, i < prm.m, static_cast<uint32_t>(i >> 2), s_lo, lsw,
+                                                   prm.rkA, st + (sg * 8) * C::kSlotBytes + g4 * 32, C::kSlotBytes,
+                                                   false, a_tile, 4 * g4, kGroups * kk + sg);
+                                } else {
+                                    const int it2 = it - kItemsA;
+                                    const int g4 = it2 / kGroups, sg = it2 % kGroups;
+                                    const int jc = tp0 + 4 * g4;
+                                    gen_block_e4m3(idx, sg * 8, jc < prm.p, static_cast<uint32_t>(jc >> 2), s_lo, lsw,
+                                                   prm.rkB, st + (sg * 8) * C::kSlotBytes + a_bytes + g4 * 32,
+                                                   C::kSlotBytes, coarse_sign, b_tile, 4 * g4, kGroups * kk + sg);
+                                }
                             }
                         }
                     }
@@ -392,14 +494,19 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                     if (tid == 0) {
                         tc::tc_fence_after_sync();
 #pragma unroll
-                        for (int h = 0; h < MH; ++h) {
-                            const uint64_t adesc =
-                                tc::sw128_kmajor_desc(tc::smem_addr(a_tile) + h * 128 * 128 + 32 * kk);
-                            const uint64_t bdesc = tc::sw128_kmajor_desc(tc::smem_addr(b_tile) + 32 * kk);
-                            tc::mma_bf16(tmem + h * BN, adesc, bdesc, idesc, j > 0 ? 1u : 0u);
-                            if constexpr (C::kAccS)   // running sum of the chunk's samples
-                                tc::mma_bf16(tmem + C::kTileCols + h * BN, adesc, bdesc, idesc,
-                                             (j > 0 || s != sa) ? 1u : 0u);
+                        for (int ks = 0; ks < C::kKSteps; ++ks) {
+                            const int koff = 32 * (kk * C::kKSteps + ks);   // bytes into the swizzle atom
+                            const bool acc = j > 0 || ks > 0;
+#pragma unroll
+                            for (int h = 0; h < MH; ++h) {
+                                const uint64_t adesc =
+                                    tc::sw128_kmajor_desc(tc::smem_addr(a_tile) + h * 128 * 128 + koff);
+                                const uint64_t bdesc = tc::sw128_kmajor_desc(tc::smem_addr(b_tile) + koff);
+                                tc::mma_bf16(tmem + h * BN, adesc, bdesc, idesc, acc ? 1u : 0u);
+                                if constexpr (C::kAccS)   // running sum of the chunk's samples
+                                    tc::mma_bf16(tmem + C::kTileCols + h * BN, adesc, bdesc, idesc,
+                                                 (acc || s != sa) ? 1u : 0u);
+                            }
                         }
                         tc::mma_commit(bar_slice(kk));
                         if (j == nsub - 1) tc::mma_commit(bar_done);
@@ -502,126 +609,138 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
     if (warp == 0) tc::tmem_dealloc(tmem, C::kTmemCols);
 }
 
-template <int MH, int BN, bool kBatch>
+template <int MH, int BN, int Q, bool kBatch>
 cudaError_t prepare(int* per_sm)
 {
-    using C = TcCfg<MH, BN>;
+    using C = TcCfg<MH, BN, Q>;
     // the attribute is per function and device; setting it again is cheap
-    cudaError_t e = cudaFuncSetAttribute(level_tc_bf16_kernel<MH, BN, kBatch>,
+    cudaError_t e = cudaFuncSetAttribute(level_tc_bf16_kernel<MH, BN, Q, kBatch>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
     if (e != cudaSuccess) return e;
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, level_tc_bf16_kernel<MH, BN, kBatch>, kThreads,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, level_tc_bf16_kernel<MH, BN, Q, kBatch>, kThreads,
                                                       C::kSmemBytes);
     if (e != cudaSuccess) return e;
     *per_sm = max(1, min(occ, 512 / C::kTmemCols));
     return cudaSuccess;
 }
 
-template <int MH, int BN>
-cudaError_t launch_cfg(const LevelParams& prm, const TcLaunch& tl, cudaStream_t st)
-{
-    using C = TcCfg<MH, BN>;
-    int per_sm = 1;
-    cudaError_t e = prepare<MH, BN, false>(&per_sm);
-    if (e != cudaSuccess) return e;
-    const int items = prm.nchunks * prm.tiles_m * prm.tiles_p;
-    const int grid = max(1, min(items, per_sm * tl.num_sms));
-    TcExtra ex{tl.err_flag, tl.timeout_ns, items, tl.scale};
-    level_tc_bf16_kernel<MH, BN, false><<<grid, kThreads, C::kSmemBytes, st>>>(prm, ex, TcBatch{});
-    return cudaGetLastError();
-}
-
-template <int MH, int BN>
-cudaError_t launch_batch_cfg(const TcBatch& bt, int grid, const TcLaunch& tl, cudaStream_t st)
-{
-    using C = TcCfg<MH, BN>;
-    // the function attributes were set by tc_batch_grid (no attribute calls while a graph is captured)
-    TcExtra ex{tl.err_flag, tl.timeout_ns, 0, 0.0f};
-    LevelParams none{};
-    level_tc_bf16_kernel<MH, BN, true><<<grid, kThreads, C::kSmemBytes, st>>>(none, ex, bt);
-    return cudaGetLastError();
-}
-
-template <int MH, int BN>
-int batch_grid(int num_sms)
-{
-    int per_sm = 1;
-    if (prepare<MH, BN, true>(&per_sm) != cudaSuccess) return 0;
-    return per_sm * num_sms;
-}
-
-template <template <int, int> class F, typename... Args>
-auto dispatch_tile(const TcTile& t, Args&&... args)
-{
-    if (t.mh == 1) {
-        switch (t.bn) {
-            case 32: return F<1, 32>::run(args...);
-            case 64: return F<1, 64>::run(args...);
-            case 128: return F<1, 128>::run(args...);
-            default: return F<1, 256>::run(args...);
-        }
-    }
-    switch (t.bn) {
-        case 32: return F<2, 32>::run(args...);
-        case 64: return F<2, 64>::run(args...);
-        case 128: return F<2, 128>::run(args...);
-        default: return F<2, 256>::run(args...);
-    }
-}
-
-template <int MH, int BN>
+template <int MH, int BN, int Q>
 struct SingleF {
     static cudaError_t run(const LevelParams& prm, const TcLaunch& tl, cudaStream_t st)
     {
-        return launch_cfg<MH, BN>(prm, tl, st);
+        using C = TcCfg<MH, BN, Q>;
+        if constexpr (!C::kFits) {
+            return cudaErrorInvalidValue;
+        } else {
+            int per_sm = 1;
+            cudaError_t e = prepare<MH, BN, Q, false>(&per_sm);
+            if (e != cudaSuccess) return e;
+            const int items = prm.nchunks * prm.tiles_m * prm.tiles_p;
+            const int grid = max(1, min(items, per_sm * tl.num_sms));
+            TcExtra ex{tl.err_flag, tl.timeout_ns, items, tl.scale};
+            level_tc_bf16_kernel<MH, BN, Q, false><<<grid, kThreads, C::kSmemBytes, st>>>(prm, ex, TcBatch{});
+            return cudaGetLastError();
+        }
     }
 };
-template <int MH, int BN>
+
+template <int MH, int BN, int Q>
 struct BatchF {
     static cudaError_t run(const TcBatch& bt, int grid, const TcLaunch& tl, cudaStream_t st)
     {
-        return launch_batch_cfg<MH, BN>(bt, grid, tl, st);
+        using C = TcCfg<MH, BN, Q>;
+        if constexpr (!C::kFits) {
+            return cudaErrorInvalidValue;
+        } else {
+            // the function attributes were set by tc_batch_grid (no attribute calls while a graph is captured)
+            TcExtra ex{tl.err_flag, tl.timeout_ns, 0, 0.0f};
+            LevelParams none{};
+            level_tc_bf16_kernel<MH, BN, Q, true><<<grid, kThreads, C::kSmemBytes, st>>>(none, ex, bt);
+            return cudaGetLastError();
+        }
     }
 };
-template <int MH, int BN>
+
+template <int MH, int BN, int Q>
 struct GridF {
-    static int run(int num_sms) { return batch_grid<MH, BN>(num_sms); }
+    static int run(int num_sms)
+    {
+        if constexpr (!TcCfg<MH, BN, Q>::kFits) {
+            return 0;
+        } else {
+            int per_sm = 1;
+            if (prepare<MH, BN, Q, true>(&per_sm) != cudaSuccess) return 0;
+            return per_sm * num_sms;
+        }
+    }
 };
+
+template <int MH, int BN, int Q>
+struct FitsF {
+    static bool run() { return TcCfg<MH, BN, Q>::kFits; }
+};
+
+template <template <int, int, int> class F, int Q, typename... Args>
+auto dispatch_bn(int mh, int bn, Args&&... args)
+{
+    if (mh == 1) {
+        switch (bn) {
+            case 32: return F<1, 32, Q>::run(args...);
+            case 64: return F<1, 64, Q>::run(args...);
+            case 128: return F<1, 128, Q>::run(args...);
+            default: return F<1, 256, Q>::run(args...);
+        }
+    }
+    switch (bn) {
+        case 32: return F<2, 32, Q>::run(args...);
+        case 64: return F<2, 64, Q>::run(args...);
+        case 128: return F<2, 128, Q>::run(args...);
+        default: return F<2, 256, Q>::run(args...);
+    }
+}
+
+template <template <int, int, int> class F, typename... Args>
+auto dispatch_tile(const TcTile& t, int q, Args&&... args)
+{
+    return q ? dispatch_bn<F, 1>(t.mh, t.bn, args...) : dispatch_bn<F, 0>(t.mh, t.bn, args...);
+}
 
 }  // namespace
 
-TcTile tc_tile_for(int64_t m, int64_t p)
+bool tc_tile_valid(const TcTile& t, int q)
+{
+    if (!((t.mh == 1 || t.mh == 2) && (t.bn == 32 || t.bn == 64 || t.bn == 128 || t.bn == 256))) return false;
+    return dispatch_tile<FitsF>(t, q);
+}
+
+TcTile tc_tile_for(int64_t m, int64_t p, int q)
 {
     TcTile t;
     t.mh = m <= 128 ? 1 : 2;
     t.bn = p <= 32 ? 32 : p <= 64 ? 64 : p <= 128 ? 128 : 256;
+    while (!tc_tile_valid(t, q) && t.bn > 32) t.bn /= 2;   // E4M3: narrower column tiles
     t.rows = 128 * t.mh;
     return t;
 }
 
-bool tc_tile_valid(const TcTile& t)
+cudaError_t launch_level_tc(const LevelParams& prm, const TcTile& tile, int q, const TcLaunch& tl, cudaStream_t st)
 {
-    return (t.mh == 1 || t.mh == 2) && (t.bn == 32 || t.bn == 64 || t.bn == 128 || t.bn == 256);
+    if (!tc_tile_valid(tile, q)) return cudaErrorInvalidValue;
+    return dispatch_tile<SingleF>(tile, q, prm, tl, st);
 }
 
-cudaError_t launch_level_tc_bf16(const LevelParams& prm, const TcTile& tile, const TcLaunch& tl, cudaStream_t st)
+int tc_batch_grid(const TcTile& tile, int q, int num_sms)
 {
-    if (!tc_tile_valid(tile)) return cudaErrorInvalidValue;
-    return dispatch_tile<SingleF>(tile, prm, tl, st);
+    if (!tc_tile_valid(tile, q)) return 0;
+    return dispatch_tile<GridF>(tile, q, num_sms);
 }
 
-int tc_batch_grid(const TcTile& tile, int num_sms)
+cudaError_t launch_level_tc_batch(const TcBatch& bt, const TcTile& tile, int q, int grid, const TcLaunch& tl,
+                                  cudaStream_t st)
 {
-    if (!tc_tile_valid(tile)) return 0;
-    return dispatch_tile<GridF>(tile, num_sms);
-}
-
-cudaError_t launch_level_tc_bf16_batch(const TcBatch& bt, const TcTile& tile, int grid, const TcLaunch& tl,
-                                       cudaStream_t st)
-{
-    if (!tc_tile_valid(tile)) return cudaErrorInvalidValue;
-    return dispatch_tile<BatchF>(tile, bt, grid, tl, st);
+    if (!tc_tile_valid(tile, q)) return cudaErrorInvalidValue;
+    return dispatch_tile<BatchF>(tile, q, bt, grid, tl, st);
 }
 
 }  // namespace mlmc
