@@ -179,6 +179,7 @@ class Plan:
                                adjoint_batch_log2)
         self.precision = precision
         self.c0, self.ratio, self.L = c0, ratio, L
+        self.pilot_n = pilot_n
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             _check(lib().mlmc_plan(arr, len(self.problems), ctypes.byref(self.options),

@@ -1,0 +1,95 @@
+"""Sample-parallel Alg. 2 over two gloo ranks on CPU (the oracle stands in for the GPU plan).
+
+Checks: the shards partition every round's sample ids into chunk-aligned contiguous pieces;
+both ranks obtain the same N_l and the same estimate; the N_l equal those of one process
+running the same rounds; the estimate equals the one-process estimate up to the order of the
+FP64 additions; the union of the ranks' evaluated ids is exactly 0 .. N_l - 1 of every level.
+"""
+import os
+import socket
+import sys
+
+import numpy as np
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+from paper_1904_00429_gb300 import distributed
+from paper_1904_00429_gb300.inputs import make_params
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.mark.parametrize("begin,count,world", [(0, 256, 2), (256, 1000, 2), (64, 5, 2), (0, 0, 3),
+                                               (128, 777, 4), (7, 130, 2)])
+def test_shards_partition_the_range(begin, count, world):
+    pieces = [distributed.shard(begin, count, r, world) for r in range(world)]
+    ids = []
+    for b, c in pieces:
+        assert c >= 0
+        ids.extend(range(b, b + c))
+    assert ids == list(range(begin, begin + count))
+    for b, c in pieces[1:]:
+        if c > 0 and b != begin:
+            assert b % distributed.ALIGN == 0
+
+
+def _problems():
+    return [make_params(6, 40, 5, seed_A=3, seed_B=4, seed_idx=5, problem_id=0),
+            make_params(4, 25, 7, seed_A=6, seed_B=7, seed_idx=8, problem_id=1)]
+
+
+EPS_REL = 0.15
+
+
+def _eps(pps):
+    return [EPS_REL * float(np.linalg.norm(pp.exact_mean())) for pp in pps]
+
+
+def _worker(rank, world, port, out_dir):
+    sys.path.insert(0, HERE)
+    from fake_plan import FakePlan
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    pps = _problems()
+    plan = FakePlan(pps, c0=2, L=2, pilot_n=8)
+    ys, Nl = distributed.estimate(plan, _eps(pps))
+    torch.save({"y": [y.clone() for y in ys], "Nl": Nl, "evaluated": plan.evaluated},
+               os.path.join(out_dir, f"rank{rank}.pt"))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def test_two_rank_estimate_matches_one_process(tmp_path):
+    sys.path.insert(0, HERE)
+    from fake_plan import FakePlan
+    world = 2
+    mp.start_processes(_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True,
+                       start_method="spawn")
+    res = [torch.load(tmp_path / f"rank{r}.pt") for r in range(world)]
+    # one process, same rounds
+    pps = _problems()
+    ref = FakePlan(pps, c0=2, L=2, pilot_n=8)
+    ref.level_stats_batch([(q, l, 0, 8) for q in range(2) for l in range(3)])
+    Nl_ref = ref.allocate(_eps(pps))
+    ref.level_stats_batch([(q, l, 8, Nl_ref[q][l] - 8) for q in range(2) for l in range(3) if Nl_ref[q][l] > 8])
+    y_ref = ref.telescoping_sum()
+    assert res[0]["Nl"] == res[1]["Nl"] == Nl_ref
+    assert max(Nl_ref[0]) > 8 and max(Nl_ref[1]) > 8      # the allocation asked for a top-up
+    for q in range(2):
+        assert torch.equal(res[0]["y"][q], res[1]["y"][q])
+        assert torch.allclose(res[0]["y"][q], y_ref[q], rtol=1e-12, atol=1e-12 * float(y_ref[q].abs().max()))
+        for l in range(3):
+            ids = sorted(res[0]["evaluated"][(q, l)] + res[1]["evaluated"][(q, l)])
+            assert ids == list(range(Nl_ref[q][l]))
+            # both ranks carried about half of the top-up
+            share = len(res[1]["evaluated"][(q, l)]) / Nl_ref[q][l]
+            assert 0.4 < share < 0.6, share
