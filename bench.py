@@ -50,10 +50,10 @@ TRAFFIC = {
     # outer products), used for every level
     "fp32": {"dram_bytes_per_outer_product": {0: 823.1e6 / 262144, 8: 823.1e6 / 262144},
              "source": "profiles/level_cuda_core_f32_mlmc_256x65536x256.md"},
-    # DRAM bytes (read + write) per sampled outer product of the 256 x 256 tile kernel at level 0
-    # and level 8 (captures of 1,048,576 and 39,845,888 outer products); levels in between are
-    # interpolated linearly in l
-    "bf16": {"dram_bytes_per_outer_product": {0: 3460.0, 8: 2768.0},
+    # DRAM bytes (read + write) per sampled outer product of the CTA-pair kernel (tile 3256) at
+    # level 0 and level 8 (captures of 1,048,576 and 39,845,888 outer products); levels in between
+    # are interpolated linearly in l
+    "bf16": {"dram_bytes_per_outer_product": {0: 3.0427e9 / 1048576, 8: 109.0608e9 / 39845888},
              "source": "profiles/level_tc_bf16_mlmc_256x65536x256.md"},
     "fp8": None,
 }
@@ -561,6 +561,7 @@ PROFILE_CASES = {
     # name: (precision, level, samples) on the 256x65536x256 workload (parameters 256 MiB > L2)
     "tc_bf16_level0": ("bf16", 0, 16384),
     "tc_bf16_level8": ("bf16", 8, 2432),
+    "tc_bf16_pair_level8": ("bf16", 8, 2432),
     "tc_e4m3_level0": ("fp8", 0, 16384),
     "cuda_core_f32_level0": ("fp32", 0, 4096),
 }
@@ -588,7 +589,8 @@ def run_profile_case(args):
         plan.backward([G])
     else:
         prec, level, count = PROFILE_CASES[args.profile_case]
-        plan = binding.Plan([binding.ProblemSpec(*ts)], c0=64, L=8, precision=prec)
+        plan = binding.Plan([binding.ProblemSpec(*ts)], c0=64, L=8, precision=prec,
+                            tile_override=3256 if "pair" in args.profile_case else 0)
         for i in range(3):
             plan.level_stats(0, level, i * count, count)
     plan.synchronize()

@@ -109,8 +109,11 @@ typedef struct {
     int64_t pilot_n;     /* pilot samples per level used by mlmc_estimate (>= 2) */
     double nl_scale;     /* factor on the allocated N_l (Remark 2.6 oversampling control), > 0 */
     int64_t timeout_ns;  /* bound on any device-side wait; 0 = 2 s */
-    int32_t tile_override; /* BF16 tile: 0 = automatic; else 1000 * (rows / 128) + columns, one of
-                              1032 1064 1128 1256 2032 2064 2128 2256 (e.g. 2128 = 256 x 128) */
+    int32_t tile_override; /* tensor-core tile: 0 = automatic; else 1000 * (rows / 128) + columns,
+                              one of 1032 1064 1128 1256 2032 2064 2128 2256 (e.g. 2128 = 256 x 128;
+                              E4M3: 1032 1064 1128 2032 2064), or 3256: a cluster of two CTAs of
+                              128 x 256 sharing one 256 x 256 tile (BF16, single-problem launches;
+                              the default for outputs above 128 x 128) */
     int32_t adjoint_batch_log2; /* mlmc_backward replays at most 2^this sampled products per batch
                                    (0 = 26; at least c_L + 1 are always taken); scratch is 8 B each */
 } mlmc_options;
@@ -199,10 +202,11 @@ typedef struct {
  * waves stay the same.  The tile is options->tile_override if set, else the
  * autotuner's: the first call times every candidate tile on the first chunk
  * of each range and keeps the fastest for the plan (mlmc_get_batch_tile).
- * Tiles of at most 256 accumulator columns (all but 2256) keep each chunk's
- * running sum of D in tensor memory, so with any of them the per-level sums
- * of D are the same bit for bit; the 2256 tile adds scaled samples in global
- * memory and agrees with them up to FP32 rounding.  The sums of ||D||^2 are
+ * Tiles of at most 256 accumulator columns per CTA (all but 2256, including
+ * the pair 3256 of single-problem launches) keep each chunk's running sum of
+ * D in tensor memory, so with any of them the per-level sums of D are the same
+ * bit for bit; the 2256 tile adds scaled samples in global memory and agrees
+ * with them up to FP32 rounding.  Batched launches do not use 3256.  The sums of ||D||^2 are
  * grouped by output tile, so they agree across tiles up to rounding.  Other
  * precisions: one launch sequence per range, as mlmc_level_stats.  Problems
  * whose m x p FP32 partial exceeds 1 GiB: MLMC_ERR_UNSUPPORTED.

@@ -68,6 +68,9 @@ struct ProblemState {
     ProblemState() { std::fill(prefix, prefix + MLMC_MAX_LEVELS, true); }
     int tiles_m = 1, tiles_p = 1;
     TcTile tile{0, 0, 0};   // tensor-core tile of the single-problem launches
+    TcMaps maps{};          // row-gather maps of PAB for `tile`
+    TcMaps batch_maps{};    // ... and for the plan's batched tile
+    int32_t batch_maps_tile = 0;
     int max_chunks = 1;
 };
 
@@ -164,13 +167,19 @@ double level_cost(const mlmc_options& o, int l)
 uint2 key(uint32_t seed, uint32_t pid) { return make_uint2(seed, pid); }
 
 // Tile ids: 1000 * (rows / 128) + columns, e.g. 2128 = 256 rows x 128 columns.
+// 3256 = a cluster pair of 128 x 256 CTAs sharing one 256 x 256 tile.
 TcTile decode_tile(int32_t id)
 {
-    TcTile t{id / 1000, id % 1000, 128 * (id / 1000)};
+    if (id / 1000 == 3) return TcTile{1, id % 1000, 128, 1};
+    TcTile t{id / 1000, id % 1000, 128 * (id / 1000), 0};
     return t;
 }
 
-int32_t encode_tile(const TcTile& t) { return t.mh > 0 ? 1000 * t.mh + t.bn : 0; }
+int32_t encode_tile(const TcTile& t)
+{
+    if (t.mh <= 0) return 0;
+    return t.pair ? 3000 + t.bn : 1000 * t.mh + t.bn;
+}
 
 const int32_t kTileIds[8] = {1032, 1064, 1128, 1256, 2032, 2064, 2128, 2256};
 
@@ -306,6 +315,7 @@ mlmc_status run_level(mlmc_plan_t* plan, ProblemState& ps, int level, uint64_t s
         prm.s_end = std::min<uint64_t>(s_end, (cb + nb) * ch);
         cudaError_t err;
         if (tensor_core_precision(o.precision)) {
+            prm.maps = ps.maps;
             TcLaunch tl{plan->err_flag, plan->timeout_ns, static_cast<float>(double(ps.n) / double(c)), plan->num_sms};
             err = launch_level_tc(prm, ps.tile, tc_format(o), tl, plan->stream);
         } else {
@@ -411,6 +421,11 @@ mlmc_status build_waves(mlmc_plan_t* plan, const std::vector<BatchRange>& ranges
         LevelParams base = base_params(plan, ps, r.level);
         base.tiles_m = tm;
         base.tiles_p = tp;
+        if (ps.batch_maps_tile != encode_tile(tile)) {
+            tc_encode_maps(&ps.batch_maps, ps.PAB, ps.n, ps.ld, tc_stage_width_a(tile), tc_stage_width_b(tile));
+            ps.batch_maps_tile = encode_tile(tile);
+        }
+        base.maps = ps.batch_maps;
         const uint64_t ch = uint64_t(base.chunk);
         const uint64_t s_end = r.s0 + r.count;
         uint64_t cb = r.s0 / ch;
@@ -587,7 +602,7 @@ mlmc_status autotune_batch_tile(mlmc_plan_t* plan, const std::vector<BatchRange>
     if (err == cudaSuccess) err = cudaEventCreate(&e1);
     if (check_cuda(plan, err, "autotuner events") != MLMC_OK) return plan->sticky;
     double best = 1e300;
-    TcTile best_tile = tc_tile_for(mmax, pmax, tc_format(plan->opt));
+    TcTile best_tile = tc_tile_for(mmax, pmax, tc_format(plan->opt), false);
     mlmc_status st = MLMC_OK;
     for (int c = 0; c < 8 && st == MLMC_OK; ++c) {
         const TcTile t = decode_tile(kTileIds[c]);
@@ -633,6 +648,8 @@ mlmc_status run_batch(mlmc_plan_t* plan, const std::vector<BatchRange>& ranges)
     if (st != MLMC_OK) return st;
     if (plan->batch_tile.mh == 0) {
         if (plan->opt.tile_override) {
+            if (decode_tile(plan->opt.tile_override).pair)
+                return fail(MLMC_ERR_UNSUPPORTED, "tile 3256 (CTA pairs) serves single-problem launches only");
             plan->batch_tile = decode_tile(plan->opt.tile_override);
             plan->batch_grid =
                 std::min(tc_batch_grid(plan->batch_tile, tc_format(plan->opt), plan->num_sms), kBatchMaxGrid);
@@ -735,7 +752,8 @@ mlmc_status mlmc_plan(const mlmc_problem* problems, int32_t nprob, const mlmc_op
         ps.p_pad = (ps.p + 3) / 4 * 4;
         if (tensor_core_precision(options->precision)) {
             const TcTile tile = options->tile_override ? decode_tile(options->tile_override)
-                                                       : tc_tile_for(ps.m, ps.p, options->precision == MLMC_FP8_E4M3 ? 1 : 0);
+                                                       : tc_tile_for(ps.m, ps.p, options->precision == MLMC_FP8_E4M3 ? 1 : 0,
+                                                                     true);
             ps.tile = tile;
             ps.tiles_m = int((ps.m + tile.rows - 1) / tile.rows);
             ps.tiles_p = int((ps.p + tile.bn - 1) / tile.bn);
@@ -770,6 +788,8 @@ mlmc_status mlmc_plan(const mlmc_problem* problems, int32_t nprob, const mlmc_op
             delete plan;
             return fail(MLMC_ERR_CUDA, "layout kernel: %s", cudaGetErrorString(err));
         }
+        if (tensor_core_precision(options->precision))
+            tc_encode_maps(&ps.maps, ps.PAB, ps.n, ps.ld, tc_stage_width_a(ps.tile), tc_stage_width_b(ps.tile));
     }
     if (cudaMalloc(&plan->partial_sum, max_partial) != cudaSuccess) return oom("chunk partials");
     if (cudaMalloc(reinterpret_cast<void**>(&plan->partial_q), sizeof(double) * max_q) != cudaSuccess)

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "mlmc.h"
@@ -24,6 +25,15 @@ inline int chunk_samples(int64_t c_l)
     return ch;
 }
 
+// Tensor maps of the interleaved parameter table for the tensor-core kernel's row gathers: the
+// table seen as n rows of (m_pad + p_pad) 8-byte (M, S) pairs, with a box of one row and
+// `wa` (A part) or `wb` (B part) pairs.  valid = 0: gather with plain bulk copies instead.
+struct TcMaps {   // CUtensorMap brings its own 64-byte alignment
+    CUtensorMap a;
+    CUtensorMap b;
+    int wa, wb, valid, pad;
+};
+
 // Arguments of one level-kernel launch over samples [s_begin, s_end).
 struct LevelParams {
     const void* PA;       // row k: (M_ik, S_ik) pairs, i < m_pad (gathered column k of [M|S])
@@ -45,6 +55,7 @@ struct LevelParams {
     int tiles_m, tiles_p;
     void* partial_sum;    // [nchunks][m][p] of T
     double* partial_q;    // [nchunks][tiles_m * tiles_p]
+    TcMaps maps;          // tensor-core kernel only
 };
 
 // Tile geometry of the CUDA-core level kernel.
@@ -58,8 +69,10 @@ cudaError_t launch_level_cuda_core_f32(const LevelParams& prm, cudaStream_t st);
 CudaCoreTile cuda_core_tile(int precision);
 
 // Tensor-core (BF16) level kernel: tile of (128 * mh) rows x bn columns per CTA.
+// Tensor-core tile: mh x 128 rows x bn columns per CTA; pair = 1: a cluster of two CTAs of 128
+// rows each shares one 256 x bn tile (bn = 256), each generating half of B for both.
 struct TcTile {
-    int mh, bn, rows;
+    int mh, bn, rows, pair;
 };
 struct TcLaunch {
     int* err_flag;        // device word set to an mlmc_status when a bounded wait gives up
@@ -78,7 +91,15 @@ struct TcBatch {
 
 // Tensor-core level kernel.  q selects the operand format: 0 = bfloat16, 1 = FP8 E4M3 with
 // per-(row, 32-slot block) power-of-two scales (dequantised into the same bf16 MMA).
-TcTile tc_tile_for(int64_t m, int64_t p, int q);
+// Encode the row-gather maps of a table (base, n rows, ld floats per row) for a tile whose A part
+// spans wa pairs and B part wb pairs (<= 256 each); returns false if the driver lacks the call.
+bool tc_encode_maps(TcMaps* maps, const void* base, int64_t n, int64_t ld, int wa, int wb);
+// Pairs of the A and B parts a tile's CTA stages per slot.
+int tc_stage_width_a(const TcTile& t);
+int tc_stage_width_b(const TcTile& t);
+// Default tile: bf16 outputs with more than 128 rows and columns use the cluster pair (single-
+// problem launches, allow_pair); otherwise mh = 1 or 2 and the narrowest bn covering p.
+TcTile tc_tile_for(int64_t m, int64_t p, int q, bool allow_pair);
 bool tc_tile_valid(const TcTile& t, int q);
 cudaError_t launch_level_tc(const LevelParams& prm, const TcTile& tile, int q, const TcLaunch& tl, cudaStream_t st);
 // CTAs of a batched launch for this tile (resident CTAs per SM x SMs); 0 on error.  Also sets

@@ -23,6 +23,8 @@
 //     order is fixed) and accumulate ||D||_F^2.
 // Every mbarrier wait is bounded by a %globaltimer deadline; on timeout the kernel records
 // MLMC_ERR_TIMEOUT and leaves after freeing its tensor memory.
+#include <cstring>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -43,16 +45,24 @@ constexpr int kGenBarrier = 1;              // named barrier of the generator wa
 // Operand formats: Q = 0 rounds the generated entries to bfloat16; Q = 1 quantises them to FP8
 // E4M3 with a power-of-two scale per (row of A or column of B, 32-slot block) and feeds the
 // dequantised values (exact in bfloat16) to the same MMA.
-template <int MH, int BN, int Q>
+// P = 1: a cluster pair of CTAs shares one 256-row x BN tile; each CTA owns 128 rows (MH = 1),
+// generates its rows of A and half of the B columns, and copies that half into the peer's B tile
+// (one bulk shared-to-shared copy per sub-block).  Pairs keep four slices of 32 K elements in
+// 64-byte-swizzled tiles (one per slice), so each CTA's half of a slice is one contiguous run and
+// the peer has three sub-blocks of slack before a slice is reused.
+template <int MH, int BN, int Q, int P = 0>
 struct TcCfg {
-    static constexpr int kSub = Q ? 32 : 16;               // slots per sub-block (one E4M3 scale block)
+    static constexpr int kSub = (Q || P) ? 32 : 16;        // slots per sub-block (one E4M3 scale block)
     static constexpr int kKSteps = kSub / 16;              // MMA K steps per sub-block
-    static constexpr int kSlices = 64 / kSub;              // sub-blocks per 128-byte swizzle atom (64 bf16)
+    static constexpr int kSlices = P ? 4 : 64 / kSub;      // sub-blocks in flight (128-byte atom: 64 bf16)
     static constexpr int kRows = 128 * MH;                 // output rows of a tile
-    static constexpr int kABytes = kRows * 128;            // kRows x 64 bf16, 128-byte swizzled
-    static constexpr int kBBytes = BN * 128;               // BN x 64 bf16 (B transposed, K-major)
+    static constexpr int kASliceBytes = kRows * 64;        // pairs: one 64-byte-swizzled slice of A
+    static constexpr int kBSliceBytes = BN * 64;           // pairs: one 64-byte-swizzled slice of B
+    static constexpr int kABytes = P ? kSlices * kASliceBytes : kRows * 128;   // else kRows x 64 bf16, 128-B swizzle
+    static constexpr int kBBytes = P ? kSlices * kBSliceBytes : BN * 128;      // B transposed, K-major
     static constexpr int kTileBytes = kABytes + kBBytes;
-    static constexpr int kSlotBytes = (kRows + BN) * 8;     // staged FP32 (M, S) pairs of A, then of B
+    static constexpr int kBGen = P ? BN / 2 : BN;           // B columns generated (and staged) by this CTA
+    static constexpr int kSlotBytes = (kRows + kBGen) * 8;  // staged FP32 (M, S) pairs of A, then of B
     static constexpr int kStageBytes = kSub * kSlotBytes;
     static constexpr int kTileCols = MH * BN;
     // Tiles of at most 256 accumulator columns also keep the chunk's running sum of D in tensor
@@ -61,14 +71,17 @@ struct TcCfg {
     static constexpr int kAccCols = kAccS ? 2 * kTileCols : kTileCols;
     static constexpr int kTmemCols = kAccCols <= 32 ? 32 : kAccCols <= 64 ? 64 : kAccCols <= 128 ? 128
                                      : kAccCols <= 256 ? 256 : 512;
-    // barriers: full[2], empty[2], slice[4], done
-    static constexpr int kNumBars = 2 + 2 + kSlices + 1;
+    // barriers: full[2], empty[2], slice[kSlices], done, and for pairs peer[kSlices] (the peer's B half landed)
+    static constexpr int kNumBars = 2 + 2 + kSlices + 1 + (P ? kSlices : 0);
     static constexpr int kBookBytes = 2 * kSub * 4 /*idx*/ + kNumBars * 8 + 16 /*tmem, abort*/ + kGenWarps * 8 +
-                                      2 * static_cast<int>(sizeof(LevelParams)) /*job copies*/;
+                                      (P ? 0 : 2 * static_cast<int>(sizeof(LevelParams)) +
+                                                   static_cast<int>(alignof(LevelParams)))
+                                      /*job copies of batched launches (pairs run single-problem launches)*/;
     static constexpr int kSmemBytes = 1024 /*align slack*/ + kTileBytes + 2 * kStageBytes + kBookBytes;
     static_assert(kAccCols <= 512, "tile exceeds tensor memory");
     static_assert(BN % 16 == 0 && BN >= 32 && BN <= 256, "N of the MMA");
-    static constexpr bool kFits = kSmemBytes <= 227 * 1024;   // E4M3's 32-slot staging rules out wide tiles
+    static constexpr bool kFits = kSmemBytes <= 227 * 1024 &&   // E4M3's 32-slot staging rules out wide tiles
+                                  (!P || (MH == 1 && BN == 256 && Q == 0));
 };
 
 struct TcExtra {
@@ -87,6 +100,14 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
 // Generate one block of (4 rows of A, or 4 columns of B) x (8 slots) entries from staged (M, S)
 // pairs and write them as bf16 into the swizzled tile: tile rows row0 .. row0+3, 16-byte chunk
 // `chunk`.  Staged pairs of slot u start at stage + u * stride (8 floats: (M,S) x 4).
+// kSw: the tile's swizzle, 128 or 64 bytes per row.
+template <int kSw>
+__device__ __forceinline__ uint32_t tile_offset(int row, int chunk)
+{
+    return kSw == 128 ? tc::sw128_offset(row, chunk) : tc::sw64_offset(row, chunk);
+}
+
+template <int kSw = 128>
 __device__ __forceinline__ void gen_block(const int* idx, int slot0, bool valid_rows, uint32_t rowgrp,
                                           uint32_t s_lo, uint32_t lsw, const PhiloxRoundKeys& rk,
                                           const unsigned char* stage,
@@ -95,7 +116,8 @@ __device__ __forceinline__ void gen_block(const int* idx, int slot0, bool valid_
     if (!valid_rows) {
         // padding rows (or columns) of the tile: zeros, no random numbers needed
 #pragma unroll
-        for (int r = 0; r < 4; ++r) *reinterpret_cast<uint4*>(tile + tc::sw128_offset(row0 + r, chunk)) = make_uint4(0, 0, 0, 0);
+        for (int r = 0; r < 4; ++r)
+            *reinterpret_cast<uint4*>(tile + tile_offset<kSw>(row0 + r, chunk)) = make_uint4(0, 0, 0, 0);
         return;
     }
     // Branch-free: the eight Philox blocks are independent dependency chains, computed for every
@@ -126,7 +148,7 @@ __device__ __forceinline__ void gen_block(const int* idx, int slot0, bool valid_
     for (int r = 0; r < 4; ++r) {
         const uint4 packed = make_uint4(pack_bf16x2(v[r][0], v[r][1]), pack_bf16x2(v[r][2], v[r][3]),
                                         pack_bf16x2(v[r][4], v[r][5]), pack_bf16x2(v[r][6], v[r][7]));
-        *reinterpret_cast<uint4*>(tile + tc::sw128_offset(row0 + r, chunk)) = packed;
+        *reinterpret_cast<uint4*>(tile + tile_offset<kSw>(row0 + r, chunk)) = packed;
     }
 }
 
@@ -201,12 +223,13 @@ __device__ __forceinline__ void gen_block_e4m3(const int* idx, int slot0, bool v
     }
 }
 
-template <int MH, int BN, int Q, bool kBatch>
+template <int MH, int BN, int Q, bool kBatch, int P = 0>
 __global__ void __launch_bounds__(kThreads, 1)
 level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra ex, const TcBatch bt)
 {
-    using C = TcCfg<MH, BN, Q>;
+    using C = TcCfg<MH, BN, Q, P>;
     static_assert(C::kFits, "shared memory");
+    static_assert(!(P && kBatch), "pairs run single-problem launches");
     constexpr int kSub = C::kSub;
     constexpr int kSlices = C::kSlices;
     extern __shared__ unsigned char smem_raw[];
@@ -220,8 +243,11 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
     uint32_t* tmem_s = reinterpret_cast<uint32_t*>(bars + C::kNumBars);
     volatile int* abort_s = reinterpret_cast<volatile int*>(tmem_s + 1);
     double* red_s = reinterpret_cast<double*>(tmem_s + 4);
-    // batched launches: each role keeps its own copy of the current job's parameters
-    LevelParams* job_prod = reinterpret_cast<LevelParams*>(red_s + kGenWarps);
+    // batched launches: each role keeps its own copy of the current job's parameters (aligned as
+    // the type requires: it embeds tensor maps)
+    LevelParams* job_prod = reinterpret_cast<LevelParams*>(
+        (reinterpret_cast<uintptr_t>(red_s + kGenWarps) + alignof(LevelParams) - 1) &
+        ~static_cast<uintptr_t>(alignof(LevelParams) - 1));
     LevelParams* job_gen = job_prod + 1;
 
     const int tid = threadIdx.x;
@@ -232,6 +258,9 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
     auto bar_full = [&](int b) { return bars0 + 8 * b; };
     auto bar_empty = [&](int b) { return bars0 + 8 * (2 + b); };
     auto bar_slice = [&](int kk) { return bars0 + 8 * (4 + kk); };
+    auto bar_peer = [&](int kk) { return bars0 + 8 * (4 + kSlices + 1 + kk); };
+    const uint32_t crank = P ? tc::cluster_ctarank() : 0u;   // this CTA's half of a pair
+    const uint32_t peer = crank ^ 1u;
 
     if (warp == 0) tc::tmem_alloc(tc::smem_addr(tmem_s), C::kTmemCols);
     if (tid == 0) {
@@ -239,15 +268,21 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
             tc::mbar_init(bar_full(b), 1);
             tc::mbar_init(bar_empty(b), kGenWarps);
         }
-        for (int kk = 0; kk < kSlices; ++kk) tc::mbar_init(bar_slice(kk), 1);
+        // a slice is free again once this CTA's MMA and, for pairs, the peer's MMA have read it
+        for (int kk = 0; kk < kSlices; ++kk) tc::mbar_init(bar_slice(kk), P ? 2 : 1);
         tc::mbar_init(bar_done, 1);
+        if constexpr (P)
+            for (int kk = 0; kk < kSlices; ++kk) tc::mbar_init(bar_peer(kk), 1);
         tc::mbar_init_fence();
         *abort_s = 0;
     }
     tc::tc_fence_before_sync();
     __syncthreads();
+    if constexpr (P) tc::cluster_sync();   // the peer's barriers exist before anything reaches them
     tc::tc_fence_after_sync();
     const uint32_t tmem = *tmem_s;
+    // pairs: the peer's B tile in the cluster's shared window
+    const uint32_t peer_b_tile = P ? tc::map_to_cta(tc::smem_addr(b_tile), peer) : 0u;
 
     // Work items: (chunk cy, output tile) of the launch's level, or, in a batched launch, the
     // CTA's list of (job, chunk, tile) items prepared by the host.
@@ -275,32 +310,75 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                 const int ncy = static_cast<int>((it >> 40) & 0xFFu);
                 const int tile = static_cast<int>(it >> 48);
                 bool go = true;
-                for (int cy = cy0; cy < cy0 + ncy && go; ++cy) go = body_fn(*copy, cy, tile);
+                // tensor maps are read from the job table in global memory (not the shared copy)
+                const TcMaps* maps = &bt.jobs[job].maps;
+                for (int cy = cy0; cy < cy0 + ncy && go; ++cy) go = body_fn(*copy, cy, tile, maps);
                 if (!go) break;
             }
+        } else if constexpr (P) {
+            // both CTAs of a cluster walk the same (chunk, pair of row tiles, column tile) items
+            const int pair_tiles = ((prm_arg.tiles_m + 1) / 2) * prm_arg.tiles_p;
+            const int total = prm_arg.nchunks * pair_tiles;
+            const int cid = static_cast<int>(blockIdx.x >> 1), ncl = static_cast<int>(gridDim.x >> 1);
+            for (int item = cid; item < total; item += ncl)
+                if (!body_fn(prm_arg, item / pair_tiles, item % pair_tiles, &prm_arg.maps)) break;
         } else {
             const int tiles_n = prm_arg.tiles_m * prm_arg.tiles_p;
             const int total = prm_arg.nchunks * tiles_n;
             for (int item = blockIdx.x; item < total; item += gridDim.x)
-                if (!body_fn(prm_arg, item / tiles_n, item % tiles_n)) break;
+                if (!body_fn(prm_arg, item / tiles_n, item % tiles_n, &prm_arg.maps)) break;
         }
+    };
+
+    // Tile geometry of an item: first row and column, the column of this CTA's generated B part,
+    // and the (chunk, tile) index of its sum of squares (-1: a pair's row tile beyond m).
+    struct Geo {
+        int tm0, tp0, bcol0, qtile;
+    };
+    auto geometry = [&](const LevelParams& prm, int tile) {
+        Geo g;
+        if constexpr (P) {
+            const int prow = tile / prm.tiles_p, col = tile % prm.tiles_p;
+            const int row_idx = 2 * prow + static_cast<int>(crank);
+            g.tm0 = row_idx * C::kRows;
+            g.tp0 = col * BN;
+            g.bcol0 = g.tp0 + static_cast<int>(crank) * C::kBGen;
+            g.qtile = row_idx < prm.tiles_m ? row_idx * prm.tiles_p + col : -1;
+        } else {
+            g.tm0 = (tile / prm.tiles_p) * C::kRows;
+            g.tp0 = (tile % prm.tiles_p) * BN;
+            g.bcol0 = g.tp0;
+            g.qtile = tile;
+        }
+        return g;
     };
 
     if (warp == kGenWarps) {
         // ---------------- producer warp: indices + TMA bulk copies of the sampled pairs ----------
         uint32_t g = 0;  // sub-blocks produced by this CTA
         bool aborted = false;
-        for_each_item(job_prod, [&](const LevelParams& prm, int cy, int tile) -> bool {
+        const TcMaps* fenced = nullptr;   // batched: job-table maps already acquired by this warp
+        for_each_item(job_prod, [&](const LevelParams& prm, int cy, int tile, const TcMaps* maps) -> bool {
+            if constexpr (kBatch) {
+                // the job table is rewritten between batched calls: reload cached descriptors
+                if (maps != fenced && prm.maps.valid) {
+                    tc::tensormap_acquire(&maps->a);
+                    tc::tensormap_acquire(&maps->b);
+                    fenced = maps;
+                }
+            }
             const int tiles_n = prm.tiles_m * prm.tiles_p;
             const float* PA = static_cast<const float*>(prm.PA);
             const float* PB = static_cast<const float*>(prm.PB);
             const int nsub = (prm.c + kSub - 1) / kSub;
-            const int tm0 = (tile / prm.tiles_p) * C::kRows;
-            const int tp0 = (tile % prm.tiles_p) * BN;
-            const uint32_t a_bytes = static_cast<uint32_t>(min(C::kRows, prm.m_pad - tm0)) * 8u;
-            const uint32_t b_bytes = static_cast<uint32_t>(min(BN, prm.p_pad - tp0)) * 8u;
-            // PB rows start right after PA's in the plan's interleaved layout
-            const bool whole_row = tiles_n == 1 && PB == PA + 2 * prm.m_pad && prm.ldPA == prm.ldPB;
+            const Geo geo = geometry(prm, tile);
+            const int tm0 = geo.tm0;
+            const uint32_t a_bytes = static_cast<uint32_t>(max(0, min(C::kRows, prm.m_pad - tm0))) * 8u;
+            const uint32_t b_bytes = static_cast<uint32_t>(max(0, min(C::kBGen, prm.p_pad - geo.bcol0))) * 8u;
+            (void)tiles_n;
+            (void)PB;
+            // row gathers need maps encoded for exactly this tile's staging widths
+            const bool gather = prm.maps.valid != 0 && prm.maps.wa == C::kRows && prm.maps.wb == C::kBGen;
             const uint64_t chunk = prm.chunk0 + static_cast<uint64_t>(cy);
             const uint64_t sa = max(prm.s_begin, chunk * static_cast<uint64_t>(prm.chunk));
             const uint64_t sb = min(prm.s_end, (chunk + 1) * static_cast<uint64_t>(prm.chunk));
@@ -329,20 +407,38 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                     }
                     __syncwarp();
                     const int nvalid = min(kSub, prm.c - t0);
-                    if (lane == 0)
-                        tc::mbar_arrive_expect_tx(bar_full(b), static_cast<uint32_t>(nvalid) * (a_bytes + b_bytes));
-                    __syncwarp();
-                    if (lane < nvalid) {
-                        const int k = idx[lane];
-                        unsigned char* dst = staging + b * C::kStageBytes + lane * C::kSlotBytes;
-                        const float* row = PA + static_cast<int64_t>(k) * prm.ldPA;
-                        if (whole_row) {
-                            // one tile covers every row and column: A and B pairs are one contiguous run
-                            tc::bulk_copy_g2s(tc::smem_addr(dst), row, a_bytes + b_bytes, bar_full(b));
-                        } else {
-                            tc::bulk_copy_g2s(tc::smem_addr(dst), row + 2 * tm0, a_bytes, bar_full(b));
-                            tc::bulk_copy_g2s(tc::smem_addr(dst + a_bytes),
-                                              PB + static_cast<int64_t>(k) * prm.ldPB + 2 * tp0, b_bytes, bar_full(b));
+                    // staging buffer b: the A parts of the kSub slots, then their B parts
+                    unsigned char* stg = staging + b * C::kStageBytes;
+                    const uint32_t a_region = tc::smem_addr(stg);
+                    const uint32_t b_region = a_region + static_cast<uint32_t>(kSub * C::kRows * 8);
+                    if (gather) {
+                        // TMA row gathers, four slots per instruction (boxes of kRows and kBGen pairs)
+                        const int groups = (nvalid + 3) / 4;
+                        if (lane == 0)
+                            tc::mbar_arrive_expect_tx(bar_full(b),
+                                                      static_cast<uint32_t>(groups * 4 * (C::kRows + C::kBGen) * 8));
+                        __syncwarp();
+                        if (lane < groups) {
+                            const int r0 = max(idx[4 * lane], 0), r1 = max(idx[4 * lane + 1], 0);
+                            const int r2 = max(idx[4 * lane + 2], 0), r3 = max(idx[4 * lane + 3], 0);
+                            tc::tma_gather4(a_region + static_cast<uint32_t>(4 * lane * C::kRows * 8), &maps->a, tm0,
+                                            r0, r1, r2, r3, bar_full(b));
+                            tc::tma_gather4(b_region + static_cast<uint32_t>(4 * lane * C::kBGen * 8), &maps->b,
+                                            prm.m_pad + geo.bcol0, r0, r1, r2, r3, bar_full(b));
+                        }
+                    } else {
+                        if (lane == 0)
+                            tc::mbar_arrive_expect_tx(bar_full(b), static_cast<uint32_t>(nvalid) * (a_bytes + b_bytes));
+                        __syncwarp();
+                        if (lane < nvalid) {
+                            const int k = idx[lane];
+                            const float* row = PA + static_cast<int64_t>(k) * prm.ldPA;
+                            if (a_bytes)
+                                tc::bulk_copy_g2s(a_region + static_cast<uint32_t>(lane * C::kRows * 8), row + 2 * tm0,
+                                                  a_bytes, bar_full(b));
+                            if (b_bytes)
+                                tc::bulk_copy_g2s(b_region + static_cast<uint32_t>(lane * C::kBGen * 8),
+                                                  row + 2 * (prm.m_pad + geo.bcol0), b_bytes, bar_full(b));
                         }
                     }
                     __syncwarp();
@@ -354,24 +450,26 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
         // ---------------- generator warps: entries, MMA issue, drain ----------------------------
         constexpr uint32_t idesc = tc::idesc_bf16_f32(128, BN);
         constexpr int kItemsA = (C::kRows / 4) * (kSub / 8);
-        constexpr int kItemsB = (BN / 4) * (kSub / 8);
+        constexpr int kItemsB = (C::kBGen / 4) * (kSub / 8);
         uint32_t g = 0;  // sub-blocks consumed
+        uint32_t peer_par = 0;    // bit kk: parity of the peer's arrivals on peer barrier kk (pairs)
         uint32_t slice_par = 0;   // bit kk: parity of the MMAs issued on slice kk so far
         uint32_t slice_seen = 0;  // bit kk: slice kk has been used
         uint32_t done_count = 0;
         bool aborted = false;
-        for_each_item(job_gen, [&](const LevelParams& prm, int cy, int tile) -> bool {
+        for_each_item(job_gen, [&](const LevelParams& prm, int cy, int tile, const TcMaps*) -> bool {
             const int tiles_n = prm.tiles_m * prm.tiles_p;
             const int nsub = (prm.c + kSub - 1) / kSub;
             const bool coarse_sign = prm.l > 0;
             const float scale = static_cast<float>(prm.w_fine);
-            const int tm0 = (tile / prm.tiles_p) * C::kRows;
-            const int tp0 = (tile % prm.tiles_p) * BN;
+            const Geo geo = geometry(prm, tile);
+            const int tm0 = geo.tm0;
+            const int tp0 = geo.tp0;
+            const int brow0 = geo.bcol0 - tp0;   // first row of this CTA's part of the transposed B tile
             const uint64_t chunk = prm.chunk0 + static_cast<uint64_t>(cy);
             const uint64_t sa = max(prm.s_begin, chunk * static_cast<uint64_t>(prm.chunk));
             const uint64_t sb = min(prm.s_end, (chunk + 1) * static_cast<uint64_t>(prm.chunk));
             float* part = static_cast<float*>(prm.partial_sum) + static_cast<int64_t>(cy) * prm.m * prm.p;
-            const int a_bytes = min(C::kRows, prm.m_pad - tm0) * 8;  // B pairs follow A's in a staged slot
             double q = 0.0;
             const double scale_sq = static_cast<double>(scale) * static_cast<double>(scale);
             // Drain mapping.  MH == 2: warp group h reads M-half h (all BN columns); MH == 1: the two
@@ -437,7 +535,8 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                         atomicExch(ex.err_flag, MLMC_ERR_TIMEOUT);
                     }
                     const int* idx = idx_s + b * kSub;
-                    const unsigned char* st = staging + b * C::kStageBytes;
+                    const unsigned char* st = staging + b * C::kStageBytes;   // A parts of the slots
+                    const unsigned char* stB = st + kSub * C::kRows * 8;          // then their B parts
                     ok = __all_sync(0xffffffffu, ok);   // whole warps generate or skip (E4M3 uses shuffles)
                     if (ok) {
                         constexpr int kGroups = kSub / 8;   // 8-slot groups per sub-block
@@ -449,18 +548,31 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                                     const int g4 = it % (C::kRows / 4);
                                     const int sg = it / (C::kRows / 4);
                                     const int i = tm0 + 4 * g4;
-                                    gen_block(idx, sg * 8, i < prm.m, static_cast<uint32_t>(i >> 2), s_lo, lsw,
-                                              prm.rkA, st + (sg * 8) * C::kSlotBytes + g4 * 32, C::kSlotBytes, false,
-                                              a_tile, 4 * g4, kGroups * kk + sg);
+                                    if constexpr (P)
+                                        gen_block<64>(idx, sg * 8, i < prm.m, static_cast<uint32_t>(i >> 2), s_lo,
+                                                      lsw, prm.rkA, st + (sg * 8) * (C::kRows * 8) + g4 * 32,
+                                                      C::kRows * 8, false, a_tile + kk * C::kASliceBytes, 4 * g4, sg);
+                                    else
+                                        gen_block(idx, sg * 8, i < prm.m, static_cast<uint32_t>(i >> 2), s_lo, lsw,
+                                                  prm.rkA, st + (sg * 8) * (C::kRows * 8) + g4 * 32, C::kRows * 8,
+                                                  false, a_tile, 4 * g4, kGroups * kk + sg);
                                 } else {
-                                    // 4 columns of B (rows of the transposed tile) x 8 slots, sign folded in
+                                    // 4 columns of B (rows of the transposed tile) x 8 slots, sign folded in;
+                                    // a pair also writes them into the peer's B tile
                                     const int it2 = it - kItemsA;
-                                    const int g4 = it2 % (BN / 4);
-                                    const int sg = it2 / (BN / 4);
-                                    const int jc = tp0 + 4 * g4;
-                                    gen_block(idx, sg * 8, jc < prm.p, static_cast<uint32_t>(jc >> 2), s_lo, lsw,
-                                              prm.rkB, st + (sg * 8) * C::kSlotBytes + a_bytes + g4 * 32,
-                                              C::kSlotBytes, coarse_sign, b_tile, 4 * g4, kGroups * kk + sg);
+                                    const int g4 = it2 % (C::kBGen / 4);
+                                    const int sg = it2 / (C::kBGen / 4);
+                                    const int jc = geo.bcol0 + 4 * g4;
+                                    if constexpr (P)
+                                        gen_block<64>(idx, sg * 8, jc < prm.p, static_cast<uint32_t>(jc >> 2), s_lo,
+                                                      lsw, prm.rkB, stB + (sg * 8) * (C::kBGen * 8) + g4 * 32,
+                                                      C::kBGen * 8, coarse_sign, b_tile + kk * C::kBSliceBytes,
+                                                      brow0 + 4 * g4, sg);
+                                    else
+                                        gen_block(idx, sg * 8, jc < prm.p, static_cast<uint32_t>(jc >> 2), s_lo, lsw,
+                                                  prm.rkB, stB + (sg * 8) * (C::kBGen * 8) + g4 * 32,
+                                                  C::kBGen * 8, coarse_sign, b_tile, brow0 + 4 * g4,
+                                                  kGroups * kk + sg);
                                 }
                             } else {
                                 // E4M3: the kGroups threads of one row group are adjacent lanes, so the
@@ -469,15 +581,15 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                                     const int g4 = it / kGroups, sg = it % kGroups;
                                     const int i = tm0 + 4 * g4;
                                     gen_block_e4m3(idx, sg * 8, i < prm.m, static_cast<uint32_t>(i >> 2), s_lo, lsw,
-                                                   prm.rkA, st + (sg * 8) * C::kSlotBytes + g4 * 32, C::kSlotBytes,
+                                                   prm.rkA, st + (sg * 8) * (C::kRows * 8) + g4 * 32, C::kRows * 8,
                                                    false, a_tile, 4 * g4, kGroups * kk + sg);
                                 } else {
                                     const int it2 = it - kItemsA;
                                     const int g4 = it2 / kGroups, sg = it2 % kGroups;
-                                    const int jc = tp0 + 4 * g4;
+                                    const int jc = geo.bcol0 + 4 * g4;
                                     gen_block_e4m3(idx, sg * 8, jc < prm.p, static_cast<uint32_t>(jc >> 2), s_lo, lsw,
-                                                   prm.rkB, st + (sg * 8) * C::kSlotBytes + a_bytes + g4 * 32,
-                                                   C::kSlotBytes, coarse_sign, b_tile, 4 * g4, kGroups * kk + sg);
+                                                   prm.rkB, stB + (sg * 8) * (C::kBGen * 8) + g4 * 32,
+                                                   C::kBGen * 8, coarse_sign, b_tile, 4 * g4, kGroups * kk + sg);
                                 }
                             }
                         }
@@ -491,25 +603,64 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                         aborted = true;
                         break;
                     }
-                    if (tid == 0) {
+                    // MMAs of sub-block jj (slice kj) into D and, for tiles that keep it, the chunk sum S
+                    auto issue_mma = [&](int jj, int kj) {
                         tc::tc_fence_after_sync();
 #pragma unroll
                         for (int ks = 0; ks < C::kKSteps; ++ks) {
-                            const int koff = 32 * (kk * C::kKSteps + ks);   // bytes into the swizzle atom
-                            const bool acc = j > 0 || ks > 0;
+                            const int koff = 32 * (kj * C::kKSteps + ks);   // bytes into the swizzle atom
+                            const bool acc = jj > 0 || ks > 0;
 #pragma unroll
                             for (int h = 0; h < MH; ++h) {
+                                // pairs: slice kj has its own 64-byte-swizzled A and B tiles
                                 const uint64_t adesc =
-                                    tc::sw128_kmajor_desc(tc::smem_addr(a_tile) + h * 128 * 128 + koff);
-                                const uint64_t bdesc = tc::sw128_kmajor_desc(tc::smem_addr(b_tile) + koff);
+                                    P ? tc::sw64_kmajor_desc(tc::smem_addr(a_tile) + kj * C::kASliceBytes + 32 * ks)
+                                      : tc::sw128_kmajor_desc(tc::smem_addr(a_tile) + h * 128 * 128 + koff);
+                                const uint64_t bdesc =
+                                    P ? tc::sw64_kmajor_desc(tc::smem_addr(b_tile) + kj * C::kBSliceBytes + 32 * ks)
+                                      : tc::sw128_kmajor_desc(tc::smem_addr(b_tile) + koff);
                                 tc::mma_bf16(tmem + h * BN, adesc, bdesc, idesc, acc ? 1u : 0u);
                                 if constexpr (C::kAccS)   // running sum of the chunk's samples
                                     tc::mma_bf16(tmem + C::kTileCols + h * BN, adesc, bdesc, idesc,
                                                  (acc || s != sa) ? 1u : 0u);
                             }
                         }
-                        tc::mma_commit(bar_slice(kk));
-                        if (j == nsub - 1) tc::mma_commit(bar_done);
+                        if constexpr (P)
+                            tc::mma_commit_multicast(bar_slice(kj), 0x3);   // both CTAs wait for this slice
+                        else
+                            tc::mma_commit(bar_slice(kj));
+                        if (jj == nsub - 1) tc::mma_commit(bar_done);
+                    };
+                    if constexpr (P) {
+                        // Pairs: send our half of this slice of B to the peer (async proxy, counted on its
+                        // barrier); the MMAs of a sub-block are issued one sub-block later, once the
+                        // peer's half has had a sub-block's time to land, and at the sample's end.
+                        if (tid == 0) {
+                            const uint32_t off = static_cast<uint32_t>(kk * C::kBSliceBytes + brow0 * 64);
+                            const uint32_t bytes = static_cast<uint32_t>(C::kBGen * 64);
+                            tc::bulk_copy_s2s_cluster(peer_b_tile + off, tc::smem_addr(b_tile) + off, bytes,
+                                                      tc::map_to_cta(bar_peer(kk), peer));
+                            tc::mbar_arrive_expect_tx(bar_peer(kk), bytes);
+                            auto wait_peer = [&](int kj) {
+                                if (!tc::mbar_wait_cluster_bounded(bar_peer(kj), (peer_par >> kj) & 1u,
+                                                                   tc::globaltimer() + ex.timeout_ns)) {
+                                    *abort_s = 1;
+                                    atomicExch(ex.err_flag, MLMC_ERR_TIMEOUT);
+                                }
+                                peer_par ^= 1u << kj;
+                            };
+                            if (j > 0) {
+                                const int kprev = (j - 1) % kSlices;
+                                wait_peer(kprev);
+                                issue_mma(j - 1, kprev);
+                            }
+                            if (j == nsub - 1) {
+                                wait_peer(kk);
+                                issue_mma(j, kk);
+                            }
+                        }
+                    } else if (tid == 0) {
+                        issue_mma(j, kk);
                     }
                     slice_par ^= 1u << kk;
                     slice_seen |= 1u << kk;
@@ -593,7 +744,7 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
             if (tid == 0) {
                 double t = 0.0;
                 for (int w = 0; w < kGenWarps; ++w) t += red_s[w];
-                prm.partial_q[static_cast<int64_t>(cy) * tiles_n + tile] = t;
+                if (geo.qtile >= 0) prm.partial_q[static_cast<int64_t>(cy) * tiles_n + geo.qtile] = t;
             }
             tc::named_barrier(kGenBarrier, kGenThreads);
             return true;
@@ -606,6 +757,7 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
     }
     tc::tc_fence_before_sync();
     __syncthreads();
+    if constexpr (P) tc::cluster_sync();   // no remote store or arrival can reach a CTA that left
     if (warp == 0) tc::tmem_dealloc(tmem, C::kTmemCols);
 }
 
@@ -676,6 +828,37 @@ struct GridF {
     }
 };
 
+// A cluster pair (two CTAs, 128 rows each) on one 256 x 256 output tile.
+cudaError_t launch_pair(const LevelParams& prm, const TcLaunch& tl, cudaStream_t st)
+{
+    using C = TcCfg<1, 256, 0, 1>;
+    auto kern = level_tc_bf16_kernel<1, 256, 0, false, 1>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = C::kSmemBytes;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3(2 * static_cast<unsigned>(tl.num_sms / 2));
+    int max_clusters = 0;
+    e = cudaOccupancyMaxActiveClusters(&max_clusters, kern, &cfg);
+    if (e != cudaSuccess) return e;
+    const int pair_items = prm.nchunks * ((prm.tiles_m + 1) / 2) * prm.tiles_p;
+    const int clusters = max(1, min(pair_items, max(1, max_clusters)));
+    cfg.gridDim = dim3(2 * static_cast<unsigned>(clusters));
+    TcExtra ex{tl.err_flag, tl.timeout_ns, pair_items, tl.scale};
+    e = cudaLaunchKernelEx(&cfg, kern, prm, ex, TcBatch{});
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
 template <int MH, int BN, int Q>
 struct FitsF {
     static bool run() { return TcCfg<MH, BN, Q>::kFits; }
@@ -708,38 +891,85 @@ auto dispatch_tile(const TcTile& t, int q, Args&&... args)
 
 }  // namespace
 
+int tc_stage_width_a(const TcTile& t) { return t.pair ? 128 : 128 * t.mh; }
+int tc_stage_width_b(const TcTile& t) { return t.pair ? t.bn / 2 : t.bn; }
+
+bool tc_encode_maps(TcMaps* maps, const void* base, int64_t n, int64_t ld, int wa, int wb)
+{
+    std::memset(maps, 0, sizeof(TcMaps));
+    using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static Encode encode = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            encode = reinterpret_cast<Encode>(fn);
+        looked_up = true;
+    }
+    if (!encode || wa < 2 || wb < 2 || wa > 256 || wb > 256 || (ld % 2) != 0) return false;
+    // n rows of ld / 2 eight-byte (M, S) pairs; rows ld * 4 bytes apart; boxes of one row
+    const cuuint64_t dims[2] = {static_cast<cuuint64_t>(ld / 2), static_cast<cuuint64_t>(n)};
+    const cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * 4};
+    const cuuint32_t estr[2] = {1, 1};
+    if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || (strides[0] & 15) != 0) return false;
+    const cuuint32_t box_a[2] = {static_cast<cuuint32_t>(wa), 1};
+    const cuuint32_t box_b[2] = {static_cast<cuuint32_t>(wb), 1};
+    void* g = const_cast<void*>(base);
+    if (encode(&maps->a, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, g, dims, strides, box_a, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    if (encode(&maps->b, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, g, dims, strides, box_b, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    maps->wa = wa;
+    maps->wb = wb;
+    maps->valid = 1;
+    return true;
+}
+
 bool tc_tile_valid(const TcTile& t, int q)
 {
+    if (t.pair) return t.mh == 1 && t.bn == 256 && q == 0;
     if (!((t.mh == 1 || t.mh == 2) && (t.bn == 32 || t.bn == 64 || t.bn == 128 || t.bn == 256))) return false;
     return dispatch_tile<FitsF>(t, q);
 }
 
-TcTile tc_tile_for(int64_t m, int64_t p, int q)
+TcTile tc_tile_for(int64_t m, int64_t p, int q, bool allow_pair)
 {
-    TcTile t;
+    TcTile t{};
+    if (allow_pair && q == 0 && m > 128 && p > 128) return TcTile{1, 256, 128, 1};   // cluster pair
     t.mh = m <= 128 ? 1 : 2;
     t.bn = p <= 32 ? 32 : p <= 64 ? 64 : p <= 128 ? 128 : 256;
     while (!tc_tile_valid(t, q) && t.bn > 32) t.bn /= 2;   // E4M3: narrower column tiles
     t.rows = 128 * t.mh;
+    t.pair = 0;
     return t;
 }
 
 cudaError_t launch_level_tc(const LevelParams& prm, const TcTile& tile, int q, const TcLaunch& tl, cudaStream_t st)
 {
     if (!tc_tile_valid(tile, q)) return cudaErrorInvalidValue;
+    if (tile.pair) return launch_pair(prm, tl, st);
     return dispatch_tile<SingleF>(tile, q, prm, tl, st);
 }
 
 int tc_batch_grid(const TcTile& tile, int q, int num_sms)
 {
-    if (!tc_tile_valid(tile, q)) return 0;
+    if (!tc_tile_valid(tile, q) || tile.pair) return 0;
     return dispatch_tile<GridF>(tile, q, num_sms);
 }
 
 cudaError_t launch_level_tc_batch(const TcBatch& bt, const TcTile& tile, int q, int grid, const TcLaunch& tl,
                                   cudaStream_t st)
 {
-    if (!tc_tile_valid(tile, q)) return cudaErrorInvalidValue;
+    if (!tc_tile_valid(tile, q) || tile.pair) return cudaErrorInvalidValue;
     return dispatch_tile<BatchF>(tile, q, bt, grid, tl, st);
 }
 

@@ -73,10 +73,106 @@ __device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uin
                  : "memory");
 }
 
+// TMA row gather: four rows r0..r3 of the 2-D tensor described by `tmap` (a CUtensorMap in
+// param, constant or global memory; box of one row), each starting at element column `col`,
+// land back to back at shared `dst`; completion is reported to `bar` as transaction bytes.
+// col * element size must be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_gather4(uint32_t dst, const void* tmap, int col, int r0, int r1, int r2, int r3,
+                                            uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(col), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(bar)
+        : "memory");
+}
+
+// A tensor map in global memory that may have been rewritten since the last kernel read it:
+// make its current contents visible to this thread's later tensor copies (descriptor caches).
+__device__ __forceinline__ void tensormap_acquire(const void* tmap)
+{
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(tmap))
+                 : "memory");
+}
+
 // Barrier over the first `count` threads of the CTA (named barrier `id`, 1..15).
 __device__ __forceinline__ void named_barrier(int id, int count)
 {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// ---- thread-block clusters (CTA pairs sharing an operand tile) ----
+
+__device__ __forceinline__ uint32_t cluster_ctarank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Address of the same shared-memory location in CTA `rank` of the cluster (shared::cluster window).
+__device__ __forceinline__ uint32_t map_to_cta(uint32_t saddr, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void st_cluster_v4(uint32_t caddr, uint4 v)
+{
+    asm volatile("st.shared::cluster.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(caddr), "r"(v.x), "r"(v.y), "r"(v.z),
+                 "r"(v.w)
+                 : "memory");
+}
+
+// Generic-proxy writes to shared memory of the cluster become visible to the async proxy.
+__device__ __forceinline__ void fence_proxy_async_cluster()
+{
+    asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
+}
+
+// Arrive (release, cluster scope) on an mbarrier of another CTA of the cluster.
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t caddr)
+{
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(caddr) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait (acquire at cluster scope) for a barrier that other CTAs arrive on.
+__device__ __forceinline__ bool mbar_wait_cluster_bounded(uint32_t bar, uint32_t parity, uint64_t deadline)
+{
+    for (;;) {
+        if (mbar_try_wait_cluster(bar, parity)) return true;
+        if (globaltimer() > deadline) return false;
+    }
+}
+
+// Bulk copy (async proxy) of `bytes` (multiple of 16) from this CTA's shared memory `src` to
+// `dst` in another CTA of the cluster; completion is counted as transaction bytes on the
+// mbarrier `bar` of that CTA (dst and bar are shared::cluster addresses, e.g. from map_to_cta).
+__device__ __forceinline__ void bulk_copy_s2s_cluster(uint32_t dst, uint32_t src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     dst),
+                 "r"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+// Whole-cluster execution barrier (every thread of every CTA of the cluster).
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 // Fire-and-forget vector reduction into global memory.
@@ -134,6 +230,14 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
                  : "memory");
 }
 
+// The same, arriving on the mbarrier at this shared-memory offset in every CTA of `cta_mask`.
+__device__ __forceinline__ void mma_commit_multicast(uint32_t bar, uint16_t cta_mask)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+                 ::"r"(bar), "h"(cta_mask)
+                 : "memory");
+}
+
 // 32 lanes x 32 consecutive 32-bit columns: thread L of the warp receives lane (base + L).
 __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, float v[32])
 {
@@ -185,6 +289,20 @@ __device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t saddr)
     return d;
 }
 
+// The same for the 64-byte swizzled layout: rows of 32 bf16 (64 bytes), 8-row groups 512 bytes
+// apart, tile base 512-byte aligned; advancing the start address by 32 bytes selects the second
+// 16-element K step.
+__device__ __forceinline__ uint64_t sw64_kmajor_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);  // start address
+    d |= static_cast<uint64_t>(1) << 16;                   // leading byte offset (unused here)
+    d |= static_cast<uint64_t>(512 >> 4) << 32;            // stride byte offset: 8 rows x 64 B
+    d |= static_cast<uint64_t>(1) << 46;                   // descriptor version
+    d |= static_cast<uint64_t>(4) << 61;                   // swizzle: 64 B
+    return d;
+}
+
 // Instruction descriptor: bf16 A and B, f32 accumulator, both K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N)
 {
@@ -199,6 +317,13 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N)
 __device__ __forceinline__ uint32_t sw128_offset(int row, int chunk)
 {
     return static_cast<uint32_t>((row >> 3) * 1024 + (row & 7) * 128 + ((chunk ^ (row & 7)) << 4));
+}
+
+// Byte offset of (row, 16-byte chunk 0..3) inside a 64-byte-swizzled K-major tile (the chunk
+// index is XORed with bits 1-2 of the row).
+__device__ __forceinline__ uint32_t sw64_offset(int row, int chunk)
+{
+    return static_cast<uint32_t>(row * 64 + ((chunk ^ ((row >> 1) & 3)) << 4));
 }
 
 }  // namespace tc

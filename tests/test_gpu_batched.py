@@ -42,14 +42,19 @@ def _specs(shapes, seed0=0):
 
 
 def _single_tile(m, p):
-    # the single-problem launch's tile for an m x p output: 128 or 256 rows, 32..256 columns
+    # the single-problem launch's tile for an m x p output: the CTA pair 3256 above 128 x 128,
+    # else 128 or 256 rows and 32..256 columns
+    if m > 128 and p > 128:
+        return 3256
     mh = 1 if m <= 128 else 2
     bn = 32 if p <= 32 else 64 if p <= 64 else 128 if p <= 128 else 256
     return 1000 * mh + bn
 
 
 def _sum_in_tmem(tile_id):
-    return (tile_id // 1000) * (tile_id % 1000) <= 256
+    # the pair's CTAs hold 128 x 256 each, like tile 1256
+    rows, cols = (1, 256) if tile_id // 1000 == 3 else (tile_id // 1000, tile_id % 1000)
+    return rows * cols <= 256
 
 
 def _states(plan, nprob, L):

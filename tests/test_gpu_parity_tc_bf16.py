@@ -134,3 +134,35 @@ def test_bf16_rejects_other_ratios():
         ts = [torch.from_numpy(x).to(dev) for x in (pp.M, pp.S, pp.Mp, pp.Sp)]
         binding.Plan([binding.ProblemSpec(*ts)], c0=4, L=2, ratio=3, precision="bf16")
     assert e.value.status == 6
+
+
+PAIR_CASES = [
+    (256, 65536, 256, 64, 8, [(0, 0), (0, 777), (2, 5), (8, 1)]),     # the large workload's shape
+    (200, 3000, 300, 32, 2, [(0, 4), (2, 11)]),                       # ragged rows, two column tiles
+    (300, 2000, 260, 16, 3, [(0, 0), (3, 5)]),                        # three row tiles: one pair half empty
+]
+
+
+@pytest.mark.parametrize("m,n,p,c0,L,picks", PAIR_CASES)
+def test_bf16_cta_pair_tile_matches_oracle_and_single_cta_tile(m, n, p, c0, L, picks):
+    """Tile 3256 (two CTAs of a cluster share a 256 x 256 tile, each generating half of B for both)
+    against the FP64 oracle, and its level sums against the 128 x 256 single-CTA tile (the same
+    MMA chain per element, so the sums agree bit for bit)."""
+    pp = make_params(m, n, p, seed_A=3, seed_B=4, seed_idx=5, problem_id=1, dtype=np.float32)
+    orc = _orc(pp)
+    lv = oracle.Levels(c0, 2, L)
+    with _plan(pp, c0, L, tile_override=3256) as plan:
+        for l, s in picks:
+            c = lv.cl(l)
+            D = plan.debug_sample(0, l, s).cpu().numpy()
+            Dref, _, _, mag = oracle.sample(orc, lv, l, s)
+            assert np.all(np.abs(D - Dref) / mag <= tau_bf16(c)), (l, s)
+    with _plan(pp, c0, L, tile_override=3256) as a, _plan(pp, c0, L, tile_override=1256) as b:
+        for l in range(min(L, 3) + 1):
+            a.level_stats(0, l, 0, 96)
+            b.level_stats(0, l, 0, 96)
+            na, sa, qa = a.get_level_state(0, l)
+            nb, sb, qb = b.get_level_state(0, l)
+            assert na == nb == 96
+            assert torch.equal(sa, sb)
+            assert qa == qb
