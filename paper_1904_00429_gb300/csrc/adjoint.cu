@@ -122,6 +122,22 @@ __global__ void scan_add_kernel(int64_t* __restrict__ data, int64_t count, const
 }
 
 // --- 3. segment reduction ---------------------------------------------------------------
+
+// Normals of the replayed entries: the form the forward kernel of the plan's precision used.
+// BF16 plans draw them with the special-function-unit Box-Muller of the tensor-core kernel, so
+// the straight-through gradient sees the very entries the forward rounded.
+template <typename T>
+__device__ __forceinline__ void adj_normals(uint4 w, T z[4], bool sfu)
+{
+    if constexpr (sizeof(T) == 4) {
+        if (sfu)
+            normals4_mufu(w, z);
+        else
+            Normals<T>::four(w, z);
+    } else {
+        Normals<T>::four(w, z);
+    }
+}
 template <typename T>
 __device__ __forceinline__ T round_operand(T x, bool bf16)
 {
@@ -252,7 +268,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) segment_kernel(const AdjSegmen
                         make_uint4(static_cast<uint32_t>((o0 >> 2) + g4), static_cast<uint32_t>(k),
                                    static_cast<uint32_t>(s), level_sample_word(static_cast<int>(rec & 31), s)),
                         rk_out);
-                    Normals<T>::four(w, z);
+                    adj_normals<T>(w, z, prm.bf16 != 0);
                 }
 #pragma unroll
                 for (int h = 0; h < 4; ++h) zo[j * OB + 4 * g4 + h] = z[h];
@@ -278,7 +294,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) segment_kernel(const AdjSegmen
                                        level_sample_word(static_cast<int>(rec & 31), s)),
                             rk_in);
                         T z[4];
-                        Normals<T>::four(w, z);
+                        adj_normals<T>(w, z, prm.bf16 != 0);
 #pragma unroll
                         for (int h = 0; h < 4; ++h)
                             if (x + h < kin) v[h] = round_operand(fma(row[2 * (x + h) + 1], z[h], row[2 * (x + h)]), prm.bf16);
