@@ -52,7 +52,9 @@ constexpr int kGenBarrier = 1;              // named barrier of the generator wa
 // the peer has three sub-blocks of slack before a slice is reused.
 template <int MH, int BN, int Q, int P = 0>
 struct TcCfg {
-    static constexpr int kSub = (Q || P) ? 32 : 16;        // slots per sub-block (one E4M3 scale block)
+    // Slots per sub-block: 32 for E4M3 (one scale block), pairs, and small tiles whose 16-slot
+    // sub-block would leave generator threads idle ((rows + BN) / 4 x 2 items for 256 threads)
+    static constexpr int kSub = (Q || P || 128 * MH + BN <= 256) ? 32 : 16;
     static constexpr int kKSteps = kSub / 16;              // MMA K steps per sub-block
     static constexpr int kSlices = P ? 4 : 64 / kSub;      // sub-blocks in flight (128-byte atom: 64 bf16)
     static constexpr int kRows = 128 * MH;                 // output rows of a tile
