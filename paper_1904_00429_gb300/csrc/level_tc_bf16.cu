@@ -74,7 +74,7 @@ struct TcCfg {
     static constexpr int kTmemCols = kAccCols <= 32 ? 32 : kAccCols <= 64 ? 64 : kAccCols <= 128 ? 128
                                      : kAccCols <= 256 ? 256 : 512;
     // barriers: full[2], empty[2], slice[kSlices], done, and for pairs peer[kSlices] (the peer's B half landed)
-    static constexpr int kNumBars = 2 + 2 + kSlices + 1 + (P ? kSlices : 0);
+    static constexpr int kNumBars = 2 + 2 + kSlices + 1 + (P ? kSlices : 0) + 1 /*abort drain*/;
     static constexpr int kBookBytes = 2 * kSub * 4 /*idx*/ + kNumBars * 8 + 16 /*tmem, abort*/ + kGenWarps * 8 +
                                       (P ? 0 : 2 * static_cast<int>(sizeof(LevelParams)) +
                                                    static_cast<int>(alignof(LevelParams)))
@@ -261,6 +261,7 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
     auto bar_empty = [&](int b) { return bars0 + 8 * (2 + b); };
     auto bar_slice = [&](int kk) { return bars0 + 8 * (4 + kk); };
     auto bar_peer = [&](int kk) { return bars0 + 8 * (4 + kSlices + 1 + kk); };
+    const uint32_t bar_quiesce = bars0 + 8 * (C::kNumBars - 1);   // used once, after an abort
     const uint32_t crank = P ? tc::cluster_ctarank() : 0u;   // this CTA's half of a pair
     const uint32_t peer = crank ^ 1u;
 
@@ -273,6 +274,7 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
         // a slice is free again once this CTA's MMA and, for pairs, the peer's MMA have read it
         for (int kk = 0; kk < kSlices; ++kk) tc::mbar_init(bar_slice(kk), P ? 2 : 1);
         tc::mbar_init(bar_done, 1);
+        tc::mbar_init(bar_quiesce, 1);
         if constexpr (P)
             for (int kk = 0; kk < kSlices; ++kk) tc::mbar_init(bar_peer(kk), 1);
         tc::mbar_init_fence();
@@ -751,10 +753,11 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
             tc::named_barrier(kGenBarrier, kGenThreads);
             return true;
         }, true);
-        // after an abort make sure no MMA is still writing TMEM before it is freed
+        // after an abort make sure no MMA is still writing TMEM before it is freed: a barrier used
+        // for nothing else completes its first phase once every MMA issued so far has completed
         if (aborted && tid == 0) {
-            tc::mma_commit(bar_done);
-            tc::mbar_wait_bounded(bar_done, done_count & 1, tc::globaltimer() + ex.timeout_ns);
+            tc::mma_commit(bar_quiesce);
+            tc::mbar_wait_bounded(bar_quiesce, 0, tc::globaltimer() + ex.timeout_ns);
         }
     }
     tc::tc_fence_before_sync();
