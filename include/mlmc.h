@@ -112,8 +112,8 @@ typedef struct {
     int32_t tile_override; /* tensor-core tile: 0 = automatic; else 1000 * (rows / 128) + columns,
                               one of 1032 1064 1128 1256 2032 2064 2128 2256 (e.g. 2128 = 256 x 128;
                               E4M3: 1032 1064 1128 2032 2064), or 3256: a cluster of two CTAs of
-                              128 x 256 sharing one 256 x 256 tile (BF16, single-problem launches;
-                              the default for outputs above 128 x 128) */
+                              128 x 256 sharing one 256 x 256 tile (BF16 and E4M3, single-problem
+                              launches; the default for outputs above 128 x 128) */
     int32_t adjoint_batch_log2; /* mlmc_backward replays at most 2^this sampled products per batch
                                    (0 = 26; at least c_L + 1 are always taken); scratch is 8 B each */
 } mlmc_options;

@@ -198,7 +198,7 @@ mlmc_status validate(const mlmc_problem* problems, int32_t nprob, const mlmc_opt
     if (o->timeout_ns < 0) return fail(MLMC_ERR_INVALID_ARG, "timeout_ns must be >= 0");
     if (o->tile_override != 0 && !tc_tile_valid(decode_tile(o->tile_override), o->precision == MLMC_FP8_E4M3 ? 1 : 0))
         return fail(MLMC_ERR_INVALID_ARG, "tile_override %d is not a tile id of this precision (1032 .. 2256; "
-                    "E4M3: 1032 1064 1128 2032 2064)", o->tile_override);
+                    "E4M3: 1032 1064 1128 2032 2064; pairs 3256)", o->tile_override);
     if (o->adjoint_batch_log2 < 0 || o->adjoint_batch_log2 > 40)
         return fail(MLMC_ERR_INVALID_ARG, "adjoint_batch_log2 must be in [0, 40]");
     for (int32_t q = 0; q < nprob; ++q) {

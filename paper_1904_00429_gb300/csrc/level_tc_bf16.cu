@@ -83,7 +83,7 @@ struct TcCfg {
     static_assert(kAccCols <= 512, "tile exceeds tensor memory");
     static_assert(BN % 16 == 0 && BN >= 32 && BN <= 256, "N of the MMA");
     static constexpr bool kFits = kSmemBytes <= 227 * 1024 &&   // E4M3's 32-slot staging rules out wide tiles
-                                  (!P || (MH == 1 && BN == 256 && Q == 0));
+                                  (!P || (MH == 1 && BN == 256));
 };
 
 struct TcExtra {
@@ -167,6 +167,7 @@ __device__ __forceinline__ float e4m3_block_scale(float absmax)
     return ldexpf(1.0f, e);
 }
 
+template <int kSw = 128>
 __device__ __forceinline__ void gen_block_e4m3(const int* idx, int slot0, bool valid_rows, uint32_t rowgrp,
                                                uint32_t s_lo, uint32_t lsw, const PhiloxRoundKeys& rk,
                                                const unsigned char* stage, int stride, bool odd_negative,
@@ -220,7 +221,7 @@ __device__ __forceinline__ void gen_block_e4m3(const int* idx, int slot0, bool v
             const float2 d = __half22float2(*reinterpret_cast<const __half2*>(&hr));
             packed[u2] = pack_bf16x2(d.x * sc, d.y * sc);
         }
-        *reinterpret_cast<uint4*>(tile + tc::sw128_offset(row0 + r, chunk)) =
+        *reinterpret_cast<uint4*>(tile + tile_offset<kSw>(row0 + r, chunk)) =
             make_uint4(packed[0], packed[1], packed[2], packed[3]);
     }
 }
@@ -581,19 +582,33 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                             } else {
                                 // E4M3: the kGroups threads of one row group are adjacent lanes, so the
                                 // block maximum is a shuffle; a warp is all-A or all-B (kItemsA % 32 == 0)
+                                // (pairs: slice tiles in the 64-byte swizzle, as for bfloat16)
                                 if (it < kItemsA) {
                                     const int g4 = it / kGroups, sg = it % kGroups;
                                     const int i = tm0 + 4 * g4;
-                                    gen_block_e4m3(idx, sg * 8, i < prm.m, static_cast<uint32_t>(i >> 2), s_lo, lsw,
-                                                   prm.rkA, st + (sg * 8) * (C::kRows * 8) + g4 * 32, C::kRows * 8,
-                                                   false, a_tile, 4 * g4, kGroups * kk + sg);
+                                    if constexpr (P)
+                                        gen_block_e4m3<64>(idx, sg * 8, i < prm.m, static_cast<uint32_t>(i >> 2), s_lo,
+                                                           lsw, prm.rkA, st + (sg * 8) * (C::kRows * 8) + g4 * 32,
+                                                           C::kRows * 8, false, a_tile + kk * C::kASliceBytes, 4 * g4,
+                                                           sg);
+                                    else
+                                        gen_block_e4m3(idx, sg * 8, i < prm.m, static_cast<uint32_t>(i >> 2), s_lo, lsw,
+                                                       prm.rkA, st + (sg * 8) * (C::kRows * 8) + g4 * 32, C::kRows * 8,
+                                                       false, a_tile, 4 * g4, kGroups * kk + sg);
                                 } else {
                                     const int it2 = it - kItemsA;
                                     const int g4 = it2 / kGroups, sg = it2 % kGroups;
                                     const int jc = geo.bcol0 + 4 * g4;
-                                    gen_block_e4m3(idx, sg * 8, jc < prm.p, static_cast<uint32_t>(jc >> 2), s_lo, lsw,
-                                                   prm.rkB, stB + (sg * 8) * (C::kBGen * 8) + g4 * 32,
-                                                   C::kBGen * 8, coarse_sign, b_tile, 4 * g4, kGroups * kk + sg);
+                                    if constexpr (P)
+                                        gen_block_e4m3<64>(idx, sg * 8, jc < prm.p, static_cast<uint32_t>(jc >> 2), s_lo,
+                                                           lsw, prm.rkB, stB + (sg * 8) * (C::kBGen * 8) + g4 * 32,
+                                                           C::kBGen * 8, coarse_sign, b_tile + kk * C::kBSliceBytes,
+                                                           brow0 + 4 * g4, sg);
+                                    else
+                                        gen_block_e4m3(idx, sg * 8, jc < prm.p, static_cast<uint32_t>(jc >> 2), s_lo, lsw,
+                                                       prm.rkB, stB + (sg * 8) * (C::kBGen * 8) + g4 * 32,
+                                                       C::kBGen * 8, coarse_sign, b_tile, brow0 + 4 * g4,
+                                                       kGroups * kk + sg);
                                 }
                             }
                         }
@@ -834,10 +849,11 @@ struct GridF {
 };
 
 // A cluster pair (two CTAs, 128 rows each) on one 256 x 256 output tile.
+template <int Q>
 cudaError_t launch_pair(const LevelParams& prm, const TcLaunch& tl, cudaStream_t st)
 {
-    using C = TcCfg<1, 256, 0, 1>;
-    auto kern = level_tc_bf16_kernel<1, 256, 0, false, 1>;
+    using C = TcCfg<1, 256, Q, 1>;
+    auto kern = level_tc_bf16_kernel<1, 256, Q, false, 1>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
     if (e != cudaSuccess) return e;
     cudaLaunchAttribute attr[1];
@@ -941,7 +957,7 @@ bool tc_encode_maps(TcMaps* maps, const void* base, int64_t n, int64_t ld, int w
 
 bool tc_tile_valid(const TcTile& t, int q)
 {
-    if (t.pair) return t.mh == 1 && t.bn == 256 && q == 0;
+    if (t.pair) return t.mh == 1 && t.bn == 256 && (q == 0 || q == 1);
     if (!((t.mh == 1 || t.mh == 2) && (t.bn == 32 || t.bn == 64 || t.bn == 128 || t.bn == 256))) return false;
     return dispatch_tile<FitsF>(t, q);
 }
@@ -949,7 +965,7 @@ bool tc_tile_valid(const TcTile& t, int q)
 TcTile tc_tile_for(int64_t m, int64_t p, int q, bool allow_pair)
 {
     TcTile t{};
-    if (allow_pair && q == 0 && m > 128 && p > 128) return TcTile{1, 256, 128, 1};   // cluster pair
+    if (allow_pair && m > 128 && p > 128) return TcTile{1, 256, 128, 1};   // cluster pair
     t.mh = m <= 128 ? 1 : 2;
     t.bn = p <= 32 ? 32 : p <= 64 ? 64 : p <= 128 ? 128 : 256;
     while (!tc_tile_valid(t, q) && t.bn > 32) t.bn /= 2;   // E4M3: narrower column tiles
@@ -961,7 +977,7 @@ TcTile tc_tile_for(int64_t m, int64_t p, int q, bool allow_pair)
 cudaError_t launch_level_tc(const LevelParams& prm, const TcTile& tile, int q, const TcLaunch& tl, cudaStream_t st)
 {
     if (!tc_tile_valid(tile, q)) return cudaErrorInvalidValue;
-    if (tile.pair) return launch_pair(prm, tl, st);
+    if (tile.pair) return q ? launch_pair<1>(prm, tl, st) : launch_pair<0>(prm, tl, st);
     return dispatch_tile<SingleF>(tile, q, prm, tl, st);
 }
 
