@@ -348,6 +348,15 @@ MLMC_API mlmc_status mlmc_debug_normals(mlmc_plan_t* plan, int32_t prob, int32_t
 MLMC_API mlmc_status mlmc_debug_sample(mlmc_plan_t* plan, int32_t prob, int32_t level, uint64_t sample,
                               double* D_dev);
 
+/* Failure detection (no counterpart in the paper): launch on the plan's stream
+ * a kernel whose bounded wait can never be satisfied (an mbarrier that nothing
+ * arrives on).  After timeout_ns (0 < timeout_ns <= 10 s) it gives up and
+ * records MLMC_ERR_TIMEOUT in the plan's device error word, exactly as a level
+ * kernel whose wait gave up does, so the next synchronising call returns
+ * MLMC_ERR_TIMEOUT and the error sticks to the plan.  Nothing faults; the
+ * CUDA context stays usable for other plans. */
+MLMC_API mlmc_status mlmc_debug_bounded_wait(mlmc_plan_t* plan, int64_t timeout_ns);
+
 #ifdef __cplusplus
 }
 #endif

@@ -102,6 +102,7 @@ def lib() -> ctypes.CDLL:
             "mlmc_debug_indices": [P, I32, I32, U64, I64, I64, P],
             "mlmc_debug_normals": [P, I32, I32, I32, U64, I64, I64, I64, P],
             "mlmc_debug_sample": [P, I32, I32, U64, P],
+            "mlmc_debug_bounded_wait": [P, I64],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -339,6 +340,10 @@ class Plan:
         _check(lib().mlmc_debug_normals(self._h, prob, which, level, sample, k, row0, count, _ptr(out)),
                "mlmc_debug_normals")
         return out
+
+    def debug_bounded_wait(self, timeout_ns: int):
+        """Launch a kernel whose bounded wait must give up (failure-detection check)."""
+        _check(lib().mlmc_debug_bounded_wait(self._h, int(timeout_ns)), "mlmc_debug_bounded_wait")
 
     def debug_sample(self, prob: int, level: int, sample: int) -> torch.Tensor:
         m, _, p = self.shapes[prob]

@@ -1359,4 +1359,16 @@ mlmc_status mlmc_debug_sample(mlmc_plan_t* plan, int32_t prob, int32_t level, ui
     return check_cuda(plan, err, "debug sample copy");
 }
 
+mlmc_status mlmc_debug_bounded_wait(mlmc_plan_t* plan, int64_t timeout_ns)
+{
+    mlmc_status st = enter(plan);
+    if (st != MLMC_OK) return st;
+    if (timeout_ns <= 0 || timeout_ns > int64_t(10000000000)) return fail(MLMC_ERR_INVALID_ARG, "timeout_ns must be in (0, 10 s]");
+    DeviceGuard g(plan->device);
+    cudaError_t err = launch_bounded_wait_probe(plan->err_flag, uint64_t(timeout_ns), plan->stream);
+    if (check_cuda(plan, err, "bounded-wait probe launch") != MLMC_OK) return plan->sticky;
+    plan->launches += 1;
+    return MLMC_OK;
+}
+
 }  // extern "C"

@@ -94,6 +94,9 @@ struct TcBatch {
 // Encode the row-gather maps of a table (base, n rows, ld floats per row) for a tile whose A part
 // spans wa pairs and B part wb pairs (<= 256 each); returns false if the driver lacks the call.
 bool tc_encode_maps(TcMaps* maps, const void* base, int64_t n, int64_t ld, int wa, int wb);
+// One warp waits (bounded by timeout_ns) on an mbarrier that nothing arrives on and records
+// MLMC_ERR_TIMEOUT in err_flag when it gives up.
+cudaError_t launch_bounded_wait_probe(int* err_flag, uint64_t timeout_ns, cudaStream_t st);
 // Pairs of the A and B parts a tile's CTA stages per slot.
 int tc_stage_width_a(const TcTile& t);
 int tc_stage_width_b(const TcTile& t);

@@ -41,6 +41,7 @@ constexpr int kGenWarps = 8;
 constexpr int kGenThreads = kGenWarps * 32;
 constexpr int kThreads = kGenThreads + 32;  // + producer warp
 constexpr int kGenBarrier = 1;              // named barrier of the generator warps
+constexpr uint64_t kDrainNs = 100000000ull;   // bound on waiting for own copies in flight after an abort
 
 // Operand formats: Q = 0 rounds the generated entries to bfloat16; Q = 1 quantises them to FP8
 // E4M3 with a power-of-two scale per (row of A or column of B, 32-slot block) and feeds the
@@ -451,6 +452,13 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
             }
             return !aborted;
         }, false);
+        if (aborted) {
+            // copies issued for the last two sub-blocks may still be landing in the staging buffers:
+            // wait for them (bounded) before this CTA can exit
+            for (uint32_t gp = g >= 2 ? g - 2 : 0; gp < g; ++gp)
+                tc::mbar_wait_bounded(bar_full(static_cast<int>(gp & 1)), (gp >> 1) & 1,
+                                      tc::globaltimer() + kDrainNs);
+        }
     } else {
         // ---------------- generator warps: entries, MMA issue, drain ----------------------------
         constexpr uint32_t idesc = tc::idesc_bf16_f32(128, BN);
@@ -458,6 +466,7 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
         constexpr int kItemsB = (C::kBGen / 4) * (kSub / 8);
         uint32_t g = 0;  // sub-blocks consumed
         uint32_t peer_par = 0;    // bit kk: parity of the peer's arrivals on peer barrier kk (pairs)
+        int peer_armed = -1;      // pairs, thread 0: slice whose peer copy is expected but not yet waited for
         uint32_t slice_par = 0;   // bit kk: parity of the MMAs issued on slice kk so far
         uint32_t slice_seen = 0;  // bit kk: slice kk has been used
         uint32_t done_count = 0;
@@ -660,6 +669,7 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                             tc::bulk_copy_s2s_cluster(peer_b_tile + off, tc::smem_addr(b_tile) + off, bytes,
                                                       tc::map_to_cta(bar_peer(kk), peer));
                             tc::mbar_arrive_expect_tx(bar_peer(kk), bytes);
+                            peer_armed = kk;
                             auto wait_peer = [&](int kj) {
                                 if (!tc::mbar_wait_cluster_bounded(bar_peer(kj), (peer_par >> kj) & 1u,
                                                                    tc::globaltimer() + ex.timeout_ns)) {
@@ -667,6 +677,7 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                                     atomicExch(ex.err_flag, MLMC_ERR_TIMEOUT);
                                 }
                                 peer_par ^= 1u << kj;
+                                if (kj == peer_armed) peer_armed = -1;
                             };
                             if (j > 0) {
                                 const int kprev = (j - 1) % kSlices;
@@ -772,12 +783,24 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
         // for nothing else completes its first phase once every MMA issued so far has completed
         if (aborted && tid == 0) {
             tc::mma_commit(bar_quiesce);
-            tc::mbar_wait_bounded(bar_quiesce, 0, tc::globaltimer() + ex.timeout_ns);
+            tc::mbar_wait_bounded(bar_quiesce, 0, tc::globaltimer() + kDrainNs);
+            // pairs: the peer's half of the last slice may still be arriving in our B tile
+            if (P && peer_armed >= 0)
+                tc::mbar_wait_cluster_bounded(bar_peer(peer_armed), (peer_par >> peer_armed) & 1u,
+                                              tc::globaltimer() + kDrainNs);
         }
     }
     tc::tc_fence_before_sync();
     __syncthreads();
-    if constexpr (P) tc::cluster_sync();   // no remote store or arrival can reach a CTA that left
+    if constexpr (P) {
+        tc::cluster_sync();   // no remote copy or arrival can reach a CTA that left
+        if (*abort_s) {
+            // after an abort a copy the peer sent for a sub-block we never reached may still be in
+            // flight (it cannot be waited for): give it time to land before the CTA exits
+            const uint64_t until = tc::globaltimer() + 50000;
+            while (tc::globaltimer() < until) __nanosleep(1000);
+        }
+    }
     if (warp == 0) tc::tmem_dealloc(tmem, C::kTmemCols);
 }
 
@@ -910,7 +933,28 @@ auto dispatch_tile(const TcTile& t, int q, Args&&... args)
     return q ? dispatch_bn<F, 1>(t.mh, t.bn, args...) : dispatch_bn<F, 0>(t.mh, t.bn, args...);
 }
 
+// Verification of the bounded waits: one warp waits on an mbarrier that nothing arrives on;
+// when the wait gives up it records MLMC_ERR_TIMEOUT in the error word, as the level kernels do.
+__global__ void bounded_wait_probe_kernel(int* err_flag, uint64_t timeout_ns)
+{
+    __shared__ __align__(8) uint64_t bar;
+    const uint32_t b = tc::smem_addr(&bar);
+    if (threadIdx.x == 0) {
+        tc::mbar_init(b, 1);
+        tc::mbar_init_fence();
+    }
+    __syncthreads();
+    const bool ok = tc::mbar_wait_bounded(b, 0, tc::globaltimer() + timeout_ns);
+    if (!ok && threadIdx.x == 0) atomicExch(err_flag, MLMC_ERR_TIMEOUT);
+}
+
 }  // namespace
+
+cudaError_t launch_bounded_wait_probe(int* err_flag, uint64_t timeout_ns, cudaStream_t st)
+{
+    bounded_wait_probe_kernel<<<1, 32, 0, st>>>(err_flag, timeout_ns);
+    return cudaGetLastError();
+}
 
 int tc_stage_width_a(const TcTile& t) { return t.pair ? 128 : 128 * t.mh; }
 int tc_stage_width_b(const TcTile& t) { return t.pair ? t.bn / 2 : t.bn; }
