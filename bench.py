@@ -50,10 +50,11 @@ TRAFFIC = {
     # outer products), used for every level
     "fp32": {"dram_bytes_per_outer_product": {0: 823.1e6 / 262144, 8: 823.1e6 / 262144},
              "source": "profiles/level_cuda_core_f32_mlmc_256x65536x256.md"},
-    # DRAM bytes (read + write) per sampled outer product of the CTA-pair kernel (tile 3256) at
-    # level 0 and level 8 (captures of 1,048,576 and 39,845,888 outer products); levels in between
-    # are interpolated linearly in l
-    "bf16": {"dram_bytes_per_outer_product": {0: 3.0427e9 / 1048576, 8: 109.0608e9 / 39845888},
+    # DRAM bytes (read + write) per sampled outer product of the CTA-pair kernel (tile 3256), per
+    # level, from a capture of dram__bytes_{read,write}.sum (one ncu pass) over every level launch
+    # of the timed steps of this workload
+    "bf16": {"dram_bytes_per_outer_product": {0: 2899.4, 1: 2898.7, 2: 2899.5, 3: 2816.4, 4: 2775.5,
+                                              5: 2754.3, 6: 2744.9, 7: 2738.7, 8: 2736.7},
              "source": "profiles/level_tc_bf16_mlmc_256x65536x256.md"},
     "fp8": None,
 }
@@ -61,7 +62,9 @@ TRAFFIC = {
 
 def dram_per_outer(prec, level):
     t = TRAFFIC[prec]["dram_bytes_per_outer_product"]
-    f = min(max(level / 8.0, 0.0), 1.0)
+    if level in t:
+        return t[level]
+    f = min(max(level / 8.0, 0.0), 1.0)   # levels without a measurement: linear between 0 and 8
     return t[0] + (t[8] - t[0]) * f
 
 
