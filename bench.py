@@ -581,6 +581,23 @@ def run_profile_case(args):
     from paper_1904_00429_gb300.inputs import make_params, make_target
 
     dev = torch.device("cuda:0")
+    if args.profile_case == "batched_8_problems":
+        # the first 8 problems of the batched workload, 128 x 128 tile, 256 samples per level
+        from paper_1904_00429_gb300.inputs import batched_shapes
+        specs, ranges = [], []
+        for q, (m, n, p, L) in enumerate(batched_shapes(BATCHED["count"], BATCHED["shape_seed"])[:8]):
+            pq = make_params(m, n, p, law="gauss", seed_A=2 * q, seed_B=2 * q + 1, seed_idx=2, problem_id=q,
+                             dtype=np.float32)
+            specs.append(binding.ProblemSpec(*[torch.from_numpy(x).to(dev) for x in (pq.M, pq.S, pq.Mp, pq.Sp)],
+                                             seed_A=2 * q, seed_B=2 * q + 1, seed_idx=2, problem_id=q, L=L))
+            ranges += [(q, l) for l in range(L + 1)]
+        plan = binding.Plan(specs, c0=BATCHED["c0"], L=8, precision="bf16", tile_override=1128)
+        for i in range(3):
+            plan.level_stats_batch([(q, l, 256 * i, 256) for q, l in ranges])
+        plan.synchronize()
+        plan.close()
+        print(json.dumps({"profile_case": args.profile_case, "status": "ok"}), flush=True)
+        return
     pp = make_params(256, 65536, 256, seed_A=0, seed_B=1, dtype=np.float32)
     ts = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (pp.M, pp.S, pp.Mp, pp.Sp)]
     if args.profile_case == "adjoint":
@@ -613,7 +630,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the backward measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-problem batched measurement")
-    ap.add_argument("--profile-case", choices=sorted(list(PROFILE_CASES) + ["adjoint"]), default=None,
+    ap.add_argument("--profile-case", choices=sorted(list(PROFILE_CASES) + ["adjoint", "batched_8_problems"]),
+                    default=None,
                     help="run one small kernel invocation for ncu instead of the benchmark")
     args = ap.parse_args()
     if args.profile_case:

@@ -10,12 +10,14 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "internal.h"
 #include "mlmc.h"
@@ -126,6 +128,17 @@ struct DeviceGuard {
     }
 };
 
+// Host-side fault injection for testing the error paths (nothing reaches the GPU):
+// MLMC_FAULT=alloc  -> mlmc_plan fails as if a device allocation failed (MLMC_ERR_OOM), before
+//                      any CUDA call;
+// MLMC_FAULT=launch -> every level launch fails as if the launch had been refused (MLMC_ERR_CUDA);
+// MLMC_FAULT=cancel -> the first call after mlmc_plan cancels the plan (MLMC_ERR_CUDA, sticky).
+bool fault_is(const char* what)
+{
+    const char* f = std::getenv("MLMC_FAULT");
+    return f && std::strcmp(f, what) == 0;
+}
+
 mlmc_status set_sticky(mlmc_plan_t* plan, mlmc_status st)
 {
     if (plan && plan->sticky == MLMC_OK && st != MLMC_OK) {
@@ -145,6 +158,8 @@ mlmc_status check_cuda(mlmc_plan_t* plan, cudaError_t err, const char* what)
 mlmc_status enter(mlmc_plan_t* plan)
 {
     if (!plan) return fail(MLMC_ERR_INVALID_ARG, "null plan");
+    if (plan->sticky == MLMC_OK && fault_is("cancel"))
+        return set_sticky(plan, fail(MLMC_ERR_CUDA, "injected fault: plan cancelled"));
     if (plan->sticky != MLMC_OK) {
         g_last_error = plan->sticky_msg;
         return plan->sticky;
@@ -305,6 +320,15 @@ mlmc_status run_level(mlmc_plan_t* plan, ProblemState& ps, int level, uint64_t s
     const uint64_t s_end = s0 + count;
     const uint64_t ch = uint64_t(chunk_samples(c));
     prm.chunk = int(ch);
+    if (fault_is("launch"))
+        return set_sticky(plan, fail(MLMC_ERR_CUDA, "injected fault: level kernel launch refused"));
+    // one NVTX range per level call, named after the level (visible in profiler timelines)
+    char range[32];
+    std::snprintf(range, sizeof(range), "mlmc level %d", level);
+    nvtxRangePushA(range);
+    struct PopRange {
+        ~PopRange() { nvtxRangePop(); }
+    } pop_range;
     const uint64_t chunk_first = s0 / ch;
     const uint64_t chunk_last = (s_end - 1) / ch;
     for (uint64_t cb = chunk_first; cb <= chunk_last; cb += uint64_t(ps.max_chunks)) {
@@ -644,6 +668,12 @@ mlmc_status autotune_batch_tile(mlmc_plan_t* plan, const std::vector<BatchRange>
 
 mlmc_status run_batch(mlmc_plan_t* plan, const std::vector<BatchRange>& ranges)
 {
+    if (fault_is("launch"))
+        return set_sticky(plan, fail(MLMC_ERR_CUDA, "injected fault: batched launch refused"));
+    nvtxRangePushA("mlmc batched levels");
+    struct PopRange {
+        ~PopRange() { nvtxRangePop(); }
+    } pop_range;
     mlmc_status st = batch_setup(plan);
     if (st != MLMC_OK) return st;
     if (plan->batch_tile.mh == 0) {
@@ -723,6 +753,7 @@ mlmc_status mlmc_plan(const mlmc_problem* problems, int32_t nprob, const mlmc_op
     *plan_out = nullptr;
     mlmc_status st = validate(problems, nprob, options);
     if (st != MLMC_OK) return st;
+    if (fault_is("alloc")) return fail(MLMC_ERR_OOM, "injected fault: device allocation of the plan failed");
     mlmc_plan_t* plan = new (std::nothrow) mlmc_plan_s();
     if (!plan) return fail(MLMC_ERR_OOM, "host allocation failed");
     if (cudaGetDevice(&plan->device) != cudaSuccess) {

@@ -70,3 +70,31 @@ def test_bounded_wait_rejects_bad_bounds():
             with pytest.raises(binding.MLMCError) as e:
                 plan.debug_bounded_wait(bad)
             assert e.value.status == 1
+
+
+def test_injected_launch_failure_is_reported_and_sticks(monkeypatch):
+    pp = make_params(32, 256, 24, dtype=np.float32)
+    with binding.Plan([_spec(pp)], c0=8, L=1, precision="bf16") as plan:
+        monkeypatch.setenv("MLMC_FAULT", "launch")
+        with pytest.raises(binding.MLMCError) as e:
+            plan.level_stats(0, 0, 0, 8)
+        assert e.value.status == 2 and "injected" in str(e.value)
+        with pytest.raises(binding.MLMCError) as e:
+            plan.level_stats_batch([(0, 1, 0, 8)])
+        assert e.value.status == 2
+        monkeypatch.delenv("MLMC_FAULT")
+        with pytest.raises(binding.MLMCError) as e:      # sticky
+            plan.level_stats(0, 0, 0, 8)
+        assert e.value.status == 2
+
+
+def test_injected_cancel(monkeypatch):
+    pp = make_params(32, 256, 24, dtype=np.float32)
+    with binding.Plan([_spec(pp)], c0=8, L=1, precision="fp32") as plan:
+        monkeypatch.setenv("MLMC_FAULT", "cancel")
+        with pytest.raises(binding.MLMCError) as e:
+            plan.level_stats(0, 0, 0, 8)
+        assert e.value.status == 2
+        monkeypatch.delenv("MLMC_FAULT")
+        with pytest.raises(binding.MLMCError):
+            plan.synchronize()
