@@ -147,7 +147,8 @@ PAIR_CASES = [
 def test_bf16_cta_pair_tile_matches_oracle_and_single_cta_tile(m, n, p, c0, L, picks):
     """Tile 3256 (two CTAs of a cluster share a 256 x 256 tile, each generating half of B for both)
     against the FP64 oracle, and its level sums against the 128 x 256 single-CTA tile (the same
-    MMA chain per element, so the sums agree bit for bit)."""
+    MMA chain per element, so the sums of D agree bit for bit; the sums of ||D||^2 are grouped by
+    the drain's column split, so they agree up to rounding)."""
     pp = make_params(m, n, p, seed_A=3, seed_B=4, seed_idx=5, problem_id=1, dtype=np.float32)
     orc = _orc(pp)
     lv = oracle.Levels(c0, 2, L)
@@ -165,4 +166,4 @@ def test_bf16_cta_pair_tile_matches_oracle_and_single_cta_tile(m, n, p, c0, L, p
             nb, sb, qb = b.get_level_state(0, l)
             assert na == nb == 96
             assert torch.equal(sa, sb)
-            assert qa == qb
+            assert abs(qa - qb) <= 1e-12 * qb
