@@ -352,7 +352,7 @@ def _roofline(res, W, peaks, peak_kind):
 ADJOINT = dict(name="adjoint_256x65536x256", m=256, n=65536, p=256, c0=64, R=2, L=8, N=256, precision="bf16")
 
 
-def _measure_adjoint(args, host, dev, stream):
+def _measure_adjoint(args, host, dev, stream, peaks, peak_kind):
     """Backward of the loss ||Yhat - T||_F^2 through mlmc_backward: A 256 x 65536, B 65536 x 256,
     c_l = 64 * 2^l for l = 0..8, N_l = 256 samples per level, BF16 forward (straight-through
     adjoint).  Times exactly ``args.steps`` backward calls after ``args.warmup`` untimed ones."""
@@ -387,16 +387,21 @@ def _measure_adjoint(args, host, dev, stream):
     records = A["N"] * sum(A["c0"] * A["R"]**l for l in range(A["L"] + 1))
     # two contractions (G b and G^T a) of m x p FMAs per sampled product
     flops = 2.0 * 2.0 * A["m"] * A["p"] * records
+    # normals the replay needs at least: per record and side, the contracted vector and the
+    # output-side normals (m + p), twice
+    normals = 2.0 * (A["m"] + A["p"]) * records
     t = statistics.mean(ms) / 1e3
     plan.close()
     achieved = flops / t / 1e12
+    peak, src = peaks["bf16_tflops_sustained"], f"bf16_tflops_sustained ({peak_kind})"
     return {"workload": A["name"], "metric": "backward time (mlmc_backward, all four gradients)",
             "value": t, "unit": "s", "ms_per_backward": [round(x, 4) for x in ms], "records": records,
             "N_l": [A["N"]] * (A["L"] + 1), "precision": A["precision"], "gpu_launches": launches,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)",
-                         "kernel": "segment_kernel<float>"}}
+            "normals_per_s": normals / t,
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None, "peak_source": src,
+                         "flops": "useful: 4 m p per record (the hi/lo split of G issues twice that)",
+                         "kernel": "segment_tc_kernel"}}
 
 
 BATCHED = dict(name="batched_64_problems", count=64, shape_seed=7, c0=32, R=2, pilot=256, rel_rmse=1e-3,
@@ -549,7 +554,7 @@ def run_ours(args):
                                        "roofline": _roofline(o, W, peaks, peak_kind), "clocks": o["clocks"]}
                            for o in others}
     if not args.no_adjoint and world == 1:
-        line["adjoint"] = _measure_adjoint(args, host, dev, stream)
+        line["adjoint"] = _measure_adjoint(args, host, dev, stream, peaks, peak_kind)
     if not args.no_batched and world == 1:
         line["batched"] = _measure_batched(args, dev, stream, peaks, peak_kind)
     if not args.no_cpu_baseline and world == 1:

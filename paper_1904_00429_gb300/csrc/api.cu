@@ -1278,8 +1278,15 @@ mlmc_status backward_problem(mlmc_plan_t* plan, ProblemState& ps, const double* 
         if (err == cudaSuccess) err = adjoint_scatter(lv, keyI, n, o.ratio, cursor, records, plan->stream);
         sp.total = recs;
         for (int side = 0; side < 2 && err == cudaSuccess; ++side) {
-            sp.ob = adjoint_output_block(side == 0 ? int(p) : int(m), f64);
-            err = adjoint_segments(sp, f64, side, plan->num_sms, plan->stream);
+            const int kin = side == 0 ? int(p) : int(m);
+            if (o.precision == MLMC_BF16 && adjoint_tc_supported(kin)) {
+                // bfloat16 vectors: the contraction with G runs on the tensor cores
+                TcLaunch tl{plan->err_flag, plan->timeout_ns, 0.0f, plan->num_sms};
+                err = adjoint_segments_tc(sp, side, tl, plan->stream);
+            } else {
+                sp.ob = adjoint_output_block(kin, f64);
+                err = adjoint_segments(sp, f64, side, plan->num_sms, plan->stream);
+            }
         }
         if (check_cuda(plan, err, "adjoint batch") != MLMC_OK) return plan->sticky;
         plan->launches += 9;   // count, five scan passes, scatter, two segment reductions

@@ -194,6 +194,10 @@ size_t adjoint_segment_smem(int kin, int opt, bool f64);
 // Register-tile width (1, 2 or 4) for kin contracted entries; 0 if none fits in shared memory.
 int adjoint_output_block(int kin, bool f64);
 cudaError_t adjoint_segments(const AdjSegmentParams& prm, bool f64, int side, int num_sms, cudaStream_t st);
+// Tensor-core segment reduction for BF16 plans (vectors exact in bfloat16, G split into bfloat16
+// hi and lo parts): contracted dimension up to 256.
+bool adjoint_tc_supported(int kin);
+cudaError_t adjoint_segments_tc(const AdjSegmentParams& prm, int side, const TcLaunch& tl, cudaStream_t st);
 cudaError_t adjoint_write_A(const double* src, int64_t n, int64_t m, void* dst, int64_t ld, int dtype, cudaStream_t st);
 cudaError_t adjoint_write_B(const double* src, int64_t n, int64_t p, void* dst, int64_t ld, int dtype, cudaStream_t st);
 

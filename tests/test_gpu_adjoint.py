@@ -9,7 +9,9 @@ Bars:
   * BF16 (straight-through): against the oracle's bfloat16 emulation the operands agree
     except where an FP32 and an FP64 value round to different bfloat16 neighbours, so a
     Frobenius bar of 1e-3 holds; against the unrounded oracle the operand rounding (2^-8)
-    shows, 2^-6 in Frobenius norm.
+    shows, 2^-6 in Frobenius norm.  Contracted dimensions up to 256 run on the tensor cores with
+    G split into bfloat16 hi and lo parts (2^-16 relative per product, FP32 accumulation), the
+    same bars; BF16_CASES mix both kernels (k_in = 300 keeps the CUDA-core one).
 The gradient is also checked against central differences of the GPU estimator itself: the
 estimate is a polynomial of degree two in the parameters (bilinear in A and B), so the
 central difference is exact up to rounding.
@@ -95,7 +97,13 @@ def test_backward_fp32_matches_oracle(m, n, p, c0, L, Nl):
         assert np.linalg.norm(a - b) <= 2e-6 * np.linalg.norm(b), (name, np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-@pytest.mark.parametrize("m,n,p,c0,L,Nl", ADJ_CASES[:2])
+BF16_CASES = ADJ_CASES + [
+    (256, 4000, 129, 16, 3, [64, 33, 16, 9]),      # two 128-output blocks on one side, ragged other
+    (129, 2000, 256, 32, 2, [70, 65, 1]),           # k_in = 256 and 129, records not a multiple of 64
+]
+
+
+@pytest.mark.parametrize("m,n,p,c0,L,Nl", BF16_CASES)
 def test_backward_bf16_straight_through(m, n, p, c0, L, Nl):
     pp = make_params(m, n, p, seed_A=1, seed_B=2, seed_idx=3, problem_id=4, dtype=np.float32)
     G = _gauss((m, p), 13)
