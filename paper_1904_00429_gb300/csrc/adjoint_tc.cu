@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) segment_tc_kernel(const AdjSegm
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                            ~static_cast<uintptr_t>(1023));
-    constexpr int kG4 = ATOMS * 16;   // Philox blocks per contracted vector
+    constexpr int kG8 = ATOMS * 8;   // 16-byte chunks (8 entries) per contracted vector
     const int kin = side == 0 ? prm.p : prm.m;
     const int kout = side == 0 ? prm.m : prm.p;
     const int o0 = blockIdx.y * kTcOut;
@@ -123,6 +123,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) segment_tc_kernel(const AdjSegm
     const int group = warp >> 2;    // records kGroupRec * group ..
     const int o_loc = quarter * 32 + lane;
     float* zw = zslab + warp * 128;
+    const uint64_t desc_hi = tc::sw128_kmajor_desc(tc::smem_addr(g_hi));
+    const uint64_t desc_lo = tc::sw128_kmajor_desc(tc::smem_addr(g_lo));
+    const uint64_t desc_v0 = tc::sw128_kmajor_desc(tc::smem_addr(vt));
 
     // chunks of this CTA's segments k = blockIdx.x + i gridDim.x, in order (uniform across the CTA)
     int64_t k_it = blockIdx.x, c_next = 0, seg_end = 0;
@@ -180,35 +183,44 @@ __global__ void __launch_bounds__(kTcThreads, 1) segment_tc_kernel(const AdjSegm
                 row_k = cur.k;
             }
             __syncthreads();
-            // the chunk's contracted vectors, bfloat16, as the K-major B operand (one row per record)
+            // the chunk's contracted vectors, bfloat16, as the K-major B operand (one row per record);
+            // a thread builds one 16-byte swizzle chunk (8 entries, two Philox blocks) at a time
             unsigned char* vb = vt + buf * (ATOMS * kTcRec * 128);
             const uint64_t* rb = rec_s + buf * kTcRec;
-            for (int e = tid; e < kTcRec * kG4; e += kTcThreads) {
-                const int j = e / kG4, g4 = e % kG4;
-                const int x = 4 * g4;
-                float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-                if (j < cur.nc && x < kin) {
+#pragma unroll 1
+            for (int e = tid; e < kTcRec * kG8; e += kTcThreads) {
+                const int j = e / kG8, c8 = e % kG8;
+                const int x = 8 * c8;
+                uint4 packed = make_uint4(0u, 0u, 0u, 0u);
+                if (j < cur.nc) {
                     const uint64_t rec = rb[j];
                     const uint64_t s = rec >> 6;
-                    const uint4 w = philox4x32_10_rk(
-                        make_uint4(static_cast<uint32_t>(g4), static_cast<uint32_t>(cur.k), static_cast<uint32_t>(s),
-                                   level_sample_word(static_cast<int>(rec & 31), s)),
+                    const uint32_t lsw = level_sample_word(static_cast<int>(rec & 31), s);
+                    const uint4 w0 = philox4x32_10_rk(
+                        make_uint4(static_cast<uint32_t>(2 * c8), static_cast<uint32_t>(cur.k), static_cast<uint32_t>(s), lsw),
                         rk_in);
-                    float z[4];
-                    normals4_mufu(w, z);
-                    const float4 p0 = reinterpret_cast<const float4*>(row_s)[2 * g4];
-                    const float4 p1 = reinterpret_cast<const float4*>(row_s)[2 * g4 + 1];
-                    v[0] = fmaf(p0.y, z[0], p0.x);
-                    v[1] = fmaf(p0.w, z[1], p0.z);
-                    v[2] = fmaf(p1.y, z[2], p1.x);
-                    v[3] = fmaf(p1.w, z[3], p1.z);
+                    const uint4 w1 = philox4x32_10_rk(
+                        make_uint4(static_cast<uint32_t>(2 * c8 + 1), static_cast<uint32_t>(cur.k), static_cast<uint32_t>(s), lsw),
+                        rk_in);
+                    float z[8];
+                    normals4_mufu(w0, z);
+                    normals4_mufu(w1, z + 4);
+                    const float4* rp = reinterpret_cast<const float4*>(row_s) + 4 * c8;
+                    float v[8];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 pq = rp[q];   // (M, S) of entries x + 2q, x + 2q + 1
+                        v[2 * q] = x + 2 * q < kin ? fmaf(pq.y, z[2 * q], pq.x) : 0.0f;
+                        v[2 * q + 1] = x + 2 * q + 1 < kin ? fmaf(pq.w, z[2 * q + 1], pq.z) : 0.0f;
+                    }
+                    const __nv_bfloat162 b0 = __floats2bfloat162_rn(v[0], v[1]);
+                    const __nv_bfloat162 b1 = __floats2bfloat162_rn(v[2], v[3]);
+                    const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[4], v[5]);
+                    const __nv_bfloat162 b3 = __floats2bfloat162_rn(v[6], v[7]);
+                    packed = make_uint4(*reinterpret_cast<const uint32_t*>(&b0), *reinterpret_cast<const uint32_t*>(&b1),
+                                        *reinterpret_cast<const uint32_t*>(&b2), *reinterpret_cast<const uint32_t*>(&b3));
                 }
-                const __nv_bfloat162 lo2 = __floats2bfloat162_rn(v[0], v[1]);
-                const __nv_bfloat162 hi2 = __floats2bfloat162_rn(v[2], v[3]);
-                const uint32_t off = static_cast<uint32_t>((x >> 6) * kTcRec * 128) + tc::sw128_offset(j, (x & 63) >> 3) +
-                                     2u * static_cast<uint32_t>(x & 7);
-                *reinterpret_cast<uint2*>(vb + off) = make_uint2(*reinterpret_cast<const uint32_t*>(&lo2),
-                                                                 *reinterpret_cast<const uint32_t*>(&hi2));
+                *reinterpret_cast<uint4*>(vb + (x >> 6) * (kTcRec * 128) + tc::sw128_offset(j, (x & 63) >> 3)) = packed;
             }
             tc::fence_proxy_async_smem();
             tc::tc_fence_before_sync();
@@ -216,14 +228,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) segment_tc_kernel(const AdjSegm
             if (tid == 0) {
                 tc::tc_fence_after_sync();
                 const uint32_t d = tmem + static_cast<uint32_t>(buf * kTcRec);
-                const uint32_t vaddr = tc::smem_addr(vb);
+                // descriptors advance by (byte offset >> 4) in their start-address field
+                const uint64_t bdesc0 = desc_v0 + static_cast<uint64_t>((buf * ATOMS * kTcRec * 128) >> 4);
 #pragma unroll
                 for (int part = 0; part < 2; ++part) {
-                    const uint32_t ga = tc::smem_addr(part ? g_lo : g_hi);
 #pragma unroll
                     for (int ks = 0; ks < ATOMS * 4; ++ks) {
-                        const uint64_t adesc = tc::sw128_kmajor_desc(ga + (ks >> 2) * kTcOut * 128 + 32 * (ks & 3));
-                        const uint64_t bdesc = tc::sw128_kmajor_desc(vaddr + (ks >> 2) * kTcRec * 128 + 32 * (ks & 3));
+                        const uint64_t adesc = (part ? desc_lo : desc_hi) +
+                                               static_cast<uint64_t>(((ks >> 2) * kTcOut * 128 + 32 * (ks & 3)) >> 4);
+                        const uint64_t bdesc = bdesc0 + static_cast<uint64_t>(((ks >> 2) * kTcRec * 128 + 32 * (ks & 3)) >> 4);
                         tc::mma_bf16(d, adesc, bdesc, idesc, (part > 0 || ks > 0) ? 1u : 0u);
                     }
                 }
@@ -250,32 +263,34 @@ __global__ void __launch_bounds__(kTcThreads, 1) segment_tc_kernel(const AdjSegm
             const uint64_t* rb = rec_s + pb * kTcRec;
             const float* wb = omega + pb * kTcRec;
             float sm = 0.0f, ss = 0.0f;
-#pragma unroll
-            for (int r = 0; r < kGroupRec / 4; ++r) {
-                // normals of outputs o0 + 32 quarter + 4 (lane & 7) .. + 3 for record 4 r + lane / 8 of the group,
-                // passed through the warp's slab so that lane L reads output 32 quarter + L
-                const int j = group * kGroupRec + 4 * r + (lane >> 3);
+            if (group * kGroupRec < prev.nc) {   // uniform per warp; records past nc have omega = 0
+                // normals of outputs o0 + 32 quarter + 4 (lane & 7) .. + 3 for records 4 r + lane / 8 of the
+                // group, passed through the warp's slab so that lane L reads output 32 quarter + L
                 const int oq = quarter * 32 + 4 * (lane & 7);
-                float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-                if (j < prev.nc && oq < ob) {
-                    const uint64_t rec = rb[j];
+                float z[kGroupRec / 4][4];
+#pragma unroll
+                for (int r = 0; r < kGroupRec / 4; ++r) {
+                    const uint64_t rec = rb[group * kGroupRec + 4 * r + (lane >> 3)];
                     const uint64_t s = rec >> 6;
                     const uint4 w = philox4x32_10_rk(
                         make_uint4(static_cast<uint32_t>((o0 + oq) >> 2), static_cast<uint32_t>(prev.k),
                                    static_cast<uint32_t>(s), level_sample_word(static_cast<int>(rec & 31), s)),
                         rk_out);
-                    normals4_mufu(w, z);
+                    normals4_mufu(w, z[r]);
                 }
-                reinterpret_cast<float4*>(zw)[lane] = make_float4(z[0], z[1], z[2], z[3]);
-                __syncwarp();
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const int jj = 4 * r + t;
-                    const float wu = wb[group * kGroupRec + jj] * u[jj];
-                    sm += wu;
-                    ss = fmaf(wu, zw[t * 32 + lane], ss);
+                for (int r = 0; r < kGroupRec / 4; ++r) {
+                    reinterpret_cast<float4*>(zw)[lane] = make_float4(z[r][0], z[r][1], z[r][2], z[r][3]);
+                    __syncwarp();
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const int jj = 4 * r + t;
+                        const float wu = wb[group * kGroupRec + jj] * u[jj];
+                        sm += wu;
+                        ss = fmaf(wu, zw[t * 32 + lane], ss);
+                    }
+                    __syncwarp();
                 }
-                __syncwarp();
             }
             accM += static_cast<double>(sm);
             accS += static_cast<double>(ss);
