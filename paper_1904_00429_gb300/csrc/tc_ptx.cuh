@@ -150,6 +150,12 @@ __device__ __forceinline__ void bulk_copy_s2s_cluster(uint32_t dst, uint32_t src
                  : "memory");
 }
 
+// 32-bit store to shared memory of another CTA of the cluster (shared::cluster address).
+__device__ __forceinline__ void st_cluster_u32(uint32_t addr, uint32_t v)
+{
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
 // Whole-cluster execution barrier (every thread of every CTA of the cluster).
 __device__ __forceinline__ void cluster_sync()
 {
