@@ -229,7 +229,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) segment_tc_kernel(const AdjSegm
                     tid < cur.nc ? wtab[((rec_pf >> 5) & 1) * MLMC_MAX_LEVELS + (rec_pf & 31)] : 0.0f;
             }
             if (cur.k != row_k) {
-                if (tid < 2 * ATOMS * 64) row_s[tid] = row_pf;
+                // float f of the row (pair f / 2) goes to float4 (f / 4 % 4) kG8 + f / 16, so that
+                // threads of consecutive 8-entry chunks read consecutive float4s
+                if (tid < 2 * ATOMS * 64) row_s[(((tid >> 2) & 3) * kG8 + (tid >> 4)) * 4 + (tid & 3)] = row_pf;
                 row_k = cur.k;
             }
             have_n = advance(nxt);
@@ -262,11 +264,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) segment_tc_kernel(const AdjSegm
                     float z[8];
                     normals4_mufu(w0, z);
                     normals4_mufu(w1, z + 4);
-                    const float4* rp = reinterpret_cast<const float4*>(row_s) + 4 * c8;
+                    const float4* rp = reinterpret_cast<const float4*>(row_s) + c8;
                     float v[8];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const float4 pq = rp[q];   // (M, S) of entries x + 2q, x + 2q + 1
+                        const float4 pq = rp[q * kG8];   // (M, S) of entries x + 2q, x + 2q + 1
                         v[2 * q] = x + 2 * q < kin ? fmaf(pq.y, z[2 * q], pq.x) : 0.0f;
                         v[2 * q + 1] = x + 2 * q + 1 < kin ? fmaf(pq.w, z[2 * q + 1], pq.z) : 0.0f;
                     }
