@@ -48,13 +48,13 @@ FP64_PEAK_TFLOPS = 1.25
 TRAFFIC = {
     # DRAM bytes per sampled outer product of the 64 x 64 tile kernel (level-0 capture of 262144
     # outer products), used for every level
-    "fp32": {"dram_bytes_per_outer_product": {0: 823.1e6 / 262144, 8: 823.1e6 / 262144},
+    "fp32": {"dram_bytes_per_outer_product": {0: 790.9e6 / 262144, 8: 790.9e6 / 262144},
              "source": "profiles/level_cuda_core_f32_mlmc_256x65536x256.md"},
     # DRAM bytes (read + write) per sampled outer product of the CTA-pair kernel (tile 3256), per
     # level, from a capture of dram__bytes_{read,write}.sum (one ncu pass) over every level launch
     # of the timed steps of this workload
-    "bf16": {"dram_bytes_per_outer_product": {0: 2899.4, 1: 2898.7, 2: 2899.5, 3: 2816.4, 4: 2775.5,
-                                              5: 2754.3, 6: 2744.9, 7: 2738.7, 8: 2736.7},
+    "bf16": {"dram_bytes_per_outer_product": {0: 2816.7, 1: 2776.2, 2: 2775.0, 3: 2775.5, 4: 2775.7,
+                                              5: 2755.3, 6: 2744.3, 7: 2739.4, 8: 2737.2},
              "source": "profiles/level_tc_bf16_mlmc_256x65536x256.md"},
     "fp8": None,
 }

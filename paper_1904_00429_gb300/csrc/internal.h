@@ -15,13 +15,15 @@ namespace mlmc {
 // per chunk and folded into a level in chunk order, so the result does not
 // depend on grid shapes or on how sample ranges are split at chunk boundaries.
 // The plan's kernels use chunk_samples(c_l) (8 to 64, a power of two: cheap
-// samples get longer chunks); the no-allocation entry point uses kChunk.
+// samples get longer chunks: the longest with at most 8192 sampled products, or 8
+// samples; this bounds the FP32 accumulation of a chunk sum); the no-allocation
+// entry point uses kChunk.
 constexpr int kChunk = 8;
 constexpr int kMaxChunkSamples = 64;
 inline int chunk_samples(int64_t c_l)
 {
     int ch = 8;
-    while (ch < kMaxChunkSamples && int64_t(ch) * 2 * c_l <= 2048) ch *= 2;
+    while (ch < kMaxChunkSamples && int64_t(ch) * 2 * c_l <= 8192) ch *= 2;
     return ch;
 }
 
