@@ -357,6 +357,18 @@ MLMC_API mlmc_status mlmc_debug_sample(mlmc_plan_t* plan, int32_t prob, int32_t 
  * CUDA context stays usable for other plans. */
 MLMC_API mlmc_status mlmc_debug_bounded_wait(mlmc_plan_t* plan, int64_t timeout_ns);
 
+/* Measurement (no counterpart in the paper): the rate, in entries per second, at which this GPU
+ * generates the sampled entries of the reduced-precision paths on their own -- one Philox4x32-10
+ * block per four normals, special-function-unit Box-Muller per pair (rng counter layout and
+ * transforms as in the level kernels), A = M + S z in FP32 and the bfloat16 rounding -- with no
+ * gathers, contraction or statistics, at full occupancy.  Each sampled outer product of an
+ * m x p problem needs m + p entries, so (m + p) / rate is the generation bound per outer product
+ * beside the HBM and tensor bounds.  Runs a warm-up and three timed launches (about 1.5 ms each
+ * on a GB300) on `cuda_stream` (a cudaStream_t, NULL for the legacy default stream) and
+ * synchronises it; allocates 1 KiB of device memory for the duration of the call.  Returns
+ * MLMC_ERR_INVALID_ARG for a null output pointer, MLMC_ERR_CUDA on a CUDA error. */
+MLMC_API mlmc_status mlmc_measure_generation_rate(void* cuda_stream, double* entries_per_s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -103,6 +103,7 @@ def lib() -> ctypes.CDLL:
             "mlmc_debug_normals": [P, I32, I32, I32, U64, I64, I64, I64, P],
             "mlmc_debug_sample": [P, I32, I32, U64, P],
             "mlmc_debug_bounded_wait": [P, I64],
+            "mlmc_measure_generation_rate": [P, ctypes.POINTER(ctypes.c_double)],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -360,3 +361,13 @@ def debug_philox(ctr: torch.Tensor, key: torch.Tensor, stream=None) -> torch.Ten
     _check(lib().mlmc_debug_philox(_ptr(ctr.contiguous()), _ptr(key.contiguous()), count, _ptr(out),
                                    _stream_handle(stream)), "mlmc_debug_philox")
     return out
+
+
+def generation_rate(stream=None) -> float:
+    """Entries per second the GPU generates on their own (Philox4x32-10, special-function
+    Box-Muller, M + S z, bfloat16) at full occupancy: the generation bound of the
+    reduced-precision level kernels.  Synchronises the stream."""
+    out = ctypes.c_double(0.0)
+    _check(lib().mlmc_measure_generation_rate(_stream_handle(stream), ctypes.byref(out)),
+           "mlmc_measure_generation_rate")
+    return out.value

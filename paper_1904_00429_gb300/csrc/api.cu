@@ -1397,6 +1397,18 @@ mlmc_status mlmc_debug_sample(mlmc_plan_t* plan, int32_t prob, int32_t level, ui
     return check_cuda(plan, err, "debug sample copy");
 }
 
+mlmc_status mlmc_measure_generation_rate(void* cuda_stream, double* entries_per_s)
+{
+    if (!entries_per_s) return fail(MLMC_ERR_INVALID_ARG, "mlmc_measure_generation_rate: null output");
+    int dev = 0, sms = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (err == cudaSuccess) err = measure_generation_rate(static_cast<cudaStream_t>(cuda_stream), sms, entries_per_s);
+    if (err != cudaSuccess)
+        return fail(MLMC_ERR_CUDA, "mlmc_measure_generation_rate: %s", cudaGetErrorString(err));
+    return MLMC_OK;
+}
+
 mlmc_status mlmc_debug_bounded_wait(mlmc_plan_t* plan, int64_t timeout_ns)
 {
     mlmc_status st = enter(plan);

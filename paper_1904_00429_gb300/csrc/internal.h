@@ -203,6 +203,11 @@ cudaError_t adjoint_segments_tc(const AdjSegmentParams& prm, int side, const TcL
 cudaError_t adjoint_write_A(const double* src, int64_t n, int64_t m, void* dst, int64_t ld, int dtype, cudaStream_t st);
 cudaError_t adjoint_write_B(const double* src, int64_t n, int64_t p, void* dst, int64_t ld, int dtype, cudaStream_t st);
 
+// Entries per second of the generation alone (Philox4x32-10, special-function Box-Muller,
+// M + S z, bfloat16) at full occupancy: the ceiling of the reduced-precision level kernels'
+// entry generation.  Synchronises `st`.
+cudaError_t measure_generation_rate(cudaStream_t st, int num_sms, double* entries_per_s);
+
 // Set the thread-local message returned by mlmc_last_error().
 mlmc_status report_error(mlmc_status st, const char* msg);
 

@@ -167,3 +167,15 @@ def test_bf16_cta_pair_tile_matches_oracle_and_single_cta_tile(m, n, p, c0, L, p
             assert na == nb == 96
             assert torch.equal(sa, sb)
             assert abs(qa - qb) <= 1e-12 * qb
+
+
+def test_generation_rate_is_measured():
+    """mlmc_measure_generation_rate: entries per second of generation alone.  152 SMs at about
+    2 GHz issue at most ~1.2e12 warp instructions per second and an entry costs tens of thread
+    instructions, so any sane measurement lies between 1e11 and 1e14 entries/s; two calls agree
+    to a few per cent (best of three launches each)."""
+    r1 = binding.generation_rate()
+    r2 = binding.generation_rate()
+    print(f"generation rate: {r1:.3e} / {r2:.3e} entries/s")
+    assert 1e11 < r1 < 1e14 and 1e11 < r2 < 1e14
+    assert abs(r1 - r2) <= 0.1 * max(r1, r2)
