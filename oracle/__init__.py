@@ -24,6 +24,7 @@ _HDR = os.path.join(_HERE, "mlmc_oracle.h")
 _LIB = os.path.join(_HERE, "libmlmc_oracle.so")
 
 QUANT_NONE, QUANT_BF16, QUANT_E4M3 = 0, 1, 2
+F_IDENTITY, F_ABS_STEP = 0, 1
 
 _lock = threading.Lock()
 _lib = None
@@ -80,6 +81,10 @@ def lib():
                 "orc_allocate": (I, [I, P, P, D, D, I64, P]),
                 "orc_estimate": (I, [P, P, D, I64, D, I, P, P, P, P]),
                 "orc_adjoint": (None, [P, P, P, P, I, P, P, P, P]),
+                "orc_f": (D, [I, D]),
+                "orc_sample_f": (None, [P, P, I, U64, I, I, P, P, P, P]),
+                "orc_level_stats_f": (None, [P, P, I, U64, U64, I, I, P, P, P]),
+                "orc_estimate_f": (I, [P, P, D, I64, D, I, I, I, P, P, P, P, P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -186,20 +191,27 @@ def sketch(A, B, idx, off=0, stride=1, cnt=None) -> np.ndarray:
     return out
 
 
-def sample(pr: Problem, lv: Levels, l: int, s: int, quant: int = QUANT_NONE):
-    """One coupled sample: returns (D, P_fine, P_coarse, mag), each m x p."""
+def f(fkind: int, x: float) -> float:
+    """The targeted function (F_IDENTITY, or F_ABS_STEP: |x| H(2 - x) with H(0) = 1)."""
+    return lib().orc_f(fkind, float(x))
+
+
+def sample(pr: Problem, lv: Levels, l: int, s: int, quant: int = QUANT_NONE, fkind: int = F_IDENTITY):
+    """One coupled sample: returns (D, P_fine, P_coarse, mag), each m x p; D = f(P_fine) -
+    f(P_coarse) (f(P_fine) at level 0)."""
     shp = (pr.m, pr.p)
     D, Pf, Pc, mag = np.zeros(shp), np.zeros(shp), np.zeros(shp), np.zeros(shp)
-    lib().orc_sample(pr.ref, lv.ref, l, s, quant, _ptr(D), _ptr(Pf), _ptr(Pc), _ptr(mag))
+    lib().orc_sample_f(pr.ref, lv.ref, l, s, quant, fkind, _ptr(D), _ptr(Pf), _ptr(Pc), _ptr(mag))
     return D, Pf, Pc, mag
 
 
-def level_stats(pr: Problem, lv: Levels, l: int, s0: int, N: int, quant: int = QUANT_NONE):
+def level_stats(pr: Problem, lv: Levels, l: int, s0: int, N: int, quant: int = QUANT_NONE,
+                fkind: int = F_IDENTITY):
     """Returns (mean m x p, M2 total, mag_mean m x p) over samples s0 .. s0+N-1."""
     mean = np.zeros((pr.m, pr.p))
     mag = np.zeros((pr.m, pr.p))
     M2 = ctypes.c_double(0.0)
-    lib().orc_level_stats(pr.ref, lv.ref, l, s0, N, quant, _ptr(mean), ctypes.addressof(M2), _ptr(mag))
+    lib().orc_level_stats_f(pr.ref, lv.ref, l, s0, N, quant, fkind, _ptr(mean), ctypes.addressof(M2), _ptr(mag))
     return mean, M2.value, mag
 
 
@@ -225,6 +237,23 @@ def estimate(pr: Problem, lv: Levels, eps: float, pilot: int = 256, nl_scale: fl
     if rc != 0:
         raise ValueError("orc_estimate rejected its arguments")
     return Y, Nl, V, means
+
+
+def estimate_f(pr: Problem, lv: Levels, eps: float, fkind: int = F_IDENTITY, adaptive: bool = False,
+               pilot: int = 256, nl_scale: float = 1.0, quant: int = QUANT_NONE):
+    """Alg. 2 with the targeted function, L fixed at lv.L or chosen adaptively up to lv.L.
+    Returns (Yhat, L, Nl[:L+1], V[:L+1], means[:L+1])."""
+    Y = np.zeros((pr.m, pr.p))
+    Nl = np.zeros(lv.L + 1, dtype=np.int64)
+    V = np.zeros(lv.L + 1)
+    means = np.zeros((lv.L + 1, pr.m, pr.p))
+    L = ctypes.c_int(-1)
+    rc = lib().orc_estimate_f(pr.ref, lv.ref, eps, pilot, nl_scale, quant, fkind, int(bool(adaptive)), _ptr(Y),
+                              ctypes.addressof(L), _ptr(Nl), _ptr(V), _ptr(means))
+    if rc != 0:
+        raise ValueError("orc_estimate_f rejected its arguments")
+    k = L.value
+    return Y, k, Nl[:k + 1], V[:k + 1], means[:k + 1]
 
 
 def adjoint(pr: Problem, lv: Levels, Nl, G, quant: int = QUANT_NONE):

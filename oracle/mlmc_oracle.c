@@ -298,8 +298,17 @@ static void sampled_sum(int64_t m, int64_t p, const realisation* rz, int64_t fir
     for (int64_t e = 0; e < m * p; ++e) out[e] *= scale;
 }
 
-void orc_sample(const orc_problem* pr, const orc_levels* lv, int l, uint64_t s, int quant,
-                double* D, double* Pf, double* Pc, double* mag)
+double orc_f(int fkind, double x)
+{
+    switch (fkind) {
+    case ORC_F_IDENTITY: return x;
+    case ORC_F_ABS_STEP: return (2.0 - x >= 0.0) ? fabs(x) : 0.0;   /* |x| H(2 - x), H(0) = 1 */
+    default: return NAN;
+    }
+}
+
+void orc_sample_f(const orc_problem* pr, const orc_levels* lv, int l, uint64_t s, int quant, int fkind,
+                  double* D, double* Pf, double* Pc, double* mag)
 {
     int64_t m = pr->m, n = pr->n, p = pr->p;
     size_t sz = sizeof(double) * (size_t)(m * p);
@@ -323,12 +332,21 @@ void orc_sample(const orc_problem* pr, const orc_levels* lv, int l, uint64_t s, 
         int64_t cc = c / lv->R;
         sampled_sum(m, p, &rz, lv->R - 1, lv->R, (double)n / (double)cc, coarse, mag);
     }
-    for (int64_t e = 0; e < m * p; ++e) D[e] = fine[e] - coarse[e];
+    /* P_l - P_{l-1} with the targeted function applied to each estimate (Alg. 1); at l = 0
+     * there is no coarse estimate */
+    for (int64_t e = 0; e < m * p; ++e)
+        D[e] = l > 0 ? orc_f(fkind, fine[e]) - orc_f(fkind, coarse[e]) : orc_f(fkind, fine[e]);
     if (Pf) memcpy(Pf, fine, sz);
     if (Pc) memcpy(Pc, coarse, sz);
     free_realisation(&rz);
     free(fine);
     free(coarse);
+}
+
+void orc_sample(const orc_problem* pr, const orc_levels* lv, int l, uint64_t s, int quant,
+                double* D, double* Pf, double* Pc, double* mag)
+{
+    orc_sample_f(pr, lv, l, s, quant, ORC_F_IDENTITY, D, Pf, Pc, mag);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -343,13 +361,13 @@ typedef struct {
 } welford;
 
 static void welford_add_samples(const orc_problem* pr, const orc_levels* lv, int l, uint64_t s0,
-                                uint64_t N, int quant, welford* w)
+                                uint64_t N, int quant, int fkind, welford* w)
 {
     int64_t mp = pr->m * pr->p;
     double* D = (double*)malloc(sizeof(double) * (size_t)mp);
     double* mg = w->mag ? (double*)malloc(sizeof(double) * (size_t)mp) : NULL;
     for (uint64_t k = 0; k < N; ++k) {
-        orc_sample(pr, lv, l, s0 + k, quant, D, NULL, NULL, mg);
+        orc_sample_f(pr, lv, l, s0 + k, quant, fkind, D, NULL, NULL, mg);
         w->count += 1;
         double inv = 1.0 / (double)w->count;
         for (int64_t e = 0; e < mp; ++e) {
@@ -370,8 +388,8 @@ static double welford_total_m2(const welford* w, int64_t mp)
     return t;
 }
 
-void orc_level_stats(const orc_problem* pr, const orc_levels* lv, int l, uint64_t s0, uint64_t N,
-                     int quant, double* mean, double* M2, double* mag_mean)
+void orc_level_stats_f(const orc_problem* pr, const orc_levels* lv, int l, uint64_t s0, uint64_t N,
+                       int quant, int fkind, double* mean, double* M2, double* mag_mean)
 {
     int64_t mp = pr->m * pr->p;
     welford w;
@@ -381,9 +399,15 @@ void orc_level_stats(const orc_problem* pr, const orc_levels* lv, int l, uint64_
     w.mag = mag_mean;
     memset(mean, 0, sizeof(double) * (size_t)mp);
     if (mag_mean) memset(mag_mean, 0, sizeof(double) * (size_t)mp);
-    welford_add_samples(pr, lv, l, s0, N, quant, &w);
+    welford_add_samples(pr, lv, l, s0, N, quant, fkind, &w);
     *M2 = welford_total_m2(&w, mp);
     free(w.m2);
+}
+
+void orc_level_stats(const orc_problem* pr, const orc_levels* lv, int l, uint64_t s0, uint64_t N,
+                     int quant, double* mean, double* M2, double* mag_mean)
+{
+    orc_level_stats_f(pr, lv, l, s0, N, quant, ORC_F_IDENTITY, mean, M2, mag_mean);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -406,35 +430,56 @@ int orc_allocate(int L, const double* V, const double* C, double eps, double nl_
     return 0;
 }
 
-int orc_estimate(const orc_problem* pr, const orc_levels* lv, double eps, int64_t pilot,
-                 double nl_scale, int quant, double* Yhat, int64_t* Nl, double* V, double* means)
+static double mean_norm(const welford* w, int64_t mp)
 {
-    int L = lv->L;
+    double t = 0.0;
+    for (int64_t e = 0; e < mp; ++e) t += w->mean[e] * w->mean[e];
+    return sqrt(t);
+}
+
+int orc_estimate_f(const orc_problem* pr, const orc_levels* lv, double eps, int64_t pilot, double nl_scale,
+                   int quant, int fkind, int adaptive, double* Yhat, int* L_used, int64_t* Nl, double* V,
+                   double* means)
+{
+    int Lmax = lv->L;
     int64_t mp = pr->m * pr->p;
-    if (L < 0 || pilot < 2) return -1;
-    welford* acc = (welford*)calloc((size_t)(L + 1), sizeof(welford));
-    double* C = (double*)malloc(sizeof(double) * (size_t)(L + 1));
-    for (int l = 0; l <= L; ++l) {
+    if (Lmax < 0 || pilot < 2 || !(eps > 0.0)) return -1;
+    welford* acc = (welford*)calloc((size_t)(Lmax + 1), sizeof(welford));
+    double* C = (double*)malloc(sizeof(double) * (size_t)(Lmax + 1));
+    for (int l = 0; l <= Lmax; ++l) {
         acc[l].mean = (double*)calloc((size_t)mp, sizeof(double));
         acc[l].m2 = (double*)calloc((size_t)mp, sizeof(double));
         acc[l].mag = NULL;
         C[l] = orc_cost(lv, l);
     }
-    /* pilot run on every level, then V_l from it */
-    for (int l = 0; l <= L; ++l) {
-        welford_add_samples(pr, lv, l, 0, (uint64_t)pilot, quant, &acc[l]);
-        V[l] = welford_total_m2(&acc[l], mp) / (double)(pilot - 1);
-    }
-    int rc = orc_allocate(L, V, C, eps, nl_scale, pilot, Nl);
-    if (rc == 0) {
-        /* top-ups continue each level at the next unused sample id, keeping the
-         * pilot samples (Alg. 2 reuses earlier evaluations of Y_l) */
+    /* Alg. 2: fixed L runs one round on levels 0..L.  Adaptive: rounds on levels 0..L for
+     * L = 0, 1, ...; each round pilots the new finest level, re-allocates every level from the
+     * variances of all samples held and tops them up (never discarding samples); the loop stops
+     * once at least three levels are in and the finest level's mean satisfies
+     * ||Y_L||_F < (sqrt(R) + 1) eps / sqrt(2) (Remark 3.5, Eq. L_num_bound_matrix), or at the
+     * largest L. */
+    int L = adaptive ? 0 : Lmax;
+    int rc = 0;
+    for (;;) {
+        for (int l = 0; l <= L; ++l) {
+            uint64_t have = acc[l].count;
+            if (have < (uint64_t)pilot) welford_add_samples(pr, lv, l, have, (uint64_t)pilot - have, quant, fkind, &acc[l]);
+            V[l] = welford_total_m2(&acc[l], mp) / (double)(acc[l].count - 1);
+        }
+        rc = orc_allocate(L, V, C, eps, nl_scale, pilot, Nl);
+        if (rc != 0) break;
         for (int l = 0; l <= L; ++l) {
             uint64_t have = acc[l].count;
             if ((uint64_t)Nl[l] > have)
-                welford_add_samples(pr, lv, l, have, (uint64_t)Nl[l] - have, quant, &acc[l]);
+                welford_add_samples(pr, lv, l, have, (uint64_t)Nl[l] - have, quant, fkind, &acc[l]);
+            Nl[l] = (int64_t)acc[l].count;
             V[l] = welford_total_m2(&acc[l], mp) / (double)(acc[l].count - 1);
         }
+        if (!adaptive || L == Lmax) break;
+        if (L >= 2 && mean_norm(&acc[L], mp) < (sqrt((double)lv->R) + 1.0) * eps / sqrt(2.0)) break;
+        L += 1;
+    }
+    if (rc == 0) {
         /* telescoping sum (Eq. hatY) */
         for (int64_t e = 0; e < mp; ++e) {
             double y = 0.0;
@@ -444,14 +489,21 @@ int orc_estimate(const orc_problem* pr, const orc_levels* lv, double eps, int64_
         if (means)
             for (int l = 0; l <= L; ++l)
                 memcpy(means + (size_t)l * (size_t)mp, acc[l].mean, sizeof(double) * (size_t)mp);
+        if (L_used) *L_used = L;
     }
-    for (int l = 0; l <= L; ++l) {
+    for (int l = 0; l <= Lmax; ++l) {
         free(acc[l].mean);
         free(acc[l].m2);
     }
     free(acc);
     free(C);
     return rc;
+}
+
+int orc_estimate(const orc_problem* pr, const orc_levels* lv, double eps, int64_t pilot,
+                 double nl_scale, int quant, double* Yhat, int64_t* Nl, double* V, double* means)
+{
+    return orc_estimate_f(pr, lv, eps, pilot, nl_scale, quant, ORC_F_IDENTITY, 0, Yhat, NULL, Nl, V, means);
 }
 
 /* ------------------------------------------------------------------------- */

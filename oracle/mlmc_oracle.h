@@ -64,6 +64,12 @@ typedef struct {
  * (emulation of the reduced-precision forms; none for the plain method). */
 enum { ORC_QUANT_NONE = 0, ORC_QUANT_BF16 = 1, ORC_QUANT_E4M3 = 2 };
 
+/* The targeted function f of f^(AB), applied entrywise (Sec. 3): the identity (the
+ * estimator of E[AB]), or f(x) = |x| H(2 - x) with H the Heaviside step, H(0) = 1 (the function
+ * of the paper's matrix example, Sec. 5.2). */
+enum { ORC_F_IDENTITY = 0, ORC_F_ABS_STEP = 1 };
+double orc_f(int fkind, double x);
+
 /* Philox4x32-10 and Philox4x64-10 block functions (Salmon et al., SC'11). */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
@@ -109,6 +115,11 @@ void orc_sketch(int64_t m, int64_t n, int64_t p, const double* A, const double* 
 void orc_sample(const orc_problem* pr, const orc_levels* lv, int l, uint64_t s, int quant,
                 double* D, double* Pf, double* Pc, double* mag);
 
+/* The same with the targeted function: D = f(Pf) - f(Pc) entrywise for l > 0 and D = f(Pf) at
+ * l = 0 (Alg. 1 with f^); Pf, Pc and mag are as above (before f). */
+void orc_sample_f(const orc_problem* pr, const orc_levels* lv, int l, uint64_t s, int quant, int fkind,
+                  double* D, double* Pf, double* Pc, double* mag);
+
 /* Power-of-two scale of one block of 32 consecutive slots of one row of the
  * sampled A (or one column of the sampled B): 2^ceil(log2(absmax / 448)),
  * 1 when the block is all zero. */
@@ -119,6 +130,10 @@ double orc_e4m3_block_scale(double absmax);
  * and the per-entry mean of mag (may be NULL).  Welford updates in sample order. */
 void orc_level_stats(const orc_problem* pr, const orc_levels* lv, int l, uint64_t s0, uint64_t N,
                      int quant, double* mean, double* M2, double* mag_mean);
+
+/* The same with the targeted function (D as in orc_sample_f). */
+void orc_level_stats_f(const orc_problem* pr, const orc_levels* lv, int l, uint64_t s0, uint64_t N,
+                       int quant, int fkind, double* mean, double* M2, double* mag_mean);
 
 /* N_l from the variance-optimal allocation (Remark 3.6, Giles' Eq. 12 with the
  * sum running over V_j C_j):  N_l = ceil(nl_scale * 2 eps^-2 sqrt(V_l / C_l)
@@ -132,6 +147,17 @@ int orc_allocate(int L, const double* V, const double* C, double eps, double nl_
  * ((L+1) x m x p).  Returns 0, or -1 on bad input. */
 int orc_estimate(const orc_problem* pr, const orc_levels* lv, double eps, int64_t pilot,
                  double nl_scale, int quant, double* Yhat, int64_t* Nl, double* V, double* means);
+
+/* Alg. 2 with the targeted function and, if adaptive, the choice of L: rounds on levels 0..L
+ * for L = 0, 1, ... (each round: pilot samples on the new finest level, V_l from all samples
+ * held, N_l by orc_allocate over levels 0..L, top-ups from the next unused sample id); the loop
+ * ends after the first round with at least three levels whose finest mean satisfies
+ * ||Y_L||_F < (sqrt(R) + 1) eps / sqrt(2) (Remark 3.5, Eq. L_num_bound_matrix), or after the
+ * round with L = lv->L.  adaptive = 0: one round with L = lv->L (orc_estimate).  Outputs as in
+ * orc_estimate over levels 0..*L_used; Nl and V hold the final sample counts and variances. */
+int orc_estimate_f(const orc_problem* pr, const orc_levels* lv, double eps, int64_t pilot, double nl_scale,
+                   int quant, int fkind, int adaptive, double* Yhat, int* L_used, int64_t* Nl, double* V,
+                   double* means);
 
 /* Gradient of <G, Yhat> for Yhat = sum_l (1/N_l) sum_{s<N_l} D_{l,s}, with the
  * draws (indices and Z) held fixed: dM, dS (m x n), dMp, dSp (n x p).  The
