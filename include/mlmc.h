@@ -116,12 +116,29 @@ typedef struct {
                               launches; the default for outputs above 128 x 128) */
     int32_t adjoint_batch_log2; /* mlmc_backward replays at most 2^this sampled products per batch
                                    (0 = 26; at least c_L + 1 are always taken); scratch is 8 B each */
+    int32_t f;           /* mlmc_function applied entrywise to each sketch (Sec. 3): the estimator then
+                            targets E[f(AB)] with D = f(P_l) - f(P_{l-1}) (Alg. 1).  Anything but the
+                            identity needs MLMC_FP64 or MLMC_FP32 and has no mlmc_backward */
+    int32_t adaptive_L;  /* 0: mlmc_estimate uses the problem's L.  1: Alg. 2 chooses L: rounds on
+                            levels 0..L for L = 0, 1, ... (the new finest level gets pilot_n samples,
+                            every level is re-allocated from the variances of all samples held and
+                            topped up), stopping after the first round with at least three levels
+                            whose finest mean satisfies ||Y_L||_F < (sqrt(R) + 1) eps / sqrt(2)
+                            (Remark 3.5, Eq. L_num_bound_matrix), or at the problem's L */
 } mlmc_options;
+
+/* Targeted functions f (mlmc_options.f). */
+typedef enum {
+    MLMC_F_IDENTITY = 0, /* f(x) = x: the estimator of E[AB] */
+    MLMC_F_ABS_STEP = 1  /* f(x) = |x| H(2 - x), H the Heaviside step with H(0) = 1 (the paper's
+                            matrix example, Sec. 5.2) */
+} mlmc_function;
 
 /* Report of one problem after mlmc_estimate. */
 typedef struct {
-    int32_t L;
-    int32_t reserved;
+    int32_t L;                      /* finest level used (chosen by Alg. 2 when adaptive_L) */
+    int32_t bias_unmet;             /* adaptive_L: 1 if the problem's L was reached without the
+                                       finest mean meeting the bound, else 0 */
     int64_t N[MLMC_MAX_LEVELS];     /* samples per level */
     double V[MLMC_MAX_LEVELS];      /* single-sample variance V_l (Remark 3.6) */
     double cost[MLMC_MAX_LEVELS];   /* C_l of the allocation: c_0, then c_l + c_{l-1} */

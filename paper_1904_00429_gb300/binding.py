@@ -25,6 +25,7 @@ MAX_LEVELS = 32
 STATUS = {0: "MLMC_OK", 1: "MLMC_ERR_INVALID_ARG", 2: "MLMC_ERR_CUDA", 3: "MLMC_ERR_OOM",
           4: "MLMC_ERR_TIMEOUT", 5: "MLMC_ERR_NUMERIC", 6: "MLMC_ERR_UNSUPPORTED", 7: "MLMC_ERR_STATE"}
 PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2, "fp8": 3, "fp8_e4m3": 3}
+FUNCTION = {"identity": 0, "abs_step": 1}   # mlmc_function
 DTYPE = {torch.float64: 0, torch.float32: 1}
 
 
@@ -46,7 +47,8 @@ class Problem(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("c0", ctypes.c_int32), ("ratio", ctypes.c_int32), ("L", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("pilot_n", ctypes.c_int64), ("nl_scale", ctypes.c_double),
-                ("timeout_ns", ctypes.c_int64), ("tile_override", ctypes.c_int32), ("adjoint_batch_log2", ctypes.c_int32)]
+                ("timeout_ns", ctypes.c_int64), ("tile_override", ctypes.c_int32), ("adjoint_batch_log2", ctypes.c_int32),
+                ("f", ctypes.c_int32), ("adaptive_L", ctypes.c_int32)]
 
 
 class Range(ctypes.Structure):
@@ -55,14 +57,14 @@ class Range(ctypes.Structure):
 
 
 class Report(ctypes.Structure):
-    _fields_ = [("L", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    _fields_ = [("L", ctypes.c_int32), ("bias_unmet", ctypes.c_int32),
                 ("N", ctypes.c_int64 * MAX_LEVELS), ("V", ctypes.c_double * MAX_LEVELS),
                 ("cost", ctypes.c_double * MAX_LEVELS), ("mean_norm", ctypes.c_double * MAX_LEVELS),
                 ("rmse_pred", ctypes.c_double), ("eps_abs", ctypes.c_double), ("outer_products", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         L = self.L
-        return {"L": L, "N": list(self.N[:L + 1]), "V": list(self.V[:L + 1]), "cost": list(self.cost[:L + 1]),
+        return {"L": L, "bias_unmet": bool(self.bias_unmet), "N": list(self.N[:L + 1]), "V": list(self.V[:L + 1]), "cost": list(self.cost[:L + 1]),
                 "mean_norm": list(self.mean_norm[:L + 1]), "rmse_pred": self.rmse_pred, "eps_abs": self.eps_abs,
                 "outer_products": self.outer_products}
 
@@ -153,7 +155,8 @@ class Plan:
 
     def __init__(self, problems: Sequence[ProblemSpec], *, c0: int, L: int, ratio: int = 2,
                  precision: str = "fp32", pilot_n: int = 256, nl_scale: float = 1.0,
-                 timeout_ns: int = 0, tile_override: int = 0, adjoint_batch_log2: int = 0, stream=None):
+                 timeout_ns: int = 0, tile_override: int = 0, adjoint_batch_log2: int = 0,
+                 f: str = "identity", adaptive_L: bool = False, stream=None):
         self.problems = list(problems)
         self.device = self.problems[0].M.device
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -178,7 +181,7 @@ class Plan:
             self.shapes.append((m, n, p))
             self.levels.append(pr.L if pr.L >= 0 else L)
         self.options = Options(c0, ratio, L, PRECISION[precision], pilot_n, nl_scale, timeout_ns, tile_override,
-                               adjoint_batch_log2)
+                               adjoint_batch_log2, FUNCTION[f], int(bool(adaptive_L)))
         self.precision = precision
         self.c0, self.ratio, self.L = c0, ratio, L
         self.pilot_n = pilot_n

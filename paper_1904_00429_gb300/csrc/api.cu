@@ -216,6 +216,10 @@ mlmc_status validate(const mlmc_problem* problems, int32_t nprob, const mlmc_opt
                     "E4M3: 1032 1064 1128 2032 2064; pairs 3256)", o->tile_override);
     if (o->adjoint_batch_log2 < 0 || o->adjoint_batch_log2 > 40)
         return fail(MLMC_ERR_INVALID_ARG, "adjoint_batch_log2 must be in [0, 40]");
+    if (o->f != MLMC_F_IDENTITY && o->f != MLMC_F_ABS_STEP) return fail(MLMC_ERR_INVALID_ARG, "unknown f %d", o->f);
+    if (o->f != MLMC_F_IDENTITY && o->precision != MLMC_FP64 && o->precision != MLMC_FP32)
+        return fail(MLMC_ERR_UNSUPPORTED, "a targeted function other than the identity needs FP64 or FP32");
+    if (o->adaptive_L != 0 && o->adaptive_L != 1) return fail(MLMC_ERR_INVALID_ARG, "adaptive_L must be 0 or 1");
     for (int32_t q = 0; q < nprob; ++q) {
         const mlmc_problem& pr = problems[q];
         const int L = pr.L >= 0 ? pr.L : o->L;
@@ -343,8 +347,8 @@ mlmc_status run_level(mlmc_plan_t* plan, ProblemState& ps, int level, uint64_t s
             TcLaunch tl{plan->err_flag, plan->timeout_ns, static_cast<float>(double(ps.n) / double(c)), plan->num_sms};
             err = launch_level_tc(prm, ps.tile, tc_format(o), tl, plan->stream);
         } else {
-            err = plan->f64 ? launch_level_cuda_core_f64(prm, plan->stream)
-                            : launch_level_cuda_core_f32(prm, plan->stream);
+            err = plan->f64 ? launch_level_cuda_core_f64(prm, plan->opt.f, plan->stream)
+                            : launch_level_cuda_core_f32(prm, plan->opt.f, plan->stream);
         }
         if (check_cuda(plan, err, "level kernel launch") != MLMC_OK) return plan->sticky;
         plan->launches += 3;  // level kernel, merge of sums, merge of sums of squares
@@ -1071,6 +1075,25 @@ mlmc_status mlmc_launch_count(const mlmc_plan_t* plan, uint64_t* count)
     return MLMC_OK;
 }
 
+namespace {
+
+// ||Y_l||_F: the norm of level l's mean, read back from its FP64 sum.
+mlmc_status level_mean_norm(mlmc_plan_t* plan, const ProblemState& ps, int l, double* out)
+{
+    const int64_t mp = ps.m * ps.p;
+    std::vector<double> sums(static_cast<size_t>(mp));
+    cudaError_t err = cudaMemcpyAsync(sums.data(), ps.sum + int64_t(l) * mp, sizeof(double) * size_t(mp),
+                                      cudaMemcpyDeviceToHost, plan->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(plan->stream);
+    if (check_cuda(plan, err, "read level mean") != MLMC_OK) return plan->sticky;
+    double nrm = 0.0;
+    for (double v : sums) nrm += v * v;
+    *out = ps.N.v[l] > 0 ? std::sqrt(nrm) / double(ps.N.v[l]) : 0.0;
+    return MLMC_OK;
+}
+
+}  // namespace
+
 mlmc_status mlmc_estimate(mlmc_plan_t* plan, const double* eps_abs, double* yhat_dev, mlmc_report* reports)
 {
     mlmc_status st = enter(plan);
@@ -1098,42 +1121,76 @@ mlmc_status mlmc_estimate(mlmc_plan_t* plan, const double* eps_abs, double* yhat
         }
         return MLMC_OK;
     };
-    // pilot run on every level of every problem
-    std::vector<BatchRange> todo;
-    for (size_t q = 0; q < plan->probs.size(); ++q) {
-        const ProblemState& ps = plan->probs[q];
-        for (int l = 0; l <= ps.L; ++l)
-            if (ps.N.v[l] < pilot) todo.push_back(BatchRange{int(q), l, ps.N.v[l], pilot - ps.N.v[l]});
-    }
-    if ((st = run_ranges(todo)) != MLMC_OK) return st;
-    // allocation from the pilot variances, then top-ups from the next unused sample id
-    todo.clear();
-    for (size_t q = 0; q < plan->probs.size(); ++q) {
-        ProblemState& ps = plan->probs[q];
-        double M2[MLMC_MAX_LEVELS];
-        if ((st = level_M2(plan, ps, 0, ps.L + 1, M2)) != MLMC_OK) return st;
-        double V[MLMC_MAX_LEVELS], C[MLMC_MAX_LEVELS], root_sum = 0.0;
-        for (int l = 0; l <= ps.L; ++l) {
-            V[l] = std::max(0.0, M2[l] / double(ps.N.v[l] - 1));
-            C[l] = level_cost(o, l);
-            if (!std::isfinite(V[l])) return set_sticky(plan, fail(MLMC_ERR_NUMERIC, "problem %zu level %d: V_l not finite", q, l));
-            root_sum += std::sqrt(V[l] * C[l]);
+    // Alg. 2 in rounds.  Fixed L: one round on levels 0..L.  adaptive_L: rounds on levels 0..Lc
+    // for Lc = 0, 1, ...; a problem stops after the first round with Lc >= 2 whose finest mean
+    // satisfies ||Y_Lc||_F < (sqrt(R) + 1) eps / sqrt(2) (Remark 3.5), or at its own L.  Every
+    // round pilots the levels that lack it, re-allocates from the variances of all samples held
+    // and tops up from the next unused sample id (samples are never discarded).
+    const size_t np = plan->probs.size();
+    std::vector<int> Lc(np), running(np, 1), unmet(np, 0);
+    for (size_t q = 0; q < np; ++q) Lc[q] = o.adaptive_L ? 0 : plan->probs[q].L;
+    for (;;) {
+        std::vector<BatchRange> todo;
+        for (size_t q = 0; q < np; ++q) {
+            if (!running[q]) continue;
+            const ProblemState& ps = plan->probs[q];
+            for (int l = 0; l <= Lc[q]; ++l)
+                if (ps.N.v[l] < pilot) todo.push_back(BatchRange{int(q), l, ps.N.v[l], pilot - ps.N.v[l]});
         }
-        for (int l = 0; l <= ps.L; ++l) {
-            const double target = o.nl_scale * 2.0 / (eps_abs[q] * eps_abs[q]) * std::sqrt(V[l] / C[l]) * root_sum;
-            if (!(target < 9.0e18)) return set_sticky(plan, fail(MLMC_ERR_NUMERIC, "allocated N_l overflows"));
-            const uint64_t nl = std::max<uint64_t>(uint64_t(std::ceil(target)), pilot);
-            ps.Nl_est[l] = int64_t(std::max<uint64_t>(nl, ps.N.v[l]));
-            if (nl > ps.N.v[l]) todo.push_back(BatchRange{int(q), l, ps.N.v[l], nl - ps.N.v[l]});
+        if ((st = run_ranges(todo)) != MLMC_OK) return st;
+        // allocation from the variances held, then top-ups from the next unused sample id
+        todo.clear();
+        for (size_t q = 0; q < np; ++q) {
+            if (!running[q]) continue;
+            ProblemState& ps = plan->probs[q];
+            const int L = Lc[q];
+            double M2[MLMC_MAX_LEVELS];
+            if ((st = level_M2(plan, ps, 0, L + 1, M2)) != MLMC_OK) return st;
+            double V[MLMC_MAX_LEVELS], C[MLMC_MAX_LEVELS], root_sum = 0.0;
+            for (int l = 0; l <= L; ++l) {
+                V[l] = std::max(0.0, M2[l] / double(ps.N.v[l] - 1));
+                C[l] = level_cost(o, l);
+                if (!std::isfinite(V[l])) return set_sticky(plan, fail(MLMC_ERR_NUMERIC, "problem %zu level %d: V_l not finite", q, l));
+                root_sum += std::sqrt(V[l] * C[l]);
+            }
+            for (int l = 0; l <= L; ++l) {
+                const double target = o.nl_scale * 2.0 / (eps_abs[q] * eps_abs[q]) * std::sqrt(V[l] / C[l]) * root_sum;
+                if (!(target < 9.0e18)) return set_sticky(plan, fail(MLMC_ERR_NUMERIC, "allocated N_l overflows"));
+                const uint64_t nl = std::max<uint64_t>(uint64_t(std::ceil(target)), pilot);
+                ps.Nl_est[l] = int64_t(std::max<uint64_t>(nl, ps.N.v[l]));
+                if (nl > ps.N.v[l]) todo.push_back(BatchRange{int(q), l, ps.N.v[l], nl - ps.N.v[l]});
+            }
         }
+        if ((st = run_ranges(todo)) != MLMC_OK) return st;
+        bool more = false;
+        for (size_t q = 0; q < np; ++q) {
+            if (!running[q]) continue;
+            ProblemState& ps = plan->probs[q];
+            if (!o.adaptive_L) {
+                running[q] = 0;
+                continue;
+            }
+            double nrm = 0.0;
+            if (Lc[q] >= 2 && (st = level_mean_norm(plan, ps, Lc[q], &nrm)) != MLMC_OK) return st;
+            if (Lc[q] >= 2 && nrm < (std::sqrt(double(o.ratio)) + 1.0) * eps_abs[q] / std::sqrt(2.0)) {
+                running[q] = 0;
+            } else if (Lc[q] == ps.L) {
+                running[q] = 0;
+                unmet[q] = 1;
+            } else {
+                Lc[q] += 1;
+                more = true;
+            }
+        }
+        if (!more) break;
     }
-    if ((st = run_ranges(todo)) != MLMC_OK) return st;
     // telescoping sum and report
     int64_t off = 0;
     for (size_t q = 0; q < plan->probs.size(); ++q) {
         ProblemState& ps = plan->probs[q];
         const int64_t mp = ps.m * ps.p;
-        cudaError_t err = launch_telescoping(ps.sum, ps.N, ps.L + 1, mp, yhat_dev + off, plan->stream);
+        const int L = Lc[q];
+        cudaError_t err = launch_telescoping(ps.sum, ps.N, L + 1, mp, yhat_dev + off, plan->stream);
         if (check_cuda(plan, err, "telescoping launch") != MLMC_OK) return plan->sticky;
         plan->launches += 1;
         off += mp;
@@ -1142,12 +1199,13 @@ mlmc_status mlmc_estimate(mlmc_plan_t* plan, const double* eps_abs, double* yhat
             mlmc_report& r = reports[q];
             std::memset(&r, 0, sizeof(r));
             double M2[MLMC_MAX_LEVELS];
-            if ((st = level_M2(plan, ps, 0, ps.L + 1, M2)) != MLMC_OK) return st;
-            r.L = ps.L;
+            if ((st = level_M2(plan, ps, 0, L + 1, M2)) != MLMC_OK) return st;
+            r.L = L;
+            r.bias_unmet = unmet[q];
             r.eps_abs = eps_abs[q];
             double var = 0.0;
             std::vector<double> sums(static_cast<size_t>(mp));
-            for (int l = 0; l <= ps.L; ++l) {
+            for (int l = 0; l <= L; ++l) {
                 r.N[l] = int64_t(ps.N.v[l]);
                 r.V[l] = M2[l] / double(ps.N.v[l] - 1);
                 r.cost[l] = level_cost(o, l);
@@ -1308,6 +1366,8 @@ mlmc_status mlmc_backward(mlmc_plan_t* plan, const double* G_dev, void* const* d
     mlmc_status st = enter(plan);
     if (st != MLMC_OK) return st;
     if (!G_dev || !dM_dev || !dS_dev || !dMp_dev || !dSp_dev) return fail(MLMC_ERR_INVALID_ARG, "null argument");
+    if (plan->opt.f != MLMC_F_IDENTITY)
+        return fail(MLMC_ERR_UNSUPPORTED, "mlmc_backward: the replay is the adjoint of the linear estimator (f = x)");
     if (plan->opt.precision == MLMC_FP8_E4M3)
         return fail(MLMC_ERR_UNSUPPORTED, "mlmc_backward: the E4M3 block scales couple the slots of a sample; "
                     "use an FP32 or BF16 plan for gradients");

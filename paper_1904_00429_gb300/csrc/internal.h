@@ -66,8 +66,9 @@ struct CudaCoreTile {
 };
 
 // Launchers (return the launch error, if any).
-cudaError_t launch_level_cuda_core_f64(const LevelParams& prm, cudaStream_t st);
-cudaError_t launch_level_cuda_core_f32(const LevelParams& prm, cudaStream_t st);
+// f: the targeted function (mlmc_function), applied to the fine and coarse estimates apart.
+cudaError_t launch_level_cuda_core_f64(const LevelParams& prm, int f, cudaStream_t st);
+cudaError_t launch_level_cuda_core_f32(const LevelParams& prm, int f, cudaStream_t st);
 CudaCoreTile cuda_core_tile(int precision);
 
 // Tensor-core (BF16) level kernel: tile of (128 * mh) rows x bn columns per CTA.

@@ -14,6 +14,9 @@
 // tile is added to a running per-chunk sum and its squared Frobenius norm to
 // a running FP64 scalar; at the end of the chunk both are written as
 // partials, which the merge kernel folds into the level in chunk order.
+// With a targeted function f (F != 0) the fine and coarse estimates are kept apart,
+//     P_l = (n/c_l) sum_t A[:, r_t] B[r_t, :],   P_{l-1} = (n/c_{l-1}) sum_{t coarse} ...,
+// in two register tiles, and D_s = f(P_l) - f(P_{l-1}) entrywise (f(P_0) at level 0).
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -55,7 +58,15 @@ struct Pair4<double> {
     }
 };
 
-template <typename T, int TM, int TP, int TK, int RM, int RP>
+// The targeted functions of mlmc_function: F = 1 is |x| H(2 - x) with H(0) = 1.
+template <int F, typename T>
+__device__ __forceinline__ T targeted(T x)
+{
+    if constexpr (F == 1) return (T(2) - x >= T(0)) ? fabs(x) : T(0);
+    return x;
+}
+
+template <typename T, int TM, int TP, int TK, int RM, int RP, int F>
 __global__ void __launch_bounds__((TM / RM) * (TP / RP))
 level_cuda_core_kernel(const LevelParams prm)
 {
@@ -66,7 +77,7 @@ level_cuda_core_kernel(const LevelParams prm)
     __shared__ __align__(16) T As[TK][TM];
     __shared__ __align__(16) T Bs[TK][TP];
     __shared__ int idx_s[TK];
-    __shared__ T w_s[TK];
+    __shared__ T w_s[TK];   // F = 0: the slot's weight; F != 0: 1 on coarse slots, else 0
     __shared__ double red_s[NT / 32];
 
     const int tid = threadIdx.x;
@@ -84,6 +95,7 @@ level_cuda_core_kernel(const LevelParams prm)
     const T* PB = static_cast<const T*>(prm.PB);
     const T wf = static_cast<T>(prm.w_fine);
     const T wc = static_cast<T>(prm.w_coarse);
+    const T wcn = static_cast<T>(prm.w_fine - prm.w_coarse);   // n / c_{l-1}
 
     T sum[RM][RP];
 #pragma unroll
@@ -96,10 +108,11 @@ level_cuda_core_kernel(const LevelParams prm)
         const uint32_t lsw = level_sample_word(prm.l, s);
         const uint32_t s_lo = static_cast<uint32_t>(s);
         T acc[RM][RP];
+        T accc[RM][RP];   // F != 0: the coarse estimate's sum
 #pragma unroll
         for (int i = 0; i < RM; ++i)
 #pragma unroll
-            for (int j = 0; j < RP; ++j) acc[i][j] = T(0);
+            for (int j = 0; j < RP; ++j) acc[i][j] = accc[i][j] = T(0);
 
         for (int k0 = 0; k0 < prm.c; k0 += TK) {
             // 1. indices and weights of slots k0 .. k0 + TK - 1
@@ -114,7 +127,10 @@ level_cuda_core_kernel(const LevelParams prm)
                         const bool valid = te < prm.c;
                         const bool coarse = prm.l > 0 && (te % prm.R) == prm.R - 1;
                         idx_s[2 * h + e] = valid ? static_cast<int>(e ? r1 : r0) : -1;
-                        w_s[2 * h + e] = valid ? (coarse ? wc : wf) : T(0);
+                        if constexpr (F == 0)
+                            w_s[2 * h + e] = valid ? (coarse ? wc : wf) : T(0);
+                        else
+                            w_s[2 * h + e] = (valid && coarse) ? T(1) : T(0);
                     }
                 } else {
                     idx_s[2 * h] = idx_s[2 * h + 1] = -1;
@@ -157,7 +173,7 @@ level_cuda_core_kernel(const LevelParams prm)
                     T z[4];
                     Normals<T>::four(w, z);
                     const Pair4<T> ms = Pair4<T>::load(PB + static_cast<int64_t>(k) * prm.ldPB + 2 * j);
-                    const T wt = w_s[tt];
+                    const T wt = F == 0 ? w_s[tt] : T(1);   // F != 0: weights applied per estimate
 #pragma unroll
                     for (int r = 0; r < 4; ++r) b[r] = wt * fma(ms.v[2 * r + 1], z[r], ms.v[2 * r]);
                 }
@@ -178,10 +194,27 @@ level_cuda_core_kernel(const LevelParams prm)
                 for (int i = 0; i < RM; ++i)
 #pragma unroll
                     for (int j = 0; j < RP; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+                if constexpr (F != 0) {
+                    if (w_s[tt] != T(0)) {   // coarse slot (uniform across the CTA)
+#pragma unroll
+                        for (int i = 0; i < RM; ++i)
+#pragma unroll
+                            for (int j = 0; j < RP; ++j) accc[i][j] = fma(av[i], bv[j], accc[i][j]);
+                    }
+                }
             }
             __syncthreads();
         }
 
+        if constexpr (F != 0) {
+            // D = f(P_l) - f(P_{l-1}) entrywise; f(P_0) at level 0
+#pragma unroll
+            for (int i = 0; i < RM; ++i)
+#pragma unroll
+                for (int j = 0; j < RP; ++j)
+                    acc[i][j] = prm.l > 0 ? targeted<F>(wf * acc[i][j]) - targeted<F>(wcn * accc[i][j])
+                                          : targeted<F>(wf * acc[i][j]);
+        }
         // per-sample statistics: running sum of D and of ||D||_F^2
         T qs = T(0);
 #pragma unroll
@@ -219,11 +252,15 @@ level_cuda_core_kernel(const LevelParams prm)
 }
 
 template <typename T, int TM, int TP, int TK, int RM, int RP>
-cudaError_t launch(const LevelParams& prm, cudaStream_t st)
+cudaError_t launch(const LevelParams& prm, int f, cudaStream_t st)
 {
     constexpr int NT = (TM / RM) * (TP / RP);
     dim3 grid(prm.tiles_m * prm.tiles_p, prm.nchunks);
-    level_cuda_core_kernel<T, TM, TP, TK, RM, RP><<<grid, NT, 0, st>>>(prm);
+    switch (f) {
+    case MLMC_F_IDENTITY: level_cuda_core_kernel<T, TM, TP, TK, RM, RP, 0><<<grid, NT, 0, st>>>(prm); break;
+    case MLMC_F_ABS_STEP: level_cuda_core_kernel<T, TM, TP, TK, RM, RP, 1><<<grid, NT, 0, st>>>(prm); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
@@ -231,14 +268,14 @@ cudaError_t launch(const LevelParams& prm, cudaStream_t st)
 
 CudaCoreTile cuda_core_tile(int /*precision*/) { return CudaCoreTile{64, 64}; }
 
-cudaError_t launch_level_cuda_core_f64(const LevelParams& prm, cudaStream_t st)
+cudaError_t launch_level_cuda_core_f64(const LevelParams& prm, int f, cudaStream_t st)
 {
-    return launch<double, 64, 64, 32, 4, 4>(prm, st);
+    return launch<double, 64, 64, 32, 4, 4>(prm, f, st);
 }
 
-cudaError_t launch_level_cuda_core_f32(const LevelParams& prm, cudaStream_t st)
+cudaError_t launch_level_cuda_core_f32(const LevelParams& prm, int f, cudaStream_t st)
 {
-    return launch<float, 64, 64, 32, 4, 4>(prm, st);
+    return launch<float, 64, 64, 32, 4, 4>(prm, f, st);
 }
 
 }  // namespace mlmc
