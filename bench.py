@@ -506,6 +506,74 @@ def _measure_ladder(args, rels, W, host, exact, dev, stream, projected):
             "unit": "s", "rungs": rungs, "projected_1e-3_s": projected}
 
 
+NONLINEAR = dict(name="abs_step_64x1024x64", m=64, n=1024, p=64, c0=16, R=2, Lmax=12, pilot=256, eps_entry=0.01,
+                 precision="fp32")
+
+
+def _nonlinear_params():
+    """The E[f(AB)] workload's parameters: the precision workload's laws (M ~ U[-1,1], S ~ U[0.1,1],
+    seeds 0 and 1) with A scaled by 2 / sqrt(n) and shifted by 2 / n, so that the entries of AB
+    are O(1) and straddle the jump of f at 2."""
+    from paper_1904_00429_gb300.inputs import make_params
+    Nw = NONLINEAR
+    pp = make_params(Nw["m"], Nw["n"], Nw["p"], seed_A=0, seed_B=1, dtype=np.float64)
+    k = 2.0 / math.sqrt(Nw["n"])
+    return [x.astype(np.float32) for x in (pp.M * k + 2.0 / Nw["n"], pp.S * k, pp.Mp, pp.Sp)]
+
+
+def _measure_nonlinear(args, dev, stream):
+    """E[f(AB)] with f(x) = |x| H(2 - x) (the paper's matrix example) on the CUDA cores (FP32):
+    Alg. 2 with the adaptive choice of L, end to end through mlmc_estimate, against standard MC
+    at the finest level MLMC chose (Eq. Phigh: one level of c_L draws, the same variance target
+    eps^2 / 2), whose time is measured on a bounded batch and projected to its allocated N."""
+    import torch
+
+    from paper_1904_00429_gb300 import binding
+
+    Nw = NONLINEAR
+    ts = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in _nonlinear_params()]
+    eps = Nw["eps_entry"] * math.sqrt(Nw["m"] * Nw["p"])
+    spec = binding.ProblemSpec(*ts, seed_A=7, seed_B=8, seed_idx=9, problem_id=0)
+    with binding.Plan([spec], c0=Nw["c0"], L=Nw["Lmax"], ratio=Nw["R"], precision=Nw["precision"], f="abs_step",
+                      adaptive_L=True, pilot_n=Nw["pilot"], stream=stream) as plan:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        (Y,), (rep,) = plan.estimate([eps])
+        torch.cuda.synchronize()
+        t_mlmc = time.perf_counter() - t0
+    L = rep["L"]
+    cL = Nw["c0"] * Nw["R"] ** L
+    # standard MC at the finest level: pilot, allocation, then a bounded timed batch
+    with binding.Plan([spec], c0=cL, L=0, ratio=Nw["R"], precision=Nw["precision"], f="abs_step",
+                      pilot_n=Nw["pilot"], stream=stream) as mc:
+        mc.level_stats(0, 0, 0, Nw["pilot"])
+        N_mc = int(mc.allocate([eps])[0][0])
+        batch = max(64, min(N_mc, int(2e8 // cL)))
+        mc.level_stats(0, 0, Nw["pilot"], 64)   # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mc.level_stats(0, 0, Nw["pilot"] + 64, batch)
+        torch.cuda.synchronize()
+        per_sample = (time.perf_counter() - t0) / batch
+    t_mc = N_mc * per_sample
+    # FMAs of the fine contraction (2 m p per outer product; the coarse slots add their own
+    # contraction on top) over the end-to-end time, host rounds included
+    achieved = 2.0 * Nw["m"] * Nw["p"] * rep["outer_products"] / t_mlmc / 1e12
+    return {"workload": Nw["name"], "metric": "time to RMSE eps for E[f(AB)], f(x) = |x| H(2 - x)", "unit": "s",
+            "eps_abs": eps, "precision": Nw["precision"],
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)",
+                         "kernel": "level_cuda_core_kernel<float, F = |x| H(2 - x)>",
+                         "note": "end to end (pilot and allocation rounds of Alg. 2 included)"},
+            "mlmc": {"value": t_mlmc, "L": L, "bias_unmet": rep["bias_unmet"], "N_l": rep["N"],
+                     "outer_products": rep["outer_products"], "rmse_pred": rep["rmse_pred"],
+                     "level_mean_norms": rep["mean_norm"], "timing": "end to end through mlmc_estimate"},
+            "mc_finest_level": {"value": t_mc, "c": cL, "N": N_mc, "outer_products": float(N_mc) * cL,
+                                "timing": f"{batch} samples timed, projected to N"},
+            "mc_over_mlmc": t_mc / t_mlmc}
+
+
 BATCHED = dict(name="batched_64_problems", count=64, shape_seed=7, c0=32, R=2, pilot=256, rel_rmse=1e-3,
                step_outer=4.0e8, precision="bf16")
 
@@ -663,6 +731,8 @@ def run_ours(args):
         line["adjoint"] = _measure_adjoint(args, host, dev, stream, peaks, peak_kind)
     if not args.no_batched and world == 1:
         line["batched"] = _measure_batched(args, dev, stream, peaks, peak_kind)
+    if not args.no_nonlinear and world == 1:
+        line["nonlinear"] = _measure_nonlinear(args, dev, stream)
     if args.ladder and world == 1:
         rels = [float(x) for x in args.ladder.split(",")]
         line["ladder"] = _measure_ladder(args, rels, W, host, mu, dev, stream, T)
@@ -750,6 +820,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the backward measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-problem batched measurement")
+    ap.add_argument("--no-nonlinear", action="store_true", help="skip the E[f(AB)] adaptive-L measurement")
     ap.add_argument("--ladder", default="", help="comma-separated relative RMSE targets to run end to end "
                     "through mlmc_estimate (e.g. 3e-2; about a minute each at 3e-2)")
     ap.add_argument("--profile-case", choices=sorted(list(PROFILE_CASES) + ["adjoint", "batched_8_problems"]),
