@@ -49,7 +49,8 @@ class _Problem(ctypes.Structure):
                 ("M", ctypes.c_void_p), ("S", ctypes.c_void_p),
                 ("Mp", ctypes.c_void_p), ("Sp", ctypes.c_void_p),
                 ("seed_A", ctypes.c_uint32), ("seed_B", ctypes.c_uint32),
-                ("seed_idx", ctypes.c_uint32), ("problem_id", ctypes.c_uint32)]
+                ("seed_idx", ctypes.c_uint32), ("problem_id", ctypes.c_uint32),
+                ("q", ctypes.c_void_p), ("Q", ctypes.c_void_p)]
 
 
 class _Levels(ctypes.Structure):
@@ -82,6 +83,8 @@ def lib():
                 "orc_estimate": (I, [P, P, D, I64, D, I, P, P, P, P]),
                 "orc_adjoint": (None, [P, P, P, P, I, P, P, P, P]),
                 "orc_f": (D, [I, D]),
+                "orc_xi_optimal": (None, [P, P, P]),
+                "orc_index_xi": (I64, [U32, U32, I, U64, I64, I64, P, P]),
                 "orc_sample_f": (None, [P, P, I, U64, I, I, P, P, P, P]),
                 "orc_level_stats_f": (None, [P, P, I, U64, U64, I, I, P, P, P]),
                 "orc_estimate_f": (I, [P, P, D, I64, D, I, I, I, P, P, P, P, P]),
@@ -105,7 +108,8 @@ def _f64(a) -> np.ndarray:
 class Problem:
     """One E[AB] problem: A = M + S o Z (m x n), B = M' + S' o Z' (n x p), FP64 row-major."""
 
-    def __init__(self, M, S, Mp, Sp, seed_A=0, seed_B=1, seed_idx=2, problem_id=0):
+    def __init__(self, M, S, Mp, Sp, seed_A=0, seed_B=1, seed_idx=2, problem_id=0, sampling: str = "uniform"):
+        """sampling: "uniform" (xi^u, Eq. unique) or "optimal" (xi** of Thm 3.1)."""
         self.M, self.S, self.Mp, self.Sp = _f64(M), _f64(S), _f64(Mp), _f64(Sp)
         m, n = self.M.shape
         n2, p = self.Mp.shape
@@ -113,7 +117,19 @@ class Problem:
         self.m, self.n, self.p = m, n, p
         self.seeds = (seed_A, seed_B, seed_idx, problem_id)
         self._c = _Problem(m, n, p, _ptr(self.M), _ptr(self.S), _ptr(self.Mp), _ptr(self.Sp),
-                           seed_A, seed_B, seed_idx, problem_id)
+                           seed_A, seed_B, seed_idx, problem_id, None, None)
+        self.q = self.Q = None
+        if sampling == "optimal":
+            self.q, self.Q = np.zeros(n), np.zeros(n)
+            lib().orc_xi_optimal(ctypes.byref(self._c), _ptr(self.q), _ptr(self.Q))
+            self._c.q, self._c.Q = _ptr(self.q), _ptr(self.Q)
+        elif sampling != "uniform":
+            raise ValueError(sampling)
+
+    @property
+    def xi(self):
+        """The sampling probabilities (uniform: 1/n each)."""
+        return np.full(self.n, 1.0 / self.n) if self.Q is None else self.q / self.Q[-1]
 
     @property
     def ref(self):
@@ -160,6 +176,11 @@ def uniform(w: int) -> float:
 
 def normal(seed, problem_id, l, s, row, k) -> float:
     return lib().orc_normal(seed, problem_id, l, s, row, k)
+
+
+def index_xi(pr: "Problem", l, s, t) -> int:
+    """Index of slot t under the problem's xi** (inverse of its cumulative law)."""
+    return int(lib().orc_index_xi(pr.seeds[2], pr.seeds[3], l, s, t, pr.n, _ptr(pr.q), _ptr(pr.Q)))
 
 
 def index(seed_idx, problem_id, l, s, t, n) -> int:

@@ -121,6 +121,55 @@ int64_t orc_index(uint32_t seed_idx, uint32_t problem_id, int l, uint64_t s, int
     return (int64_t)(uint64_t)(prod >> 64);
 }
 
+void orc_xi_optimal(const orc_problem* pr, double* q, double* Q)
+{
+    int64_t m = pr->m, n = pr->n, p = pr->p;
+    double run = 0.0;
+    for (int64_t j = 0; j < n; ++j) {
+        double ea = 0.0, eb = 0.0;   /* E||A_{:,j}||^2 and E||B_{j,:}||^2: E[(M + S Z)^2] = M^2 + S^2 */
+        for (int64_t i = 0; i < m; ++i) {
+            double mm = pr->M[i * n + j] * pr->M[i * n + j];
+            double ss = pr->S[i * n + j] * pr->S[i * n + j];
+            ea += mm + ss;
+        }
+        for (int64_t k = 0; k < p; ++k) {
+            double mm = pr->Mp[j * p + k] * pr->Mp[j * p + k];
+            double ss = pr->Sp[j * p + k] * pr->Sp[j * p + k];
+            eb += mm + ss;
+        }
+        q[j] = sqrt(ea * eb);
+        run += q[j];
+        Q[j] = run;
+    }
+}
+
+int64_t orc_index_xi(uint32_t seed_idx, uint32_t problem_id, int l, uint64_t s, int64_t t, int64_t n,
+                     const double* q, const double* Q)
+{
+    uint32_t ctr[4] = { (uint32_t)(t >> 1), 0xFFFFFFFFu, (uint32_t)s, level_sample_word(l, s) };
+    uint32_t key[2] = { seed_idx, problem_id };
+    uint32_t w[4];
+    orc_philox4x32_10(ctr, key, w);
+    uint64_t word = (t & 1) ? (((uint64_t)w[3] << 32) | w[2]) : (((uint64_t)w[1] << 32) | w[0]);
+    double u = (double)(word >> 11) * 0x1p-53;
+    double x = u * Q[n - 1];
+    if (!(x < Q[n - 1])) {
+        int64_t j = n - 1;
+        while (j > 0 && !(q[j] > 0.0)) --j;
+        return j;
+    }
+    /* smallest j with x < Q[j] */
+    int64_t lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (x < Q[mid])
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return lo;
+}
+
 int64_t orc_cl(const orc_levels* lv, int l)
 {
     int64_t c = lv->c0;
@@ -207,6 +256,7 @@ typedef struct {
     double* Bsel;    /* c_l x p: row t is B[r_t, :] of this realisation */
     double* Aabs;    /* m x c_l: |M| + |S| |Z| of the same entries */
     double* Babs;    /* c_l x p: |M'| + |S'| |Z'| of the same entries */
+    double* g;       /* c_l: 1 under xi^u (the n is in the estimate's scale); Q[n-1] / q[r_t] = 1 / xi**_{r_t} */
 } realisation;
 
 static void quantise_e4m3_blocks(double* X, int64_t rows, int64_t cols, int along_rows)
@@ -238,14 +288,23 @@ static int draw_realisation(const orc_problem* pr, const orc_levels* lv, int l, 
     int64_t m = pr->m, n = pr->n, p = pr->p;
     int64_t c = orc_cl(lv, l);
     rz->c = c;
-    rz->r = NULL; rz->Asel = rz->Bsel = rz->Aabs = rz->Babs = NULL;
+    rz->r = NULL; rz->Asel = rz->Bsel = rz->Aabs = rz->Babs = rz->g = NULL;
     rz->r = (int64_t*)malloc(sizeof(int64_t) * (size_t)c);
+    rz->g = (double*)malloc(sizeof(double) * (size_t)c);
     rz->Asel = (double*)malloc(sizeof(double) * (size_t)(m * c));
     rz->Bsel = (double*)malloc(sizeof(double) * (size_t)(c * p));
     rz->Aabs = (double*)malloc(sizeof(double) * (size_t)(m * c));
     rz->Babs = (double*)malloc(sizeof(double) * (size_t)(c * p));
-    if (!rz->r || !rz->Asel || !rz->Bsel || !rz->Aabs || !rz->Babs) return -1;
-    for (int64_t t = 0; t < c; ++t) rz->r[t] = orc_index(pr->seed_idx, pr->problem_id, l, s, t, n);
+    if (!rz->r || !rz->g || !rz->Asel || !rz->Bsel || !rz->Aabs || !rz->Babs) return -1;
+    for (int64_t t = 0; t < c; ++t) {
+        if (pr->Q) {
+            rz->r[t] = orc_index_xi(pr->seed_idx, pr->problem_id, l, s, t, n, pr->q, pr->Q);
+            rz->g[t] = pr->Q[n - 1] / pr->q[rz->r[t]];
+        } else {
+            rz->r[t] = orc_index(pr->seed_idx, pr->problem_id, l, s, t, n);
+            rz->g[t] = 1.0;
+        }
+    }
     for (int64_t t = 0; t < c; ++t) {
         int64_t k = rz->r[t];
         for (int64_t i = 0; i < m; ++i) {
@@ -272,6 +331,7 @@ static int draw_realisation(const orc_problem* pr, const orc_levels* lv, int l, 
 static void free_realisation(realisation* rz)
 {
     free(rz->r);
+    free(rz->g);
     free(rz->Asel);
     free(rz->Bsel);
     free(rz->Aabs);
@@ -286,12 +346,13 @@ static void sampled_sum(int64_t m, int64_t p, const realisation* rz, int64_t fir
     int64_t c = rz->c;
     memset(out, 0, sizeof(double) * (size_t)(m * p));
     for (int64_t t = first; t < c; t += stride) {
+        double g = rz->g[t];
         for (int64_t i = 0; i < m; ++i) {
             double a = rz->Asel[i * c + t];
             for (int64_t j = 0; j < p; ++j) {
                 double b = rz->Bsel[t * p + j];
-                out[i * p + j] += a * b;
-                if (mag) mag[i * p + j] += fabs(scale) * rz->Aabs[i * c + t] * rz->Babs[t * p + j];
+                out[i * p + j] += a * (g * b);
+                if (mag) mag[i * p + j] += fabs(scale) * g * rz->Aabs[i * c + t] * rz->Babs[t * p + j];
             }
         }
     }
@@ -326,11 +387,13 @@ void orc_sample_f(const orc_problem* pr, const orc_levels* lv, int l, uint64_t s
     }
     int64_t c = rz.c;
     /* fine: all c_l draws, scale n / c_l */
-    sampled_sum(m, p, &rz, 0, 1, (double)n / (double)c, fine, mag);
+    /* under xi** the 1 / xi_{r_t} are per slot (in g) and the scale is 1 / c */
+    double nn = pr->Q ? 1.0 : (double)n;
+    sampled_sum(m, p, &rz, 0, 1, nn / (double)c, fine, mag);
     if (l > 0) {
         /* coarse: draws r_{jR}, j = 1..c_{l-1} (0-based slots jR - 1), scale n / c_{l-1} */
         int64_t cc = c / lv->R;
-        sampled_sum(m, p, &rz, lv->R - 1, lv->R, (double)n / (double)cc, coarse, mag);
+        sampled_sum(m, p, &rz, lv->R - 1, lv->R, nn / (double)cc, coarse, mag);
     }
     /* P_l - P_{l-1} with the targeted function applied to each estimate (Alg. 1); at l = 0
      * there is no coarse estimate */
@@ -521,7 +584,7 @@ static void adjoint_terms(const orc_problem* pr, const realisation* rz, int l, u
         for (int64_t i = 0; i < m; ++i) {
             double g = 0.0; /* (G b)_i */
             for (int64_t j = 0; j < p; ++j) g += G[i * p + j] * rz->Bsel[t * p + j];
-            g *= weight;
+            g *= weight * rz->g[t];
             double z = orc_normal(pr->seed_A, pr->problem_id, l, s, i, k);
             dM[i * n + k] += g;
             dS[i * n + k] += g * z;
@@ -529,7 +592,7 @@ static void adjoint_terms(const orc_problem* pr, const realisation* rz, int l, u
         for (int64_t j = 0; j < p; ++j) {
             double h = 0.0; /* (G^T a)_j */
             for (int64_t i = 0; i < m; ++i) h += G[i * p + j] * rz->Asel[i * c + t];
-            h *= weight;
+            h *= weight * rz->g[t];
             double z = orc_normal(pr->seed_B, pr->problem_id, l, s, j, k);
             dMp[k * p + j] += h;
             dSp[k * p + j] += h * z;
@@ -556,13 +619,14 @@ void orc_adjoint(const orc_problem* pr, const orc_levels* lv, const int64_t* Nl,
             }
             int64_t c = rz.c;
             /* + fine estimate */
-            adjoint_terms(pr, &rz, l, (uint64_t)s, 0, 1, inv_n * (double)n / (double)c, G,
+            double nn = pr->Q ? 1.0 : (double)n;   /* xi**: the 1 / xi are per slot */
+            adjoint_terms(pr, &rz, l, (uint64_t)s, 0, 1, inv_n * nn / (double)c, G,
                           dM, dS, dMp, dSp);
             if (l > 0) {
                 /* - coarse estimate */
                 int64_t cc = c / lv->R;
                 adjoint_terms(pr, &rz, l, (uint64_t)s, lv->R - 1, lv->R,
-                              -inv_n * (double)n / (double)cc, G, dM, dS, dMp, dSp);
+                              -inv_n * nn / (double)cc, G, dM, dS, dMp, dSp);
             }
             free_realisation(&rz);
         }

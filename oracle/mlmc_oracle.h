@@ -51,6 +51,12 @@ typedef struct {
     const double *M, *S;    /* m x n, row-major */
     const double *Mp, *Sp;  /* n x p, row-major */
     uint32_t seed_A, seed_B, seed_idx, problem_id;
+    /* Sampling law of the indices: NULL for the uniform xi^u (Eq. unique); else the
+     * variance-optimal xi** of Thm 3.1 (Eq. optproM) given by q[j] = sqrt(E||A_{:,j}||^2
+     * E||B_{j,:}||^2) and its running sums Q[j] = q[0] + ... + q[j] (orc_xi_optimal), so that
+     * xi**_j = q[j] / Q[n-1]. */
+    const double* q;
+    const double* Q;
 } orc_problem;
 
 /* Level schedule: c_l = c0 * R^l sampled indices at level l = 0..L. */
@@ -84,6 +90,17 @@ double orc_normal(uint32_t seed, uint32_t problem_id, int l, uint64_t s, int64_t
 /* Sampled index r_t in {0..n-1} of slot t (uniform xi, Eq. unique). */
 int64_t orc_index(uint32_t seed_idx, uint32_t problem_id, int l, uint64_t s, int64_t t, int64_t n);
 
+/* The weights of xi** (Thm 3.1, Eq. optproM) from the entry laws: E||A_{:,j}||^2 =
+ * sum_i (M_ij^2 + S_ij^2) and E||B_{j,:}||^2 = sum_k (M'_jk^2 + S'_jk^2), summed in index order;
+ * q[j] = sqrt of their product; Q[j] = q[0] + ... + q[j] in index order.  n entries each. */
+void orc_xi_optimal(const orc_problem* pr, double* q, double* Q);
+
+/* Sampled index of slot t under xi**: the slot's 64-bit word (as in orc_index) gives
+ * u = (word >> 11) 2^-53 in [0, 1); x = u Q[n-1] (one rounding); r_t is the smallest j with
+ * x < Q[j] (inverse of the cumulative law), or the last j with q[j] > 0 if there is none. */
+int64_t orc_index_xi(uint32_t seed_idx, uint32_t problem_id, int l, uint64_t s, int64_t t, int64_t n,
+                     const double* q, const double* Q);
+
 /* c_l = c0 R^l. */
 int64_t orc_cl(const orc_levels* lv, int l);
 
@@ -103,7 +120,8 @@ void orc_sketch(int64_t m, int64_t n, int64_t p, const double* A, const double* 
 
 /* One coupled sample of level l (Alg. 1, one loop iteration).  Outputs (each
  * m x p, row-major, any may be NULL except D):
- *   Pf  = fine estimate from all c_l draws,
+ *   Pf  = fine estimate from all c_l draws, (1/c_l) sum_t A[:,r_t] B[r_t,:] / xi_{r_t}
+ *         (Eq. matrixsketch: n/c_l times the plain sum under xi^u),
  *   Pc  = coarse estimate from the draws r_{jR}, j = 1..c_{l-1} (zero at l = 0),
  *   D   = Pf - Pc,
  *   mag = sum over the products that enter D of |weight| (|M_ik| + |S_ik Z_ik|)
