@@ -125,7 +125,20 @@ typedef struct {
                             topped up), stopping after the first round with at least three levels
                             whose finest mean satisfies ||Y_L||_F < (sqrt(R) + 1) eps / sqrt(2)
                             (Remark 3.5, Eq. L_num_bound_matrix), or at the problem's L */
+    int32_t sampling;    /* mlmc_sampling: the law of the sampled indices.  MLMC_XI_OPTIMAL needs
+                            MLMC_FP64 or MLMC_FP32 and has no mlmc_backward */
 } mlmc_options;
+
+/* Index laws (mlmc_options.sampling). */
+typedef enum {
+    MLMC_XI_UNIFORM = 0, /* xi_j = 1/n (Eq. unique); index floor(word64 n / 2^64) */
+    MLMC_XI_OPTIMAL = 1  /* xi**_j proportional to q_j = sqrt(E||A_{:,j}||^2 E||B_{j,:}||^2), E[(M + S Z)^2]
+                            = M^2 + S^2 (Thm 3.1, Eq. optproM).  mlmc_plan computes q_j (sums over i and
+                            k in index order, FP64) and Q_j = q_0 + ... + q_j (one sequential pass, so
+                            plan time grows with n).  Slot t draws u = (word64 >> 11) 2^-53, x = u Q_{n-1}
+                            and takes the smallest j with x < Q_j; its weight is Q_{n-1} / (c q_j) in the
+                            fine estimate (and Q_{n-1} / (c_{l-1} q_j) in the coarse one) */
+} mlmc_sampling;
 
 /* Targeted functions f (mlmc_options.f). */
 typedef enum {

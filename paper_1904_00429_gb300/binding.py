@@ -26,6 +26,7 @@ STATUS = {0: "MLMC_OK", 1: "MLMC_ERR_INVALID_ARG", 2: "MLMC_ERR_CUDA", 3: "MLMC_
           4: "MLMC_ERR_TIMEOUT", 5: "MLMC_ERR_NUMERIC", 6: "MLMC_ERR_UNSUPPORTED", 7: "MLMC_ERR_STATE"}
 PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2, "fp8": 3, "fp8_e4m3": 3}
 FUNCTION = {"identity": 0, "abs_step": 1}   # mlmc_function
+SAMPLING = {"uniform": 0, "optimal": 1}     # mlmc_sampling
 DTYPE = {torch.float64: 0, torch.float32: 1}
 
 
@@ -48,7 +49,7 @@ class Options(ctypes.Structure):
     _fields_ = [("c0", ctypes.c_int32), ("ratio", ctypes.c_int32), ("L", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("pilot_n", ctypes.c_int64), ("nl_scale", ctypes.c_double),
                 ("timeout_ns", ctypes.c_int64), ("tile_override", ctypes.c_int32), ("adjoint_batch_log2", ctypes.c_int32),
-                ("f", ctypes.c_int32), ("adaptive_L", ctypes.c_int32)]
+                ("f", ctypes.c_int32), ("adaptive_L", ctypes.c_int32), ("sampling", ctypes.c_int32)]
 
 
 class Range(ctypes.Structure):
@@ -156,7 +157,7 @@ class Plan:
     def __init__(self, problems: Sequence[ProblemSpec], *, c0: int, L: int, ratio: int = 2,
                  precision: str = "fp32", pilot_n: int = 256, nl_scale: float = 1.0,
                  timeout_ns: int = 0, tile_override: int = 0, adjoint_batch_log2: int = 0,
-                 f: str = "identity", adaptive_L: bool = False, stream=None):
+                 f: str = "identity", adaptive_L: bool = False, sampling: str = "uniform", stream=None):
         self.problems = list(problems)
         self.device = self.problems[0].M.device
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -181,7 +182,7 @@ class Plan:
             self.shapes.append((m, n, p))
             self.levels.append(pr.L if pr.L >= 0 else L)
         self.options = Options(c0, ratio, L, PRECISION[precision], pilot_n, nl_scale, timeout_ns, tile_override,
-                               adjoint_batch_log2, FUNCTION[f], int(bool(adaptive_L)))
+                               adjoint_batch_log2, FUNCTION[f], int(bool(adaptive_L)), SAMPLING[sampling])
         self.precision = precision
         self.c0, self.ratio, self.L = c0, ratio, L
         self.pilot_n = pilot_n

@@ -74,6 +74,9 @@ struct ProblemState {
     TcMaps batch_maps{};    // ... and for the plan's batched tile
     int32_t batch_maps_tile = 0;
     int max_chunks = 1;
+    double* xi_q = nullptr;   // xi** (MLMC_XI_OPTIMAL): weights q_k and their running sums Q_k (n each)
+    double* xi_Q = nullptr;
+    double xi_Qtot = 0.0;
 };
 
 struct mlmc_plan_s {
@@ -220,6 +223,10 @@ mlmc_status validate(const mlmc_problem* problems, int32_t nprob, const mlmc_opt
     if (o->f != MLMC_F_IDENTITY && o->precision != MLMC_FP64 && o->precision != MLMC_FP32)
         return fail(MLMC_ERR_UNSUPPORTED, "a targeted function other than the identity needs FP64 or FP32");
     if (o->adaptive_L != 0 && o->adaptive_L != 1) return fail(MLMC_ERR_INVALID_ARG, "adaptive_L must be 0 or 1");
+    if (o->sampling != MLMC_XI_UNIFORM && o->sampling != MLMC_XI_OPTIMAL)
+        return fail(MLMC_ERR_INVALID_ARG, "unknown sampling law %d", o->sampling);
+    if (o->sampling != MLMC_XI_UNIFORM && o->precision != MLMC_FP64 && o->precision != MLMC_FP32)
+        return fail(MLMC_ERR_UNSUPPORTED, "the xi** sampling law needs FP64 or FP32");
     for (int32_t q = 0; q < nprob; ++q) {
         const mlmc_problem& pr = problems[q];
         const int L = pr.L >= 0 ? pr.L : o->L;
@@ -247,6 +254,8 @@ void free_plan(mlmc_plan_t* plan)
         cudaFree(ps.PAB);
         cudaFree(ps.sum);
         cudaFree(ps.sumsq);
+        cudaFree(ps.xi_q);
+        cudaFree(ps.xi_Q);
     }
     cudaFree(plan->partial_sum);
     cudaFree(plan->partial_q);
@@ -321,6 +330,9 @@ mlmc_status run_level(mlmc_plan_t* plan, ProblemState& ps, int level, uint64_t s
     prm.tiles_p = ps.tiles_p;
     prm.partial_sum = plan->partial_sum;
     prm.partial_q = plan->partial_q;
+    prm.xi_q = ps.xi_q;
+    prm.xi_Q = ps.xi_Q;
+    prm.xi_Qtot = ps.xi_Qtot;
     const uint64_t s_end = s0 + count;
     const uint64_t ch = uint64_t(chunk_samples(c));
     prm.chunk = int(ch);
@@ -825,6 +837,27 @@ mlmc_status mlmc_plan(const mlmc_problem* problems, int32_t nprob, const mlmc_op
         }
         if (tensor_core_precision(options->precision))
             tc_encode_maps(&ps.maps, ps.PAB, ps.n, ps.ld, tc_stage_width_a(ps.tile), tc_stage_width_b(ps.tile));
+        if (options->sampling == MLMC_XI_OPTIMAL) {
+            // xi** (Thm 3.1) from the laid-out parameters; its total must be a positive number
+            if (cudaMalloc(reinterpret_cast<void**>(&ps.xi_q), sizeof(double) * size_t(ps.n)) != cudaSuccess ||
+                cudaMalloc(reinterpret_cast<void**>(&ps.xi_Q), sizeof(double) * size_t(ps.n)) != cudaSuccess)
+                return oom("xi** tables");
+            err = launch_xi_optimal(ps.PAB, plan->f64, ps.ld, ps.m, ps.m_pad, ps.n, ps.p, ps.xi_q, ps.xi_Q, plan->stream);
+            if (err == cudaSuccess)
+                err = cudaMemcpyAsync(&ps.xi_Qtot, ps.xi_Q + (ps.n - 1), sizeof(double), cudaMemcpyDeviceToHost,
+                                      plan->stream);
+            if (err == cudaSuccess) err = cudaStreamSynchronize(plan->stream);
+            if (err != cudaSuccess) {
+                free_plan(plan);
+                delete plan;
+                return fail(MLMC_ERR_CUDA, "xi** tables: %s", cudaGetErrorString(err));
+            }
+            if (!(ps.xi_Qtot > 0.0) || !std::isfinite(ps.xi_Qtot)) {
+                free_plan(plan);
+                delete plan;
+                return fail(MLMC_ERR_NUMERIC, "xi**: the column weights of a problem sum to %g", ps.xi_Qtot);
+            }
+        }
     }
     if (cudaMalloc(&plan->partial_sum, max_partial) != cudaSuccess) return oom("chunk partials");
     if (cudaMalloc(reinterpret_cast<void**>(&plan->partial_q), sizeof(double) * max_q) != cudaSuccess)
@@ -1368,6 +1401,8 @@ mlmc_status mlmc_backward(mlmc_plan_t* plan, const double* G_dev, void* const* d
     if (!G_dev || !dM_dev || !dS_dev || !dMp_dev || !dSp_dev) return fail(MLMC_ERR_INVALID_ARG, "null argument");
     if (plan->opt.f != MLMC_F_IDENTITY)
         return fail(MLMC_ERR_UNSUPPORTED, "mlmc_backward: the replay is the adjoint of the linear estimator (f = x)");
+    if (plan->opt.sampling != MLMC_XI_UNIFORM)
+        return fail(MLMC_ERR_UNSUPPORTED, "mlmc_backward: the replay weights slots uniformly (xi^u)");
     if (plan->opt.precision == MLMC_FP8_E4M3)
         return fail(MLMC_ERR_UNSUPPORTED, "mlmc_backward: the E4M3 block scales couple the slots of a sample; "
                     "use an FP32 or BF16 plan for gradients");
@@ -1419,8 +1454,10 @@ mlmc_status mlmc_debug_indices(mlmc_plan_t* plan, int32_t prob, int32_t level, u
     if (t0 < 0 || count < 0 || (count > 0 && !idx_dev)) return fail(MLMC_ERR_INVALID_ARG, "bad slot range");
     DeviceGuard g(plan->device);
     ProblemState& ps = plan->probs[size_t(prob)];
-    cudaError_t err = launch_debug_indices(key(ps.desc.seed_idx, ps.desc.problem_id), level, sample, ps.n, t0, count,
-                                           idx_dev, plan->stream);
+    cudaError_t err = ps.xi_Q ? launch_debug_indices_xi(key(ps.desc.seed_idx, ps.desc.problem_id), level, sample, ps.n, t0,
+                                                        count, ps.xi_Q, ps.xi_q, idx_dev, plan->stream)
+                              : launch_debug_indices(key(ps.desc.seed_idx, ps.desc.problem_id), level, sample, ps.n, t0,
+                                                     count, idx_dev, plan->stream);
     return check_cuda(plan, err, "debug_indices");
 }
 

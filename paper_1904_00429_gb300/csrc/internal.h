@@ -57,6 +57,9 @@ struct LevelParams {
     int tiles_m, tiles_p;
     void* partial_sum;    // [nchunks][m][p] of T
     double* partial_q;    // [nchunks][tiles_m * tiles_p]
+    const double* xi_q;   // xi** (CUDA-core kernel): weights q (n), or null for the uniform law
+    const double* xi_Q;   // their running sums (n)
+    double xi_Qtot;       // Q[n-1]
     TcMaps maps;          // tensor-core kernel only
 };
 
@@ -208,6 +211,14 @@ cudaError_t adjoint_write_B(const double* src, int64_t n, int64_t p, void* dst, 
 // M + S z, bfloat16) at full occupancy: the ceiling of the reduced-precision level kernels'
 // entry generation.  Synchronises `st`.
 cudaError_t measure_generation_rate(cudaStream_t st, int num_sms, double* entries_per_s);
+
+// xi** of Thm 3.1 from the plan's parameter layout (rows k of PA / PB hold the (M, S) pairs of
+// column k of A / row k of B): q[k] = sqrt(sum_i (M^2 + S^2) * sum_j (M'^2 + S'^2)) in index order
+// without contraction, Q[k] = q[0] + ... + q[k] in one sequential pass.
+cudaError_t launch_xi_optimal(const void* PAB, bool f64, int64_t ld, int64_t m, int64_t m_pad, int64_t n,
+                              int64_t p, double* q, double* Q, cudaStream_t st);
+cudaError_t launch_debug_indices_xi(uint2 keyI, int l, uint64_t s, int64_t n, int64_t t0, int64_t count,
+                                    const double* Q, const double* q, int64_t* out, cudaStream_t st);
 
 // Set the thread-local message returned by mlmc_last_error().
 mlmc_status report_error(mlmc_status st, const char* msg);

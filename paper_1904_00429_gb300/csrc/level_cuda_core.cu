@@ -66,7 +66,7 @@ __device__ __forceinline__ T targeted(T x)
     return x;
 }
 
-template <typename T, int TM, int TP, int TK, int RM, int RP, int F>
+template <typename T, int TM, int TP, int TK, int RM, int RP, int F, bool XI>
 __global__ void __launch_bounds__((TM / RM) * (TP / RP))
 level_cuda_core_kernel(const LevelParams prm)
 {
@@ -78,6 +78,7 @@ level_cuda_core_kernel(const LevelParams prm)
     __shared__ __align__(16) T Bs[TK][TP];
     __shared__ int idx_s[TK];
     __shared__ T w_s[TK];   // F = 0: the slot's weight; F != 0: 1 on coarse slots, else 0
+    __shared__ T g_s[TK];   // F != 0 under xi**: the slot's 1 / xi_{r_t} (folded into B)
     __shared__ double red_s[NT / 32];
 
     const int tid = threadIdx.x;
@@ -96,6 +97,12 @@ level_cuda_core_kernel(const LevelParams prm)
     const T wf = static_cast<T>(prm.w_fine);
     const T wc = static_cast<T>(prm.w_coarse);
     const T wcn = static_cast<T>(prm.w_fine - prm.w_coarse);   // n / c_{l-1}
+    // xi** (Thm 3.1): per-slot weights 1 / xi_{r_t} = Q[n-1] / q[r_t], estimates scaled by 1 / c
+    constexpr bool xi = XI;   // prm.xi_Q is set
+    const double inv_c = 1.0 / static_cast<double>(prm.c);
+    const double inv_cc = prm.l > 0 ? 1.0 / static_cast<double>(prm.c / prm.R) : 0.0;
+    const T sf = xi ? static_cast<T>(inv_c) : wf;     // F != 0: scale of the fine estimate
+    const T sc = xi ? static_cast<T>(inv_cc) : wcn;   // and of the coarse one
 
     T sum[RM][RP];
 #pragma unroll
@@ -120,17 +127,32 @@ level_cuda_core_kernel(const LevelParams prm)
                 const int t = k0 + 2 * h;
                 if (t < prm.c) {
                     int64_t r0, r1;
-                    index_pair(prm.keyI, lsw, s_lo, t >> 1, static_cast<uint64_t>(prm.n), r0, r1);
+                    double g[2] = {1.0, 1.0};
+                    if constexpr (xi) {
+                        uint64_t w0, w1;
+                        index_words(prm.keyI, lsw, s_lo, t >> 1, w0, w1);
+                        r0 = index_from_cdf(w0, prm.xi_Q, prm.xi_q, prm.n);
+                        r1 = index_from_cdf(w1, prm.xi_Q, prm.xi_q, prm.n);
+                        g[0] = __ddiv_rn(prm.xi_Qtot, prm.xi_q[r0]);
+                        g[1] = __ddiv_rn(prm.xi_Qtot, prm.xi_q[r1]);
+                    } else {
+                        index_pair(prm.keyI, lsw, s_lo, t >> 1, static_cast<uint64_t>(prm.n), r0, r1);
+                    }
 #pragma unroll
                     for (int e = 0; e < 2; ++e) {
                         const int te = t + e;
                         const bool valid = te < prm.c;
                         const bool coarse = prm.l > 0 && (te % prm.R) == prm.R - 1;
                         idx_s[2 * h + e] = valid ? static_cast<int>(e ? r1 : r0) : -1;
-                        if constexpr (F == 0)
-                            w_s[2 * h + e] = valid ? (coarse ? wc : wf) : T(0);
-                        else
+                        if constexpr (F == 0) {
+                            if constexpr (xi)
+                                w_s[2 * h + e] = valid ? static_cast<T>(g[e] * (coarse ? inv_c - inv_cc : inv_c)) : T(0);
+                            else
+                                w_s[2 * h + e] = valid ? (coarse ? wc : wf) : T(0);
+                        } else {
                             w_s[2 * h + e] = (valid && coarse) ? T(1) : T(0);
+                            g_s[2 * h + e] = valid ? static_cast<T>(g[e]) : T(0);
+                        }
                     }
                 } else {
                     idx_s[2 * h] = idx_s[2 * h + 1] = -1;
@@ -173,7 +195,8 @@ level_cuda_core_kernel(const LevelParams prm)
                     T z[4];
                     Normals<T>::four(w, z);
                     const Pair4<T> ms = Pair4<T>::load(PB + static_cast<int64_t>(k) * prm.ldPB + 2 * j);
-                    const T wt = F == 0 ? w_s[tt] : T(1);   // F != 0: weights applied per estimate
+                    // F != 0: the per-estimate scales are applied at the end; xi** folds 1 / xi here
+                    const T wt = F == 0 ? w_s[tt] : (xi ? g_s[tt] : T(1));
 #pragma unroll
                     for (int r = 0; r < 4; ++r) b[r] = wt * fma(ms.v[2 * r + 1], z[r], ms.v[2 * r]);
                 }
@@ -212,8 +235,8 @@ level_cuda_core_kernel(const LevelParams prm)
             for (int i = 0; i < RM; ++i)
 #pragma unroll
                 for (int j = 0; j < RP; ++j)
-                    acc[i][j] = prm.l > 0 ? targeted<F>(wf * acc[i][j]) - targeted<F>(wcn * accc[i][j])
-                                          : targeted<F>(wf * acc[i][j]);
+                    acc[i][j] = prm.l > 0 ? targeted<F>(sf * acc[i][j]) - targeted<F>(sc * accc[i][j])
+                                          : targeted<F>(sf * acc[i][j]);
         }
         // per-sample statistics: running sum of D and of ||D||_F^2
         T qs = T(0);
@@ -256,9 +279,12 @@ cudaError_t launch(const LevelParams& prm, int f, cudaStream_t st)
 {
     constexpr int NT = (TM / RM) * (TP / RP);
     dim3 grid(prm.tiles_m * prm.tiles_p, prm.nchunks);
-    switch (f) {
-    case MLMC_F_IDENTITY: level_cuda_core_kernel<T, TM, TP, TK, RM, RP, 0><<<grid, NT, 0, st>>>(prm); break;
-    case MLMC_F_ABS_STEP: level_cuda_core_kernel<T, TM, TP, TK, RM, RP, 1><<<grid, NT, 0, st>>>(prm); break;
+    const bool xi = prm.xi_Q != nullptr;
+    switch (f * 2 + (xi ? 1 : 0)) {
+    case 0: level_cuda_core_kernel<T, TM, TP, TK, RM, RP, 0, false><<<grid, NT, 0, st>>>(prm); break;
+    case 1: level_cuda_core_kernel<T, TM, TP, TK, RM, RP, 0, true><<<grid, NT, 0, st>>>(prm); break;
+    case 2: level_cuda_core_kernel<T, TM, TP, TK, RM, RP, 1, false><<<grid, NT, 0, st>>>(prm); break;
+    case 3: level_cuda_core_kernel<T, TM, TP, TK, RM, RP, 1, true><<<grid, NT, 0, st>>>(prm); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

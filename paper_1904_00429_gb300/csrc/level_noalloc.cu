@@ -258,6 +258,8 @@ extern "C" mlmc_status mlmc_level_stats_noalloc(const mlmc_problem* problem, con
         return noalloc_fail(MLMC_ERR_UNSUPPORTED, "parameter dtype must match the precision (F64/FP64, F32/FP32)");
     if (o.c0 < 1 || o.ratio < 2) return noalloc_fail(MLMC_ERR_INVALID_ARG, "c0 must be >= 1 and ratio >= 2");
     if (o.f != MLMC_F_IDENTITY) return noalloc_fail(MLMC_ERR_UNSUPPORTED, "the no-alloc entry point evaluates f = x only");
+    if (o.sampling != MLMC_XI_UNIFORM)
+        return noalloc_fail(MLMC_ERR_UNSUPPORTED, "the no-alloc entry point draws indices uniformly only");
     if (pr.m < 1 || pr.p < 1 || pr.m > 65536 || pr.p > 65536 || pr.n < 1 || pr.n >= (int64_t(1) << 31))
         return noalloc_fail(MLMC_ERR_INVALID_ARG, "m, p must be in [1, 65536] and n in [1, 2^31)");
     if (pr.ldA < pr.n || pr.ldB < pr.p) return noalloc_fail(MLMC_ERR_INVALID_ARG, "leading dimension too small");

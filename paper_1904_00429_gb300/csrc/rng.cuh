@@ -91,6 +91,39 @@ __device__ __forceinline__ void index_pair(uint2 key, uint32_t lsw, uint32_t s_l
     r_odd = static_cast<int64_t>(__umul64hi(odd, n));
 }
 
+// Index r_t for one slot's 64-bit word under a tabulated law (xi** of Thm 3.1): u = (word >> 11)
+// 2^-53 in [0, 1), x = u Q[n-1], r = the smallest j with x < Q[j] (Q the running sums of the
+// weights q), or the last j with q[j] > 0 when rounding put x at Q[n-1].  Binary search over Q.
+__device__ __forceinline__ int64_t index_from_cdf(uint64_t word, const double* __restrict__ Q,
+                                                  const double* __restrict__ q, int64_t n)
+{
+    const double Qtot = Q[n - 1];
+    const double x = __dmul_rn(__ull2double_rn(word >> 11) * 0x1p-53, Qtot);
+    if (!(x < Qtot)) {
+        int64_t j = n - 1;
+        while (j > 0 && !(q[j] > 0.0)) --j;
+        return j;
+    }
+    int64_t lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (x < Q[mid])
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return lo;
+}
+
+// The two 64-bit index words of slot pair (t & ~1, t | 1) of one sample (even slot first).
+__device__ __forceinline__ void index_words(uint2 key, uint32_t lsw, uint32_t s_lo, int64_t t_pair, uint64_t& even,
+                                            uint64_t& odd)
+{
+    const uint4 w = philox4x32_10(make_uint4(static_cast<uint32_t>(t_pair), kIndexStream, s_lo, lsw), key);
+    even = (static_cast<uint64_t>(w.y) << 32) | w.x;
+    odd = (static_cast<uint64_t>(w.w) << 32) | w.z;
+}
+
 // ---- FP64 normals ---------------------------------------------------------
 
 __device__ __forceinline__ double uniform_f64(uint32_t w)

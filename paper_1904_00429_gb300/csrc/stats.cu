@@ -205,6 +205,49 @@ __global__ void debug_indices_kernel(uint2 keyI, int l, uint64_t s, int64_t n, i
     out[e] = (t & 1) ? r1 : r0;
 }
 
+__global__ void debug_indices_xi_kernel(uint2 keyI, int l, uint64_t s, int64_t n, int64_t t0, int64_t count,
+                                        const double* Q, const double* q, int64_t* out)
+{
+    const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= count) return;
+    const int64_t t = t0 + e;
+    uint64_t w0, w1;
+    index_words(keyI, level_sample_word(l, s), static_cast<uint32_t>(s), t >> 1, w0, w1);
+    out[e] = index_from_cdf((t & 1) ? w1 : w0, Q, q, n);
+}
+
+// q[k] of xi**: one thread per k, sums in index order with separate roundings (no contraction).
+template <typename T>
+__global__ void xi_weights_kernel(const T* __restrict__ PAB, int64_t ld, int64_t m, int64_t m_pad, int64_t n,
+                                  int64_t p, double* q)
+{
+    const int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const T* row = PAB + k * ld;
+    double ea = 0.0, eb = 0.0;
+    for (int64_t i = 0; i < m; ++i) {
+        const double mv = static_cast<double>(row[2 * i]), sv = static_cast<double>(row[2 * i + 1]);
+        ea = __dadd_rn(ea, __dadd_rn(__dmul_rn(mv, mv), __dmul_rn(sv, sv)));
+    }
+    const T* rb = row + 2 * m_pad;
+    for (int64_t j = 0; j < p; ++j) {
+        const double mv = static_cast<double>(rb[2 * j]), sv = static_cast<double>(rb[2 * j + 1]);
+        eb = __dadd_rn(eb, __dadd_rn(__dmul_rn(mv, mv), __dmul_rn(sv, sv)));
+    }
+    q[k] = __dsqrt_rn(__dmul_rn(ea, eb));
+}
+
+// Q[k] = q[0] + ... + q[k]: one sequential pass (the order fixes every rounding).
+__global__ void xi_scan_kernel(const double* __restrict__ q, int64_t n, double* Q)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    double run = 0.0;
+    for (int64_t k = 0; k < n; ++k) {
+        run = __dadd_rn(run, q[k]);
+        Q[k] = run;
+    }
+}
+
 template <typename T>
 __global__ void debug_normals_kernel(uint2 key, int l, uint64_t s, int64_t k, int64_t row0, int64_t count,
                                      double* out)
@@ -309,6 +352,29 @@ cudaError_t launch_debug_indices(uint2 keyI, int l, uint64_t s, int64_t n, int64
 {
     if (count <= 0) return cudaSuccess;
     debug_indices_kernel<<<blocks_for(count, 256), 256, 0, st>>>(keyI, l, s, n, t0, count, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_debug_indices_xi(uint2 keyI, int l, uint64_t s, int64_t n, int64_t t0, int64_t count,
+                                    const double* Q, const double* q, int64_t* out, cudaStream_t st)
+{
+    if (count <= 0) return cudaSuccess;
+    debug_indices_xi_kernel<<<static_cast<unsigned>((count + 255) / 256), 256, 0, st>>>(keyI, l, s, n, t0, count, Q, q,
+                                                                                         out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xi_optimal(const void* PAB, bool f64, int64_t ld, int64_t m, int64_t m_pad, int64_t n,
+                              int64_t p, double* q, double* Q, cudaStream_t st)
+{
+    const unsigned blocks = static_cast<unsigned>((n + 255) / 256);
+    if (f64)
+        xi_weights_kernel<double><<<blocks, 256, 0, st>>>(static_cast<const double*>(PAB), ld, m, m_pad, n, p, q);
+    else
+        xi_weights_kernel<float><<<blocks, 256, 0, st>>>(static_cast<const float*>(PAB), ld, m, m_pad, n, p, q);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    xi_scan_kernel<<<1, 1, 0, st>>>(q, n, Q);
     return cudaGetLastError();
 }
 

@@ -52,7 +52,7 @@ def test_last_error_is_empty_before_any_call():
 def test_struct_layouts_match_the_header():
     # int64 m,n,p; 2 ptr; int64; 2 ptr; int64; int32 x2; uint32 x4 -> 96 bytes on LP64
     assert ctypes.sizeof(binding.Problem) == 3 * 8 + 2 * 8 + 8 + 2 * 8 + 8 + 2 * 4 + 4 * 4
-    assert ctypes.sizeof(binding.Options) == 4 * 4 + 8 + 8 + 8 + 4 + 4 + 4 + 4
+    assert ctypes.sizeof(binding.Options) == 4 * 4 + 8 + 8 + 8 + 4 + 4 + 4 + 4 + 4 + 4   # tail padding to 8
     assert ctypes.sizeof(binding.Report) == 8 + 32 * 8 * 4 + 3 * 8
 
 
