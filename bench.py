@@ -574,6 +574,55 @@ def _measure_nonlinear(args, dev, stream):
             "mc_over_mlmc": t_mc / t_mlmc}
 
 
+XI = dict(name="sparse_rows_64x4096x64", m=64, n=4096, p=64, c0=16, R=2, L=5, pilot=256, rel_rmse=1e-2,
+          precision="fp32", row_density=0.2)
+
+
+def _xi_params():
+    """The structure of the paper's matrix example (Sec. 5.2: entries of A growing with the
+    column index, B with Bernoulli(0.2) support) in this model's laws: the precision workload's
+    M ~ U[-1,1], S ~ U[0.1,1] (seeds 0 and 1), column k of M and S scaled by 4 (k + 1) / n, and
+    each row of M' and S' kept with probability 0.2 (Philox-seeded draw, seed 2), else zero."""
+    from paper_1904_00429_gb300.inputs import make_params
+    X = XI
+    pp = make_params(X["m"], X["n"], X["p"], seed_A=0, seed_B=1, dtype=np.float64)
+    col = 4.0 * (np.arange(X["n"]) + 1.0) / X["n"]
+    keep = (np.random.Generator(np.random.Philox(1002)).uniform(size=X["n"]) < X["row_density"])[:, None]
+    return [x.astype(np.float32) for x in (pp.M * col, pp.S * col, pp.Mp * keep, pp.Sp * keep)]
+
+
+def _measure_xi(args, dev, stream):
+    """MLMC of E[AB] under the uniform law xi^u and the variance-optimal xi** (Thm 3.1) on the
+    same problem and target, each end to end through mlmc_estimate (pilot, allocation, top-up)."""
+    import torch
+
+    from paper_1904_00429_gb300 import binding
+
+    X = XI
+    params = _xi_params()
+    ts = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in params]
+    mu = params[0].astype(np.float64) @ params[2].astype(np.float64)
+    eps = X["rel_rmse"] * float(np.linalg.norm(mu))
+    out = {}
+    for law in ("uniform", "optimal"):
+        spec = binding.ProblemSpec(*ts, seed_A=3, seed_B=4, seed_idx=5, problem_id=0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with binding.Plan([spec], c0=X["c0"], L=X["L"], ratio=X["R"], precision=X["precision"], pilot_n=X["pilot"],
+                          sampling=law, stream=stream) as plan:
+            (Y,), (rep,) = plan.estimate([eps])
+            torch.cuda.synchronize()
+            t = time.perf_counter() - t0
+        err = float(np.linalg.norm(Y.cpu().numpy() - mu))
+        out[law] = {"value": t, "N_l": rep["N"], "V_l": rep["V"], "outer_products": rep["outer_products"],
+                    "rmse_pred": rep["rmse_pred"], "error": err,
+                    "timing": "end to end through mlmc_estimate, plan creation included"}
+    return {"workload": X["name"], "metric": "time to rel. RMSE 1e-2 for E[AB] under xi^u and xi**", "unit": "s",
+            "eps_abs": eps, "precision": X["precision"], "uniform": out["uniform"], "optimal": out["optimal"],
+            "uniform_over_optimal": out["uniform"]["value"] / out["optimal"]["value"],
+            "V0_uniform_over_optimal": out["uniform"]["V_l"][0] / out["optimal"]["V_l"][0]}
+
+
 BATCHED = dict(name="batched_64_problems", count=64, shape_seed=7, c0=32, R=2, pilot=256, rel_rmse=1e-3,
                step_outer=4.0e8, precision="bf16")
 
@@ -733,6 +782,8 @@ def run_ours(args):
         line["batched"] = _measure_batched(args, dev, stream, peaks, peak_kind)
     if not args.no_nonlinear and world == 1:
         line["nonlinear"] = _measure_nonlinear(args, dev, stream)
+    if not args.no_xi and world == 1:
+        line["xi"] = _measure_xi(args, dev, stream)
     if args.ladder and world == 1:
         rels = [float(x) for x in args.ladder.split(",")]
         line["ladder"] = _measure_ladder(args, rels, W, host, mu, dev, stream, T)
@@ -821,6 +872,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the backward measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-problem batched measurement")
     ap.add_argument("--no-nonlinear", action="store_true", help="skip the E[f(AB)] adaptive-L measurement")
+    ap.add_argument("--no-xi", action="store_true", help="skip the xi^u / xi** comparison")
     ap.add_argument("--ladder", default="", help="comma-separated relative RMSE targets to run end to end "
                     "through mlmc_estimate (e.g. 3e-2; about a minute each at 3e-2)")
     ap.add_argument("--profile-case", choices=sorted(list(PROFILE_CASES) + ["adjoint", "batched_8_problems"]),

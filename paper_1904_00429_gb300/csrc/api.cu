@@ -76,6 +76,7 @@ struct ProblemState {
     int max_chunks = 1;
     double* xi_q = nullptr;   // xi** (MLMC_XI_OPTIMAL): weights q_k and their running sums Q_k (n each)
     double* xi_Q = nullptr;
+    int* xi_G = nullptr;      // guide table of Q (n buckets)
     double xi_Qtot = 0.0;
 };
 
@@ -256,6 +257,7 @@ void free_plan(mlmc_plan_t* plan)
         cudaFree(ps.sumsq);
         cudaFree(ps.xi_q);
         cudaFree(ps.xi_Q);
+        cudaFree(ps.xi_G);
     }
     cudaFree(plan->partial_sum);
     cudaFree(plan->partial_q);
@@ -333,6 +335,7 @@ mlmc_status run_level(mlmc_plan_t* plan, ProblemState& ps, int level, uint64_t s
     prm.xi_q = ps.xi_q;
     prm.xi_Q = ps.xi_Q;
     prm.xi_Qtot = ps.xi_Qtot;
+    prm.xi_G = ps.xi_G;
     const uint64_t s_end = s0 + count;
     const uint64_t ch = uint64_t(chunk_samples(c));
     prm.chunk = int(ch);
@@ -840,9 +843,11 @@ mlmc_status mlmc_plan(const mlmc_problem* problems, int32_t nprob, const mlmc_op
         if (options->sampling == MLMC_XI_OPTIMAL) {
             // xi** (Thm 3.1) from the laid-out parameters; its total must be a positive number
             if (cudaMalloc(reinterpret_cast<void**>(&ps.xi_q), sizeof(double) * size_t(ps.n)) != cudaSuccess ||
-                cudaMalloc(reinterpret_cast<void**>(&ps.xi_Q), sizeof(double) * size_t(ps.n)) != cudaSuccess)
+                cudaMalloc(reinterpret_cast<void**>(&ps.xi_Q), sizeof(double) * size_t(ps.n)) != cudaSuccess ||
+                cudaMalloc(reinterpret_cast<void**>(&ps.xi_G), sizeof(int) * size_t(ps.n)) != cudaSuccess)
                 return oom("xi** tables");
-            err = launch_xi_optimal(ps.PAB, plan->f64, ps.ld, ps.m, ps.m_pad, ps.n, ps.p, ps.xi_q, ps.xi_Q, plan->stream);
+            err = launch_xi_optimal(ps.PAB, plan->f64, ps.ld, ps.m, ps.m_pad, ps.n, ps.p, ps.xi_q, ps.xi_Q, ps.xi_G,
+                                    plan->stream);
             if (err == cudaSuccess)
                 err = cudaMemcpyAsync(&ps.xi_Qtot, ps.xi_Q + (ps.n - 1), sizeof(double), cudaMemcpyDeviceToHost,
                                       plan->stream);
@@ -1455,7 +1460,7 @@ mlmc_status mlmc_debug_indices(mlmc_plan_t* plan, int32_t prob, int32_t level, u
     DeviceGuard g(plan->device);
     ProblemState& ps = plan->probs[size_t(prob)];
     cudaError_t err = ps.xi_Q ? launch_debug_indices_xi(key(ps.desc.seed_idx, ps.desc.problem_id), level, sample, ps.n, t0,
-                                                        count, ps.xi_Q, ps.xi_q, idx_dev, plan->stream)
+                                                        count, ps.xi_Q, ps.xi_q, ps.xi_G, idx_dev, plan->stream)
                               : launch_debug_indices(key(ps.desc.seed_idx, ps.desc.problem_id), level, sample, ps.n, t0,
                                                      count, idx_dev, plan->stream);
     return check_cuda(plan, err, "debug_indices");

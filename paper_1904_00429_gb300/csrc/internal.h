@@ -60,6 +60,7 @@ struct LevelParams {
     const double* xi_q;   // xi** (CUDA-core kernel): weights q (n), or null for the uniform law
     const double* xi_Q;   // their running sums (n)
     double xi_Qtot;       // Q[n-1]
+    const int* xi_G;      // guide table of the running sums (n buckets)
     TcMaps maps;          // tensor-core kernel only
 };
 
@@ -214,11 +215,12 @@ cudaError_t measure_generation_rate(cudaStream_t st, int num_sms, double* entrie
 
 // xi** of Thm 3.1 from the plan's parameter layout (rows k of PA / PB hold the (M, S) pairs of
 // column k of A / row k of B): q[k] = sqrt(sum_i (M^2 + S^2) * sum_j (M'^2 + S'^2)) in index order
-// without contraction, Q[k] = q[0] + ... + q[k] in one sequential pass.
+// without contraction, Q[k] = q[0] + ... + q[k] in one sequential pass, and the guide table G
+// (G[b] = the smallest j with Q[j] > b Q[n-1] / n) that lets a draw start its search near the answer.
 cudaError_t launch_xi_optimal(const void* PAB, bool f64, int64_t ld, int64_t m, int64_t m_pad, int64_t n,
-                              int64_t p, double* q, double* Q, cudaStream_t st);
+                              int64_t p, double* q, double* Q, int* G, cudaStream_t st);
 cudaError_t launch_debug_indices_xi(uint2 keyI, int l, uint64_t s, int64_t n, int64_t t0, int64_t count,
-                                    const double* Q, const double* q, int64_t* out, cudaStream_t st);
+                                    const double* Q, const double* q, const int* G, int64_t* out, cudaStream_t st);
 
 // Set the thread-local message returned by mlmc_last_error().
 mlmc_status report_error(mlmc_status st, const char* msg);

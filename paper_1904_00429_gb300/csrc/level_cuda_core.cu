@@ -79,6 +79,11 @@ level_cuda_core_kernel(const LevelParams prm)
     __shared__ int idx_s[TK];
     __shared__ T w_s[TK];   // F = 0: the slot's weight; F != 0: 1 on coarse slots, else 0
     __shared__ T g_s[TK];   // F != 0 under xi**: the slot's 1 / xi_{r_t} (folded into B)
+    // xi**: a sample's draws (c_l <= kXiPre) are made up front by every thread (each needs a few
+    // dependent table reads) instead of by TK / 2 threads per chunk of slots
+    constexpr int kXiPre = 1024;
+    __shared__ int idx_pre[XI ? kXiPre : 1];
+    __shared__ double g_pre[XI ? kXiPre : 1];
     __shared__ double red_s[NT / 32];
 
     const int tid = threadIdx.x;
@@ -121,6 +126,24 @@ level_cuda_core_kernel(const LevelParams prm)
 #pragma unroll
             for (int j = 0; j < RP; ++j) acc[i][j] = accc[i][j] = T(0);
 
+        const bool pre = XI && prm.c <= kXiPre;
+        if constexpr (XI) {
+            if (pre) {
+                for (int h = tid; 2 * h < prm.c; h += NT) {
+                    uint64_t w0, w1;
+                    index_words(prm.keyI, lsw, s_lo, h, w0, w1);
+                    const int64_t r0 = index_from_cdf(w0, prm.xi_Q, prm.xi_q, prm.xi_G, prm.n);
+                    idx_pre[2 * h] = static_cast<int>(r0);
+                    g_pre[2 * h] = __ddiv_rn(prm.xi_Qtot, prm.xi_q[r0]);
+                    if (2 * h + 1 < prm.c) {
+                        const int64_t r1 = index_from_cdf(w1, prm.xi_Q, prm.xi_q, prm.xi_G, prm.n);
+                        idx_pre[2 * h + 1] = static_cast<int>(r1);
+                        g_pre[2 * h + 1] = __ddiv_rn(prm.xi_Qtot, prm.xi_q[r1]);
+                    }
+                }
+                __syncthreads();
+            }
+        }
         for (int k0 = 0; k0 < prm.c; k0 += TK) {
             // 1. indices and weights of slots k0 .. k0 + TK - 1
             for (int h = tid; h < TK / 2; h += NT) {
@@ -129,12 +152,19 @@ level_cuda_core_kernel(const LevelParams prm)
                     int64_t r0, r1;
                     double g[2] = {1.0, 1.0};
                     if constexpr (xi) {
-                        uint64_t w0, w1;
-                        index_words(prm.keyI, lsw, s_lo, t >> 1, w0, w1);
-                        r0 = index_from_cdf(w0, prm.xi_Q, prm.xi_q, prm.n);
-                        r1 = index_from_cdf(w1, prm.xi_Q, prm.xi_q, prm.n);
-                        g[0] = __ddiv_rn(prm.xi_Qtot, prm.xi_q[r0]);
-                        g[1] = __ddiv_rn(prm.xi_Qtot, prm.xi_q[r1]);
+                        if (pre) {
+                            r0 = idx_pre[t];
+                            g[0] = g_pre[t];
+                            r1 = t + 1 < prm.c ? idx_pre[t + 1] : 0;
+                            g[1] = t + 1 < prm.c ? g_pre[t + 1] : 0.0;
+                        } else {
+                            uint64_t w0, w1;
+                            index_words(prm.keyI, lsw, s_lo, t >> 1, w0, w1);
+                            r0 = index_from_cdf(w0, prm.xi_Q, prm.xi_q, prm.xi_G, prm.n);
+                            r1 = index_from_cdf(w1, prm.xi_Q, prm.xi_q, prm.xi_G, prm.n);
+                            g[0] = __ddiv_rn(prm.xi_Qtot, prm.xi_q[r0]);
+                            g[1] = __ddiv_rn(prm.xi_Qtot, prm.xi_q[r1]);
+                        }
                     } else {
                         index_pair(prm.keyI, lsw, s_lo, t >> 1, static_cast<uint64_t>(prm.n), r0, r1);
                     }

@@ -93,26 +93,27 @@ __device__ __forceinline__ void index_pair(uint2 key, uint32_t lsw, uint32_t s_l
 
 // Index r_t for one slot's 64-bit word under a tabulated law (xi** of Thm 3.1): u = (word >> 11)
 // 2^-53 in [0, 1), x = u Q[n-1], r = the smallest j with x < Q[j] (Q the running sums of the
-// weights q), or the last j with q[j] > 0 when rounding put x at Q[n-1].  Binary search over Q.
+// weights q), or the last j with q[j] > 0 when rounding put x at Q[n-1].  The guide table G (n
+// buckets; G[b] = the smallest j with Q[j] > b Q[n-1] / n, see xi_guide_kernel) gives a start
+// at or below the answer, from which a forward scan finds it: the same j as a full search.
 __device__ __forceinline__ int64_t index_from_cdf(uint64_t word, const double* __restrict__ Q,
-                                                  const double* __restrict__ q, int64_t n)
+                                                  const double* __restrict__ q, const int* __restrict__ G,
+                                                  int64_t n)
 {
     const double Qtot = Q[n - 1];
-    const double x = __dmul_rn(__ull2double_rn(word >> 11) * 0x1p-53, Qtot);
+    const double u = __ull2double_rn(word >> 11) * 0x1p-53;
+    const double x = __dmul_rn(u, Qtot);
     if (!(x < Qtot)) {
         int64_t j = n - 1;
         while (j > 0 && !(q[j] > 0.0)) --j;
         return j;
     }
-    int64_t lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int64_t mid = lo + (hi - lo) / 2;
-        if (x < Q[mid])
-            hi = mid;
-        else
-            lo = mid + 1;
-    }
-    return lo;
+    // bucket of x, one bucket lower to absorb the rounding of u n and of the bucket bounds
+    int64_t b = static_cast<int64_t>(u * static_cast<double>(n));
+    b = b < 1 ? 0 : (b > n ? n - 1 : b - 1);
+    int64_t j = G[b];
+    while (!(x < Q[j])) ++j;   // ends: x < Q[n-1]
+    return j;
 }
 
 // The two 64-bit index words of slot pair (t & ~1, t | 1) of one sample (even slot first).

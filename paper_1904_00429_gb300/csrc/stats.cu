@@ -206,14 +206,14 @@ __global__ void debug_indices_kernel(uint2 keyI, int l, uint64_t s, int64_t n, i
 }
 
 __global__ void debug_indices_xi_kernel(uint2 keyI, int l, uint64_t s, int64_t n, int64_t t0, int64_t count,
-                                        const double* Q, const double* q, int64_t* out)
+                                        const double* Q, const double* q, const int* G, int64_t* out)
 {
     const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (e >= count) return;
     const int64_t t = t0 + e;
     uint64_t w0, w1;
     index_words(keyI, level_sample_word(l, s), static_cast<uint32_t>(s), t >> 1, w0, w1);
-    out[e] = index_from_cdf((t & 1) ? w1 : w0, Q, q, n);
+    out[e] = index_from_cdf((t & 1) ? w1 : w0, Q, q, G, n);
 }
 
 // q[k] of xi**: one thread per k, sums in index order with separate roundings (no contraction).
@@ -235,6 +235,24 @@ __global__ void xi_weights_kernel(const T* __restrict__ PAB, int64_t ld, int64_t
         eb = __dadd_rn(eb, __dadd_rn(__dmul_rn(mv, mv), __dmul_rn(sv, sv)));
     }
     q[k] = __dsqrt_rn(__dmul_rn(ea, eb));
+}
+
+// Guide table of the cumulative law: G[b] = the smallest j with Q[j] > b Q[n-1] / n (a lower
+// bound for every x in bucket b; exactness of the draw does not depend on it).
+__global__ void xi_guide_kernel(const double* __restrict__ Q, int64_t n, int* G)
+{
+    const int64_t b = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (b >= n) return;
+    const double thr = static_cast<double>(b) / static_cast<double>(n) * Q[n - 1];
+    int64_t lo = 0, hi = n - 1;   // Q[n-1] > thr for b < n (up to rounding: clamped below)
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (Q[mid] > thr)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    G[b] = static_cast<int>(lo);
 }
 
 // Q[k] = q[0] + ... + q[k]: one sequential pass (the order fixes every rounding).
@@ -356,16 +374,16 @@ cudaError_t launch_debug_indices(uint2 keyI, int l, uint64_t s, int64_t n, int64
 }
 
 cudaError_t launch_debug_indices_xi(uint2 keyI, int l, uint64_t s, int64_t n, int64_t t0, int64_t count,
-                                    const double* Q, const double* q, int64_t* out, cudaStream_t st)
+                                    const double* Q, const double* q, const int* G, int64_t* out, cudaStream_t st)
 {
     if (count <= 0) return cudaSuccess;
     debug_indices_xi_kernel<<<static_cast<unsigned>((count + 255) / 256), 256, 0, st>>>(keyI, l, s, n, t0, count, Q, q,
-                                                                                         out);
+                                                                                         G, out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_xi_optimal(const void* PAB, bool f64, int64_t ld, int64_t m, int64_t m_pad, int64_t n,
-                              int64_t p, double* q, double* Q, cudaStream_t st)
+                              int64_t p, double* q, double* Q, int* G, cudaStream_t st)
 {
     const unsigned blocks = static_cast<unsigned>((n + 255) / 256);
     if (f64)
@@ -375,6 +393,9 @@ cudaError_t launch_xi_optimal(const void* PAB, bool f64, int64_t ld, int64_t m, 
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     xi_scan_kernel<<<1, 1, 0, st>>>(q, n, Q);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    xi_guide_kernel<<<blocks, 256, 0, st>>>(Q, n, G);
     return cudaGetLastError();
 }
 
