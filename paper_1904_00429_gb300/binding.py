@@ -186,6 +186,7 @@ class Plan:
         self.precision = precision
         self.c0, self.ratio, self.L = c0, ratio, L
         self.pilot_n = pilot_n
+        self.nl_scale = nl_scale
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             _check(lib().mlmc_plan(arr, len(self.problems), ctypes.byref(self.options),

@@ -14,6 +14,7 @@ The driver works on any object with the plan methods used below (``binding.Plan`
 """
 from __future__ import annotations
 
+import math
 from typing import List, Optional, Sequence, Tuple
 
 import torch
@@ -90,14 +91,83 @@ def _run_round(plan, ranges: Sequence[Tuple[int, int, int, int]], merged: _Merge
     _allreduce_round(plan, merged, group, device)
 
 
-def estimate(plan, eps_abs: Sequence[float], group=None, device: Optional[torch.device] = None):
-    """Alg. 2 with the finest level fixed, its samples sharded over the ranks of ``group``.
+def _allocate(plan, merged: _Merged, q: int, L: int, eps: float) -> List[int]:
+    """N_l of levels 0..L (Remark 3.6 with C_0 = c_0, C_l = c_l + c_{l-1}) from the merged sums."""
+    c = [plan.c0 * plan.ratio ** l for l in range(L + 1)]
+    V, C = [], []
+    for l in range(L + 1):
+        N, s, sq = merged.state[(q, l)]
+        M2 = sq - float((s * s).sum()) / N
+        V.append(max(0.0, M2 / (N - 1)))
+        C.append(float(c[0] if l == 0 else c[l] + c[l - 1]))
+    root = sum(math.sqrt(v * cc) for v, cc in zip(V, C))
+    return [max(plan.pilot_n, int(math.ceil(plan.nl_scale * 2.0 / eps**2 * math.sqrt(v / cc) * root)))
+            for v, cc in zip(V, C)]
 
-    Returns (list of m x p FP64 estimates, list of per-problem N_l).  Every rank returns the
-    same values.  ``device`` is where the reduction buffer lives (the plan's device for NCCL,
-    CPU for gloo)."""
+
+def _mean_norm(merged: _Merged, q: int, l: int) -> float:
+    N, s, _ = merged.state[(q, l)]
+    return float(torch.linalg.norm(s.double())) / N if N > 0 else 0.0
+
+
+def _estimate_adaptive(plan, eps_abs, group, device):
+    """Alg. 2 choosing L per problem: rounds on levels 0..L_q for L_q = 0, 1, ... (pilot on the new
+    level, allocation over levels 0..L_q from the merged sums, top-ups), stopping after the first
+    round with L_q >= 2 whose finest mean satisfies ||Y_L||_F < (sqrt(R) + 1) eps / sqrt(2)
+    (Remark 3.5), or at the plan's L for the problem.  The decisions use merged statistics, so
+    every rank takes the same ones."""
+    merged = _Merged(plan)
+    nprob = len(plan.problems)
+    Lc = [0] * nprob
+    running = [True] * nprob
+    pilot = plan.pilot_n
+    while True:
+        ranges = []
+        for q in range(nprob):
+            if running[q]:
+                for l in range(Lc[q] + 1):
+                    have = merged.state[(q, l)][0]
+                    if have < pilot:
+                        ranges.append((q, l, have, pilot - have))
+        _run_round(plan, ranges, merged, group, device)
+        ranges = []
+        for q in range(nprob):
+            if running[q]:
+                Nl = _allocate(plan, merged, q, Lc[q], eps_abs[q])
+                for l in range(Lc[q] + 1):
+                    have = merged.state[(q, l)][0]
+                    if Nl[l] > have:
+                        ranges.append((q, l, have, Nl[l] - have))
+        _run_round(plan, ranges, merged, group, device)
+        more = False
+        for q in range(nprob):
+            if not running[q]:
+                continue
+            bound = (math.sqrt(plan.ratio) + 1.0) * eps_abs[q] / math.sqrt(2.0)
+            if Lc[q] >= 2 and _mean_norm(merged, q, Lc[q]) < bound:
+                running[q] = False
+            elif Lc[q] == plan.levels[q]:
+                running[q] = False
+            else:
+                Lc[q] += 1
+                more = True
+        if not more:
+            break
+    return plan.telescoping_sum(), [[merged.state[(q, l)][0] for l in range(Lc[q] + 1)] for q in range(nprob)]
+
+
+def estimate(plan, eps_abs: Sequence[float], group=None, device: Optional[torch.device] = None,
+             adaptive: bool = False):
+    """Alg. 2 with its samples sharded over the ranks of ``group``: the finest level fixed at the
+    plan's L, or (``adaptive``) chosen by Alg. 2's while loop (Remark 3.5).
+
+    Returns (list of m x p FP64 estimates, list of per-problem N_l, one entry per level used).
+    Every rank returns the same values.  ``device`` is where the reduction buffer lives (the
+    plan's device for NCCL, CPU for gloo)."""
     if device is None:
         device = torch.device("cpu") if dist.get_backend(group) == "gloo" else plan.device
+    if adaptive:
+        return _estimate_adaptive(plan, eps_abs, group, device)
     merged = _Merged(plan)
     pilot = plan.pilot_n
     ranges = []

@@ -14,12 +14,13 @@ import oracle
 
 
 class FakePlan:
-    def __init__(self, pps, *, c0, L, ratio=2, pilot_n=8, nl_scale=1.0):
+    def __init__(self, pps, *, c0, L, ratio=2, pilot_n=8, nl_scale=1.0, fkind=0):
         self.problems = list(pps)
         self.levels = [L] * len(self.problems)
         self.c0, self.ratio, self.L = c0, ratio, L
         self.pilot_n = pilot_n
         self.nl_scale = nl_scale
+        self.fkind = fkind
         self.device = torch.device("cpu")
         self._orc = [oracle.Problem(*pp.f64(), seed_A=pp.seed_A, seed_B=pp.seed_B, seed_idx=pp.seed_idx,
                                     problem_id=pp.problem_id) for pp in self.problems]
@@ -35,7 +36,7 @@ class FakePlan:
     def level_stats(self, q, l, begin, count):
         st = self.state[(q, l)]
         for s in range(begin, begin + count):
-            D = oracle.sample(self._orc[q], self._lv, l, s)[0]
+            D = oracle.sample(self._orc[q], self._lv, l, s, fkind=self.fkind)[0]
             st[1] += torch.from_numpy(D)
             st[2] += float((D * D).sum())
             self.evaluated[(q, l)].append(s)
@@ -81,6 +82,8 @@ class FakePlan:
             Y = None
             for l in range(self.L + 1):
                 N, s, _ = self.state[(q, l)]
+                if N == 0:   # levels never run add nothing (as in the C library)
+                    continue
                 Y = s / N if Y is None else Y + s / N
             out.append(Y)
         return out

@@ -15,6 +15,7 @@ import torch
 import torch.distributed as dist
 import torch.multiprocessing as mp
 
+import oracle
 from paper_1904_00429_gb300 import distributed
 from paper_1904_00429_gb300.inputs import make_params
 
@@ -93,3 +94,52 @@ def test_two_rank_estimate_matches_one_process(tmp_path):
             # both ranks carried about half of the top-up
             share = len(res[1]["evaluated"][(q, l)]) / Nl_ref[q][l]
             assert 0.4 < share < 0.6, share
+
+
+def _bias_params():
+    # m = p = 2, n = 16, entries of AB spread around the jump of f(x) = |x| H(2 - x)
+    from paper_1904_00429_gb300.inputs import ProblemParams
+    rng = np.random.default_rng(9)
+    M = rng.uniform(0.2, 0.6, (2, 16))
+    S = np.full((2, 16), 0.3)
+    Mp = rng.uniform(0.05, 0.35, (16, 2))
+    Sp = np.full((16, 2), 0.1)
+    return ProblemParams(M, S, Mp, Sp, 21, 22, 23, 0, {"law": "custom"})
+
+
+ADAPT_EPS = 0.08
+
+
+def _adaptive_worker(rank, world, port, out_dir):
+    sys.path.insert(0, HERE)
+    from fake_plan import FakePlan
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    plan = FakePlan([_bias_params()], c0=1, L=10, pilot_n=32, fkind=oracle.F_ABS_STEP)
+    ys, Nl = distributed.estimate(plan, [ADAPT_EPS], adaptive=True)
+    torch.save({"y": [y.clone() for y in ys], "Nl": Nl, "evaluated": plan.evaluated},
+               os.path.join(out_dir, f"rank{rank}.pt"))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_adaptive_L_matches_the_oracle(tmp_path):
+    """Alg. 2 with the adaptive L (E[f(AB)], f(x) = |x| H(2 - x)) sharded over two gloo ranks:
+    the same finest level and N_l as the oracle's single-process Alg. 2, the same estimate up to
+    the order of the FP64 additions, and every sample id evaluated exactly once."""
+    world = 2
+    mp.start_processes(_adaptive_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True,
+                       start_method="spawn")
+    res = [torch.load(tmp_path / f"rank{r}.pt") for r in range(world)]
+    pp = _bias_params()
+    orc = oracle.Problem(*pp.f64(), seed_A=21, seed_B=22, seed_idx=23, problem_id=0)
+    Yref, Lref, Nref, _, _ = oracle.estimate_f(orc, oracle.Levels(1, 2, 10), ADAPT_EPS, fkind=oracle.F_ABS_STEP,
+                                               adaptive=True, pilot=32)
+    assert Lref >= 3
+    assert res[0]["Nl"] == res[1]["Nl"] == [list(Nref)]
+    assert torch.equal(res[0]["y"][0], res[1]["y"][0])
+    np.testing.assert_allclose(res[0]["y"][0].numpy(), Yref, rtol=1e-11, atol=1e-13)
+    for l in range(Lref + 1):
+        ids = sorted(res[0]["evaluated"][(0, l)] + res[1]["evaluated"][(0, l)])
+        assert ids == list(range(int(Nref[l])))
