@@ -250,14 +250,16 @@ MLMC_API mlmc_status mlmc_level_stats_batch(mlmc_plan_t* plan, const mlmc_range*
  * 1256 2032 2064 2128 2256 (negative: not tried). */
 MLMC_API mlmc_status mlmc_get_batch_tile(const mlmc_plan_t* plan, int32_t* tile_id, double* timings_ms);
 
-/* ---- estimator (Alg. 2 with the finest level fixed) ---------------------------------- */
+/* ---- estimator (Alg. 2) ------------------------------------------------------------- */
 
 /* mlmc_estimate: for every problem, run pilot_n samples on every level not
  * yet holding that many, take V_l, allocate N_l = ceil(nl_scale 2 eps^-2
  * sqrt(V_l/C_l) sum_j sqrt(V_j C_j)) with C_0 = c_0, C_l = c_l + c_{l-1}
  * (Remark 3.6; at least pilot_n), evaluate the missing samples pilot_n ..
  * N_l - 1 (earlier samples are kept, as Alg. 2 reuses them), and write
- * Yhat = sum_l Y_l (Eq. hatY).  eps_abs: host array of nprob absolute
+ * Yhat = sum_l Y_l (Eq. hatY).  With options.adaptive_L the levels are taken
+ * one round at a time as described there, and Yhat sums the levels up to the
+ * finest one used (mlmc_report.L).  eps_abs: host array of nprob absolute
  * Frobenius tolerances (> 0).  yhat_dev: device FP64 buffer holding every
  * problem's m x p estimate back to back in problem order.  reports: host
  * array of nprob reports, or NULL.  Synchronises the plan's stream (the
