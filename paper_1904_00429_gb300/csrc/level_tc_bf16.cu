@@ -82,6 +82,8 @@ struct TcCfg {
                                       /*job copies of batched launches (pairs run single-problem launches)*/;
     static constexpr int kSmemBytes = 1024 /*align slack*/ + kTileBytes + 2 * kStageBytes + kBookBytes;
     static_assert(kAccCols <= 512, "tile exceeds tensor memory");
+    static_assert(kTmemCols >= kAccCols, "the allocation holds the accumulators");
+    static_assert(kKSteps * 16 == kSub, "a sub-block is a whole number of K = 16 MMA steps");
     static_assert(BN % 16 == 0 && BN >= 32 && BN <= 256, "N of the MMA");
     static constexpr bool kFits = kSmemBytes <= 227 * 1024 &&   // E4M3's 32-slot staging rules out wide tiles
                                   (!P || (MH == 1 && BN == 256));
