@@ -617,8 +617,15 @@ def _measure_xi(args, dev, stream):
         out[law] = {"value": t, "N_l": rep["N"], "V_l": rep["V"], "outer_products": rep["outer_products"],
                     "rmse_pred": rep["rmse_pred"], "error": err,
                     "timing": "end to end through mlmc_estimate, plan creation included"}
+    # FMAs of the contraction (2 m p per sampled outer product) over the end-to-end time of xi**
+    achieved = 2.0 * X["m"] * X["p"] * out["optimal"]["outer_products"] / out["optimal"]["value"] / 1e12
     return {"workload": X["name"], "metric": "time to rel. RMSE 1e-2 for E[AB] under xi^u and xi**", "unit": "s",
             "eps_abs": eps, "precision": X["precision"], "uniform": out["uniform"], "optimal": out["optimal"],
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)",
+                         "kernel": "level_cuda_core_kernel<float, XI>",
+                         "note": "xi** run end to end (plan creation, pilot and allocation included)"},
             "uniform_over_optimal": out["uniform"]["value"] / out["optimal"]["value"],
             "V0_uniform_over_optimal": out["uniform"]["V_l"][0] / out["optimal"]["V_l"][0]}
 
