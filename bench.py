@@ -846,6 +846,17 @@ def run_profile_case(args):
         plan.close()
         print(json.dumps({"profile_case": args.profile_case, "status": "ok"}), flush=True)
         return
+    if args.profile_case == "cuda_core_f32_xi_level3":
+        # the xi** variant of the CUDA-core kernel on the sparse-row workload, level 3 (c = 128)
+        xt = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in _xi_params()]
+        plan = binding.Plan([binding.ProblemSpec(*xt, seed_A=3, seed_B=4, seed_idx=5)], c0=XI["c0"], L=XI["L"],
+                            precision="fp32", sampling="optimal")
+        for i in range(3):
+            plan.level_stats(0, 3, i * 19456, 19456)
+        plan.synchronize()
+        plan.close()
+        print(json.dumps({"profile_case": args.profile_case, "status": "ok"}), flush=True)
+        return
     pp = make_params(256, 65536, 256, seed_A=0, seed_B=1, dtype=np.float32)
     ts = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (pp.M, pp.S, pp.Mp, pp.Sp)]
     if args.profile_case == "adjoint":
@@ -882,7 +893,8 @@ def main():
     ap.add_argument("--no-xi", action="store_true", help="skip the xi^u / xi** comparison")
     ap.add_argument("--ladder", default="", help="comma-separated relative RMSE targets to run end to end "
                     "through mlmc_estimate (e.g. 3e-2; about a minute each at 3e-2)")
-    ap.add_argument("--profile-case", choices=sorted(list(PROFILE_CASES) + ["adjoint", "batched_8_problems"]),
+    ap.add_argument("--profile-case", choices=sorted(list(PROFILE_CASES) + ["adjoint", "batched_8_problems",
+                                                                         "cuda_core_f32_xi_level3"]),
                     default=None,
                     help="run one small kernel invocation for ncu instead of the benchmark")
     args = ap.parse_args()
