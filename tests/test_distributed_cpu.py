@@ -143,3 +143,44 @@ def test_two_rank_adaptive_L_matches_the_oracle(tmp_path):
     for l in range(Lref + 1):
         ids = sorted(res[0]["evaluated"][(0, l)] + res[1]["evaluated"][(0, l)])
         assert ids == list(range(int(Nref[l])))
+
+
+def _second_bias_params():
+    from paper_1904_00429_gb300.inputs import ProblemParams
+    rng = np.random.default_rng(11)
+    M = rng.uniform(0.1, 0.5, (3, 12))
+    S = np.full((3, 12), 0.25)
+    Mp = rng.uniform(0.1, 0.4, (12, 2))
+    Sp = np.full((12, 2), 0.15)
+    return ProblemParams(M, S, Mp, Sp, 31, 32, 33, 1, {"law": "custom"})
+
+
+def _multi_worker(rank, world, port, out_dir):
+    sys.path.insert(0, HERE)
+    from fake_plan import FakePlan
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    plan = FakePlan([_bias_params(), _second_bias_params()], c0=1, L=10, pilot_n=32, fkind=oracle.F_ABS_STEP)
+    ys, Nl = distributed.estimate(plan, [ADAPT_EPS, 0.1], adaptive=True)
+    torch.save({"y": [y.clone() for y in ys], "Nl": Nl}, os.path.join(out_dir, f"rank{rank}.pt"))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_adaptive_L_is_decided_per_problem(tmp_path):
+    """Two problems in one plan, one rank: each stops at its own finest level, with the N_l and
+    estimate of its own single-problem Alg. 2 (rounds interleave, decisions do not)."""
+    mp.start_processes(_multi_worker, args=(1, _free_port(), str(tmp_path)), nprocs=1, join=True,
+                       start_method="spawn")
+    res = torch.load(tmp_path / "rank0.pt")
+    Ls = []
+    for q, (pp, eps) in enumerate([(_bias_params(), ADAPT_EPS), (_second_bias_params(), 0.1)]):
+        orc = oracle.Problem(*pp.f64(), seed_A=pp.seed_A, seed_B=pp.seed_B, seed_idx=pp.seed_idx,
+                             problem_id=pp.problem_id)
+        Yref, Lref, Nref, _, _ = oracle.estimate_f(orc, oracle.Levels(1, 2, 10), eps, fkind=oracle.F_ABS_STEP,
+                                                   adaptive=True, pilot=32)
+        assert res["Nl"][q] == list(Nref)
+        np.testing.assert_allclose(res["y"][q].numpy(), Yref, rtol=1e-11, atol=1e-13)
+        Ls.append(Lref)
+    assert Ls[0] != Ls[1], Ls   # the case exercises problems that stop at different levels
