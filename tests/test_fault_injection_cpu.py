@@ -55,3 +55,39 @@ def test_invalid_arguments_are_reported_before_anything_else(monkeypatch):
     st = binding.lib().mlmc_plan(arr, 1, ctypes.byref(opts), None, ctypes.byref(h))
     assert st == 1
     assert "c0" in binding.lib().mlmc_last_error().decode()
+
+
+@pytest.mark.parametrize("fields,status,word", [
+    # (precision, f, adaptive_L, sampling) -> status, a word of the message
+    (("fp32", 7, 0, 0), 1, "unknown f"),  # unknown targeted function
+    (("fp32", 0, 2, 0), 1, "adaptive_L"),
+    (("fp32", 0, 0, 5), 1, "sampling"),
+    (("bf16", 1, 0, 0), 6, "FP64 or FP32"),   # f needs the CUDA-core path
+    (("fp8", 0, 0, 1), 6, "FP64 or FP32"),    # so does xi**
+])
+def test_option_combinations_are_validated_on_the_host(monkeypatch, fields, status, word):
+    """Targeted function, adaptive L and sampling law are checked before any device work (the
+    injected allocation fault would otherwise be reported)."""
+    monkeypatch.setenv("MLMC_FAULT", "alloc")
+    prec, f, adaptive, sampling = fields
+    arr = (binding.Problem * 1)(_problem())
+    opts = binding.Options(4, 2, 2, binding.PRECISION[prec], 8, 1.0, 0, 0, 0, f, adaptive, sampling)
+    h = ctypes.c_void_p()
+    st = binding.lib().mlmc_plan(arr, 1, ctypes.byref(opts), None, ctypes.byref(h))
+    assert st == status and h.value is None
+    assert word in binding.lib().mlmc_last_error().decode()
+
+
+def test_valid_new_options_pass_validation(monkeypatch):
+    monkeypatch.setenv("MLMC_FAULT", "alloc")
+    for prec in ("fp64", "fp32"):
+        arr = (binding.Problem * 1)(_problem())
+        opts = binding.Options(4, 2, 2, binding.PRECISION[prec], 8, 1.0, 0, 0, 0, 1, 1, 1)
+        h = ctypes.c_void_p()
+        st = binding.lib().mlmc_plan(arr, 1, ctypes.byref(opts), None, ctypes.byref(h))
+        assert st == 3   # reached the (injected) allocation: validation accepted f, adaptive L and xi**
+
+
+def test_generation_rate_rejects_a_null_output():
+    st = binding.lib().mlmc_measure_generation_rate(None, None)
+    assert st == 1
