@@ -23,7 +23,7 @@ _SRC = os.path.join(_HERE, "mlmc_oracle.c")
 _HDR = os.path.join(_HERE, "mlmc_oracle.h")
 _LIB = os.path.join(_HERE, "libmlmc_oracle.so")
 
-QUANT_NONE, QUANT_BF16, QUANT_E4M3 = 0, 1, 2
+QUANT_NONE, QUANT_BF16, QUANT_E4M3, QUANT_E4M3_RNE = 0, 1, 2, 3
 F_IDENTITY, F_ABS_STEP = 0, 1
 
 _lock = threading.Lock()
@@ -75,6 +75,8 @@ def lib():
                 "orc_cost": (D, [P, I]),
                 "orc_round_bf16": (D, [D]),
                 "orc_round_e4m3": (D, [D]),
+                "orc_round_e4m3_sr": (D, [D, U32]),
+                "orc_e4m3_dither": (U32, [U32, U32, I, U64, I64, I64]),
                 "orc_e4m3_block_scale": (D, [D]),
                 "orc_sketch": (None, [I64, I64, I64, P, P, P, I64, I64, I64, P]),
                 "orc_sample": (None, [P, P, I, U64, I, P, P, P, P]),
@@ -193,6 +195,14 @@ def round_bf16(x: float) -> float:
 
 def round_e4m3(x: float) -> float:
     return lib().orc_round_e4m3(x)
+
+
+def round_e4m3_sr(y: float, d: int) -> float:
+    return lib().orc_round_e4m3_sr(y, d)
+
+
+def e4m3_dither(seed, problem_id, l, s, row, t) -> int:
+    return int(lib().orc_e4m3_dither(seed, problem_id, l, s, row, t))
 
 
 def e4m3_block_scale(absmax: float) -> float:

@@ -218,6 +218,39 @@ double orc_round_e4m3(double x)
     return copysign(r, x);
 }
 
+/* Stochastic rounding to the E4M3 grid: |y| lies in [lo, lo + h) with lo on the grid and h the
+ * grid spacing there; the result is lo + h when (d + 1/2) 2^-16 < (|y| - lo) / h for the 16-bit
+ * dither d, else lo, with the sign of y.  A uniform d makes the rounding unbiased up to the
+ * dither's resolution: averaged over the 2^16 dithers the result is y within 2^-17 h. */
+double orc_round_e4m3_sr(double y, uint32_t d)
+{
+    if (y == 0.0 || isnan(y)) return y;
+    double ay = fabs(y);
+    if (ay >= 448.0) return copysign(448.0, y);
+    int e = ilogb(ay);
+    if (e < -6) e = -6;
+    double h = ldexp(1.0, e - 3);
+    double lo = floor(ay / h) * h;
+    double f = (ay - lo) / h;                       /* exact: h is a power of two */
+    double r = (f * 65536.0 > (double)(d & 0xFFFFu) + 0.5) ? lo + h : lo;
+    return copysign(r, y);
+}
+
+/* Dither of the E4M3 rounding of the sampled entry in row `row` (a row of A, or a column of B)
+ * and slot t of sample s of level l: Philox4x32-10 with the entry's key (seed_A or seed_B,
+ * problem) and counter (row / 4, 2^31 + t / 2, s_lo, level word) -- a stream of its own: the
+ * normals use counter word 1 = k < 2^31 and the indices 2^32 - 1 -- word row mod 4, its low 16
+ * bits for even t and its high 16 bits for odd t. */
+uint32_t orc_e4m3_dither(uint32_t seed, uint32_t problem_id, int l, uint64_t s, int64_t row, int64_t t)
+{
+    uint32_t ctr[4] = { (uint32_t)(row >> 2), 0x80000000u | (uint32_t)(t >> 1), (uint32_t)s, level_sample_word(l, s) };
+    uint32_t key[2] = { seed, problem_id };
+    uint32_t w[4];
+    orc_philox4x32_10(ctr, key, w);
+    uint32_t word = w[row & 3];
+    return (t & 1) ? (word >> 16) : (word & 0xFFFFu);
+}
+
 double orc_e4m3_block_scale(double absmax)
 {
     if (!(absmax > 0.0)) return 1.0;
@@ -259,10 +292,14 @@ typedef struct {
     double* g;       /* c_l: 1 under xi^u (the n is in the estimate's scale); Q[n-1] / q[r_t] = 1 / xi**_{r_t} */
 } realisation;
 
-static void quantise_e4m3_blocks(double* X, int64_t rows, int64_t cols, int along_rows)
+/* Block-scaled E4M3 of the sampled A (along_rows: blocks of 32 consecutive slots within each row)
+ * or of the sampled B (blocks of 32 consecutive slots within each column): the block's scale
+ * 2^e from its absmax, then every entry x -> 2^e q(x / 2^e), q the E4M3 rounding -- stochastic
+ * (orc_round_e4m3_sr with the entry's dither, seed = the seed of A or of B) when sr is set, else
+ * round to nearest even. */
+static void quantise_e4m3_blocks(double* X, int64_t rows, int64_t cols, int along_rows, int sr,
+                                 uint32_t seed, uint32_t problem_id, int l, uint64_t s)
 {
-    /* along_rows: blocks of 32 consecutive columns within each row (sampled A);
-     * otherwise blocks of 32 consecutive rows within each column (sampled B). */
     int64_t outer = along_rows ? rows : cols;
     int64_t inner = along_rows ? cols : rows;
     for (int64_t o = 0; o < outer; ++o) {
@@ -276,7 +313,9 @@ static void quantise_e4m3_blocks(double* X, int64_t rows, int64_t cols, int alon
             double scale = orc_e4m3_block_scale(absmax);
             for (int64_t t = b0; t < b1; ++t) {
                 double* v = along_rows ? &X[o * cols + t] : &X[t * cols + o];
-                *v = orc_round_e4m3(*v / scale) * scale;
+                double q = sr ? orc_round_e4m3_sr(*v / scale, orc_e4m3_dither(seed, problem_id, l, s, o, t))
+                              : orc_round_e4m3(*v / scale);
+                *v = q * scale;
             }
         }
     }
@@ -321,9 +360,10 @@ static int draw_realisation(const orc_problem* pr, const orc_levels* lv, int l, 
     if (quant == ORC_QUANT_BF16) {
         for (int64_t e = 0; e < m * c; ++e) rz->Asel[e] = orc_round_bf16(rz->Asel[e]);
         for (int64_t e = 0; e < c * p; ++e) rz->Bsel[e] = orc_round_bf16(rz->Bsel[e]);
-    } else if (quant == ORC_QUANT_E4M3) {
-        quantise_e4m3_blocks(rz->Asel, m, c, 1);
-        quantise_e4m3_blocks(rz->Bsel, c, p, 0);
+    } else if (quant == ORC_QUANT_E4M3 || quant == ORC_QUANT_E4M3_RNE) {
+        int sr = quant == ORC_QUANT_E4M3;
+        quantise_e4m3_blocks(rz->Asel, m, c, 1, sr, pr->seed_A, pr->problem_id, l, s);
+        quantise_e4m3_blocks(rz->Bsel, c, p, 0, sr, pr->seed_B, pr->problem_id, l, s);
     }
     return 0;
 }

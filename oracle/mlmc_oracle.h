@@ -68,7 +68,9 @@ typedef struct {
 
 /* Operand rounding applied to every sampled entry before the products
  * (emulation of the reduced-precision forms; none for the plain method). */
-enum { ORC_QUANT_NONE = 0, ORC_QUANT_BF16 = 1, ORC_QUANT_E4M3 = 2 };
+/* ORC_QUANT_E4M3: block-scaled E4M3 with stochastic rounding (the library's FP8 form);
+ * ORC_QUANT_E4M3_RNE: the same with round to nearest even (kept to measure its bias). */
+enum { ORC_QUANT_NONE = 0, ORC_QUANT_BF16 = 1, ORC_QUANT_E4M3 = 2, ORC_QUANT_E4M3_RNE = 3 };
 
 /* The targeted function f of f^(AB), applied entrywise (Sec. 3): the identity (the
  * estimator of E[AB]), or f(x) = |x| H(2 - x) with H the Heaviside step, H(0) = 1 (the function
@@ -112,6 +114,16 @@ double orc_cost(const orc_levels* lv, int l);
 double orc_round_bf16(double x);
 double orc_round_e4m3(double x);
 
+/* Stochastic rounding of y (|y| <= 448) to the E4M3 grid with the 16-bit dither d: the upper of
+ * the two neighbouring grid values when (d + 1/2) 2^-16 < the fractional position of |y| between
+ * them, else the lower one; unbiased over a uniform d up to 2^-17 of the spacing. */
+double orc_round_e4m3_sr(double y, uint32_t d);
+
+/* The 16-bit dither of sampled entry (row, slot t) of sample s of level l: Philox4x32-10 with key
+ * (seed, problem_id) and counter (row / 4, 2^31 + t / 2, s mod 2^32, level word), word row mod 4,
+ * low half for even t, high half for odd t. */
+uint32_t orc_e4m3_dither(uint32_t seed, uint32_t problem_id, int l, uint64_t s, int64_t row, int64_t t);
+
 /* The sketch of Eq. matrixsketch for given operands and index positions:
  *   out = (n / cnt) * sum_{j=0}^{cnt-1} A[:, idx[off + j*stride]] B[idx[off + j*stride], :]
  * A is m x n and B is n x p, both row-major; out is m x p. */
@@ -129,7 +141,8 @@ void orc_sketch(int64_t m, int64_t n, int64_t p, const double* A, const double* 
  *         rounding error, including that of the generated entries, is measured.
  * quant rounds every sampled A and B entry first (ORC_QUANT_*); for E4M3 the
  * scales are the power-of-two absmax block scales described in
- * orc_e4m3_block_scale. */
+ * orc_e4m3_block_scale, and the rounding is stochastic with the entries'
+ * dithers (orc_e4m3_dither) unless ORC_QUANT_E4M3_RNE asks for nearest even. */
 void orc_sample(const orc_problem* pr, const orc_levels* lv, int l, uint64_t s, int quant,
                 double* D, double* Pf, double* Pc, double* mag);
 
