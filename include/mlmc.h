@@ -76,7 +76,10 @@ typedef enum {
     MLMC_FP64 = 0,     /* FP64 entries, FP64 CUDA-core contraction */
     MLMC_FP32 = 1,     /* FP32 entries, FP32 CUDA-core contraction */
     MLMC_BF16 = 2,     /* FP32 entries rounded to bfloat16, tensor-core contraction, FP32 accumulation */
-    MLMC_FP8_E4M3 = 3  /* FP32 entries scaled per 32-slot block and rounded to E4M3, FP32 accumulation */
+    MLMC_FP8_E4M3 = 3  /* FP32 entries scaled per 32-slot block (power of two from the block's absmax)
+                          and rounded to E4M3 stochastically (a 16-bit dither per entry from a Philox
+                          stream of its own), FP32 accumulation: unbiased, where rounding to nearest
+                          on the E4M3 grid shrinks the entries by about 1e-3 of their mean */
 } mlmc_precision;
 
 /* Element type of the caller's parameter matrices. */
@@ -113,7 +116,8 @@ typedef struct {
                               one of 1032 1064 1128 1256 2032 2064 2128 2256 (e.g. 2128 = 256 x 128;
                               E4M3: 1032 1064 1128 2032 2064), or 3256: a cluster of two CTAs of
                               128 x 256 sharing one 256 x 256 tile (BF16 and E4M3, single-problem
-                              launches; the default for outputs above 128 x 128) */
+                              launches; the default for outputs above 128 x 128), or 4256: the
+                              same pair with 16 generator warps on 4-slot items */
     int32_t adjoint_batch_log2; /* mlmc_backward replays at most 2^this sampled products per batch
                                    (0 = 26; at least c_L + 1 are always taken); scratch is 8 B each */
     int32_t f;           /* mlmc_function applied entrywise to each sketch (Sec. 3): the estimator then
@@ -184,12 +188,15 @@ MLMC_API mlmc_status mlmc_plan_destroy(mlmc_plan_t* plan);
 
 /* mlmc_level_stats: evaluate samples s = sample_begin .. sample_begin+count-1
  * of level `level` of problem `prob` (Alg. 1, one loop iteration each) and
- * fold them into that level's running statistics: the count, the FP64
- * per-entry sum of D and the FP64 sum of ||D||_F^2.  Samples are pure
- * functions of their ids, so disjoint ranges may be evaluated in any order
- * and split across calls; the statistics are bit-identical for any split at
- * multiples of 64 sample ids and in any case equal up to rounding.
- * count = 0 is a no-op. */
+ * fold them into that level's running statistics: the count N, the FP64
+ * per-entry sum of D and the FP64 M2 = sum_s ||D_s - mean||_F^2.  Within a
+ * chunk of consecutive sample ids the kernels grow M2 by Welford's update;
+ * chunks are folded into the level in chunk order by Chan's pairwise update
+ * (the variance of Remark 3.6 without the cancellation of a one-pass formula).
+ * Samples are pure functions of their ids, so disjoint ranges may be
+ * evaluated in any order and split across calls; the statistics are
+ * bit-identical for any split at multiples of 64 sample ids and in any case
+ * equal up to rounding.  count = 0 is a no-op. */
 MLMC_API mlmc_status mlmc_level_stats(mlmc_plan_t* plan, int32_t prob, int32_t level, uint64_t sample_begin,
                              uint64_t count);
 
@@ -200,13 +207,30 @@ MLMC_API mlmc_status mlmc_level_stats(mlmc_plan_t* plan, int32_t prob, int32_t l
 MLMC_API mlmc_status mlmc_get_level_stats(mlmc_plan_t* plan, int32_t prob, int32_t level, uint64_t* N,
                                  double* mean_dev, double* M2);
 
-/* Raw accumulator state of one level for checkpointing: N, the per-entry sum
- * of D (m x p FP64, device) and the sum of ||D||_F^2.  Get synchronises the
- * plan's stream; set replaces the state (resume continues at sample id N). */
+/* Accumulator state of one level for checkpointing and for merging the
+ * statistics of several processes: N, the per-entry sum of D (m x p FP64,
+ * device) and M2 = sum_s ||D_s - mean||_F^2 (host FP64).  Get synchronises the
+ * plan's stream; set replaces the state (resume continues at sample id N; the
+ * caller vouches that the state holds the sample ids 0 .. N-1, which
+ * mlmc_backward relies on).  M2 must be finite and >= 0, else
+ * MLMC_ERR_INVALID_ARG. */
 MLMC_API mlmc_status mlmc_get_level_state(mlmc_plan_t* plan, int32_t prob, int32_t level, uint64_t* N,
-                                 double* sum_dev, double* sumsq);
+                                 double* sum_dev, double* M2);
 MLMC_API mlmc_status mlmc_set_level_state(mlmc_plan_t* plan, int32_t prob, int32_t level, uint64_t N,
-                                 const double* sum_dev, double sumsq);
+                                 const double* sum_dev, double M2);
+
+/* mlmc_merge_level_state: fold another state of the same level (N samples
+ * disjoint from the held ones; sum_dev m x p FP64 on the plan's device; M2
+ * host FP64, finite and >= 0) into the held one with Chan's pairwise update
+ * (Eq. hatYl and Remark 3.6 over the union of the samples):
+ *     M2 <- M2 + M2' + N N' / (N + N') ||sum/N - sum'/N'||_F^2,
+ *     sum <- sum + sum',  N <- N + N'.
+ * Several processes that evaluate disjoint sample ranges obtain the same
+ * statistics by merging every process's state in one fixed order.  N = 0 is a
+ * no-op.  The flag of mlmc_backward (ids 0 .. N-1 held) is left as it was.
+ * Synchronises the plan's stream. */
+MLMC_API mlmc_status mlmc_merge_level_state(mlmc_plan_t* plan, int32_t prob, int32_t level, uint64_t N,
+                                            const double* sum_dev, double M2);
 
 /* Empty the statistics of one level (level < 0: every level of the problem). */
 MLMC_API mlmc_status mlmc_reset_level_stats(mlmc_plan_t* plan, int32_t prob, int32_t level);
@@ -227,7 +251,7 @@ typedef struct {
  * samples, output tile) work items, packed into waves (at most 1 GiB of chunk
  * partials, 4096 (problem, level) runs and 2^20 items each), balanced over
  * persistent CTAs longest item first, and each wave runs as one persistent
- * kernel launch plus one merge launch; up to four waves are captured in one
+ * kernel launch plus two merge launches; up to four waves are captured in one
  * CUDA graph, which is replayed while the tile, the CTA count and the number of
  * waves stay the same.  The tile is options->tile_override if set, else the
  * autotuner's: the first call times every candidate tile on the first chunk
@@ -236,8 +260,10 @@ typedef struct {
  * the pair 3256 of single-problem launches) keep each chunk's running sum of
  * D in tensor memory, so with any of them the per-level sums of D are the same
  * bit for bit; the 2256 tile adds scaled samples in global memory and agrees
- * with them up to FP32 rounding.  Batched launches do not use 3256.  The sums of ||D||^2 are
- * grouped by output tile, so they agree across tiles up to rounding.  Other
+ * with them up to FP32 rounding.  Batched launches do not use 3256.  The M2
+ * are grouped by output tile, so they agree across tiles up to rounding; with
+ * the same tile a batched call and the same ranges run one by one give the
+ * same bits.  Other
  * precisions: one launch sequence per range, as mlmc_level_stats.  Problems
  * whose m x p FP32 partial exceeds 1 GiB: MLMC_ERR_UNSUPPORTED.
  * Scratch: the first BF16 call allocates 1 GiB of partials and about 40 MiB
@@ -276,6 +302,21 @@ MLMC_API mlmc_status mlmc_estimate(mlmc_plan_t* plan, const double* eps_abs, dou
  * 0..L, the rest zero).  Synchronises the plan's stream. */
 MLMC_API mlmc_status mlmc_allocate(mlmc_plan_t* plan, const double* eps_abs, int64_t* Nl);
 
+/* The allocation of Remark 3.6 over levels 0..L of problem `prob` only (L at
+ * most the problem's finest level; every level 0..L needs N >= 2): Nl (host
+ * array of L + 1) as in mlmc_allocate for the absolute tolerance eps_abs
+ * (> 0).  This is the allocation step of one round of Alg. 2's while loop,
+ * for drivers that run the rounds themselves (several processes).
+ * Synchronises the plan's stream. */
+MLMC_API mlmc_status mlmc_allocate_levels(mlmc_plan_t* plan, int32_t prob, int32_t L, double eps_abs, int64_t* Nl);
+
+/* The stopping test of Alg. 2's while loop on level L of problem `prob`
+ * (Remark 3.5, matrix form): *met = 1 if L >= 2 and
+ * ||Y_L||_F < (sqrt(R) + 1) eps_abs / sqrt(2), else 0; *mean_norm (may be
+ * NULL) = ||Y_L||_F.  Synchronises the plan's stream. */
+MLMC_API mlmc_status mlmc_bias_test(mlmc_plan_t* plan, int32_t prob, int32_t L, double eps_abs, int32_t* met,
+                                    double* mean_norm);
+
 /* Yhat of the current statistics without new samples: yhat_dev as above. */
 MLMC_API mlmc_status mlmc_telescoping_sum(mlmc_plan_t* plan, double* yhat_dev);
 
@@ -292,26 +333,31 @@ MLMC_API mlmc_status mlmc_telescoping_sum(mlmc_plan_t* plan, double* yhat_dev);
  * and arithmetic as mlmc_level_stats, reading the caller's row-major
  * parameters in place (problem->M_dev etc.; dtype F64 with precision FP64,
  * or F32 with FP32; other precisions: MLMC_ERR_UNSUPPORTED).  Writes (does
- * not accumulate) sum_dev (m x p FP64, device) = sum_s D_s and *sumsq_dev
- * (one FP64, device) = sum_s ||D_s||_F^2; count = 0 writes zeros.  Only
- * options->c0, ratio and precision are read.  Enqueued on `stream`
- * (cudaStream_t, NULL = legacy default stream).
+ * not accumulate) sum_dev (m x p FP64, device) = sum_s D_s and *M2_dev
+ * (one FP64, device) = sum_s ||D_s - mean||_F^2 (Welford within chunks of 8
+ * sample ids, Chan's update across them); count = 0 writes zeros.  Of the
+ * options, c0, ratio and precision are read, and f and sampling must be
+ * MLMC_F_IDENTITY and MLMC_XI_UNIFORM (else MLMC_ERR_UNSUPPORTED).  Enqueued
+ * on `stream` (cudaStream_t, NULL = legacy default stream).
  * Memory: calls no cudaMalloc, cudaFree or allocating library routine.  Its
  * scratch is a fixed 4 MiB array in the library's device image, present on
  * every GPU that loads the library until the process exits.  A problem is
  * accepted only if one chunk of partials fits: m*p*(8 for FP64, 4 for FP32)
- * + 8*ceil(m/64)*ceil(p/64) <= 4 MiB (for FP64, about m*p <= 520000);
- * larger sizes return MLMC_ERR_INVALID_ARG with a message.
+ * + 8*ceil(m/64)*ceil(p/64) + 8*ceil(m*p/256), each part rounded up to 256
+ * bytes, <= 4 MiB (for FP64, about m*p <= 500000); larger sizes return
+ * MLMC_ERR_INVALID_ARG with a message.
  * Set-up: the first call on each device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture starts.
+ * before any stream capture starts.  The address is kept for the life of the
+ * process; after cudaDeviceReset (or another teardown of the device's primary
+ * context) do not call this entry point again in that process.
  * Concurrency: all calls share the one array and each call overwrites it, so
  * calls whose GPU work overlaps (different streams or threads without
  * ordering) race and give wrong results; order them on one stream or with
  * events. */
 MLMC_API mlmc_status mlmc_level_stats_noalloc(const mlmc_problem* problem, const mlmc_options* options,
                                               int32_t level, uint64_t sample_begin, uint64_t count,
-                                              double* sum_dev, double* sumsq_dev, void* stream);
+                                              double* sum_dev, double* M2_dev, void* stream);
 
 /* ---- reparameterised adjoint ---------------------------------------------------------- */
 
@@ -400,6 +446,15 @@ MLMC_API mlmc_status mlmc_debug_bounded_wait(mlmc_plan_t* plan, int64_t timeout_
  * synchronises it; allocates 1 KiB of device memory for the duration of the call.  Returns
  * MLMC_ERR_INVALID_ARG for a null output pointer, MLMC_ERR_CUDA on a CUDA error. */
 MLMC_API mlmc_status mlmc_measure_generation_rate(void* cuda_stream, double* entries_per_s);
+
+/* Measurement (no counterpart in the paper): arithmetic throughput of this GPU, the denominators
+ * of the ALU rooflines.  ops_per_s (host array of 4) receives operations per second of
+ * [0] FP32 fused multiply-add, [1] FP64 fused multiply-add, [2] INT32 multiply-add and
+ * [3] special-function sine (sin.approx), each from 8 independent dependency chains per thread
+ * at full occupancy (best of three launches after a warm-up; FLOP/s = 2 x FMA/s).  Runs on
+ * `cuda_stream` and synchronises it; allocates 1 KiB of device memory for the call.  Returns
+ * MLMC_ERR_INVALID_ARG for a null output pointer, MLMC_ERR_CUDA on a CUDA error. */
+MLMC_API mlmc_status mlmc_measure_peaks(void* cuda_stream, double* ops_per_s);
 
 #ifdef __cplusplus
 }

@@ -94,6 +94,9 @@ def lib() -> ctypes.CDLL:
             "mlmc_get_level_stats": [P, I32, I32, P, P, P],
             "mlmc_get_level_state": [P, I32, I32, P, P, P],
             "mlmc_set_level_state": [P, I32, I32, U64, P, D],
+            "mlmc_merge_level_state": [P, I32, I32, U64, P, D],
+            "mlmc_allocate_levels": [P, I32, I32, D, P],
+            "mlmc_bias_test": [P, I32, I32, D, P, P],
             "mlmc_reset_level_stats": [P, I32, I32],
             "mlmc_estimate": [P, P, P, P],
             "mlmc_telescoping_sum": [P, P],
@@ -107,6 +110,7 @@ def lib() -> ctypes.CDLL:
             "mlmc_debug_sample": [P, I32, I32, U64, P],
             "mlmc_debug_bounded_wait": [P, I64],
             "mlmc_measure_generation_rate": [P, ctypes.POINTER(ctypes.c_double)],
+            "mlmc_measure_peaks": [P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -255,6 +259,7 @@ class Plan:
         return N.value, mean, M2.value
 
     def get_level_state(self, prob: int, level: int):
+        """(N, sum of D (m x p FP64 CUDA tensor), M2 = sum_s ||D_s - mean||_F^2)."""
         m, _, p = self.shapes[prob]
         s = self._out(m, p)
         N = ctypes.c_uint64()
@@ -263,9 +268,19 @@ class Plan:
                "mlmc_get_level_state")
         return N.value, s, q.value
 
-    def set_level_state(self, prob: int, level: int, N: int, sum_dev: torch.Tensor, sumsq: float):
-        _check(lib().mlmc_set_level_state(self._h, prob, level, N, _ptr(sum_dev.contiguous()), sumsq),
+    def set_level_state(self, prob: int, level: int, N: int, sum_dev: torch.Tensor, M2: float):
+        _check(lib().mlmc_set_level_state(self._h, prob, level, N, _ptr(self._dev_f64(sum_dev)), float(M2)),
                "mlmc_set_level_state")
+
+    def merge_level_state(self, prob: int, level: int, N: int, sum_dev: torch.Tensor, M2: float):
+        """Fold another (N, sum, M2) of the same level into the held one (Chan's update, in the library)."""
+        _check(lib().mlmc_merge_level_state(self._h, prob, level, N, _ptr(self._dev_f64(sum_dev)), float(M2)),
+               "mlmc_merge_level_state")
+
+    def _dev_f64(self, t: torch.Tensor) -> torch.Tensor:
+        t = t.to(device=self.device, dtype=torch.float64).contiguous()
+        self._keep = t   # alive until the (synchronous) call has used it
+        return t
 
     def reset(self, prob: int, level: int = -1):
         _check(lib().mlmc_reset_level_stats(self._h, prob, level), "mlmc_reset_level_stats")
@@ -292,6 +307,20 @@ class Plan:
         out = (ctypes.c_int64 * (nprob * MAX_LEVELS))()
         _check(lib().mlmc_allocate(self._h, eps, out), "mlmc_allocate")
         return [list(out[q * MAX_LEVELS:q * MAX_LEVELS + self.levels[q] + 1]) for q in range(nprob)]
+
+    def allocate_levels(self, prob: int, L: int, eps_abs: float):
+        """N_l of levels 0..L of one problem (Remark 3.6, one round of Alg. 2)."""
+        out = (ctypes.c_int64 * (L + 1))()
+        _check(lib().mlmc_allocate_levels(self._h, prob, L, float(eps_abs), out), "mlmc_allocate_levels")
+        return list(out)
+
+    def bias_test(self, prob: int, L: int, eps_abs: float):
+        """(met, ||Y_L||_F): Alg. 2's stopping test on level L (Remark 3.5)."""
+        met = ctypes.c_int32()
+        nrm = ctypes.c_double()
+        _check(lib().mlmc_bias_test(self._h, prob, L, float(eps_abs), ctypes.byref(met), ctypes.byref(nrm)),
+               "mlmc_bias_test")
+        return bool(met.value), nrm.value
 
     def launch_count(self) -> int:
         c = ctypes.c_uint64()
@@ -381,3 +410,12 @@ def generation_rate(stream=None) -> float:
     _check(lib().mlmc_measure_generation_rate(_stream_handle(stream), ctypes.byref(out)),
            "mlmc_measure_generation_rate")
     return out.value
+
+
+def measure_peaks(stream=None) -> dict:
+    """Measured operations per second of this GPU (mlmc_measure_peaks): FP32 and FP64 FLOP/s
+    (2 per fused multiply-add), INT32 multiply-adds/s and special-function sines/s."""
+    out = (ctypes.c_double * 4)()
+    _check(lib().mlmc_measure_peaks(_stream_handle(stream), out), "mlmc_measure_peaks")
+    return {"fp32_flops": 2.0 * out[0], "fp64_flops": 2.0 * out[1], "int32_imad_per_s": out[2],
+            "mufu_sin_per_s": out[3]}

@@ -62,7 +62,7 @@ struct ProblemState {
     void* PAB = nullptr;   // row k: [(M_ik, S_ik) for i < m_pad | (M'_kj, S'_kj) for j < p_pad]
     int64_t ld = 0;        // elements per row of PAB
     double* sum = nullptr;    // (L+1) x m x p
-    double* sumsq = nullptr;  // (L+1)
+    double* M2 = nullptr;     // (L+1): sum over the level's samples of ||D - mean||_F^2
     LevelCounts N{};
     int64_t Nl_est[MLMC_MAX_LEVELS] = {};
     bool prefix[MLMC_MAX_LEVELS];   // level l holds exactly the samples 0 .. N_l - 1
@@ -90,8 +90,9 @@ struct mlmc_plan_s {
     void* partial_sum = nullptr;
     double* partial_q = nullptr;
     double* dbg_sum = nullptr;    // one level's state for debug_sample
-    double* dbg_sumsq = nullptr;
-    double* M2_dev = nullptr;     // MLMC_MAX_LEVELS scratch for finalize
+    double* dbg_M2 = nullptr;
+    double* chan = nullptr;       // between-chunk terms of a merge (merge_groups(m p) of the largest problem)
+    double* ext_q = nullptr;      // one M2 handed to mlmc_merge_level_state
     int* err_flag = nullptr;      // set by kernels whose bounded waits give up
     int num_sms = 1;
     uint64_t timeout_ns = 2000000000ull;
@@ -107,6 +108,7 @@ struct mlmc_plan_s {
     int batch_grid = 0;
     float* batch_partial = nullptr;
     double* batch_q = nullptr;
+    double* batch_chan = nullptr;   // between-chunk terms of one wave's merges
     unsigned char* batch_dev = nullptr;    // tables of kBatchMaxWaves waves
     unsigned char* batch_host = nullptr;   // pinned staging of the same
     cudaEvent_t batch_copied = nullptr;    // recorded after the last table upload
@@ -190,6 +192,7 @@ uint2 key(uint32_t seed, uint32_t pid) { return make_uint2(seed, pid); }
 TcTile decode_tile(int32_t id)
 {
     if (id / 1000 == 3) return TcTile{1, id % 1000, 128, 1};
+    if (id / 1000 == 4) return TcTile{1, id % 1000, 128, 2};   // pair with 16 generator warps
     TcTile t{id / 1000, id % 1000, 128 * (id / 1000), 0};
     return t;
 }
@@ -197,7 +200,7 @@ TcTile decode_tile(int32_t id)
 int32_t encode_tile(const TcTile& t)
 {
     if (t.mh <= 0) return 0;
-    return t.pair ? 3000 + t.bn : 1000 * t.mh + t.bn;
+    return t.pair ? (t.pair == 2 ? 4000 : 3000) + t.bn : 1000 * t.mh + t.bn;
 }
 
 const int32_t kTileIds[8] = {1032, 1064, 1128, 1256, 2032, 2064, 2128, 2256};
@@ -217,7 +220,7 @@ mlmc_status validate(const mlmc_problem* problems, int32_t nprob, const mlmc_opt
     if (o->timeout_ns < 0) return fail(MLMC_ERR_INVALID_ARG, "timeout_ns must be >= 0");
     if (o->tile_override != 0 && !tc_tile_valid(decode_tile(o->tile_override), o->precision == MLMC_FP8_E4M3 ? 1 : 0))
         return fail(MLMC_ERR_INVALID_ARG, "tile_override %d is not a tile id of this precision (1032 .. 2256; "
-                    "E4M3: 1032 1064 1128 2032 2064; pairs 3256)", o->tile_override);
+                    "E4M3: 1032 1064 1128 2032 2064; pairs 3256, 4256)", o->tile_override);
     if (o->adjoint_batch_log2 < 0 || o->adjoint_batch_log2 > 40)
         return fail(MLMC_ERR_INVALID_ARG, "adjoint_batch_log2 must be in [0, 40]");
     if (o->f != MLMC_F_IDENTITY && o->f != MLMC_F_ABS_STEP) return fail(MLMC_ERR_INVALID_ARG, "unknown f %d", o->f);
@@ -254,7 +257,7 @@ void free_plan(mlmc_plan_t* plan)
     for (auto& ps : plan->probs) {
         cudaFree(ps.PAB);
         cudaFree(ps.sum);
-        cudaFree(ps.sumsq);
+        cudaFree(ps.M2);
         cudaFree(ps.xi_q);
         cudaFree(ps.xi_Q);
         cudaFree(ps.xi_G);
@@ -262,8 +265,10 @@ void free_plan(mlmc_plan_t* plan)
     cudaFree(plan->partial_sum);
     cudaFree(plan->partial_q);
     cudaFree(plan->dbg_sum);
-    cudaFree(plan->dbg_sumsq);
-    cudaFree(plan->M2_dev);
+    cudaFree(plan->dbg_M2);
+    cudaFree(plan->chan);
+    cudaFree(plan->ext_q);
+    cudaFree(plan->batch_chan);
     cudaFree(plan->err_flag);
     cudaFree(plan->adj_buf);
     cudaFree(plan->batch_partial);
@@ -301,9 +306,10 @@ mlmc_status check_prob_level(mlmc_plan_t* plan, int32_t prob, int32_t level)
     return MLMC_OK;
 }
 
-// Evaluate samples [s0, s0+count) of one level and fold them into (sum, sumsq).
+// Evaluate samples [s0, s0+count) of one level and fold them into (sum, M2), which hold the
+// statistics of n_before samples.
 mlmc_status run_level(mlmc_plan_t* plan, ProblemState& ps, int level, uint64_t s0, uint64_t count, double* sum,
-                      double* sumsq)
+                      double* M2, uint64_t n_before)
 {
     if (count == 0) return MLMC_OK;
     const mlmc_options& o = plan->opt;
@@ -359,17 +365,25 @@ mlmc_status run_level(mlmc_plan_t* plan, ProblemState& ps, int level, uint64_t s
         cudaError_t err;
         if (tensor_core_precision(o.precision)) {
             prm.maps = ps.maps;
+            prm.pack = tc_pack(ps.tile, tc_format(o), ps.m, c) ? 1 : 0;
+            // f = identity (the only tensor-core f): for l >= 1 the fine and coarse estimates of one
+            // realisation have the same expectation, E[D_l] = 0, so only level 0 needs Welford
+            prm.welford = level == 0 ? 1 : 0;
             TcLaunch tl{plan->err_flag, plan->timeout_ns, static_cast<float>(double(ps.n) / double(c)), plan->num_sms};
             err = launch_level_tc(prm, ps.tile, tc_format(o), tl, plan->stream);
+        } else if (ps.m == 1 && ps.p == 1 && !ps.xi_Q) {
+            err = launch_level_inner(prm, plan->f64, plan->opt.f, plan->stream);   // Sec. 2's inner product
         } else {
             err = plan->f64 ? launch_level_cuda_core_f64(prm, plan->opt.f, plan->stream)
                             : launch_level_cuda_core_f32(prm, plan->opt.f, plan->stream);
         }
         if (check_cuda(plan, err, "level kernel launch") != MLMC_OK) return plan->sticky;
-        plan->launches += 3;  // level kernel, merge of sums, merge of sums of squares
-        err = launch_merge_partials(plan->partial_sum, plan->f64, plan->partial_q, nb, ps.tiles_m * ps.tiles_p,
-                                    ps.m * ps.p, sum, sumsq, plan->stream);
+        plan->launches += 3;  // level kernel, merge of the sums, merge of the M2
+        const ChunkRun run{prm.s_begin, prm.s_end, cb, ch, n_before, nb};
+        err = launch_merge_partials(plan->partial_sum, plan->f64, plan->partial_q, ps.tiles_m * ps.tiles_p,
+                                    ps.m * ps.p, run, sum, M2, plan->chan, plan->stream);
         if (check_cuda(plan, err, "merge kernel launch") != MLMC_OK) return plan->sticky;
+        n_before += prm.s_end - prm.s_begin;
     }
     return MLMC_OK;
 }
@@ -382,6 +396,9 @@ constexpr int kBatchMaxItems = 1 << 20;                 // (job, chunk, tile) un
 constexpr int kBatchMaxWaves = 4;                       // waves per graph launch
 constexpr int kBatchMaxGrid = 4096;
 constexpr int kMergeMaxChunks = 4096;
+// between-chunk terms of one wave's merges: one per 256 entries of each job (the partials of a
+// wave hold at most kBatchPartialBytes / 4 entries), plus one per job for the rounding up
+constexpr size_t kBatchChanEntries = kBatchPartialBytes / 4 / 256 + kBatchMaxJobs;
 
 struct BatchRange {
     int prob, level;
@@ -445,11 +462,19 @@ mlmc_status build_waves(mlmc_plan_t* plan, const std::vector<BatchRange>& ranges
                         std::vector<BatchWave>& waves)
 {
     waves.clear();
-    size_t part_off = 0, q_off = 0;
+    size_t part_off = 0, q_off = 0, chan_off = 0;
     std::vector<int64_t> in_wave;   // prob * MLMC_MAX_LEVELS + level of the open wave's jobs
+    // samples each (problem, level) will hold before its next job runs (jobs run in build order)
+    std::vector<std::pair<int64_t, uint64_t>> held;
+    auto held_before = [&](int64_t lvkey, const ProblemState& ps, int level) -> uint64_t& {
+        for (auto& h : held)
+            if (h.first == lvkey) return h.second;
+        held.emplace_back(lvkey, ps.N.v[level]);
+        return held.back().second;
+    };
     auto open_wave = [&]() {
         waves.emplace_back();
-        part_off = q_off = 0;
+        part_off = q_off = chan_off = 0;
         in_wave.clear();
     };
     open_wave();
@@ -464,6 +489,8 @@ mlmc_status build_waves(mlmc_plan_t* plan, const std::vector<BatchRange>& ranges
         LevelParams base = base_params(plan, ps, r.level);
         base.tiles_m = tm;
         base.tiles_p = tp;
+        base.pack = tc_pack(tile, tc_format(plan->opt), ps.m, base.c) ? 1 : 0;
+        base.welford = r.level == 0 ? 1 : 0;   // E[D_l] = 0 for l >= 1 (f = identity)
         if (ps.batch_maps_tile != encode_tile(tile)) {
             tc_encode_maps(&ps.batch_maps, ps.PAB, ps.n, ps.ld, tc_stage_width_a(tile), tc_stage_width_b(tile));
             ps.batch_maps_tile = encode_tile(tile);
@@ -493,6 +520,12 @@ mlmc_status build_waves(mlmc_plan_t* plan, const std::vector<BatchRange>& ranges
                 continue;
             }
             const uint64_t nb = std::min<uint64_t>(room, last - cb + 1);
+            const size_t groups = size_t(merge_groups(mp));
+            if (chan_off + groups > kBatchChanEntries) {
+                if (w->jobs.empty()) return fail(MLMC_ERR_UNSUPPORTED, "batched wave cannot hold one merge");
+                open_wave();
+                continue;
+            }
             LevelParams prm = base;
             prm.chunk0 = cb;
             prm.nchunks = int(nb);
@@ -502,9 +535,13 @@ mlmc_status build_waves(mlmc_plan_t* plan, const std::vector<BatchRange>& ranges
             prm.partial_q = plan->batch_q + q_off;
             const int job = int(w->jobs.size());
             w->jobs.push_back(prm);
+            uint64_t& before = held_before(lvkey, ps, r.level);
+            const ChunkRun chunks{prm.s_begin, prm.s_end, cb, ch, before, int(nb)};
+            before += prm.s_end - prm.s_begin;
             MergeJob mj{plan->batch_partial + part_off, plan->batch_q + q_off, ps.sum + int64_t(r.level) * mp,
-                        ps.sumsq + r.level, mp, int(nb), tiles};
+                        ps.M2 + r.level, plan->batch_chan + chan_off, mp, chunks, tiles};
             w->merges.push_back(mj);
+            chan_off += groups;
             // items: runs of up to `run` chunks of one tile (fewer, larger items on long ranges)
             const uint64_t run = std::clamp<uint64_t>(nb / 64, 1, 255);
             for (uint64_t cy = 0; cy < nb; cy += run) {
@@ -558,6 +595,8 @@ mlmc_status batch_setup(mlmc_plan_t* plan)
     if (plan->batch_dev) return MLMC_OK;
     cudaError_t err = cudaMalloc(reinterpret_cast<void**>(&plan->batch_partial), kBatchPartialBytes + 256);
     if (err == cudaSuccess) err = cudaMalloc(reinterpret_cast<void**>(&plan->batch_q), sizeof(double) * kBatchMaxItems);
+    if (err == cudaSuccess)
+        err = cudaMalloc(reinterpret_cast<void**>(&plan->batch_chan), sizeof(double) * kBatchChanEntries);
     const size_t bytes = WaveLayout().stride * kBatchMaxWaves;
     if (err == cudaSuccess) err = cudaMalloc(reinterpret_cast<void**>(&plan->batch_dev), bytes);
     if (err == cudaSuccess) err = cudaMallocHost(reinterpret_cast<void**>(&plan->batch_host), bytes);
@@ -733,7 +772,7 @@ mlmc_status run_batch(mlmc_plan_t* plan, const std::vector<BatchRange>& ranges)
         }
         cudaError_t err = cudaGraphLaunch(plan->batch_exec, plan->stream);
         if (check_cuda(plan, err, "batched graph launch") != MLMC_OK) return plan->sticky;
-        plan->launches += 2 * cnt;
+        plan->launches += 3 * cnt;   // per wave: level kernel and the two merges
     }
     for (const BatchRange& r : ranges) {
         if (r.count == 0) continue;
@@ -744,19 +783,66 @@ mlmc_status run_batch(mlmc_plan_t* plan, const std::vector<BatchRange>& ranges)
     return MLMC_OK;
 }
 
-// M2 of levels [0, count) of a problem into host array (synchronises).
+// M2 of levels [first, first + count) of a problem into a host array (synchronises).
 mlmc_status level_M2(mlmc_plan_t* plan, ProblemState& ps, int first, int count, double* M2_host)
 {
-    const int64_t mp = ps.m * ps.p;
-    cudaError_t err = launch_finalize(ps.sum + int64_t(first) * mp, ps.sumsq + first, ps.N, first, count, mp,
-                                      nullptr, plan->M2_dev, plan->stream);
-    if (check_cuda(plan, err, "finalize launch") != MLMC_OK) return plan->sticky;
-    plan->launches += 1;
-    err = cudaMemcpyAsync(M2_host, plan->M2_dev, sizeof(double) * size_t(count), cudaMemcpyDeviceToHost, plan->stream);
+    cudaError_t err = cudaMemcpyAsync(M2_host, ps.M2 + first, sizeof(double) * size_t(count), cudaMemcpyDeviceToHost,
+                                      plan->stream);
     if (check_cuda(plan, err, "copy M2") != MLMC_OK) return plan->sticky;
     err = cudaStreamSynchronize(plan->stream);
     if (check_cuda(plan, err, "stream synchronize") != MLMC_OK) return plan->sticky;
     return check_device_flag(plan);
+}
+
+// ||Y_l||_F: the norm of level l's mean, read back from its FP64 sum (synchronises).
+mlmc_status level_mean_norm(mlmc_plan_t* plan, const ProblemState& ps, int l, double* out)
+{
+    const int64_t mp = ps.m * ps.p;
+    std::vector<double> sums(static_cast<size_t>(mp));
+    cudaError_t err = cudaMemcpyAsync(sums.data(), ps.sum + int64_t(l) * mp, sizeof(double) * size_t(mp),
+                                      cudaMemcpyDeviceToHost, plan->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(plan->stream);
+    if (check_cuda(plan, err, "read level mean") != MLMC_OK) return plan->sticky;
+    double nrm = 0.0;
+    for (double v : sums) nrm += v * v;
+    *out = ps.N.v[l] > 0 ? std::sqrt(nrm) / double(ps.N.v[l]) : 0.0;
+    return MLMC_OK;
+}
+
+// Remark 3.6 over levels 0..L of one problem: V_l = M2_l / (N_l - 1), C_0 = c_0,
+// C_l = c_l + c_{l-1}, N_l = max(pilot, ceil(nl_scale 2 eps^-2 sqrt(V_l / C_l) sum_j sqrt(V_j C_j))).
+mlmc_status allocation(mlmc_plan_t* plan, ProblemState& ps, int q, int L, double eps, int64_t* Nl)
+{
+    const mlmc_options& o = plan->opt;
+    for (int l = 0; l <= L; ++l)
+        if (ps.N.v[l] < 2) return fail(MLMC_ERR_STATE, "problem %d level %d holds fewer than 2 samples", q, l);
+    double M2[MLMC_MAX_LEVELS], V[MLMC_MAX_LEVELS], C[MLMC_MAX_LEVELS], root_sum = 0.0;
+    mlmc_status st = level_M2(plan, ps, 0, L + 1, M2);
+    if (st != MLMC_OK) return st;
+    for (int l = 0; l <= L; ++l) {
+        V[l] = std::max(0.0, M2[l] / double(ps.N.v[l] - 1));
+        C[l] = level_cost(o, l);
+        if (!std::isfinite(V[l])) return fail(MLMC_ERR_NUMERIC, "problem %d level %d: V_l not finite", q, l);
+        root_sum += std::sqrt(V[l] * C[l]);
+    }
+    for (int l = 0; l <= L; ++l) {
+        const double target = o.nl_scale * 2.0 / (eps * eps) * std::sqrt(V[l] / C[l]) * root_sum;
+        if (!(target < 9.0e18)) return fail(MLMC_ERR_NUMERIC, "allocated N_l overflows");
+        Nl[l] = std::max<int64_t>(int64_t(std::ceil(target)), o.pilot_n);
+    }
+    return MLMC_OK;
+}
+
+// Remark 3.5 as Alg. 2 uses it: level L (>= 2) meets the bias bound when
+// ||Y_L||_F < (sqrt(R) + 1) eps / sqrt(2).
+mlmc_status bias_test(mlmc_plan_t* plan, ProblemState& ps, int L, double eps, bool* met, double* norm)
+{
+    double nrm = 0.0;
+    mlmc_status st = level_mean_norm(plan, ps, L, &nrm);
+    if (st != MLMC_OK) return st;
+    *norm = nrm;
+    *met = L >= 2 && nrm < (std::sqrt(double(plan->opt.ratio)) + 1.0) * eps / std::sqrt(2.0);
+    return MLMC_OK;
 }
 
 }  // namespace
@@ -824,9 +910,9 @@ mlmc_status mlmc_plan(const mlmc_problem* problems, int32_t nprob, const mlmc_op
         ps.ld = 2 * (ps.m_pad + ps.p_pad);
         if (cudaMalloc(&ps.PAB, size_t(ps.n) * size_t(ps.ld) * plan->elem) != cudaSuccess) return oom("parameters");
         if (cudaMalloc(&ps.sum, sizeof(double) * mp * size_t(ps.L + 1)) != cudaSuccess) return oom("level sums");
-        if (cudaMalloc(&ps.sumsq, sizeof(double) * size_t(ps.L + 1)) != cudaSuccess) return oom("level sumsq");
+        if (cudaMalloc(&ps.M2, sizeof(double) * size_t(ps.L + 1)) != cudaSuccess) return oom("level M2");
         cudaMemsetAsync(ps.sum, 0, sizeof(double) * mp * size_t(ps.L + 1), plan->stream);
-        cudaMemsetAsync(ps.sumsq, 0, sizeof(double) * size_t(ps.L + 1), plan->stream);
+        cudaMemsetAsync(ps.M2, 0, sizeof(double) * size_t(ps.L + 1), plan->stream);
         cudaError_t err = launch_layout_A(ps.desc.M_dev, ps.desc.S_dev, ps.desc.dtype, ps.desc.ldA, ps.m, ps.n,
                                           ps.m_pad, ps.PAB, ps.ld, plan->f64, plan->stream);
         if (err == cudaSuccess)
@@ -869,9 +955,11 @@ mlmc_status mlmc_plan(const mlmc_problem* problems, int32_t nprob, const mlmc_op
         return oom("chunk sums of squares");
     if (cudaMalloc(reinterpret_cast<void**>(&plan->dbg_sum), sizeof(double) * max_mp) != cudaSuccess)
         return oom("debug state");
-    if (cudaMalloc(reinterpret_cast<void**>(&plan->dbg_sumsq), sizeof(double)) != cudaSuccess) return oom("debug state");
-    if (cudaMalloc(reinterpret_cast<void**>(&plan->M2_dev), sizeof(double) * MLMC_MAX_LEVELS) != cudaSuccess)
-        return oom("M2 scratch");
+    if (cudaMalloc(reinterpret_cast<void**>(&plan->dbg_M2), sizeof(double)) != cudaSuccess) return oom("debug state");
+    if (cudaMalloc(reinterpret_cast<void**>(&plan->chan), sizeof(double) * size_t(merge_groups(int64_t(max_mp)))) !=
+        cudaSuccess)
+        return oom("merge scratch");
+    if (cudaMalloc(reinterpret_cast<void**>(&plan->ext_q), sizeof(double)) != cudaSuccess) return oom("merge scratch");
     if (cudaMalloc(reinterpret_cast<void**>(&plan->err_flag), sizeof(int)) != cudaSuccess) return oom("error flag");
     cudaMemsetAsync(plan->err_flag, 0, sizeof(int), plan->stream);
     if (cudaDeviceGetAttribute(&plan->num_sms, cudaDevAttrMultiProcessorCount, plan->device) != cudaSuccess)
@@ -918,7 +1006,7 @@ mlmc_status mlmc_level_stats(mlmc_plan_t* plan, int32_t prob, int32_t level, uin
     ProblemState& ps = plan->probs[size_t(prob)];
     const int64_t mp = ps.m * ps.p;
     const bool continues = sample_begin == ps.N.v[level];
-    st = run_level(plan, ps, level, sample_begin, count, ps.sum + int64_t(level) * mp, ps.sumsq + level);
+    st = run_level(plan, ps, level, sample_begin, count, ps.sum + int64_t(level) * mp, ps.M2 + level, ps.N.v[level]);
     if (st == MLMC_OK) {
         ps.N.v[level] += count;
         ps.prefix[level] = ps.prefix[level] && continues;
@@ -946,7 +1034,8 @@ mlmc_status mlmc_level_stats_batch(mlmc_plan_t* plan, const mlmc_range* ranges, 
             ProblemState& ps = plan->probs[size_t(r.prob)];
             const int64_t mp = ps.m * ps.p;
             const bool continues = r.s0 == ps.N.v[r.level];
-            st = run_level(plan, ps, r.level, r.s0, r.count, ps.sum + int64_t(r.level) * mp, ps.sumsq + r.level);
+            st = run_level(plan, ps, r.level, r.s0, r.count, ps.sum + int64_t(r.level) * mp, ps.M2 + r.level,
+                           ps.N.v[r.level]);
             if (st != MLMC_OK) return st;
             ps.N.v[r.level] += r.count;
             ps.prefix[r.level] = ps.prefix[r.level] && continues;
@@ -974,15 +1063,13 @@ mlmc_status mlmc_get_level_stats(mlmc_plan_t* plan, int32_t prob, int32_t level,
     DeviceGuard g(plan->device);
     ProblemState& ps = plan->probs[size_t(prob)];
     const int64_t mp = ps.m * ps.p;
-    cudaError_t err = launch_finalize(ps.sum + int64_t(level) * mp, ps.sumsq + level, ps.N, level, 1, mp, mean_dev,
-                                      plan->M2_dev, plan->stream);
-    if (check_cuda(plan, err, "finalize launch") != MLMC_OK) return plan->sticky;
-    plan->launches += 1;
+    if (mean_dev) {
+        cudaError_t err = launch_finalize(ps.sum + int64_t(level) * mp, ps.N, level, 1, mp, mean_dev, plan->stream);
+        if (check_cuda(plan, err, "finalize launch") != MLMC_OK) return plan->sticky;
+        plan->launches += 1;
+    }
     double m2 = 0.0;
-    err = cudaMemcpyAsync(&m2, plan->M2_dev, sizeof(double), cudaMemcpyDeviceToHost, plan->stream);
-    if (check_cuda(plan, err, "copy M2") != MLMC_OK) return plan->sticky;
-    if (check_cuda(plan, cudaStreamSynchronize(plan->stream), "stream synchronize") != MLMC_OK) return plan->sticky;
-    if ((st = check_device_flag(plan)) != MLMC_OK) return st;
+    if ((st = level_M2(plan, ps, level, 1, &m2)) != MLMC_OK) return st;
     if (N) *N = ps.N.v[level];
     if (M2) *M2 = m2;
     if (!std::isfinite(m2)) return fail(MLMC_ERR_NUMERIC, "level %d: non-finite second moment", level);
@@ -990,7 +1077,7 @@ mlmc_status mlmc_get_level_stats(mlmc_plan_t* plan, int32_t prob, int32_t level,
 }
 
 mlmc_status mlmc_get_level_state(mlmc_plan_t* plan, int32_t prob, int32_t level, uint64_t* N, double* sum_dev,
-                                 double* sumsq)
+                                 double* M2)
 {
     mlmc_status st = enter(plan);
     if (st != MLMC_OK) return st;
@@ -1004,33 +1091,62 @@ mlmc_status mlmc_get_level_state(mlmc_plan_t* plan, int32_t prob, int32_t level,
                               cudaMemcpyDeviceToDevice, plan->stream);
     double q = 0.0;
     if (err == cudaSuccess)
-        err = cudaMemcpyAsync(&q, ps.sumsq + level, sizeof(double), cudaMemcpyDeviceToHost, plan->stream);
+        err = cudaMemcpyAsync(&q, ps.M2 + level, sizeof(double), cudaMemcpyDeviceToHost, plan->stream);
     if (err == cudaSuccess) err = cudaStreamSynchronize(plan->stream);
     if (check_cuda(plan, err, "read level state") != MLMC_OK) return plan->sticky;
     if ((st = check_device_flag(plan)) != MLMC_OK) return st;
     if (N) *N = ps.N.v[level];
-    if (sumsq) *sumsq = q;
+    if (M2) *M2 = q;
     return MLMC_OK;
 }
 
 mlmc_status mlmc_set_level_state(mlmc_plan_t* plan, int32_t prob, int32_t level, uint64_t N, const double* sum_dev,
-                                 double sumsq)
+                                 double M2)
 {
     mlmc_status st = enter(plan);
     if (st != MLMC_OK) return st;
     if ((st = check_prob_level(plan, prob, level)) != MLMC_OK) return st;
     if (!sum_dev) return fail(MLMC_ERR_INVALID_ARG, "null sum_dev");
+    if (!(M2 >= 0.0) || !std::isfinite(M2)) return fail(MLMC_ERR_INVALID_ARG, "M2 must be finite and >= 0");
     DeviceGuard g(plan->device);
     ProblemState& ps = plan->probs[size_t(prob)];
     const int64_t mp = ps.m * ps.p;
     cudaError_t err = cudaMemcpyAsync(ps.sum + int64_t(level) * mp, sum_dev, sizeof(double) * size_t(mp),
                                       cudaMemcpyDeviceToDevice, plan->stream);
     if (err == cudaSuccess)
-        err = cudaMemcpyAsync(ps.sumsq + level, &sumsq, sizeof(double), cudaMemcpyHostToDevice, plan->stream);
+        err = cudaMemcpyAsync(ps.M2 + level, &M2, sizeof(double), cudaMemcpyHostToDevice, plan->stream);
     if (err == cudaSuccess) err = cudaStreamSynchronize(plan->stream);
     if (check_cuda(plan, err, "write level state") != MLMC_OK) return plan->sticky;
     ps.N.v[level] = N;
     ps.prefix[level] = true;
+    ps.has_estimate = false;
+    return MLMC_OK;
+}
+
+mlmc_status mlmc_merge_level_state(mlmc_plan_t* plan, int32_t prob, int32_t level, uint64_t N, const double* sum_dev,
+                                   double M2)
+{
+    mlmc_status st = enter(plan);
+    if (st != MLMC_OK) return st;
+    if ((st = check_prob_level(plan, prob, level)) != MLMC_OK) return st;
+    if (N == 0) return MLMC_OK;
+    if (!sum_dev) return fail(MLMC_ERR_INVALID_ARG, "null sum_dev");
+    if (!(M2 >= 0.0) || !std::isfinite(M2)) return fail(MLMC_ERR_INVALID_ARG, "M2 must be finite and >= 0");
+    DeviceGuard g(plan->device);
+    ProblemState& ps = plan->probs[size_t(prob)];
+    const int64_t mp = ps.m * ps.p;
+    if (ps.N.v[level] + N < N) return fail(MLMC_ERR_INVALID_ARG, "sample count overflows");
+    // the other state is one chunk of N samples with its own sum and M2: the merge of the level
+    // kernels' chunks, with FP64 partials
+    cudaError_t err = cudaMemcpyAsync(plan->ext_q, &M2, sizeof(double), cudaMemcpyHostToDevice, plan->stream);
+    const ChunkRun run{0, N, 0, N, ps.N.v[level], 1};
+    if (err == cudaSuccess)
+        err = launch_merge_partials(sum_dev, true, plan->ext_q, 1, mp, run, ps.sum + int64_t(level) * mp,
+                                    ps.M2 + level, plan->chan, plan->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(plan->stream);
+    if (check_cuda(plan, err, "merge level state") != MLMC_OK) return plan->sticky;
+    plan->launches += 2;
+    ps.N.v[level] += N;
     ps.has_estimate = false;
     return MLMC_OK;
 }
@@ -1048,7 +1164,7 @@ mlmc_status mlmc_reset_level_stats(mlmc_plan_t* plan, int32_t prob, int32_t leve
     const int cnt = level < 0 ? ps.L + 1 : 1;
     cudaError_t err = cudaMemsetAsync(ps.sum + int64_t(first) * mp, 0, sizeof(double) * size_t(mp) * size_t(cnt),
                                       plan->stream);
-    if (err == cudaSuccess) err = cudaMemsetAsync(ps.sumsq + first, 0, sizeof(double) * size_t(cnt), plan->stream);
+    if (err == cudaSuccess) err = cudaMemsetAsync(ps.M2 + first, 0, sizeof(double) * size_t(cnt), plan->stream);
     if (check_cuda(plan, err, "reset level state") != MLMC_OK) return plan->sticky;
     for (int l = first; l < first + cnt; ++l) {
         ps.N.v[l] = 0;
@@ -1081,28 +1197,42 @@ mlmc_status mlmc_allocate(mlmc_plan_t* plan, const double* eps_abs, int64_t* Nl)
     if (st != MLMC_OK) return st;
     if (!eps_abs || !Nl) return fail(MLMC_ERR_INVALID_ARG, "null eps_abs or Nl");
     DeviceGuard g(plan->device);
-    const mlmc_options& o = plan->opt;
     for (size_t q = 0; q < plan->probs.size(); ++q) {
         ProblemState& ps = plan->probs[q];
         if (!(eps_abs[q] > 0.0) || !std::isfinite(eps_abs[q]))
             return fail(MLMC_ERR_INVALID_ARG, "eps_abs[%zu] must be finite and > 0", q);
         int64_t* row = Nl + q * MLMC_MAX_LEVELS;
         std::fill(row, row + MLMC_MAX_LEVELS, int64_t(0));
-        for (int l = 0; l <= ps.L; ++l)
-            if (ps.N.v[l] < 2) return fail(MLMC_ERR_STATE, "problem %zu level %d holds fewer than 2 samples", q, l);
-        double M2[MLMC_MAX_LEVELS], V[MLMC_MAX_LEVELS], C[MLMC_MAX_LEVELS], root_sum = 0.0;
-        if ((st = level_M2(plan, ps, 0, ps.L + 1, M2)) != MLMC_OK) return st;
-        for (int l = 0; l <= ps.L; ++l) {
-            V[l] = std::max(0.0, M2[l] / double(ps.N.v[l] - 1));
-            C[l] = level_cost(o, l);
-            root_sum += std::sqrt(V[l] * C[l]);
-        }
-        for (int l = 0; l <= ps.L; ++l) {
-            const double target = o.nl_scale * 2.0 / (eps_abs[q] * eps_abs[q]) * std::sqrt(V[l] / C[l]) * root_sum;
-            if (!(target < 9.0e18)) return fail(MLMC_ERR_NUMERIC, "allocated N_l overflows");
-            row[l] = std::max<int64_t>(int64_t(std::ceil(target)), o.pilot_n);
-        }
+        if ((st = allocation(plan, ps, int(q), ps.L, eps_abs[q], row)) != MLMC_OK) return st;
     }
+    return MLMC_OK;
+}
+
+mlmc_status mlmc_allocate_levels(mlmc_plan_t* plan, int32_t prob, int32_t L, double eps_abs, int64_t* Nl)
+{
+    mlmc_status st = enter(plan);
+    if (st != MLMC_OK) return st;
+    if (!Nl) return fail(MLMC_ERR_INVALID_ARG, "null Nl");
+    if ((st = check_prob_level(plan, prob, L)) != MLMC_OK) return st;
+    if (!(eps_abs > 0.0) || !std::isfinite(eps_abs)) return fail(MLMC_ERR_INVALID_ARG, "eps_abs must be finite and > 0");
+    DeviceGuard g(plan->device);
+    return allocation(plan, plan->probs[size_t(prob)], prob, L, eps_abs, Nl);
+}
+
+mlmc_status mlmc_bias_test(mlmc_plan_t* plan, int32_t prob, int32_t L, double eps_abs, int32_t* met,
+                           double* mean_norm)
+{
+    mlmc_status st = enter(plan);
+    if (st != MLMC_OK) return st;
+    if (!met) return fail(MLMC_ERR_INVALID_ARG, "null met");
+    if ((st = check_prob_level(plan, prob, L)) != MLMC_OK) return st;
+    if (!(eps_abs > 0.0) || !std::isfinite(eps_abs)) return fail(MLMC_ERR_INVALID_ARG, "eps_abs must be finite and > 0");
+    DeviceGuard g(plan->device);
+    bool ok = false;
+    double nrm = 0.0;
+    if ((st = bias_test(plan, plan->probs[size_t(prob)], L, eps_abs, &ok, &nrm)) != MLMC_OK) return st;
+    *met = ok ? 1 : 0;
+    if (mean_norm) *mean_norm = nrm;
     return MLMC_OK;
 }
 
@@ -1112,25 +1242,6 @@ mlmc_status mlmc_launch_count(const mlmc_plan_t* plan, uint64_t* count)
     *count = plan->launches;
     return MLMC_OK;
 }
-
-namespace {
-
-// ||Y_l||_F: the norm of level l's mean, read back from its FP64 sum.
-mlmc_status level_mean_norm(mlmc_plan_t* plan, const ProblemState& ps, int l, double* out)
-{
-    const int64_t mp = ps.m * ps.p;
-    std::vector<double> sums(static_cast<size_t>(mp));
-    cudaError_t err = cudaMemcpyAsync(sums.data(), ps.sum + int64_t(l) * mp, sizeof(double) * size_t(mp),
-                                      cudaMemcpyDeviceToHost, plan->stream);
-    if (err == cudaSuccess) err = cudaStreamSynchronize(plan->stream);
-    if (check_cuda(plan, err, "read level mean") != MLMC_OK) return plan->sticky;
-    double nrm = 0.0;
-    for (double v : sums) nrm += v * v;
-    *out = ps.N.v[l] > 0 ? std::sqrt(nrm) / double(ps.N.v[l]) : 0.0;
-    return MLMC_OK;
-}
-
-}  // namespace
 
 mlmc_status mlmc_estimate(mlmc_plan_t* plan, const double* eps_abs, double* yhat_dev, mlmc_report* reports)
 {
@@ -1152,7 +1263,7 @@ mlmc_status mlmc_estimate(mlmc_plan_t* plan, const double* eps_abs, double* yhat
             const int64_t mp = ps.m * ps.p;
             const bool continues = r.s0 == ps.N.v[r.level];
             mlmc_status s2 = run_level(plan, ps, r.level, r.s0, r.count, ps.sum + int64_t(r.level) * mp,
-                                       ps.sumsq + r.level);
+                                       ps.M2 + r.level, ps.N.v[r.level]);
             if (s2 != MLMC_OK) return s2;
             ps.N.v[r.level] += r.count;
             ps.prefix[r.level] = ps.prefix[r.level] && continues;
@@ -1182,19 +1293,10 @@ mlmc_status mlmc_estimate(mlmc_plan_t* plan, const double* eps_abs, double* yhat
             if (!running[q]) continue;
             ProblemState& ps = plan->probs[q];
             const int L = Lc[q];
-            double M2[MLMC_MAX_LEVELS];
-            if ((st = level_M2(plan, ps, 0, L + 1, M2)) != MLMC_OK) return st;
-            double V[MLMC_MAX_LEVELS], C[MLMC_MAX_LEVELS], root_sum = 0.0;
+            int64_t Nl[MLMC_MAX_LEVELS];
+            if ((st = allocation(plan, ps, int(q), L, eps_abs[q], Nl)) != MLMC_OK) return set_sticky(plan, st);
             for (int l = 0; l <= L; ++l) {
-                V[l] = std::max(0.0, M2[l] / double(ps.N.v[l] - 1));
-                C[l] = level_cost(o, l);
-                if (!std::isfinite(V[l])) return set_sticky(plan, fail(MLMC_ERR_NUMERIC, "problem %zu level %d: V_l not finite", q, l));
-                root_sum += std::sqrt(V[l] * C[l]);
-            }
-            for (int l = 0; l <= L; ++l) {
-                const double target = o.nl_scale * 2.0 / (eps_abs[q] * eps_abs[q]) * std::sqrt(V[l] / C[l]) * root_sum;
-                if (!(target < 9.0e18)) return set_sticky(plan, fail(MLMC_ERR_NUMERIC, "allocated N_l overflows"));
-                const uint64_t nl = std::max<uint64_t>(uint64_t(std::ceil(target)), pilot);
+                const uint64_t nl = uint64_t(Nl[l]);
                 ps.Nl_est[l] = int64_t(std::max<uint64_t>(nl, ps.N.v[l]));
                 if (nl > ps.N.v[l]) todo.push_back(BatchRange{int(q), l, ps.N.v[l], nl - ps.N.v[l]});
             }
@@ -1208,9 +1310,10 @@ mlmc_status mlmc_estimate(mlmc_plan_t* plan, const double* eps_abs, double* yhat
                 running[q] = 0;
                 continue;
             }
+            bool met = false;
             double nrm = 0.0;
-            if (Lc[q] >= 2 && (st = level_mean_norm(plan, ps, Lc[q], &nrm)) != MLMC_OK) return st;
-            if (Lc[q] >= 2 && nrm < (std::sqrt(double(o.ratio)) + 1.0) * eps_abs[q] / std::sqrt(2.0)) {
+            if (Lc[q] >= 2 && (st = bias_test(plan, ps, Lc[q], eps_abs[q], &met, &nrm)) != MLMC_OK) return st;
+            if (met) {
                 running[q] = 0;
             } else if (Lc[q] == ps.L) {
                 running[q] = 0;
@@ -1491,9 +1594,9 @@ mlmc_status mlmc_debug_sample(mlmc_plan_t* plan, int32_t prob, int32_t level, ui
     ProblemState& ps = plan->probs[size_t(prob)];
     const int64_t mp = ps.m * ps.p;
     cudaError_t err = cudaMemsetAsync(plan->dbg_sum, 0, sizeof(double) * size_t(mp), plan->stream);
-    if (err == cudaSuccess) err = cudaMemsetAsync(plan->dbg_sumsq, 0, sizeof(double), plan->stream);
+    if (err == cudaSuccess) err = cudaMemsetAsync(plan->dbg_M2, 0, sizeof(double), plan->stream);
     if (check_cuda(plan, err, "debug state reset") != MLMC_OK) return plan->sticky;
-    st = run_level(plan, ps, level, sample, 1, plan->dbg_sum, plan->dbg_sumsq);
+    st = run_level(plan, ps, level, sample, 1, plan->dbg_sum, plan->dbg_M2, 0);
     if (st != MLMC_OK) return st;
     err = cudaMemcpyAsync(D_dev, plan->dbg_sum, sizeof(double) * size_t(mp), cudaMemcpyDeviceToDevice, plan->stream);
     return check_cuda(plan, err, "debug sample copy");
@@ -1508,6 +1611,17 @@ mlmc_status mlmc_measure_generation_rate(void* cuda_stream, double* entries_per_
     if (err == cudaSuccess) err = measure_generation_rate(static_cast<cudaStream_t>(cuda_stream), sms, entries_per_s);
     if (err != cudaSuccess)
         return fail(MLMC_ERR_CUDA, "mlmc_measure_generation_rate: %s", cudaGetErrorString(err));
+    return MLMC_OK;
+}
+
+mlmc_status mlmc_measure_peaks(void* cuda_stream, double* ops_per_s)
+{
+    if (!ops_per_s) return fail(MLMC_ERR_INVALID_ARG, "mlmc_measure_peaks: null output");
+    int dev = 0, sms = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (err == cudaSuccess) err = measure_peaks(static_cast<cudaStream_t>(cuda_stream), sms, ops_per_s);
+    if (err != cudaSuccess) return fail(MLMC_ERR_CUDA, "mlmc_measure_peaks: %s", cudaGetErrorString(err));
     return MLMC_OK;
 }
 

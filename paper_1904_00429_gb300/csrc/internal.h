@@ -56,11 +56,15 @@ struct LevelParams {
     int nchunks;
     int tiles_m, tiles_p;
     void* partial_sum;    // [nchunks][m][p] of T
-    double* partial_q;    // [nchunks][tiles_m * tiles_p]
+    double* partial_q;    // [nchunks][tiles_m * tiles_p]: each chunk's M2 over the tile's entries
     const double* xi_q;   // xi** (CUDA-core kernel): weights q (n), or null for the uniform law
     const double* xi_Q;   // their running sums (n)
     double xi_Qtot;       // Q[n-1]
     const int* xi_G;      // guide table of the running sums (n buckets)
+    int pack;             // tensor-core kernel, 128-row tiles: two samples per accumulator (m <= 64, c % 16 == 0)
+    int welford;          // tensor-core kernel: grow each chunk's M2 sample by sample (Welford); 0: levels whose
+                          // mean is zero by construction keep the raw sum of ||D||^2 and subtract ||S||^2 / n
+                          // at the chunk's end (no cancellation when the mean is zero)
     TcMaps maps;          // tensor-core kernel only
 };
 
@@ -74,12 +78,14 @@ struct CudaCoreTile {
 cudaError_t launch_level_cuda_core_f64(const LevelParams& prm, int f, cudaStream_t st);
 cudaError_t launch_level_cuda_core_f32(const LevelParams& prm, int f, cudaStream_t st);
 CudaCoreTile cuda_core_tile(int precision);
+// The inner-product case m = p = 1 (uniform law): one warp per sample, FP64 or FP32.
+cudaError_t launch_level_inner(const LevelParams& prm, bool f64, int f, cudaStream_t st);
 
 // Tensor-core (BF16) level kernel: tile of (128 * mh) rows x bn columns per CTA.
 // Tensor-core tile: mh x 128 rows x bn columns per CTA; pair = 1: a cluster of two CTAs of 128
 // rows each shares one 256 x bn tile (bn = 256), each generating half of B for both.
 struct TcTile {
-    int mh, bn, rows, pair;
+    int mh, bn, rows, pair;   // pair: 0 single CTA, 1 cluster pair, 2 cluster pair with 16 generator warps
 };
 struct TcLaunch {
     int* err_flag;        // device word set to an mlmc_status when a bounded wait gives up
@@ -112,40 +118,63 @@ int tc_stage_width_b(const TcTile& t);
 TcTile tc_tile_for(int64_t m, int64_t p, int q, bool allow_pair);
 bool tc_tile_valid(const TcTile& t, int q);
 cudaError_t launch_level_tc(const LevelParams& prm, const TcTile& tile, int q, const TcLaunch& tl, cudaStream_t st);
+// Whether a launch of `tile` over a level with c slots packs two samples per accumulator.
+bool tc_pack(const TcTile& tile, int q, int64_t m, int64_t c);
 // CTAs of a batched launch for this tile (resident CTAs per SM x SMs); 0 on error.  Also sets
 // the kernel's shared-memory attribute, which launch_level_tc_batch relies on.
 int tc_batch_grid(const TcTile& tile, int q, int num_sms);
 cudaError_t launch_level_tc_batch(const TcBatch& bt, const TcTile& tile, int q, int grid, const TcLaunch& tl,
                                   cudaStream_t st);
 
-// One job of a batched merge: nchunks FP32 chunk partials of an m x p level (mp elements) and
-// their per-tile sums of squares, folded into the level's FP64 sum and sumsq.
+// The chunks of one launch: chunk c (0-based) is absolute chunk chunk0 + c of the level and holds
+// the sample ids [max(s_begin, (chunk0 + c) chunk), min(s_end, (chunk0 + c + 1) chunk)); the
+// level held n_before samples before the first of them.
+struct ChunkRun {
+    uint64_t s_begin, s_end, chunk0, chunk;
+    uint64_t n_before;
+    int nchunks;
+};
+__host__ __device__ inline uint64_t chunk_count(const ChunkRun& r, int c)
+{
+    const uint64_t lo = (r.chunk0 + uint64_t(c)) * r.chunk, hi = lo + r.chunk;
+    const uint64_t a = r.s_begin > lo ? r.s_begin : lo;
+    const uint64_t b = r.s_end < hi ? r.s_end : hi;
+    return b - a;
+}
+
+// Entry groups of the merge (one per kMergeThreads entries): the length of its scratch of
+// between-chunk terms.
+int merge_groups(int64_t mp);
+
+// One job of a batched merge: the FP32 chunk partials of an m x p level (mp entries) and their
+// per-tile M2, folded into the level's FP64 sum and M2; `chan` holds merge_groups(mp) doubles.
 struct MergeJob {
     const float* partial;
     const double* partial_q;
     double* sum;
-    double* sumsq;
+    double* M2;
+    double* chan;
     int64_t mp;
-    int nchunks;   // <= 4096
+    ChunkRun run;   // run.nchunks <= 4096
     int tiles;
 };
 cudaError_t launch_merge_batch(const MergeJob* jobs, const int* njobs_dev, cudaStream_t st);
 
-// Fold the partials of one launch into a level's FP64 state, in chunk order.
-cudaError_t launch_merge_partials(const void* partial_sum, bool partial_f64, const double* partial_q,
-                                  int nchunks, int tiles, int64_t mp, double* level_sum,
-                                  double* level_sumsq, cudaStream_t st);
+// Fold the partials of one launch into a level's FP64 state (sum, M2), in chunk order, with
+// Chan's pairwise update; chan_scratch holds merge_groups(mp) doubles.
+cudaError_t launch_merge_partials(const void* partial_sum, bool partial_f64, const double* partial_q, int tiles,
+                                  int64_t mp, const ChunkRun& run, double* level_sum, double* level_M2,
+                                  double* chan_scratch, cudaStream_t st);
 
 // Sample counts of the levels of one problem, passed by value to kernels.
 struct LevelCounts {
     uint64_t v[MLMC_MAX_LEVELS];
 };
 
-// mean = sum / N and M2 = sumsq - ||sum||^2 / N for `count` levels laid out
-// back to back (sum: count x mp; sumsq, M2: count), N[l] = counts.v[first + l].
-// mean may be null.
-cudaError_t launch_finalize(const double* sum, const double* sumsq, LevelCounts counts, int first, int count,
-                            int64_t mp, double* mean, double* M2, cudaStream_t st);
+// mean = sum / N for `count` levels laid out back to back (sum, mean: count x mp),
+// N[l] = counts.v[first + l].
+cudaError_t launch_finalize(const double* sum, LevelCounts counts, int first, int count, int64_t mp, double* mean,
+                            cudaStream_t st);
 
 // yhat[e] = sum_l sum_l[e] / N_l over levels with N_l > 0.
 cudaError_t launch_telescoping(const double* sum, LevelCounts counts, int levels, int64_t mp, double* yhat,
@@ -212,6 +241,9 @@ cudaError_t adjoint_write_B(const double* src, int64_t n, int64_t p, void* dst, 
 // M + S z, bfloat16) at full occupancy: the ceiling of the reduced-precision level kernels'
 // entry generation.  Synchronises `st`.
 cudaError_t measure_generation_rate(cudaStream_t st, int num_sms, double* entries_per_s);
+// Measured operations per second of FP32 FMA, FP64 FMA, INT32 multiply-add and special-function
+// sine (out[0..3]), from independent dependency chains at full occupancy.  Synchronises `st`.
+cudaError_t measure_peaks(cudaStream_t st, int num_sms, double out[4]);
 
 // xi** of Thm 3.1 from the plan's parameter layout (rows k of PA / PB hold the (M, S) pairs of
 // column k of A / row k of B): q[k] = sqrt(sum_i (M^2 + S^2) * sum_j (M'^2 + S'^2)) in index order

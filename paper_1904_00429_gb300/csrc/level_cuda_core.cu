@@ -11,9 +11,10 @@
 // column/row is contiguous in the plan's layout), generates the entries
 // A = M + S Z and w B = w (M' + S' Z') from Philox into shared memory, and
 // accumulates the outer products in a register tile.  After each sample the
-// tile is added to a running per-chunk sum and its squared Frobenius norm to
-// a running FP64 scalar; at the end of the chunk both are written as
-// partials, which the merge kernel folds into the level in chunk order.
+// tile is added to a running per-chunk sum and the chunk's M2 (sum of squared
+// deviations from the chunk mean, Welford's update) grows in a running FP64
+// scalar; at the end of the chunk both are written as partials, which the
+// merge kernel folds into the level in chunk order.
 // With a targeted function f (F != 0) the fine and coarse estimates are kept apart,
 //     P_l = (n/c_l) sum_t A[:, r_t] B[r_t, :],   P_{l-1} = (n/c_{l-1}) sum_{t coarse} ...,
 // in two register tiles, and D_s = f(P_l) - f(P_{l-1}) entrywise (f(P_0) at level 0).
@@ -114,7 +115,7 @@ level_cuda_core_kernel(const LevelParams prm)
     for (int i = 0; i < RM; ++i)
 #pragma unroll
         for (int j = 0; j < RP; ++j) sum[i][j] = T(0);
-    double q = 0.0;
+    T qw = T(0);   // the chunk's M2 (Welford terms)
 
     for (uint64_t s = sa; s < sb; ++s) {
         const uint32_t lsw = level_sample_word(prm.l, s);
@@ -268,16 +269,27 @@ level_cuda_core_kernel(const LevelParams prm)
                     acc[i][j] = prm.l > 0 ? targeted<F>(sf * acc[i][j]) - targeted<F>(sc * accc[i][j])
                                           : targeted<F>(sf * acc[i][j]);
         }
-        // per-sample statistics: running sum of D and of ||D||_F^2
-        T qs = T(0);
+        // per-sample statistics: the chunk's running sum of D and its M2 by Welford's update;
+        // with k samples before, k (D - mean_k) = k D - sum_k is one fused rounding and
+        // M2 += ||k D - sum_k||^2 / (k (k + 1))
+        const int kprev = static_cast<int>(s - sa);
+        if (kprev > 0) {
+            // in T (FP64 runs at 1/64 of the FP32 rate on this GPU: FP32 plans stay in FP32)
+            const T kf = static_cast<T>(kprev);
+            T qs = T(0);
+#pragma unroll
+            for (int i = 0; i < RM; ++i)
+#pragma unroll
+                for (int j = 0; j < RP; ++j) {
+                    const T dk = fma(kf, acc[i][j], -sum[i][j]);
+                    qs = fma(dk, dk, qs);
+                }
+            qw = fma(qs, T(1) / static_cast<T>(kprev * (kprev + 1)), qw);
+        }
 #pragma unroll
         for (int i = 0; i < RM; ++i)
 #pragma unroll
-            for (int j = 0; j < RP; ++j) {
-                qs = fma(acc[i][j], acc[i][j], qs);
-                sum[i][j] += acc[i][j];
-            }
-        q += static_cast<double>(qs);
+            for (int j = 0; j < RP; ++j) sum[i][j] += acc[i][j];
     }
 
     // chunk partials: the tile's sum of D (rows/cols inside the problem only)
@@ -292,7 +304,8 @@ level_cuda_core_kernel(const LevelParams prm)
             if (gj < prm.p) out[static_cast<int64_t>(gi) * prm.p + gj] = sum[i][j];
         }
     }
-    // and its sum of squares, reduced over the CTA in a fixed order
+    // and its M2, reduced over the CTA in a fixed order
+    double q = static_cast<double>(qw);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) q += __shfl_xor_sync(0xffffffffu, q, off);
     if ((tid & 31) == 0) red_s[tid >> 5] = q;

@@ -15,7 +15,10 @@
 // must order them (one stream, or events).  Host code cannot use the array's
 // name as a device address: the address is fetched once per device with
 // cudaGetSymbolAddress (with that device current) on the first call made on
-// that device, so make that first call before any stream capture begins.
+// that device, so make that first call before any stream capture begins.  The
+// address is kept for the life of the process: after cudaDeviceReset (or any
+// other teardown of the device's primary context) it is stale, and the entry
+// point must not be called again in that process.
 //
 // The arithmetic is the one of the plan's CUDA-core level kernel: the same
 // draws, the same fused weighted rank-c_l update and the same chunk-ordered
@@ -89,7 +92,7 @@ __global__ void __launch_bounds__(256) level_rowmajor_kernel(const LevelParams p
     for (int i = 0; i < RM; ++i)
 #pragma unroll
         for (int j = 0; j < RP; ++j) sum[i][j] = T(0);
-    double q = 0.0;
+    T qw = T(0);   // the chunk's M2 (Welford terms)
 
     for (uint64_t s = sa; s < sb; ++s) {
         const uint32_t lsw = level_sample_word(prm.l, s);
@@ -179,15 +182,25 @@ __global__ void __launch_bounds__(256) level_rowmajor_kernel(const LevelParams p
             }
             __syncthreads();
         }
-        T qs = T(0);
+        // Welford's update of the chunk's M2, as in the plan's level kernel
+        const int kprev = static_cast<int>(s - sa);
+        if (kprev > 0) {
+            // in T (FP64 runs at 1/64 of the FP32 rate on this GPU: FP32 plans stay in FP32)
+            const T kf = static_cast<T>(kprev);
+            T qs = T(0);
+#pragma unroll
+            for (int i = 0; i < RM; ++i)
+#pragma unroll
+                for (int j = 0; j < RP; ++j) {
+                    const T dk = fma(kf, acc[i][j], -sum[i][j]);
+                    qs = fma(dk, dk, qs);
+                }
+            qw = fma(qs, T(1) / static_cast<T>(kprev * (kprev + 1)), qw);
+        }
 #pragma unroll
         for (int i = 0; i < RM; ++i)
 #pragma unroll
-            for (int j = 0; j < RP; ++j) {
-                qs = fma(acc[i][j], acc[i][j], qs);
-                sum[i][j] += acc[i][j];
-            }
-        q += static_cast<double>(qs);
+            for (int j = 0; j < RP; ++j) sum[i][j] += acc[i][j];
     }
     T* out = static_cast<T*>(prm.partial_sum) + static_cast<int64_t>(blockIdx.y) * prm.m * prm.p;
 #pragma unroll
@@ -200,6 +213,7 @@ __global__ void __launch_bounds__(256) level_rowmajor_kernel(const LevelParams p
             if (gj < prm.p) out[static_cast<int64_t>(gi) * prm.p + gj] = sum[i][j];
         }
     }
+    double q = static_cast<double>(qw);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) q += __shfl_xor_sync(0xffffffffu, q, off);
     if ((tid & 31) == 0) red_s[tid >> 5] = q;
@@ -246,9 +260,9 @@ using namespace mlmc;
 
 extern "C" mlmc_status mlmc_level_stats_noalloc(const mlmc_problem* problem, const mlmc_options* options,
                                                  int32_t level, uint64_t sample_begin, uint64_t count,
-                                                 double* sum_dev, double* sumsq_dev, void* stream)
+                                                 double* sum_dev, double* M2_dev, void* stream)
 {
-    if (!problem || !options || !sum_dev || !sumsq_dev) return noalloc_fail(MLMC_ERR_INVALID_ARG, "null argument");
+    if (!problem || !options || !sum_dev || !M2_dev) return noalloc_fail(MLMC_ERR_INVALID_ARG, "null argument");
     const mlmc_problem& pr = *problem;
     const mlmc_options& o = *options;
     const bool f64 = o.precision == MLMC_FP64;
@@ -277,15 +291,17 @@ extern "C" mlmc_status mlmc_level_stats_noalloc(const mlmc_problem* problem, con
     const size_t elem = f64 ? 8 : 4;
     const int64_t mp = pr.m * pr.p;
     const size_t tiles = size_t(tiles_m) * size_t(tiles_p);
-    // bytes of `ch` chunks: their sums of squares (rounded up to 256 bytes), then their partial sums
-    auto need = [&](size_t ch) { return (ch * tiles * 8 + 255) / 256 * 256 + ch * size_t(mp) * elem; };
+    // scratch of `ch` chunks: the merge's between-chunk terms (one double per 256 entries), the
+    // chunks' M2 per tile, then their partial sums, each part starting on a 256-byte boundary
+    const size_t chan_bytes = (size_t(merge_groups(mp)) * 8 + 255) / 256 * 256;
+    auto need = [&](size_t ch) { return chan_bytes + (ch * tiles * 8 + 255) / 256 * 256 + ch * size_t(mp) * elem; };
     size_t chunks = kNoallocScratchBytes / (size_t(mp) * elem + tiles * 8);
     if (chunks > size_t(kNoallocMaxChunks)) chunks = size_t(kNoallocMaxChunks);
     while (chunks > 0 && need(chunks) > kNoallocScratchBytes) --chunks;
     if (chunks == 0)
         return noalloc_fail(MLMC_ERR_INVALID_ARG,
-                            "m*p = %lld too large for the %zu-byte no-alloc scratch (needs m*p*%zu + 8*tiles, "
-                            "rounded up to 256, <= %zu bytes)",
+                            "m*p = %lld too large for the %zu-byte no-alloc scratch (needs m*p*%zu + 8*tiles + "
+                            "8*ceil(m*p/256), each rounded up to 256, <= %zu bytes)",
                             (long long)mp, kNoallocScratchBytes, elem, kNoallocScratchBytes);
     const size_t q_bytes = (chunks * tiles * 8 + 255) / 256 * 256;
 
@@ -295,13 +311,14 @@ extern "C" mlmc_status mlmc_level_stats_noalloc(const mlmc_problem* problem, con
     if (err != cudaSuccess) return noalloc_fail(MLMC_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(err));
     // outputs are written, not accumulated: the in-order fold starts from zero
     err = cudaMemsetAsync(sum_dev, 0, sizeof(double) * size_t(mp), st);
-    if (err == cudaSuccess) err = cudaMemsetAsync(sumsq_dev, 0, sizeof(double), st);
+    if (err == cudaSuccess) err = cudaMemsetAsync(M2_dev, 0, sizeof(double), st);
     if (err != cudaSuccess) return noalloc_fail(MLMC_ERR_CUDA, "clearing outputs: %s", cudaGetErrorString(err));
     if (count == 0) return MLMC_OK;
 
-    // scratch layout: chunk sums of squares first, then the chunk partial sums
-    double* partial_q = static_cast<double*>(scratch);
-    void* partial_sum = static_cast<unsigned char*>(scratch) + q_bytes;
+    // scratch layout: the merge's between-chunk terms, the chunks' M2, then their partial sums
+    double* chan = static_cast<double*>(scratch);
+    double* partial_q = reinterpret_cast<double*>(static_cast<unsigned char*>(scratch) + chan_bytes);
+    void* partial_sum = static_cast<unsigned char*>(scratch) + chan_bytes + q_bytes;
 
     LevelParams prm{};
     prm.n = pr.n;
@@ -338,8 +355,10 @@ extern "C" mlmc_status mlmc_level_stats_noalloc(const mlmc_problem* problem, con
         else
             level_rowmajor_kernel<float><<<grid, 256, 0, st>>>(prm, src);
         err = cudaGetLastError();
+        const ChunkRun run{prm.s_begin, prm.s_end, cb, uint64_t(kChunk), prm.s_begin - sample_begin, nb};
         if (err == cudaSuccess)
-            err = launch_merge_partials(partial_sum, f64, partial_q, nb, tiles_m * tiles_p, mp, sum_dev, sumsq_dev, st);
+            err = launch_merge_partials(partial_sum, f64, partial_q, tiles_m * tiles_p, mp, run, sum_dev, M2_dev,
+                                        chan, st);
         if (err != cudaSuccess) return noalloc_fail(MLMC_ERR_CUDA, "no-alloc level launch: %s", cudaGetErrorString(err));
     }
     return MLMC_OK;

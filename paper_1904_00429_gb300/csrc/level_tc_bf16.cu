@@ -8,21 +8,29 @@
 // (exact); the magnitude n/c_l is applied to the FP32 accumulator.
 //
 // Persistent CTAs of 9 warps walk (chunk of samples, output tile) work items; a sample's slots
-// are processed in sub-blocks of 16 (one MMA K step):
-//   * producer warp (warp 8): draws the 16 slot indices of a sub-block from Philox and issues
-//     TMA bulk copies (cp.async.bulk) of the sampled (M, S) column and (M', S') row pairs of the
-//     tile into a double-buffered staging area, completing on the buffer's mbarrier;
+// are processed in sub-blocks of 16 or 32 slots:
+//   * producer warp (warp 8): draws the sub-block's slot indices from Philox and stages the
+//     sampled (M, S) column pairs of A and (M', S') row pairs of B with TMA row gathers
+//     (cp.async.bulk.tensor ... tile::gather4, four sampled rows of the interleaved parameter
+//     table per instruction; plain cp.async.bulk per row when no tensor map fits the tile) into
+//     a double-buffered staging area, completing on the buffer's mbarrier;
 //   * generator warps (0-7): wait for the staged pairs, generate A = M + S Z and
-//     sigma (M' + S' Z') with Philox and a special-function-unit Box-Muller, round to bf16 and
-//     write them into one 16-slot slice of a 128-byte-swizzled K-major tile (four slices form
-//     one swizzle atom); thread 0 then issues tcgen05.mma (M = 128 per half, N = tile width,
-//     K = 16) into TMEM and commits to the slice's mbarrier;
-//   * after the last sub-block of a sample the generator warps drain the accumulator with
-//     tcgen05.ld, add the sample's D to the chunk partial in global memory (store for the first
-//     sample of the chunk, then red.global.add: each element has one owner thread, so the
-//     order is fixed) and accumulate ||D||_F^2.
+//     sigma (M' + S' Z') with Philox and a special-function-unit Box-Muller, round them to bf16
+//     (or block-quantise them to E4M3) and write them into a swizzled K-major tile; thread 0 then
+//     issues tcgen05.mma into tensor memory and commits to the slice's mbarrier.  Tiles of at most
+//     256 accumulator columns issue each MMA twice: into D (this sample) and into S (the running
+//     sum of the chunk's samples);
+//   * after the last sub-block of a sample the generator warps read D and S back with
+//     tcgen05.ld and grow the chunk's M2 by Welford's update ((k + 1) D - S is k times the
+//     deviation of D from the mean of the k samples before it); S is stored once per chunk as the
+//     chunk partial.  The 256 x 256 single-CTA tile keeps only D in tensor memory and folds each
+//     sample into the chunk partial in global memory (one owner thread per element, read back
+//     and rewritten in sample order).
+// CTA pairs (tile 3256): a cluster of two CTAs shares one 256 x 256 tile, each generating its
+// 128 rows of A and half of B and sending that half to the peer with a shared-to-shared bulk copy.
 // Every mbarrier wait is bounded by a %globaltimer deadline; on timeout the kernel records
-// MLMC_ERR_TIMEOUT and leaves after freeing its tensor memory.
+// MLMC_ERR_TIMEOUT, waits (bounded) for its own copies and MMAs in flight and frees its tensor
+// memory before leaving.
 #include <cstring>
 
 #include <cuda_bf16.h>
@@ -37,22 +45,25 @@
 namespace mlmc {
 namespace {
 
-constexpr int kGenWarps = 8;
-constexpr int kGenThreads = kGenWarps * 32;
-constexpr int kThreads = kGenThreads + 32;  // + producer warp
 constexpr int kGenBarrier = 1;              // named barrier of the generator warps
 constexpr uint64_t kDrainNs = 100000000ull;   // bound on waiting for own copies in flight after an abort
 
 // Operand formats: Q = 0 rounds the generated entries to bfloat16; Q = 1 quantises them to FP8
-// E4M3 with a power-of-two scale per (row of A or column of B, 32-slot block) and feeds the
-// dequantised values (exact in bfloat16) to the same MMA.
+// E4M3 with a power-of-two scale per (row of A or column of B, 32-slot block) and stochastic
+// rounding, and feeds the dequantised values (exact in bfloat16) to the same MMA.
 // P = 1: a cluster pair of CTAs shares one 256-row x BN tile; each CTA owns 128 rows (MH = 1),
 // generates its rows of A and half of the B columns, and copies that half into the peer's B tile
 // (one bulk shared-to-shared copy per sub-block).  Pairs keep four slices of 32 K elements in
 // 64-byte-swizzled tiles (one per slice), so each CTA's half of a slice is one contiguous run and
 // the peer has three sub-blocks of slack before a slice is reused.
-template <int MH, int BN, int Q, int P = 0>
+// W: generator warps, 8 (with 8-slot items) or 16 (pairs only, tile 4256: 4-slot items, so that
+// every one of the 512 generator threads takes one item of a 32-slot sub-block); plus the producer.
+template <int MH, int BN, int Q, int P = 0, int W = 8>
 struct TcCfg {
+    static constexpr int kGW = W;                         // generator warps
+    static constexpr int kGT = 32 * W;                    // generator threads
+    static constexpr int kThr = kGT + 32;                  // + the producer warp
+    static constexpr int kNS = W == 16 ? 4 : 8;           // slots per generator item
     // Slots per sub-block: 32 for E4M3 (one scale block), pairs, and small tiles whose 16-slot
     // sub-block would leave generator threads idle ((rows + BN) / 4 x 2 items for 256 threads)
     static constexpr int kSub = (Q || P || 128 * MH + BN <= 256) ? 32 : 16;
@@ -76,7 +87,8 @@ struct TcCfg {
                                      : kAccCols <= 256 ? 256 : 512;
     // barriers: full[2], empty[2], slice[kSlices], done, and for pairs peer[kSlices] (the peer's B half landed)
     static constexpr int kNumBars = 2 + 2 + kSlices + 1 + (P ? kSlices : 0) + 1 /*abort drain*/;
-    static constexpr int kBookBytes = 2 * kSub * 4 /*idx*/ + kNumBars * 8 + 16 /*tmem, abort*/ + kGenWarps * 8 +
+    static constexpr int kBookBytes = 2 * kSub * 4 /*idx*/ + 2 * 2 * kSub * 4 /*idx per packed half*/ +
+                                      kNumBars * 8 + 16 /*tmem, abort*/ + kGW * 8 +
                                       (P ? 0 : 2 * static_cast<int>(sizeof(LevelParams)) +
                                                    static_cast<int>(alignof(LevelParams)))
                                       /*job copies of batched launches (pairs run single-problem launches)*/;
@@ -86,7 +98,8 @@ struct TcCfg {
     static_assert(kKSteps * 16 == kSub, "a sub-block is a whole number of K = 16 MMA steps");
     static_assert(BN % 16 == 0 && BN >= 32 && BN <= 256, "N of the MMA");
     static constexpr bool kFits = kSmemBytes <= 227 * 1024 &&   // E4M3's 32-slot staging rules out wide tiles
-                                  (!P || (MH == 1 && BN == 256));
+                                  (!P || (MH == 1 && BN == 256)) && (W == 8 || (W == 16 && P));
+
 };
 
 struct TcExtra {
@@ -102,41 +115,47 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
     return *reinterpret_cast<const uint32_t*>(&v);
 }
 
-// Generate one block of (4 rows of A, or 4 columns of B) x (8 slots) entries from staged (M, S)
-// pairs and write them as bf16 into the swizzled tile: tile rows row0 .. row0+3, 16-byte chunk
-// `chunk`.  Staged pairs of slot u start at stage + u * stride (8 floats: (M,S) x 4).
-// kSw: the tile's swizzle, 128 or 64 bytes per row.
+// Generate one block of (4 rows of A, or 4 columns of B) x (NS = 8 or 4 slots) entries from staged
+// (M, S) pairs and write them as bf16 into the swizzled tile: tile rows row0 .. row0+3, 16-byte
+// chunk `chunk` (NS = 4: its half `sub`, 8 bytes).  Staged pairs of slot u start at
+// stage + u * stride (8 floats: (M,S) x 4).  kSw: the tile's swizzle, 128 or 64 bytes per row.
 template <int kSw>
 __device__ __forceinline__ uint32_t tile_offset(int row, int chunk)
 {
     return kSw == 128 ? tc::sw128_offset(row, chunk) : tc::sw64_offset(row, chunk);
 }
 
-template <int kSw = 128>
+template <int kSw = 128, int NS = 8>
 __device__ __forceinline__ void gen_block(const int* idx, int slot0, bool valid_rows, uint32_t rowgrp,
                                           uint32_t s_lo, uint32_t lsw, const PhiloxRoundKeys& rk,
                                           const unsigned char* stage,
-                                          int stride, bool odd_negative, unsigned char* tile, int row0, int chunk)
+                                          int stride, bool odd_negative, unsigned char* tile, int row0, int chunk,
+                                          int sub = 0)
 {
+    static_assert(NS == 8 || NS == 4, "slots per item");
     if (!valid_rows) {
         // padding rows (or columns) of the tile: zeros, no random numbers needed
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
-            *reinterpret_cast<uint4*>(tile + tile_offset<kSw>(row0 + r, chunk)) = make_uint4(0, 0, 0, 0);
+        for (int r = 0; r < 4; ++r) {
+            if constexpr (NS == 8)
+                *reinterpret_cast<uint4*>(tile + tile_offset<kSw>(row0 + r, chunk)) = make_uint4(0, 0, 0, 0);
+            else
+                *reinterpret_cast<uint2*>(tile + tile_offset<kSw>(row0 + r, chunk) + sub) = make_uint2(0, 0);
+        }
         return;
     }
-    // Branch-free: the eight Philox blocks are independent dependency chains, computed for every
-    // slot (a missing slot uses k = 0) and zeroed afterwards, so they can interleave.
-    int ks[8];
-    uint4 w[8];
+    // Branch-free: the Philox blocks are independent dependency chains, computed for every slot
+    // (a missing slot uses k = 0) and zeroed afterwards, so they can interleave.
+    int ks[NS];
+    uint4 w[NS];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < NS; ++u) {
         ks[u] = idx[slot0 + u];
         w[u] = philox4x32_10_rk(make_uint4(rowgrp, static_cast<uint32_t>(max(ks[u], 0)), s_lo, lsw), rk);
     }
-    float v[4][8];
+    float v[4][NS];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < NS; ++u) {
         float z[4];
         normals4_mufu(w[u], z);
         const float4* src = reinterpret_cast<const float4*>(stage + u * stride);
@@ -151,17 +170,22 @@ __device__ __forceinline__ void gen_block(const int* idx, int slot0, bool valid_
     }
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-        const uint4 packed = make_uint4(pack_bf16x2(v[r][0], v[r][1]), pack_bf16x2(v[r][2], v[r][3]),
-                                        pack_bf16x2(v[r][4], v[r][5]), pack_bf16x2(v[r][6], v[r][7]));
-        *reinterpret_cast<uint4*>(tile + tile_offset<kSw>(row0 + r, chunk)) = packed;
+        if constexpr (NS == 8) {
+            const uint4 packed = make_uint4(pack_bf16x2(v[r][0], v[r][1]), pack_bf16x2(v[r][2], v[r][3]),
+                                            pack_bf16x2(v[r][4], v[r][5]), pack_bf16x2(v[r][6], v[r][7]));
+            *reinterpret_cast<uint4*>(tile + tile_offset<kSw>(row0 + r, chunk)) = packed;
+        } else {
+            const uint2 packed = make_uint2(pack_bf16x2(v[r][0], v[r][1]), pack_bf16x2(v[r][2], v[r][3]));
+            *reinterpret_cast<uint2*>(tile + tile_offset<kSw>(row0 + r, chunk) + sub) = packed;
+        }
     }
 }
 
 // E4M3 form of gen_block for 32-slot sub-blocks: the four adjacent lanes of one row group hold
 // the row's 32 slots (8 each).  Each row's block maximum |x| gives the scale 2^e, e the
 // smallest integer with max <= 448 * 2^e (1 for an all-zero block); x / 2^e is rounded to E4M3
-// (nearest even, saturating at 448) and the dequantised value, exact in bfloat16, is stored.
-// Every lane of the warp must call this together (shuffles).
+// stochastically (e4m3_round_sr, with the entry's 16-bit dither) and the dequantised value,
+// exact in bfloat16, is stored.  Every lane of the warp must call this together (shuffles).
 __device__ __forceinline__ float e4m3_block_scale(float absmax)
 {
     if (!(absmax > 0.0f)) return 1.0f;
@@ -170,23 +194,47 @@ __device__ __forceinline__ float e4m3_block_scale(float absmax)
     return ldexpf(1.0f, e);
 }
 
-template <int kSw = 128>
+// Stochastic rounding of y (|y| <= 448) to the E4M3 grid: with lo <= |y| < lo + h the two grid
+// neighbours (h the spacing: 2^(e-3) for |y| in [2^e, 2^(e+1)), e >= -6; 2^-9 below 2^-6), the
+// result is lo + h when (d + 1/2) 2^-16 < (|y| - lo) / h, else lo, with the sign of y -- unbiased
+// over a uniform 16-bit dither d up to 2^-17 h.  Every step is exact in FP32 (h is a power of
+// two, (|y| - lo) / h has at most 20 fraction bits).
+__device__ __forceinline__ float e4m3_round_sr(float y, uint32_t d)
+{
+    const float ay = fabsf(y);
+    int e = static_cast<int>((__float_as_uint(ay) >> 23) & 0xFFu) - 127;
+    e = max(e, -6);
+    const float h = __uint_as_float(static_cast<uint32_t>(e - 3 + 127) << 23);
+    const float inv_h = __uint_as_float(static_cast<uint32_t>(127 - (e - 3)) << 23);
+    const float t = ay * inv_h;
+    const float fl = floorf(t);
+    const float up = ((t - fl) * 65536.0f > static_cast<float>(d) + 0.5f) ? 1.0f : 0.0f;
+    return copysignf((fl + up) * h, y);
+}
+
+// kTglob0: the absolute slot of the first of the 8 slots (even), for the dither counters
+// (row group, 2^31 + slot / 2, s_lo, level word): word r of the block serves row r of the group,
+// its low half the even slot and its high half the odd one.
+template <int kSw = 128, int NS = 8>
 __device__ __forceinline__ void gen_block_e4m3(const int* idx, int slot0, bool valid_rows, uint32_t rowgrp,
                                                uint32_t s_lo, uint32_t lsw, const PhiloxRoundKeys& rk,
                                                const unsigned char* stage, int stride, bool odd_negative,
-                                               unsigned char* tile, int row0, int chunk)
+                                               unsigned char* tile, int row0, int chunk, int tglob0,
+                                               bool split16 = false, int sub = 0)
 {
-    float v[4][8];
+    // NS slots per lane: the 32 slots of a row's block sit in 32 / NS adjacent lanes
+    static_assert(NS == 8 || NS == 4, "slots per item");
+    float v[4][NS];
     if (valid_rows) {
-        int ks[8];
-        uint4 w[8];
+        int ks[NS];
+        uint4 w[NS];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < NS; ++u) {
             ks[u] = idx[slot0 + u];
             w[u] = philox4x32_10_rk(make_uint4(rowgrp, static_cast<uint32_t>(max(ks[u], 0)), s_lo, lsw), rk);
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < NS; ++u) {
             float z[4];
             normals4_mufu(w[u], z);
             const float4* src = reinterpret_cast<const float4*>(stage + u * stride);
@@ -203,37 +251,62 @@ __device__ __forceinline__ void gen_block_e4m3(const int* idx, int slot0, bool v
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
-            for (int u = 0; u < 8; ++u) v[r][u] = 0.0f;
+            for (int u = 0; u < NS; ++u) v[r][u] = 0.0f;
     }
+    // dithers of the 4 rows x NS slots: one Philox block per slot pair
+    uint4 dith[NS / 2];
+#pragma unroll
+    for (int u2 = 0; u2 < NS / 2; ++u2)
+        dith[u2] = valid_rows ? philox4x32_10_rk(make_uint4(rowgrp, 0x80000000u | static_cast<uint32_t>((tglob0 >> 1) + u2),
+                                                            s_lo, lsw),
+                                                 rk)
+                              : make_uint4(0, 0, 0, 0);
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
         float am = 0.0f;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) am = fmaxf(am, fabsf(v[r][u]));
-        am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, 1));
-        am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, 2));
+        for (int u = 0; u < NS; ++u) am = fmaxf(am, fabsf(v[r][u]));
+        // the block's maximum over its lanes (split16: slots 0-15 and 16-31 are blocks of two samples)
+        constexpr int kLanes = 32 / NS;
+#pragma unroll
+        for (int x = 1; x < kLanes; x <<= 1) {
+            const float other = __shfl_xor_sync(0xffffffffu, am, x);
+            if (!split16 || 2 * x < kLanes) am = fmaxf(am, other);
+        }
         const float sc = e4m3_block_scale(am);
         const float inv = 1.0f / sc;   // exact: a power of two
-        uint32_t packed[4];
+        uint32_t packed[NS / 2];
 #pragma unroll
-        for (int u2 = 0; u2 < 4; ++u2) {
-            const __nv_fp8x2_storage_t q =
-                __nv_cvt_float2_to_fp8x2(make_float2(v[r][2 * u2] * inv, v[r][2 * u2 + 1] * inv), __NV_SATFINITE,
-                                         __NV_E4M3);
-            const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(q, __NV_E4M3);
-            const float2 d = __half22float2(*reinterpret_cast<const __half2*>(&hr));
-            packed[u2] = pack_bf16x2(d.x * sc, d.y * sc);
+        for (int u2 = 0; u2 < NS / 2; ++u2) {
+            const uint32_t word = r == 0 ? dith[u2].x : r == 1 ? dith[u2].y : r == 2 ? dith[u2].z : dith[u2].w;
+            const float q0 = e4m3_round_sr(v[r][2 * u2] * inv, word & 0xFFFFu);
+            const float q1 = e4m3_round_sr(v[r][2 * u2 + 1] * inv, word >> 16);
+            packed[u2] = pack_bf16x2(q0 * sc, q1 * sc);
         }
-        *reinterpret_cast<uint4*>(tile + tile_offset<kSw>(row0 + r, chunk)) =
-            make_uint4(packed[0], packed[1], packed[2], packed[3]);
+        if constexpr (NS == 8)
+            *reinterpret_cast<uint4*>(tile + tile_offset<kSw>(row0 + r, chunk)) =
+                make_uint4(packed[0], packed[1], packed[2], packed[3]);
+        else
+            *reinterpret_cast<uint2*>(tile + tile_offset<kSw>(row0 + r, chunk) + sub) = make_uint2(packed[0], packed[1]);
     }
 }
 
-template <int MH, int BN, int Q, bool kBatch, int P = 0>
-__global__ void __launch_bounds__(kThreads, 1)
+// prm.pack: two samples share one accumulator (problems with m <= 64 on a 128-row tile): rows 0-63
+// hold the first sample of a group and rows 64-127 the second; the group's K positions are the
+// first sample's c_l slots followed by the second's, and each half of A is zero on the other
+// sample's positions, so one MMA chain forms both samples' D.  Each half keeps its own running
+// sum (rows of S) and Welford M2; at the end of a chunk the halves are combined by Chan's update.
+// Needs c_l % 16 == 0 (a group of 8 slots, and an E4M3 block, never straddles two samples).
+template <int MH, int BN, int Q, bool kBatch, int P = 0, int W = 8>
+__global__ void __launch_bounds__(TcCfg<MH, BN, Q, P, W>::kThr, 1)
 level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra ex, const TcBatch bt)
 {
-    using C = TcCfg<MH, BN, Q, P>;
+    using C = TcCfg<MH, BN, Q, P, W>;
+    constexpr int kGenWarps = C::kGW;
+    constexpr int kGenThreads = C::kGT;
+    constexpr int kNS = C::kNS;
+    // columns per TMEM read in the drains: the 16-warp form has fewer registers a thread
+    constexpr int kCW = W == 16 ? 32 : 64;
     static_assert(C::kFits, "shared memory");
     static_assert(!(P && kBatch), "pairs run single-problem launches");
     constexpr int kSub = C::kSub;
@@ -245,7 +318,8 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
     unsigned char* b_tile = smem + C::kABytes;
     unsigned char* staging = smem + C::kTileBytes;  // [2][kStageBytes]
     int* idx_s = reinterpret_cast<int*>(staging + 2 * C::kStageBytes);  // [2][kSub]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(idx_s + 2 * kSub);
+    int* idxh_s = idx_s + 2 * kSub;   // PK: [2 buffers][2 halves][kSub], -1 on the other sample's slots
+    uint64_t* bars = reinterpret_cast<uint64_t*>(idxh_s + 4 * kSub);
     uint32_t* tmem_s = reinterpret_cast<uint32_t*>(bars + C::kNumBars);
     volatile int* abort_s = reinterpret_cast<volatile int*>(tmem_s + 1);
     double* red_s = reinterpret_cast<double*>(tmem_s + 4);
@@ -390,10 +464,15 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
             const uint64_t chunk = prm.chunk0 + static_cast<uint64_t>(cy);
             const uint64_t sa = max(prm.s_begin, chunk * static_cast<uint64_t>(prm.chunk));
             const uint64_t sb = min(prm.s_end, (chunk + 1) * static_cast<uint64_t>(prm.chunk));
-            for (uint64_t s = sa; s < sb && !aborted; ++s) {
+            const bool PK = MH == 1 && P == 0 && prm.pack != 0;   // packed samples (uniform per item)
+            const uint64_t kG = PK ? 2 : 1;                        // samples per accumulator
+            for (uint64_t s = sa; s < sb && !aborted; s += kG) {
                 const uint32_t lsw = level_sample_word(prm.l, s);
                 const uint32_t s_lo = static_cast<uint32_t>(s);
-                for (int j = 0; j < nsub; ++j, ++g) {
+                const int ngrp = (PK && sb - s >= 2) ? 2 : 1;   // samples in this group
+                const int nK = prm.c * ngrp;                                             // K positions
+                const int nsubg = PK ? (nK + kSub - 1) / kSub : nsub;
+                for (int j = 0; j < nsubg; ++j, ++g) {
                     const int b = static_cast<int>(g & 1);
                     if (g >= 2 && !tc::mbar_wait_bounded(bar_empty(b), ((g >> 1) - 1) & 1,
                                                          tc::globaltimer() + ex.timeout_ns)) {
@@ -406,7 +485,28 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                     }
                     int* idx = idx_s + b * kSub;
                     const int t0 = j * kSub;
-                    if (lane < kSub / 2) {
+                    if (PK) {
+                        // K position kp -> sample s + h (h = kp / c_l), slot kp - h c_l; c_l is even, so a
+                        // slot pair never straddles the two samples
+                        if (lane < kSub / 2) {
+                            const int kp = t0 + 2 * lane;
+                            int64_t r0 = -1, r1 = -1;
+                            const int h = kp < nK ? kp / prm.c : 0;
+                            if (kp < nK) {
+                                const uint64_t sh = s + static_cast<uint64_t>(h);
+                                index_pair(prm.keyI, level_sample_word(prm.l, sh), static_cast<uint32_t>(sh),
+                                           (kp - h * prm.c) >> 1, static_cast<uint64_t>(prm.n), r0, r1);
+                            }
+                            const int v0 = kp < nK ? static_cast<int>(r0) : -1, v1 = kp < nK ? static_cast<int>(r1) : -1;
+                            idx[2 * lane] = v0;
+                            idx[2 * lane + 1] = v1;
+                            int* ih = idxh_s + b * 2 * kSub;
+                            ih[2 * lane] = h == 0 ? v0 : -1;
+                            ih[2 * lane + 1] = h == 0 ? v1 : -1;
+                            ih[kSub + 2 * lane] = h == 1 ? v0 : -1;
+                            ih[kSub + 2 * lane + 1] = h == 1 ? v1 : -1;
+                        }
+                    } else if (lane < kSub / 2) {
                         const int t = t0 + 2 * lane;
                         int64_t r0 = -1, r1 = -1;
                         if (t < prm.c) index_pair(prm.keyI, lsw, s_lo, t >> 1, static_cast<uint64_t>(prm.n), r0, r1);
@@ -414,7 +514,7 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                         idx[2 * lane + 1] = t + 1 < prm.c ? static_cast<int>(r1) : -1;
                     }
                     __syncwarp();
-                    const int nvalid = min(kSub, prm.c - t0);
+                    const int nvalid = min(kSub, nK - t0);
                     // staging buffer b: the A parts of the kSub slots, then their B parts
                     unsigned char* stg = staging + b * C::kStageBytes;
                     const uint32_t a_region = tc::smem_addr(stg);
@@ -461,11 +561,11 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                 tc::mbar_wait_bounded(bar_full(static_cast<int>(gp & 1)), (gp >> 1) & 1,
                                       tc::globaltimer() + kDrainNs);
         }
-    } else {
+    } else if (warp < kGenWarps) {
         // ---------------- generator warps: entries, MMA issue, drain ----------------------------
         constexpr uint32_t idesc = tc::idesc_bf16_f32(128, BN);
-        constexpr int kItemsA = (C::kRows / 4) * (kSub / 8);
-        constexpr int kItemsB = (C::kBGen / 4) * (kSub / 8);
+        constexpr int kItemsA = (C::kRows / 4) * (kSub / kNS);
+        constexpr int kItemsB = (C::kBGen / 4) * (kSub / kNS);
         uint32_t g = 0;  // sub-blocks consumed
         uint32_t peer_par = 0;    // bit kk: parity of the peer's arrivals on peer barrier kk (pairs)
         int peer_armed = -1;      // pairs, thread 0: slice whose peer copy is expected but not yet waited for
@@ -486,7 +586,8 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
             const uint64_t sa = max(prm.s_begin, chunk * static_cast<uint64_t>(prm.chunk));
             const uint64_t sb = min(prm.s_end, (chunk + 1) * static_cast<uint64_t>(prm.chunk));
             float* part = static_cast<float*>(prm.partial_sum) + static_cast<int64_t>(cy) * prm.m * prm.p;
-            double q = 0.0;
+            double q = 0.0;    // chunk-level terms (scaled)
+            float qw = 0.0f;   // Welford terms of the chunk's samples, FP32 (unscaled on tiles that keep S)
             const double scale_sq = static_cast<double>(scale) * static_cast<double>(scale);
             // Drain mapping.  MH == 2: warp group h reads M-half h (all BN columns); MH == 1: the two
             // warp groups split the columns, or group 0 takes all of them when BN < 64.
@@ -498,16 +599,27 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                 }
             } dr;
             {
-                const int hgrp = warp >> 2;
-                const bool split = MH == 1 && BN >= 64;
+                const int hgrp = warp >> 2;                 // 0 .. kGenWarps / 4 - 1
+                constexpr int kSplit = kGenWarps / 4;        // column groups of a 128-row tile
+                const bool split = MH == 1 && BN >= 32 * kSplit;
                 dr.quarter = warp & 3;
-                dr.col_tm = MH == 2 ? hgrp * BN : (split ? hgrp * (BN / 2) : 0);
+                dr.col_tm = MH == 2 ? hgrp * BN : (split ? hgrp * (BN / kSplit) : 0);
                 dr.col_d = MH == 2 ? 0 : dr.col_tm;
-                dr.ncols = MH == 2 ? BN : (split ? BN / 2 : (hgrp == 0 ? BN : 0));
+                dr.ncols = MH == 2 ? BN : (split ? BN / kSplit : (hgrp == 0 ? BN : 0));
                 dr.gi = tm0 + (MH == 2 ? hgrp * 128 : 0) + dr.quarter * 32 + lane;
             }
-            // Write (first) or add 64 drained columns starting at column cb of this thread's row.
-            auto store_cols = [&](const float* v, int cb, int nv, bool first) {
+            const bool PK = MH == 1 && P == 0 && prm.pack != 0;   // packed samples (uniform per item)
+            const uint64_t kG = PK ? 2 : 1;
+            if (PK) dr.gi = (dr.quarter & 1) * 32 + lane;          // rows 64-127: the second sample
+            const int pk_half = PK ? (warp & 3) >> 1 : 0;           // the sample of this warp's drained rows
+            // Write (first sample of the chunk) or fold 64 drained, scaled columns starting at column
+            // cb of this thread's row into the chunk partial: each element has one owner thread, so
+            // the partial is read back and rewritten in a fixed order.  Folding returns the sum of
+            // (k D - sum_k)^2 over the columns (k samples folded before: Welford's update of the
+            // chunk's M2, the caller divides by k (k + 1)).
+            auto store_cols = [&](const float* v, int cb, int nv, int kbefore) -> float {
+                float qs = 0.0f;
+                const float kf = static_cast<float>(kbefore);
 #pragma unroll
                 for (int half = 0; half < 2; ++half) {
                     const int gj0 = tp0 + dr.col_d + cb + 32 * half;
@@ -518,28 +630,40 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                     if (valid == 32 && (prm.p & 3) == 0) {
 #pragma unroll
                         for (int e4 = 0; e4 < 8; ++e4) {
-                            if (first)
-                                reinterpret_cast<float4*>(dst)[e4] =
-                                    make_float4(w[4 * e4], w[4 * e4 + 1], w[4 * e4 + 2], w[4 * e4 + 3]);
-                            else
-                                tc::red_add_v4(dst + 4 * e4, w[4 * e4], w[4 * e4 + 1], w[4 * e4 + 2], w[4 * e4 + 3]);
+                            float4 x = make_float4(w[4 * e4], w[4 * e4 + 1], w[4 * e4 + 2], w[4 * e4 + 3]);
+                            if (kbefore > 0) {
+                                const float4 pv = reinterpret_cast<const float4*>(dst)[e4];
+                                const float d0 = fmaf(kf, x.x, -pv.x), d1 = fmaf(kf, x.y, -pv.y);
+                                const float d2 = fmaf(kf, x.z, -pv.z), d3 = fmaf(kf, x.w, -pv.w);
+                                qs = fmaf(d0, d0, fmaf(d1, d1, fmaf(d2, d2, fmaf(d3, d3, qs))));
+                                x = make_float4(pv.x + x.x, pv.y + x.y, pv.z + x.z, pv.w + x.w);
+                            }
+                            reinterpret_cast<float4*>(dst)[e4] = x;
                         }
                     } else {
 #pragma unroll
                         for (int e = 0; e < 32; ++e)
                             if (e < valid) {
-                                if (first)
-                                    dst[e] = w[e];
-                                else
-                                    atomicAdd(dst + e, w[e]);
+                                float x = w[e];
+                                if (kbefore > 0) {
+                                    const float pv = dst[e];
+                                    const float d = fmaf(kf, x, -pv);
+                                    qs = fmaf(d, d, qs);
+                                    x += pv;
+                                }
+                                dst[e] = x;
                             }
                     }
                 }
+                return qs;
             };
-            for (uint64_t s = sa; s < sb && !aborted; ++s) {
+            for (uint64_t s = sa; s < sb && !aborted; s += kG) {
                 const uint32_t lsw = level_sample_word(prm.l, s);
                 const uint32_t s_lo = static_cast<uint32_t>(s);
-                for (int j = 0; j < nsub; ++j, ++g) {
+                const int ngrp = (PK && sb - s >= 2) ? 2 : 1;
+                const int nK = prm.c * ngrp;
+                const int nsubg = PK ? (nK + kSub - 1) / kSub : nsub;
+                for (int j = 0; j < nsubg; ++j, ++g) {
                     const int b = static_cast<int>(g & 1);
                     const int kk = j % kSlices;
                     bool ok = tc::mbar_wait_bounded(bar_full(b), (g >> 1) & 1, tc::globaltimer() + ex.timeout_ns);
@@ -555,9 +679,49 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                     const unsigned char* stB = st + kSub * C::kRows * 8;          // then their B parts
                     ok = __all_sync(0xffffffffu, ok);   // whole warps generate or skip (E4M3 uses shuffles)
                     if (ok) {
-                        constexpr int kGroups = kSub / 8;   // 8-slot groups per sub-block
+                        constexpr int kGroups = kSub / kNS;   // items (kNS slots) per row group and sub-block
                         for (int it = tid; it < kItemsA + kItemsB; it += kGenThreads) {
-                            if constexpr (Q == 0) {
+                            if (PK) {
+                                // packed samples: A rows 0-63 belong to sample s, rows 64-127 to s + 1 (zero
+                                // on the other sample's K positions); B's K positions to whichever owns them
+                                if (it < kItemsA) {
+                                    const int g4 = Q == 0 ? it % (C::kRows / 4) : it / kGroups;
+                                    const int sg = Q == 0 ? it / (C::kRows / 4) : it % kGroups;
+                                    const int h = g4 >> 4;
+                                    const int i = 4 * (g4 & 15);
+                                    const uint64_t sh = s + static_cast<uint64_t>(h);
+                                    const bool vr = i < prm.m && h < ngrp;
+                                    const int* ih = idxh_s + b * 2 * kSub + h * kSub;
+                                    const unsigned char* src = st + (sg * 8) * (C::kRows * 8) + (g4 & 15) * 32;
+                                    if constexpr (Q == 0)
+                                        gen_block(ih, sg * 8, vr, static_cast<uint32_t>(i >> 2), static_cast<uint32_t>(sh),
+                                                  level_sample_word(prm.l, sh), prm.rkA, src, C::kRows * 8, false,
+                                                  a_tile, 4 * g4, kGroups * kk + sg);
+                                    else
+                                        gen_block_e4m3(ih, sg * 8, vr, static_cast<uint32_t>(i >> 2),
+                                                       static_cast<uint32_t>(sh), level_sample_word(prm.l, sh), prm.rkA,
+                                                       src, C::kRows * 8, false, a_tile, 4 * g4, kGroups * kk + sg,
+                                                       j * kSub + sg * 8 - h * prm.c);
+                                } else {
+                                    const int it2 = it - kItemsA;
+                                    const int g4 = Q == 0 ? it2 % (C::kBGen / 4) : it2 / kGroups;
+                                    const int sg = Q == 0 ? it2 / (C::kBGen / 4) : it2 % kGroups;
+                                    const int jc = geo.bcol0 + 4 * g4;
+                                    const int kp0 = j * kSub + sg * 8;   // first K position of the 8 slots
+                                    const int h = kp0 < nK ? kp0 / prm.c : 0;
+                                    const uint64_t sh = s + static_cast<uint64_t>(h);
+                                    const unsigned char* src = stB + (sg * 8) * (C::kBGen * 8) + g4 * 32;
+                                    if constexpr (Q == 0)
+                                        gen_block(idx, sg * 8, jc < prm.p, static_cast<uint32_t>(jc >> 2),
+                                                  static_cast<uint32_t>(sh), level_sample_word(prm.l, sh), prm.rkB, src,
+                                                  C::kBGen * 8, coarse_sign, b_tile, brow0 + 4 * g4, kGroups * kk + sg);
+                                    else
+                                        gen_block_e4m3(idx, sg * 8, jc < prm.p, static_cast<uint32_t>(jc >> 2),
+                                                       static_cast<uint32_t>(sh), level_sample_word(prm.l, sh), prm.rkB,
+                                                       src, C::kBGen * 8, coarse_sign, b_tile, brow0 + 4 * g4,
+                                                       kGroups * kk + sg, kp0 - h * prm.c, prm.c == 16);
+                                }
+                            } else if constexpr (Q == 0) {
                                 // consecutive threads take consecutive row groups
                                 if (it < kItemsA) {
                                     // 4 rows of A x 8 slots
@@ -565,9 +729,10 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                                     const int sg = it / (C::kRows / 4);
                                     const int i = tm0 + 4 * g4;
                                     if constexpr (P)
-                                        gen_block<64>(idx, sg * 8, i < prm.m, static_cast<uint32_t>(i >> 2), s_lo,
-                                                      lsw, prm.rkA, st + (sg * 8) * (C::kRows * 8) + g4 * 32,
-                                                      C::kRows * 8, false, a_tile + kk * C::kASliceBytes, 4 * g4, sg);
+                                        gen_block<64, kNS>(idx, sg * kNS, i < prm.m, static_cast<uint32_t>(i >> 2), s_lo,
+                                                           lsw, prm.rkA, st + (sg * kNS) * (C::kRows * 8) + g4 * 32,
+                                                           C::kRows * 8, false, a_tile + kk * C::kASliceBytes, 4 * g4,
+                                                           (sg * kNS) / 8, ((sg * kNS) % 8) * 2);
                                     else
                                         gen_block(idx, sg * 8, i < prm.m, static_cast<uint32_t>(i >> 2), s_lo, lsw,
                                                   prm.rkA, st + (sg * 8) * (C::kRows * 8) + g4 * 32, C::kRows * 8,
@@ -580,10 +745,10 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                                     const int sg = it2 / (C::kBGen / 4);
                                     const int jc = geo.bcol0 + 4 * g4;
                                     if constexpr (P)
-                                        gen_block<64>(idx, sg * 8, jc < prm.p, static_cast<uint32_t>(jc >> 2), s_lo,
-                                                      lsw, prm.rkB, stB + (sg * 8) * (C::kBGen * 8) + g4 * 32,
-                                                      C::kBGen * 8, coarse_sign, b_tile + kk * C::kBSliceBytes,
-                                                      brow0 + 4 * g4, sg);
+                                        gen_block<64, kNS>(idx, sg * kNS, jc < prm.p, static_cast<uint32_t>(jc >> 2), s_lo,
+                                                           lsw, prm.rkB, stB + (sg * kNS) * (C::kBGen * 8) + g4 * 32,
+                                                           C::kBGen * 8, coarse_sign, b_tile + kk * C::kBSliceBytes,
+                                                           brow0 + 4 * g4, (sg * kNS) / 8, ((sg * kNS) % 8) * 2);
                                     else
                                         gen_block(idx, sg * 8, jc < prm.p, static_cast<uint32_t>(jc >> 2), s_lo, lsw,
                                                   prm.rkB, stB + (sg * 8) * (C::kBGen * 8) + g4 * 32,
@@ -598,28 +763,32 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                                     const int g4 = it / kGroups, sg = it % kGroups;
                                     const int i = tm0 + 4 * g4;
                                     if constexpr (P)
-                                        gen_block_e4m3<64>(idx, sg * 8, i < prm.m, static_cast<uint32_t>(i >> 2), s_lo,
-                                                           lsw, prm.rkA, st + (sg * 8) * (C::kRows * 8) + g4 * 32,
-                                                           C::kRows * 8, false, a_tile + kk * C::kASliceBytes, 4 * g4,
-                                                           sg);
+                                        gen_block_e4m3<64, kNS>(idx, sg * kNS, i < prm.m, static_cast<uint32_t>(i >> 2),
+                                                                s_lo, lsw, prm.rkA,
+                                                                st + (sg * kNS) * (C::kRows * 8) + g4 * 32, C::kRows * 8,
+                                                                false, a_tile + kk * C::kASliceBytes, 4 * g4,
+                                                                (sg * kNS) / 8, j * kSub + sg * kNS, false,
+                                                                ((sg * kNS) % 8) * 2);
                                     else
                                         gen_block_e4m3(idx, sg * 8, i < prm.m, static_cast<uint32_t>(i >> 2), s_lo, lsw,
                                                        prm.rkA, st + (sg * 8) * (C::kRows * 8) + g4 * 32, C::kRows * 8,
-                                                       false, a_tile, 4 * g4, kGroups * kk + sg);
+                                                       false, a_tile, 4 * g4, kGroups * kk + sg, j * kSub + sg * 8);
                                 } else {
                                     const int it2 = it - kItemsA;
                                     const int g4 = it2 / kGroups, sg = it2 % kGroups;
                                     const int jc = geo.bcol0 + 4 * g4;
                                     if constexpr (P)
-                                        gen_block_e4m3<64>(idx, sg * 8, jc < prm.p, static_cast<uint32_t>(jc >> 2), s_lo,
-                                                           lsw, prm.rkB, stB + (sg * 8) * (C::kBGen * 8) + g4 * 32,
-                                                           C::kBGen * 8, coarse_sign, b_tile + kk * C::kBSliceBytes,
-                                                           brow0 + 4 * g4, sg);
+                                        gen_block_e4m3<64, kNS>(idx, sg * kNS, jc < prm.p, static_cast<uint32_t>(jc >> 2),
+                                                                s_lo, lsw, prm.rkB,
+                                                                stB + (sg * kNS) * (C::kBGen * 8) + g4 * 32, C::kBGen * 8,
+                                                                coarse_sign, b_tile + kk * C::kBSliceBytes, brow0 + 4 * g4,
+                                                                (sg * kNS) / 8, j * kSub + sg * kNS, false,
+                                                                ((sg * kNS) % 8) * 2);
                                     else
                                         gen_block_e4m3(idx, sg * 8, jc < prm.p, static_cast<uint32_t>(jc >> 2), s_lo, lsw,
                                                        prm.rkB, stB + (sg * 8) * (C::kBGen * 8) + g4 * 32,
                                                        C::kBGen * 8, coarse_sign, b_tile, brow0 + 4 * g4,
-                                                       kGroups * kk + sg);
+                                                       kGroups * kk + sg, j * kSub + sg * 8);
                                 }
                             }
                         }
@@ -659,7 +828,7 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                             tc::mma_commit_multicast(bar_slice(kj), 0x3);   // both CTAs wait for this slice
                         else
                             tc::mma_commit(bar_slice(kj));
-                        if (jj == nsub - 1) tc::mma_commit(bar_done);
+                        if (jj == nsubg - 1) tc::mma_commit(bar_done);
                     };
                     if constexpr (P) {
                         // Pairs: send our half of this slice of B to the peer (async proxy, counted on its
@@ -686,7 +855,7 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                                 wait_peer(kprev);
                                 issue_mma(j - 1, kprev);
                             }
-                            if (j == nsub - 1) {
+                            if (j == nsubg - 1) {
                                 wait_peer(kk);
                                 issue_mma(j, kk);
                             }
@@ -710,24 +879,63 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                     break;
                 }
                 tc::tc_fence_after_sync();
+                // Welford's update of the chunk's M2 with k = s - sa samples folded before: the
+                // deviation of D from the mean of those k is (k D - sum_k) / k, and M2 grows by
+                // ||k D - sum_k||^2 / (k (k + 1)) (nothing for the chunk's first sample)
+                const int kbefore = static_cast<int>((s - sa) / kG);
+                // FP32 throughout (FP64 runs at 1/64 of the FP32 rate here); exact for k (k + 1) <= 2^24
+                const float wk = kbefore > 0 ? 1.0f / static_cast<float>(kbefore * (kbefore + 1)) : 0.0f;
                 if constexpr (C::kAccS) {
-                    // ||D||^2 of the sample from its accumulator; the sum stays in tensor memory
-                    for (int cb = 0; cb < dr.ncols; cb += 64) {
-                        float v[64];
-                        const uint32_t ta = dr.taddr(tmem, cb);
-                        tc::tmem_ld_32x32b_x32_nowait(ta, v);
-                        if (cb + 32 < dr.ncols) tc::tmem_ld_32x32b_x32_nowait(ta + 32, v + 32);
-                        tc::tmem_ld_wait();
-                        const int nv = min(64, dr.ncols - cb);
-                        float qs = 0.0f;
+                    // the running sum S (after this sample) sits beside D in tensor memory:
+                    // k D - sum_k = (k + 1) D - S, one fused rounding per element (PK: per half,
+                    // and a group without a second sample has nothing in rows 64-127).  Levels
+                    // whose mean is zero by construction (prm.welford == 0) keep the raw sum of
+                    // ||D||^2 instead; the chunk's M2 follows from it and ||S||^2 at the chunk's end.
+                    if (!prm.welford) {
+                        if (pk_half < ngrp) {
+                            float qsamp = 0.0f;
+                            for (int cb = 0; cb < dr.ncols; cb += kCW) {
+                                float v[kCW];
+                                const uint32_t ta = dr.taddr(tmem, cb);
+                                tc::tmem_ld_32x32b_x32_nowait(ta, v);
+                                if constexpr (kCW == 64)
+                                    if (cb + 32 < dr.ncols) tc::tmem_ld_32x32b_x32_nowait(ta + 32, v + kCW / 2);
+                                tc::tmem_ld_wait();
+                                const int nv = min(kCW, dr.ncols - cb);
+                                float qs = 0.0f;
 #pragma unroll
-                        for (int e = 0; e < 64; ++e)
-                            if (e < nv) qs = fmaf(v[e], v[e], qs);
-                        q += static_cast<double>(qs) * scale_sq;
+                                for (int e = 0; e < kCW; ++e)
+                                    if (e < nv) qs = fmaf(v[e], v[e], qs);
+                                qsamp += qs;
+                            }
+                            qw += qsamp;
+                        }
+                    } else if (kbefore > 0 && pk_half < ngrp) {
+                        const float kp1 = static_cast<float>(kbefore + 1);
+                        float qsamp = 0.0f;
+                        // columns per wait: 32 where the registers allow it (pairs, narrow tiles), else 16
+                        constexpr int kW = (W == 8 && (P || (BN <= 64 && MH == 1))) ? 32 : 16;
+                        for (int cb = 0; cb < dr.ncols; cb += kW) {   // ncols is a multiple of 32
+                            float vd[kW], vs[kW];
+#pragma unroll
+                            for (int h16 = 0; h16 < kW; h16 += 16) {
+                                tc::tmem_ld_32x32b_x16_nowait(dr.taddr(tmem, cb + h16), vd + h16);
+                                tc::tmem_ld_32x32b_x16_nowait(dr.taddr(tmem + C::kTileCols, cb + h16), vs + h16);
+                            }
+                            tc::tmem_ld_wait();
+                            float qs = 0.0f;
+#pragma unroll
+                            for (int e = 0; e < kW; ++e) {
+                                const float dk = fmaf(kp1, vd[e], -vs[e]);
+                                qs = fmaf(dk, dk, qs);
+                            }
+                            qsamp += qs;
+                        }
+                        qw = fmaf(qsamp, wk, qw);
                     }
                 } else {
-                    const bool first = (s == sa);
                     // two 32-column loads in flight per wait
+                    float qsamp = 0.0f;
                     for (int cb = 0; cb < dr.ncols; cb += 64) {
                         float v[64];
                         const uint32_t ta = dr.taddr(tmem, cb);
@@ -735,40 +943,115 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                         if (cb + 32 < dr.ncols) tc::tmem_ld_32x32b_x32_nowait(ta + 32, v + 32);
                         tc::tmem_ld_wait();
                         const int nv = min(64, dr.ncols - cb);
-                        float qs = 0.0f;
 #pragma unroll
-                        for (int e = 0; e < 64; ++e) {
-                            if (e < nv) {
-                                v[e] *= scale;
-                                qs = fmaf(v[e], v[e], qs);
-                            }
-                        }
-                        q += static_cast<double>(qs);
-                        store_cols(v, cb, nv, first);
+                        for (int e = 0; e < 64; ++e) v[e] *= scale;
+                        qsamp += store_cols(v, cb, nv, kbefore);
                     }
+                    qw = fmaf(qsamp, wk, qw);
                 }
                 tc::tc_fence_before_sync();
                 tc::named_barrier(kGenBarrier, kGenThreads);  // the accumulator may now be overwritten
             }
             if (aborted) return false;
-            if constexpr (C::kAccS) {
-                // the chunk's sum of D: one store per element of the tile
+            if (PK) {
+                // the two halves' running sums and M2 combine into the chunk's: the second half's sum
+                // is stored first, then the first half adds its own and Chan's cross term
+                // n_t n_b / (n_t + n_b) ||S_t / n_t - S_b / n_b||^2
                 tc::tc_fence_after_sync();
-                for (int cb = 0; cb < dr.ncols; cb += 64) {
-                    float v[64];
+                const int nc = static_cast<int>(sb - sa), nt = (nc + 1) / 2, nb = nc / 2;
+                if (pk_half == 1 && nb > 0) {
+                    float ssq = 0.0f;   // raw form: ||S_b||^2 (unscaled)
+                    for (int cb = 0; cb < dr.ncols; cb += 64) {
+                        float v[64];
+                        const uint32_t ta = dr.taddr(tmem + C::kTileCols, cb);
+                        tc::tmem_ld_32x32b_x32_nowait(ta, v);
+                        if (cb + 32 < dr.ncols) tc::tmem_ld_32x32b_x32_nowait(ta + 32, v + 32);
+                        tc::tmem_ld_wait();
+                        float qs = 0.0f;   // grouped as in the drain, so one sample gives exactly zero
+#pragma unroll
+                        for (int e = 0; e < 64; ++e) {
+                            if (e < min(64, dr.ncols - cb)) qs = fmaf(v[e], v[e], qs);
+                            v[e] *= scale;
+                        }
+                        ssq += qs;
+                        store_cols(v, cb, min(64, dr.ncols - cb), 0);
+                    }
+                    if (!prm.welford) q -= static_cast<double>(ssq) * scale_sq / static_cast<double>(nb);
+                }
+                tc::named_barrier(kGenBarrier, kGenThreads);   // orders the stores before the reads below
+                if (pk_half == 0) {
+                    const float inv_nt = 1.0f / static_cast<float>(nt);
+                    const float inv_nb = nb > 0 ? 1.0f / static_cast<float>(nb) : 0.0f;
+                    double cross = 0.0;
+                    float ssq = 0.0f;   // raw form: ||S_t||^2 (unscaled)
+                    for (int cb = 0; cb < dr.ncols; cb += 64) {
+                        float v[64];
+                        const uint32_t ta = dr.taddr(tmem + C::kTileCols, cb);
+                        tc::tmem_ld_32x32b_x32_nowait(ta, v);
+                        if (cb + 32 < dr.ncols) tc::tmem_ld_32x32b_x32_nowait(ta + 32, v + 32);
+                        tc::tmem_ld_wait();
+                        const int nv = min(64, dr.ncols - cb);
+                        {
+                            float qs = 0.0f;
+#pragma unroll
+                            for (int e = 0; e < 64; ++e)
+                                if (e < nv) qs = fmaf(v[e], v[e], qs);
+                            ssq += qs;
+                        }
+                        float cq = 0.0f;
+#pragma unroll
+                        for (int hh = 0; hh < 2; ++hh) {
+                            const int gj0 = tp0 + dr.col_d + cb + 32 * hh;
+                            if (32 * hh >= nv || dr.gi >= prm.m || gj0 >= prm.p) continue;
+                            float* dst = part + static_cast<int64_t>(dr.gi) * prm.p + gj0;
+                            const int valid = min(32, prm.p - gj0);
+#pragma unroll
+                            for (int e = 0; e < 32; ++e) {
+                                if (e < valid) {
+                                    const float x = v[32 * hh + e] * scale;
+                                    const float pb = nb > 0 ? dst[e] : 0.0f;
+                                    if (nb > 0) {
+                                        const float d = x * inv_nt - pb * inv_nb;
+                                        cq = fmaf(d, d, cq);
+                                    }
+                                    dst[e] = x + pb;
+                                }
+                            }
+                        }
+                        cross += static_cast<double>(cq);
+                    }
+                    if (nb > 0)
+                        q += cross * (static_cast<double>(nt) * static_cast<double>(nb) / static_cast<double>(nt + nb));
+                    if (!prm.welford) q -= static_cast<double>(ssq) * scale_sq / static_cast<double>(nt);
+                }
+                tc::tc_fence_before_sync();
+            } else if constexpr (C::kAccS) {
+                // the chunk's sum of D: one store per element of the tile (raw form: also ||S||^2)
+                tc::tc_fence_after_sync();
+                float ssq = 0.0f;
+                for (int cb = 0; cb < dr.ncols; cb += kCW) {
+                    float v[64];   // store_cols reads up to 64; the 16-warp form fills the first 32
                     const uint32_t ta = dr.taddr(tmem + C::kTileCols, cb);
                     tc::tmem_ld_32x32b_x32_nowait(ta, v);
-                    if (cb + 32 < dr.ncols) tc::tmem_ld_32x32b_x32_nowait(ta + 32, v + 32);
+                    if (kCW == 64 && cb + 32 < dr.ncols) tc::tmem_ld_32x32b_x32_nowait(ta + 32, v + 32);
                     tc::tmem_ld_wait();
-                    const int nv = min(64, dr.ncols - cb);
+                    const int nv = min(kCW, dr.ncols - cb);
+                    float qs = 0.0f;
 #pragma unroll
-                    for (int e = 0; e < 64; ++e) v[e] *= scale;
-                    store_cols(v, cb, nv, true);
+                    for (int e = 0; e < kCW; ++e) {
+                        if (e < nv) qs = fmaf(v[e], v[e], qs);
+                        v[e] *= scale;
+                    }
+                    ssq += qs;
+                    store_cols(v, cb, nv, 0);
                 }
+                if (!prm.welford) q -= static_cast<double>(ssq) * scale_sq / static_cast<double>(sb - sa);
                 tc::tc_fence_before_sync();
             }
             if (aborted) return false;
-            // work-item epilogue: sum of ||D||^2 of this tile over the chunk, fixed-order reduction
+            // the Welford terms in FP64 (tiles that keep S drained unscaled values)
+            q += static_cast<double>(qw) * (C::kAccS ? scale_sq : 1.0);
+            // work-item epilogue: the chunk's M2 over this tile, fixed-order reduction
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) q += __shfl_xor_sync(0xffffffffu, q, off);
             if (lane == 0) red_s[warp] = q;
@@ -815,7 +1098,7 @@ cudaError_t prepare(int* per_sm)
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
     if (e != cudaSuccess) return e;
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, level_tc_bf16_kernel<MH, BN, Q, kBatch>, kThreads,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, level_tc_bf16_kernel<MH, BN, Q, kBatch>, C::kThr,
                                                       C::kSmemBytes);
     if (e != cudaSuccess) return e;
     *per_sm = max(1, min(occ, 512 / C::kTmemCols));
@@ -836,7 +1119,7 @@ struct SingleF {
             const int items = prm.nchunks * prm.tiles_m * prm.tiles_p;
             const int grid = max(1, min(items, per_sm * tl.num_sms));
             TcExtra ex{tl.err_flag, tl.timeout_ns, items, tl.scale};
-            level_tc_bf16_kernel<MH, BN, Q, false><<<grid, kThreads, C::kSmemBytes, st>>>(prm, ex, TcBatch{});
+            level_tc_bf16_kernel<MH, BN, Q, false><<<grid, C::kThr, C::kSmemBytes, st>>>(prm, ex, TcBatch{});
             return cudaGetLastError();
         }
     }
@@ -853,7 +1136,7 @@ struct BatchF {
             // the function attributes were set by tc_batch_grid (no attribute calls while a graph is captured)
             TcExtra ex{tl.err_flag, tl.timeout_ns, 0, 0.0f};
             LevelParams none{};
-            level_tc_bf16_kernel<MH, BN, Q, true><<<grid, kThreads, C::kSmemBytes, st>>>(none, ex, bt);
+            level_tc_bf16_kernel<MH, BN, Q, true><<<grid, C::kThr, C::kSmemBytes, st>>>(none, ex, bt);
             return cudaGetLastError();
         }
     }
@@ -873,12 +1156,12 @@ struct GridF {
     }
 };
 
-// A cluster pair (two CTAs, 128 rows each) on one 256 x 256 output tile.
-template <int Q>
+// A cluster pair (two CTAs, 128 rows each) on one 256 x 256 output tile; W generator warps.
+template <int Q, int W>
 cudaError_t launch_pair(const LevelParams& prm, const TcLaunch& tl, cudaStream_t st)
 {
-    using C = TcCfg<1, 256, Q, 1>;
-    auto kern = level_tc_bf16_kernel<1, 256, Q, false, 1>;
+    using C = TcCfg<1, 256, Q, 1, W>;
+    auto kern = level_tc_bf16_kernel<1, 256, Q, false, 1, W>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
     if (e != cudaSuccess) return e;
     cudaLaunchAttribute attr[1];
@@ -887,7 +1170,7 @@ cudaError_t launch_pair(const LevelParams& prm, const TcLaunch& tl, cudaStream_t
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cudaLaunchConfig_t cfg = {};
-    cfg.blockDim = dim3(kThreads);
+    cfg.blockDim = dim3(C::kThr);
     cfg.dynamicSmemBytes = C::kSmemBytes;
     cfg.stream = st;
     cfg.attrs = attr;
@@ -958,6 +1241,15 @@ cudaError_t launch_bounded_wait_probe(int* err_flag, uint64_t timeout_ns, cudaSt
     return cudaGetLastError();
 }
 
+// E4M3 blocks are 32 consecutive slots of a sample: packed K positions keep them apart when c is a
+// multiple of 32 (a sub-block never straddles two samples) or c = 16 (each sample's slots form one
+// block, the two halves of a sub-block)
+bool tc_pack(const TcTile& t, int q, int64_t m, int64_t c)
+{
+    if (t.mh != 1 || t.pair || m > 64 || c % 16 != 0) return false;
+    return q == 0 || c == 16 || c % 32 == 0;
+}
+
 int tc_stage_width_a(const TcTile& t) { return t.pair ? 128 : 128 * t.mh; }
 int tc_stage_width_b(const TcTile& t) { return t.pair ? t.bn / 2 : t.bn; }
 
@@ -1011,7 +1303,7 @@ bool tc_tile_valid(const TcTile& t, int q)
 TcTile tc_tile_for(int64_t m, int64_t p, int q, bool allow_pair)
 {
     TcTile t{};
-    if (allow_pair && m > 128 && p > 128) return TcTile{1, 256, 128, 1};   // cluster pair
+    if (allow_pair && m > 128 && p > 128) return TcTile{1, 256, 128, 1};   // cluster pair (8 generator warps)
     t.mh = m <= 128 ? 1 : 2;
     t.bn = p <= 32 ? 32 : p <= 64 ? 64 : p <= 128 ? 128 : 256;
     while (!tc_tile_valid(t, q) && t.bn > 32) t.bn /= 2;   // E4M3: narrower column tiles
@@ -1023,7 +1315,8 @@ TcTile tc_tile_for(int64_t m, int64_t p, int q, bool allow_pair)
 cudaError_t launch_level_tc(const LevelParams& prm, const TcTile& tile, int q, const TcLaunch& tl, cudaStream_t st)
 {
     if (!tc_tile_valid(tile, q)) return cudaErrorInvalidValue;
-    if (tile.pair) return q ? launch_pair<1>(prm, tl, st) : launch_pair<0>(prm, tl, st);
+    if (tile.pair == 2) return q ? launch_pair<1, 16>(prm, tl, st) : launch_pair<0, 16>(prm, tl, st);
+    if (tile.pair) return q ? launch_pair<1, 8>(prm, tl, st) : launch_pair<0, 8>(prm, tl, st);
     return dispatch_tile<SingleF>(tile, q, prm, tl, st);
 }
 

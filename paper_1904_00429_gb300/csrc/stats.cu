@@ -1,10 +1,13 @@
 // stats.cu -- per-level statistics (Eq. hatYl, Remark 3.6), the telescoping
 // sum (Eq. hatY), the parameter layout copy and the verification kernels.
 //
-// A level's state is (N, per-entry FP64 sum of D, FP64 sum of ||D||_F^2).
-// Chunk partials are added to it strictly in chunk order, one thread per
-// entry, so the state is a deterministic function of the samples folded in.
-// Y_l = sum / N and V_l = (sumsq - ||sum||^2 / N) / (N - 1).
+// A level's state is (N, per-entry FP64 sum of D, FP64 M2), M2 = sum_s ||D_s - mean||_F^2.
+// The level kernels hand over, per chunk of samples, the chunk's sum of D and its own M2
+// (accumulated sample by sample with Welford's update).  The merge folds the chunks into the
+// level strictly in chunk order with Chan's pairwise update
+//     M2 <- M2 + M2_c + N n_c / (N + n_c) ||mean_c - mean||_F^2,   sum <- sum + sum_c,
+// one thread per entry for the sums, so the state is a deterministic function of the samples
+// folded in.  Y_l = sum / N and V_l = M2 / (N - 1).
 #include <algorithm>
 
 #include <cuda_runtime.h>
@@ -18,31 +21,137 @@ namespace {
 constexpr int kMergeThreads = 256;
 constexpr int kMaxMergeChunks = 4096;
 
+// Per-chunk coefficients of Chan's update, the same for every entry: computed once per block
+// and tile of chunks into shared memory.  N_c, the samples before chunk c, has a closed form
+// (n_before plus the ids of the run before the chunk), so the chunks of a tile are independent.
+constexpr int kCoefTile = 128;
+
 template <typename T>
-__global__ void merge_sum_kernel(const T* __restrict__ partial, int nchunks, int64_t mp, double* level_sum)
+struct ChanCoef {
+    T nc;        // n_c
+    T inv_nc;    // 1 / n_c
+    T inv_next;  // 1 / (N_c + n_c)
+    T w;         // N_c n_c / (N_c + n_c)
+};
+
+template <typename T>
+__device__ __forceinline__ void chan_coefs(const ChunkRun& run, int c0, int cnt, ChanCoef<T>* coef)
 {
-    const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (e >= mp) return;
-    double acc = level_sum[e];
-    int c = 0;
-    // eight independent loads in flight, then the adds in chunk order
-    for (; c + 8 <= nchunks; c += 8) {
-        double v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = static_cast<double>(partial[static_cast<int64_t>(c + u) * mp + e]);
-#pragma unroll
-        for (int u = 0; u < 8; ++u) acc += v[u];
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const int c = c0 + i;
+        const uint64_t lo = (run.chunk0 + static_cast<uint64_t>(c)) * run.chunk;
+        const uint64_t before = run.n_before + ((run.s_begin > lo ? run.s_begin : lo) - run.s_begin);
+        const uint64_t nc = chunk_count(run, c);
+        // in T: FP32 partials take FP32 coefficients (FP64 runs at 1/64 of the FP32 rate here)
+        const T nb = static_cast<T>(before), n = static_cast<T>(nc);
+        const T inv_next = T(1) / (nb + n);
+        coef[i] = ChanCoef<T>{n, T(1) / n, inv_next, nb * n * inv_next};
     }
-    for (; c < nchunks; ++c) acc += static_cast<double>(partial[static_cast<int64_t>(c) * mp + e]);
-    level_sum[e] = acc;
 }
 
-// One block: chunk totals in parallel (tiles in fixed order), then one thread
-// adds them to the level's sum of squares in chunk order.
-__global__ void merge_sumsq_kernel(const double* __restrict__ partial_q, int nchunks, int tiles,
-                                   double* level_sumsq)
+// Fold the chunk partials of entry e into its FP64 level sum, in chunk order, and return the
+// entry's share of Chan's between-chunk term, sum_c N_c n_c / (N_c + n_c) (mu_c - mu_{<c})^2
+// (N_c the samples folded before chunk c, mu_c the chunk's mean and mu_{<c} the running mean).
+// The means are carried in the partials' precision T as offsets from a shift K (the level's
+// mean when the run starts, else the first chunk's mean): t = sum_c - n_c K is one fused
+// rounding of a small number and r = sum_{<c} - N_c K stays small, so a mean far above the
+// spread cancels inside the shift instead of inside the squares.  Every thread of the block
+// calls this (the coefficient tiles are built together); `active` selects the entry's work.
+template <typename T>
+__device__ __forceinline__ double chan_fold(const T* __restrict__ partial, int64_t mp, int64_t e, bool active,
+                                            const ChunkRun& run, double* __restrict__ sum_e, ChanCoef<T>* coef)
 {
-    __shared__ double chunk_q[kMaxMergeChunks];
+    double acc = active ? *sum_e : 0.0;
+    double chan = 0.0;
+    T K = T(0), r = T(0);
+    int c = 0;
+    if (run.n_before > 0) {
+        const double N = static_cast<double>(run.n_before);
+        K = static_cast<T>(acc / N);
+        r = static_cast<T>(acc - N * static_cast<double>(K));
+    } else if (active) {
+        const T v = partial[e];
+        const T nc = static_cast<T>(chunk_count(run, 0));
+        K = v / nc;
+        r = fma(-nc, K, v);
+        acc += static_cast<double>(v);
+    }
+    if (run.n_before == 0) c = 1;
+    T inv_N = T(0);
+    for (int t0 = c; t0 < run.nchunks; t0 += kCoefTile) {
+        const int cnt = min(kCoefTile, run.nchunks - t0);
+        __syncthreads();   // the previous tile's coefficients are no longer read
+        chan_coefs<T>(run, t0, cnt, coef);
+        __syncthreads();
+        if (t0 == c) {
+            const uint64_t lo = (run.chunk0 + static_cast<uint64_t>(c)) * run.chunk;
+            const uint64_t before = run.n_before + ((run.s_begin > lo ? run.s_begin : lo) - run.s_begin);
+            inv_N = T(1) / static_cast<T>(before);
+        }
+        if (!active) continue;
+        // eight independent loads in flight, then the folds in chunk order
+        for (int i = 0; i < cnt; i += 8) {
+            const int k = min(8, cnt - i);
+            T v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                v[u] = u < k ? partial[static_cast<int64_t>(t0 + i + u) * mp + e] : T(0);
+            T grp = T(0);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (u < k) {
+                    const ChanCoef<T> cf = coef[i + u];
+                    const T t = fma(-cf.nc, K, v[u]);            // sum_c - n_c K
+                    const T d = t * cf.inv_nc - r * inv_N;       // mu_c - mu_{<c}
+                    grp = fma(cf.w * d, d, grp);
+                    r += t;
+                    acc += static_cast<double>(v[u]);
+                    inv_N = cf.inv_next;
+                }
+            }
+            chan += static_cast<double>(grp);
+        }
+    }
+    if (active) *sum_e = acc;
+    return chan;
+}
+
+// Sum of `v` over a block of kMergeThreads threads in a fixed shape; the result is valid in
+// thread 0.  `red` holds kMergeThreads / 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* red)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    __syncthreads();   // red may still be read by an earlier call
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kMergeThreads / 32; ++w) t += red[w];
+    return t;
+}
+
+// One thread per entry, one block per group of kMergeThreads entries: the sums, and each
+// group's share of the between-chunk term in chan_out[group].
+template <typename T>
+__global__ void __launch_bounds__(kMergeThreads)
+merge_chan_kernel(const T* __restrict__ partial, const ChunkRun run, int64_t mp, double* level_sum,
+                  double* chan_out)
+{
+    __shared__ double red[kMergeThreads / 32];
+    __shared__ ChanCoef<T> coef[kCoefTile];
+    const int64_t e = static_cast<int64_t>(blockIdx.x) * kMergeThreads + threadIdx.x;
+    const double chan = chan_fold<T>(partial, mp, e, e < mp, run, level_sum + e, coef);
+    const double t = block_sum(chan, red);
+    if (threadIdx.x == 0) chan_out[blockIdx.x] = t;
+}
+
+// M2 <- M2 + sum_c M2_c (chunk order; M2_c the sum over the chunk's tiles) + sum of the groups'
+// between-chunk terms (group order).  One block.
+__device__ __forceinline__ void fold_m2(const double* __restrict__ partial_q, int nchunks, int tiles,
+                                        const double* __restrict__ chan, int groups, double* level_M2,
+                                        double* chunk_q)
+{
     for (int c = threadIdx.x; c < nchunks; c += blockDim.x) {
         double t = 0.0;
         for (int x = 0; x < tiles; ++x) t += partial_q[static_cast<int64_t>(c) * tiles + x];
@@ -50,77 +159,66 @@ __global__ void merge_sumsq_kernel(const double* __restrict__ partial_q, int nch
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double acc = *level_sumsq;
+        double acc = *level_M2;
         for (int c = 0; c < nchunks; ++c) acc += chunk_q[c];
-        *level_sumsq = acc;
+        for (int g = 0; g < groups; ++g) acc += chan[g];
+        *level_M2 = acc;
     }
+    __syncthreads();
+}
+
+__global__ void merge_m2_kernel(const double* __restrict__ partial_q, int nchunks, int tiles,
+                                const double* __restrict__ chan, int groups, double* level_M2)
+{
+    __shared__ double chunk_q[kMaxMergeChunks];
+    fold_m2(partial_q, nchunks, tiles, chan, groups, level_M2, chunk_q);
 }
 
 // Batched merge: the jobs of one wave (count read from the device), each folded into its
-// level's FP64 state in chunk order exactly as merge_sum_kernel / merge_sumsq_kernel do.  The
-// grid is fixed (grid-stride over jobs in y and elements in x) so that a captured graph stays
-// valid when the wave's contents change; a wave holds at most one job per (problem, level).
-__global__ void merge_batch_kernel(const MergeJob* __restrict__ jobs, const int* __restrict__ njobs_dev)
+// level's FP64 state exactly as merge_chan_kernel / merge_m2_kernel do (the same per-entry fold,
+// the same groups of kMergeThreads entries, the same orders), so a batched call and the same
+// ranges run one by one give the same bits.  The grid is fixed (grid-stride over jobs in y and
+// entry groups in x) so that a captured graph stays valid when the wave's contents change; a
+// wave holds at most one job per (problem, level).
+__global__ void __launch_bounds__(kMergeThreads) merge_batch_kernel(const MergeJob* __restrict__ jobs,
+                                                                    const int* __restrict__ njobs_dev)
 {
-    __shared__ double chunk_q[kMaxMergeChunks];
+    __shared__ double red[kMergeThreads / 32];
+    __shared__ ChanCoef<float> coef[kCoefTile];
     const int njobs = *njobs_dev;
     for (int j = blockIdx.y; j < njobs; j += gridDim.y) {
         const MergeJob jb = jobs[j];
-        for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < jb.mp;
-             e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-            double acc = jb.sum[e];
-            int c = 0;
-            for (; c + 8 <= jb.nchunks; c += 8) {
-                float v[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) v[u] = jb.partial[static_cast<int64_t>(c + u) * jb.mp + e];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) acc += static_cast<double>(v[u]);
-            }
-            for (; c < jb.nchunks; ++c) acc += static_cast<double>(jb.partial[static_cast<int64_t>(c) * jb.mp + e]);
-            jb.sum[e] = acc;
-        }
-        if (blockIdx.x == 0) {
-            for (int c = threadIdx.x; c < jb.nchunks; c += blockDim.x) {
-                double t = 0.0;
-                for (int x = 0; x < jb.tiles; ++x) t += jb.partial_q[static_cast<int64_t>(c) * jb.tiles + x];
-                chunk_q[c] = t;
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                double acc = *jb.sumsq;
-                for (int c = 0; c < jb.nchunks; ++c) acc += chunk_q[c];
-                *jb.sumsq = acc;
-            }
-            __syncthreads();
+        const int64_t groups = (jb.mp + kMergeThreads - 1) / kMergeThreads;
+        for (int64_t g = blockIdx.x; g < groups; g += gridDim.x) {
+            const int64_t e = g * kMergeThreads + threadIdx.x;
+            const double chan = chan_fold<float>(jb.partial, jb.mp, e, e < jb.mp, jb.run, jb.sum + e, coef);
+            const double t = block_sum(chan, red);
+            if (threadIdx.x == 0) jb.chan[g] = t;
         }
     }
 }
 
-// One block per level: ||sum||^2 by a fixed-shape reduction, then M2.
-__global__ void finalize_kernel(const double* __restrict__ sum, const double* __restrict__ sumsq,
-                                const LevelCounts counts, int first, int64_t mp, double* mean, double* M2)
+__global__ void merge_batch_m2_kernel(const MergeJob* __restrict__ jobs, const int* __restrict__ njobs_dev)
 {
-    __shared__ double red[kMergeThreads / 32];
-    const int lvl = blockIdx.x;
-    const double* s = sum + static_cast<int64_t>(lvl) * mp;
+    __shared__ double chunk_q[kMaxMergeChunks];
+    const int njobs = *njobs_dev;
+    for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
+        const MergeJob jb = jobs[j];
+        const int groups = static_cast<int>((jb.mp + kMergeThreads - 1) / kMergeThreads);
+        fold_m2(jb.partial_q, jb.run.nchunks, jb.tiles, jb.chan, groups, jb.M2, chunk_q);
+    }
+}
+
+// mean = sum / N for `count` levels laid out back to back.
+__global__ void finalize_kernel(const double* __restrict__ sum, const LevelCounts counts, int first, int64_t mp,
+                                double* mean)
+{
+    const int lvl = blockIdx.y;
+    const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= mp) return;
     const uint64_t n = counts.v[first + lvl];
     const double inv = n > 0 ? 1.0 / static_cast<double>(n) : 0.0;
-    double local = 0.0;
-    for (int64_t e = threadIdx.x; e < mp; e += blockDim.x) {
-        const double v = s[e];
-        local = fma(v, v, local);
-        if (mean) mean[static_cast<int64_t>(lvl) * mp + e] = v * inv;
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) local += __shfl_xor_sync(0xffffffffu, local, off);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = local;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < kMergeThreads / 32; ++w) t += red[w];
-        M2[lvl] = n > 0 ? sumsq[lvl] - t * inv : 0.0;
-    }
+    mean[static_cast<int64_t>(lvl) * mp + e] = sum[static_cast<int64_t>(lvl) * mp + e] * inv;
 }
 
 __global__ void telescoping_kernel(const double* __restrict__ sum, const LevelCounts counts, int levels,
@@ -285,35 +383,42 @@ inline unsigned blocks_for(int64_t n, int threads) { return static_cast<unsigned
 
 }  // namespace
 
-cudaError_t launch_merge_partials(const void* partial_sum, bool partial_f64, const double* partial_q,
-                                  int nchunks, int tiles, int64_t mp, double* level_sum, double* level_sumsq,
-                                  cudaStream_t st)
+int merge_groups(int64_t mp) { return static_cast<int>((mp + kMergeThreads - 1) / kMergeThreads); }
+
+cudaError_t launch_merge_partials(const void* partial_sum, bool partial_f64, const double* partial_q, int tiles,
+                                  int64_t mp, const ChunkRun& run, double* level_sum, double* level_M2,
+                                  double* chan_scratch, cudaStream_t st)
 {
-    if (nchunks > kMaxMergeChunks) return cudaErrorInvalidValue;
-    const unsigned g = blocks_for(mp, kMergeThreads);
+    if (run.nchunks < 1 || run.nchunks > kMaxMergeChunks) return cudaErrorInvalidValue;
+    const unsigned g = static_cast<unsigned>(merge_groups(mp));
     if (partial_f64)
-        merge_sum_kernel<double><<<g, kMergeThreads, 0, st>>>(static_cast<const double*>(partial_sum), nchunks,
-                                                              mp, level_sum);
+        merge_chan_kernel<double><<<g, kMergeThreads, 0, st>>>(static_cast<const double*>(partial_sum), run, mp,
+                                                               level_sum, chan_scratch);
     else
-        merge_sum_kernel<float><<<g, kMergeThreads, 0, st>>>(static_cast<const float*>(partial_sum), nchunks,
-                                                             mp, level_sum);
+        merge_chan_kernel<float><<<g, kMergeThreads, 0, st>>>(static_cast<const float*>(partial_sum), run, mp,
+                                                              level_sum, chan_scratch);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
-    merge_sumsq_kernel<<<1, kMergeThreads, 0, st>>>(partial_q, nchunks, tiles, level_sumsq);
+    merge_m2_kernel<<<1, kMergeThreads, 0, st>>>(partial_q, run.nchunks, tiles, chan_scratch, static_cast<int>(g),
+                                                level_M2);
     return cudaGetLastError();
 }
 
 cudaError_t launch_merge_batch(const MergeJob* jobs, const int* njobs_dev, cudaStream_t st)
 {
     merge_batch_kernel<<<dim3(64, 256), kMergeThreads, 0, st>>>(jobs, njobs_dev);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    merge_batch_m2_kernel<<<256, kMergeThreads, 0, st>>>(jobs, njobs_dev);
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const double* sum, const double* sumsq, LevelCounts counts, int first, int count,
-                            int64_t mp, double* mean, double* M2, cudaStream_t st)
+cudaError_t launch_finalize(const double* sum, LevelCounts counts, int first, int count, int64_t mp, double* mean,
+                            cudaStream_t st)
 {
-    if (count <= 0) return cudaSuccess;
-    finalize_kernel<<<count, kMergeThreads, 0, st>>>(sum, sumsq, counts, first, mp, mean, M2);
+    if (count <= 0 || mp <= 0) return cudaSuccess;
+    finalize_kernel<<<dim3(blocks_for(mp, kMergeThreads), static_cast<unsigned>(count)), kMergeThreads, 0, st>>>(
+        sum, counts, first, mp, mean);
     return cudaGetLastError();
 }
 

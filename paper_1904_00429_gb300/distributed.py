@@ -3,18 +3,20 @@
 Samples of a level are independent and every draw is a pure function of (seed, problem, level,
 sample, entry), so the sample ids of each round (the pilot, then the top-up of the allocation)
 are split into contiguous, chunk-aligned shards, one per rank.  Each rank folds its shard into
-an empty copy of the level statistics, the per-level raw sums (N, sum of D, sum of ||D||_F^2)
-are added over the ranks with one all-reduce per round, and the merged statistics replace every
-rank's own, so every rank computes the same variances and the same allocation N_l (Remark 3.6)
-and the same estimate Yhat (Eq. hatY).  The merged sums equal the single-process ones up to the
-order of the FP64 additions.
+an empty copy of the level statistics; the per-level states (N, sum of D, M2) of all ranks are
+gathered with one all-gather per round, and every rank folds them, in rank order, into the
+statistics merged so far with the library's Chan update (mlmc_merge_level_state).  Every rank
+thus holds the same statistics, computes the same variances, allocation N_l (Remark 3.6,
+mlmc_allocate / mlmc_allocate_levels), stopping decisions (Remark 3.5, mlmc_bias_test) and
+estimate Yhat (Eq. hatY); they equal the single-process ones up to the order of the FP64
+operations.  No arithmetic of the method runs in this module: it moves states between
+processes and calls the library.
 
 The driver works on any object with the plan methods used below (``binding.Plan`` on a GPU);
-``torch.distributed`` provides the reduction (NCCL between GPUs, gloo on CPUs).
+``torch.distributed`` provides the exchange (NCCL between GPUs, gloo on CPUs).
 """
 from __future__ import annotations
 
-import math
 from typing import List, Optional, Sequence, Tuple
 
 import torch
@@ -45,36 +47,38 @@ def _levels(plan) -> List[Tuple[int, int]]:
 
 
 class _Merged:
-    """The merged (N, sum, sumsq) of every (problem, level), kept beside the plan."""
+    """The merged (N, sum, M2) of every (problem, level), kept beside the plan."""
 
     def __init__(self, plan):
         self.state = {}
         for q, l in _levels(plan):
-            N, s, sq = plan.get_level_state(q, l)
-            self.state[(q, l)] = [N, s.clone(), sq]
+            N, s, M2 = plan.get_level_state(q, l)
+            self.state[(q, l)] = [N, s.clone(), M2]
 
 
-def _allreduce_round(plan, merged: _Merged, group, device) -> None:
+def _gather_round(plan, merged: _Merged, group, device) -> None:
+    """All-gather every rank's round state and fold the states, in rank order, into the merged
+    statistics of the earlier rounds (on every rank, with the same calls)."""
     keys = sorted(merged.state)
     parts = []
     for q, l in keys:
-        N, s, sq = plan.get_level_state(q, l)
-        parts.append(torch.tensor([float(N), sq], dtype=torch.float64, device=device))
+        N, s, M2 = plan.get_level_state(q, l)
+        parts.append(torch.tensor([float(N), M2], dtype=torch.float64, device=device))
         parts.append(s.reshape(-1).to(device=device, dtype=torch.float64))
     flat = torch.cat(parts)
-    dist.all_reduce(flat, op=dist.ReduceOp.SUM, group=group)
+    gathered = [torch.empty_like(flat) for _ in range(dist.get_world_size(group))]
+    dist.all_gather(gathered, flat, group=group)
     off = 0
     for q, l in keys:
-        N, sq = int(round(float(flat[off]))), float(flat[off + 1])
-        off += 2
         entry = merged.state[(q, l)]
         n_el = entry[1].numel()
-        s = flat[off:off + n_el].reshape(entry[1].shape).to(entry[1].device)
-        off += n_el
-        entry[0] += N
-        entry[1] = entry[1] + s
-        entry[2] += sq
         plan.set_level_state(q, l, entry[0], entry[1], entry[2])
+        for g in gathered:
+            N, M2 = int(round(float(g[off]))), float(g[off + 1])
+            plan.merge_level_state(q, l, N, g[off + 2:off + 2 + n_el].reshape(entry[1].shape), M2)
+        off += 2 + n_el
+        N, s, M2 = plan.get_level_state(q, l)
+        merged.state[(q, l)] = [N, s.clone(), M2]
 
 
 def _run_round(plan, ranges: Sequence[Tuple[int, int, int, int]], merged: _Merged, group, device) -> None:
@@ -88,34 +92,16 @@ def _run_round(plan, ranges: Sequence[Tuple[int, int, int, int]], merged: _Merge
             mine.append((q, l, sb, sc))
     if mine:
         plan.level_stats_batch(mine)
-    _allreduce_round(plan, merged, group, device)
-
-
-def _allocate(plan, merged: _Merged, q: int, L: int, eps: float) -> List[int]:
-    """N_l of levels 0..L (Remark 3.6 with C_0 = c_0, C_l = c_l + c_{l-1}) from the merged sums."""
-    c = [plan.c0 * plan.ratio ** l for l in range(L + 1)]
-    V, C = [], []
-    for l in range(L + 1):
-        N, s, sq = merged.state[(q, l)]
-        M2 = sq - float((s * s).sum()) / N
-        V.append(max(0.0, M2 / (N - 1)))
-        C.append(float(c[0] if l == 0 else c[l] + c[l - 1]))
-    root = sum(math.sqrt(v * cc) for v, cc in zip(V, C))
-    return [max(plan.pilot_n, int(math.ceil(plan.nl_scale * 2.0 / eps**2 * math.sqrt(v / cc) * root)))
-            for v, cc in zip(V, C)]
-
-
-def _mean_norm(merged: _Merged, q: int, l: int) -> float:
-    N, s, _ = merged.state[(q, l)]
-    return float(torch.linalg.norm(s.double())) / N if N > 0 else 0.0
+    _gather_round(plan, merged, group, device)
 
 
 def _estimate_adaptive(plan, eps_abs, group, device):
     """Alg. 2 choosing L per problem: rounds on levels 0..L_q for L_q = 0, 1, ... (pilot on the new
     level, allocation over levels 0..L_q from the merged sums, top-ups), stopping after the first
     round with L_q >= 2 whose finest mean satisfies ||Y_L||_F < (sqrt(R) + 1) eps / sqrt(2)
-    (Remark 3.5), or at the plan's L for the problem.  The decisions use merged statistics, so
-    every rank takes the same ones."""
+    (Remark 3.5), or at the plan's L for the problem.  The allocation and the stopping test are
+    the library's (mlmc_allocate_levels, mlmc_bias_test) on the merged statistics, so every rank
+    takes the same decisions."""
     merged = _Merged(plan)
     nprob = len(plan.problems)
     Lc = [0] * nprob
@@ -133,7 +119,7 @@ def _estimate_adaptive(plan, eps_abs, group, device):
         ranges = []
         for q in range(nprob):
             if running[q]:
-                Nl = _allocate(plan, merged, q, Lc[q], eps_abs[q])
+                Nl = plan.allocate_levels(q, Lc[q], eps_abs[q])
                 for l in range(Lc[q] + 1):
                     have = merged.state[(q, l)][0]
                     if Nl[l] > have:
@@ -143,8 +129,7 @@ def _estimate_adaptive(plan, eps_abs, group, device):
         for q in range(nprob):
             if not running[q]:
                 continue
-            bound = (math.sqrt(plan.ratio) + 1.0) * eps_abs[q] / math.sqrt(2.0)
-            if Lc[q] >= 2 and _mean_norm(merged, q, Lc[q]) < bound:
+            if Lc[q] >= 2 and plan.bias_test(q, Lc[q], eps_abs[q])[0]:
                 running[q] = False
             elif Lc[q] == plan.levels[q]:
                 running[q] = False

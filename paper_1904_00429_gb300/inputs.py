@@ -79,6 +79,24 @@ def make_params(m: int, n: int, p: int, *, law: str = "uniform", seed_A: int = 0
     return pp.as_dtype(dtype)
 
 
+def make_concentrated_params(m: int, n: int, p: int, *, spread: float = 1e-4, seed_A: int = 0, seed_B: int = 1,
+                             seed_idx: int = 2, problem_id: int = 0, dtype=np.float64) -> ProblemParams:
+    """A problem whose sketches barely vary: every column of M is the same vector u and every
+    row of M' the same vector v (u, v ~ U[0.5, 1.5]), and S = spread u o U[0.5, 1],
+    S' = spread U[0.5, 1] o v.  A sampled outer product is then u v^T up to O(spread), so the
+    level-0 mean (about n u v^T) exceeds the spread of the samples by far more than 10^4: the
+    regime in which a variance must not be formed as a difference of large sums."""
+    ra, rb = _rng(seed_A, problem_id), _rng(seed_B, problem_id)
+    u = ra.uniform(0.5, 1.5, size=(m, 1))
+    v = rb.uniform(0.5, 1.5, size=(1, p))
+    M = np.repeat(u, n, axis=1)
+    S = spread * u * ra.uniform(0.5, 1.0, size=(m, n))
+    Mp = np.repeat(v, n, axis=0)
+    Sp = spread * v * rb.uniform(0.5, 1.0, size=(n, p))
+    pp = ProblemParams(M, S, Mp, Sp, seed_A, seed_B, seed_idx, problem_id, {"law": "concentrated"})
+    return pp.as_dtype(dtype)
+
+
 def make_target(m: int, p: int, seed: int = 3) -> np.ndarray:
     """A fixed N(0,1) target matrix T (m x p) for the loss ||Yhat - T||_F^2."""
     return _rng(seed, 0xA5).standard_normal(size=(m, p))

@@ -101,7 +101,9 @@ def test_batched_autotuned_matches_one_by_one_sums():
                 else:
                     # FP32 accumulation of at most 64 samples in two orders
                     assert float((sa - sb).abs().max()) <= 64 * 2.0**-23 * float(sb.abs().max())
-                assert abs(qa - qb) <= 1e-6 * qb
+                # M2: FP32 sums of squares per thread (at most 256 columns x 64 samples) grouped by
+                # each tile's drain, and Welford (2256) against the raw form (zero-mean levels)
+                assert abs(qa - qb) <= 2e-5 * qb
 
 
 def test_batched_many_waves_and_graph_replay():

@@ -1,6 +1,6 @@
 """Parity of the CUDA-core level kernels (FP64, FP32) with the FP64 CPU oracle, through the C ABI.
 
-Bars (derived from the arithmetic, see DESIGN.md):
+Bars (derived from the arithmetic):
   * Philox words and sampled indices: bit-exact.
   * FP64: every entry of a sample D within 1e-12 * mag, where mag is the oracle's
     sum over the products entering D of |w| (|M| + |S Z|)(|M'| + |S' Z'|); level means within

@@ -1,6 +1,6 @@
 """Parity of the BF16 tensor-core level kernel with the FP64 oracle, through the C ABI.
 
-Bars (derived from the arithmetic, see DESIGN.md):
+Bars (derived from the arithmetic):
   * against the plain FP64 oracle: |D - D_oracle| <= tau_bf16(c) * mag with
     tau_bf16(c) = 2^-7 + 2^-15 + (c + 8) 2^-23: both operands rounded to bfloat16 (unit roundoff
     2^-8 each, so 2u + u^2 per product), FP32 generation of the entries (2^-16 each), and FP32
@@ -147,8 +147,8 @@ PAIR_CASES = [
 def test_bf16_cta_pair_tile_matches_oracle_and_single_cta_tile(m, n, p, c0, L, picks):
     """Tile 3256 (two CTAs of a cluster share a 256 x 256 tile, each generating half of B for both)
     against the FP64 oracle, and its level sums against the 128 x 256 single-CTA tile (the same
-    MMA chain per element, so the sums of D agree bit for bit; the sums of ||D||^2 are grouped by
-    the drain's column split, so they agree up to rounding)."""
+    MMA chain per element, so the sums of D agree bit for bit; the M2 are grouped by the drain's
+    column split, so they agree up to FP32 rounding)."""
     pp = make_params(m, n, p, seed_A=3, seed_B=4, seed_idx=5, problem_id=1, dtype=np.float32)
     orc = _orc(pp)
     lv = oracle.Levels(c0, 2, L)
@@ -166,7 +166,9 @@ def test_bf16_cta_pair_tile_matches_oracle_and_single_cta_tile(m, n, p, c0, L, p
             nb, sb, qb = b.get_level_state(0, l)
             assert na == nb == 96
             assert torch.equal(sa, sb)
-            assert abs(qa - qb) <= 1e-12 * qb
+            # M2 is accumulated per thread in FP32 (at most 128 columns x 64 samples of squares, a
+            # relative rounding of at most 192 * 2^-24 each) and grouped by the drain's column split
+            assert abs(qa - qb) <= 2e-5 * qb
 
 
 def test_generation_rate_is_measured():

@@ -4,9 +4,11 @@ Callers inside CUDA-graph stream capture, inference-runtime plugins that must no
 their enqueue step, and applications that hand all device memory to their own pool cannot go
 through mlmc_plan (it allocates).  The no-alloc entry point keeps its scratch in a fixed array
 of the library image instead.  This test calls it through the C ABI twice in a row (the second
-call reuses the scratch the first one left behind) and compares each result with what the
-plan-based entry points (mlmc_level_stats + mlmc_get_level_state) give for the same samples,
-within the FP64 parity tolerance of the other tests (1e-12 of the summed term magnitudes).
+call reuses the scratch the first one left behind) and compares each result (the sum of D and
+the level's M2) with what the plan-based entry points (mlmc_level_stats + mlmc_get_level_state)
+give for the same samples, within the FP64 parity tolerance of the other tests (1e-12 of the
+summed term magnitudes); a problem near the size limit makes one call run several launches,
+each folding its chunks into the outputs left by the one before.
 
 The file is named so that pytest collects it last.
 """
@@ -54,9 +56,9 @@ def _plan_state(tensors, pp, c0, L, level, begin, count, precision):
                                problem_id=pp.problem_id)
     with binding.Plan([spec], c0=c0, L=L, precision=precision) as plan:
         plan.level_stats(0, level, begin, count)
-        N, s, q = plan.get_level_state(0, level)
+        N, s, M2 = plan.get_level_state(0, level)
         assert N == count
-        return s.clone(), q
+        return s.clone(), M2
 
 
 @pytest.mark.parametrize("precision,np_dtype,t_dtype,code", [("fp64", np.float64, torch.float64, 0),
@@ -80,6 +82,29 @@ def test_noalloc_matches_plan_path_on_two_calls_in_a_row(precision, np_dtype, t_
         diff = np.abs(s_na.cpu().numpy() - s_plan.cpu().numpy())
         assert np.all(diff <= bound), diff.max()
         assert abs(float(q_na.item()) - q_plan) <= tol * count * float((magm**2).sum()) + 1e-12 * q_plan
+
+
+def test_noalloc_near_its_size_limit_runs_several_launches():
+    """m = p = 700 in FP64: one chunk of partials fills most of the 4 MiB scratch, so a call over
+    50 samples starting at a ragged id runs seven launches (chunks of 8 ids), each merging into
+    the outputs of the previous one; twice in a row, against the plan path."""
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream(dev)
+    m, n, p, c0, L = 700, 300, 700, 8, 2
+    pp = make_params(m, n, p, seed_A=31, seed_B=32, seed_idx=33, problem_id=2)
+    tensors = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (pp.M, pp.S, pp.Mp, pp.Sp)]
+    orc = oracle.Problem(*pp.f64(), seed_A=31, seed_B=32, seed_idx=33, problem_id=2)
+    lv = oracle.Levels(c0, 2, L)
+    for level, begin, count in [(2, 3, 50), (1, 101, 50)]:
+        rc, s_na, q_na = _noalloc(tensors, pp, c0, level, begin, count, "fp64", 0, stream)
+        assert rc == 0, binding.lib().mlmc_last_error()
+        s_plan, q_plan = _plan_state(tensors, pp, c0, L, level, begin, count, "fp64")
+        torch.cuda.synchronize()
+        # magnitude scale of one sample's terms (the oracle on one sample is enough for the bound)
+        _, _, _, mag = oracle.sample(orc, lv, level, begin)
+        diff = np.abs(s_na.cpu().numpy() - s_plan.cpu().numpy())
+        assert np.all(diff <= 1e-12 * count * 4.0 * mag), diff.max()
+        assert abs(float(q_na.item()) - q_plan) <= 1e-11 * q_plan
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
