@@ -41,8 +41,20 @@ import numpy as np  # noqa: E402
 
 WORKLOAD = dict(name="mlmc_256x65536x256", m=256, n=65536, p=256, c0=64, R=2, L=8, pilot=256, rel_rmse=1e-3)
 FRACTION = {"fp32": 2.0**-20, "fp64": 2.0**-26, "bf16": 2.0**-18, "fp8": 2.0**-18}
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # CUDA-core FMA lanes x 2 flop x max SM clock
-FP64_PEAK_TFLOPS = 1.25
+# ALU peaks (TFLOP/s), replaced at run time by mlmc_measure_peaks (FP32 / FP64 fused multiply-add
+# chains at full occupancy on this GPU); the unit-count figure below is the fallback only
+ALU_PEAKS = {"fp32": 152 * 128 * 2 * 2.070e9 / 1e12, "fp64": None,
+             "source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived; not measured in this run)"}
+
+
+def measure_alu_peaks(stream):
+    """Measure the FP32 / FP64 peaks on this GPU (mlmc_measure_peaks) and keep them for the
+    rooflines of the CUDA-core kernels; returns the full measurement."""
+    from paper_1904_00429_gb300 import binding
+    pk = binding.measure_peaks(stream)
+    ALU_PEAKS.update({"fp32": pk["fp32_flops"] / 1e12, "fp64": pk["fp64_flops"] / 1e12,
+                      "source": "mlmc_measure_peaks in this run (FMA chains at full occupancy)"})
+    return pk
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel from one ncu capture
 # (profiles/); None once the kernel changed after the capture
 TRAFFIC = {
@@ -50,13 +62,16 @@ TRAFFIC = {
     # outer products), used for every level
     "fp32": {"dram_bytes_per_outer_product": {0: 790.9e6 / 262144, 8: 790.9e6 / 262144},
              "source": "profiles/level_cuda_core_f32_mlmc_256x65536x256.md"},
-    # DRAM bytes (read + write) per sampled outer product of the CTA-pair kernel (tile 3256), per
-    # level, from a capture of dram__bytes_{read,write}.sum (one ncu pass) over every level launch
-    # of the timed steps of this workload
-    "bf16": {"dram_bytes_per_outer_product": {0: 2816.7, 1: 2776.2, 2: 2775.0, 3: 2775.5, 4: 2775.7,
-                                              5: 2755.3, 6: 2744.3, 7: 2739.4, 8: 2737.2},
+    # DRAM bytes (read + write) per sampled outer product of the CTA-pair kernel (tile 3256) at
+    # levels 0 and 8, each from one ncu pass over one launch of the bench's profile case
+    # (16384 level-0 samples, 2432 level-8 samples of this workload); levels between are
+    # interpolated, and bench.py scales them by the outer products of its own launches
+    "bf16": {"dram_bytes_per_outer_product": {0: (2902364416 + 62743296) / 1048576,
+                                              8: (108993357568 + 76798720) / 39845888},
              "source": "profiles/level_tc_bf16_mlmc_256x65536x256.md"},
-    "fp8": None,
+    "fp8": {"dram_bytes_per_outer_product": {0: (2901204224 + 62871296) / 1048576,
+                                             8: (108976157440 + 83111680) / 39845888},
+            "source": "profiles/level_tc_bf16_mlmc_256x65536x256.md"},
 }
 
 
@@ -280,7 +295,7 @@ def _measure(args, prec, W, host, dev, rank, stream, world, with_e2e):
     def make_plan(tensors):
         spec = binding.ProblemSpec(*tensors, seed_A=0, seed_B=1, seed_idx=2, problem_id=rank)
         return binding.Plan([spec], c0=W["c0"], L=W["L"], ratio=W["R"], precision=prec, pilot_n=W["pilot"],
-                            stream=stream)
+                            tile_override=args.tile if prec in ("bf16", "fp8") else 0, stream=stream)
 
     pdtype = torch.float64 if prec == "fp64" else torch.float32
     dev_params = [h.to(dev, pdtype, non_blocking=True) for h in host]
@@ -375,10 +390,10 @@ def _roofline(res, W, peaks, peak_kind, gen_rate=None):
         traffic = {"value": dram / level_launches, "unit": "bytes per launch", "launches": level_launches,
                    "algorithmic_bytes_per_launch": bytes_alg / level_launches, "source": TRAFFIC[prec]["source"]}
     if prec in ("fp32", "fp64"):
-        peak = FP32_PEAK_TFLOPS if prec == "fp32" else FP64_PEAK_TFLOPS
+        peak = ALU_PEAKS[prec]
         achieved = flops / t / 1e12
-        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)",
+        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if peak else None, "traffic": traffic, "peak_source": ALU_PEAKS["source"],
                 "hbm_achieved_gbs": bytes_alg / t / 1e9, "hbm_peak_gbs": peaks["hbm_gbs"],
                 "kernel": f"level_cuda_core_kernel<{prec}>"}
     # tensor-core path: the slower of gathered bytes at HBM bandwidth and FLOPs at the tensor peak
@@ -506,6 +521,96 @@ def _measure_ladder(args, rels, W, host, exact, dev, stream, projected):
             "unit": "s", "rungs": rungs, "projected_1e-3_s": projected}
 
 
+TTR = dict(name="mlmc_64x1024x64", m=64, n=1024, p=64, c0=16, R=2, L=5, pilot=256)
+
+
+def _measure_ttr(args, rels, precs, dev, stream):
+    """Time-to-RMSE measured end to end on the 64 x 1024 x 64 workload (M ~ U[-1,1], S ~ U[0.1,1],
+    A from seed 0, B from seed 1, c_l = 16 * 2^l for l = 0..5): for every precision and relative
+    target a fresh plan runs Alg. 2 through mlmc_estimate (pilot of 256 samples per level, the
+    allocation of Remark 3.6 for eps = rel * ||M M'||_F, the top-up), timed on the host around the
+    call (which returns with the estimate on the device).  The achieved error ||Yhat - M M'||_F is
+    set against eps: the allocation aims at eps / sqrt(2)."""
+    import torch
+
+    from paper_1904_00429_gb300 import binding
+    from paper_1904_00429_gb300.inputs import make_params
+
+    T = TTR
+    pp = make_params(T["m"], T["n"], T["p"], seed_A=0, seed_B=1, dtype=np.float32)
+    exact = pp.exact_mean()
+    norm = float(np.linalg.norm(exact))
+    out = {"workload": T["name"], "metric": "time-to-RMSE measured end to end through mlmc_estimate",
+           "unit": "s", "m": T["m"], "n": T["n"], "p": T["p"], "c0": T["c0"], "ratio": T["R"], "L": T["L"],
+           "pilot": T["pilot"], "runs": []}
+    for prec in precs:
+        pdt = torch.float64 if prec == "fp64" else torch.float32
+        ts = [torch.from_numpy(np.ascontiguousarray(x)).to(dev, pdt) for x in (pp.M, pp.S, pp.Mp, pp.Sp)]
+        for rel in rels:
+            eps = rel * norm
+            spec = binding.ProblemSpec(*ts, seed_A=0, seed_B=1, seed_idx=2, problem_id=0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with binding.Plan([spec], c0=T["c0"], L=T["L"], ratio=T["R"], precision=prec, pilot_n=T["pilot"],
+                              stream=stream) as plan:
+                launches0 = plan.launch_count()
+                (Y,), (rep,) = plan.estimate([eps])
+                torch.cuda.synchronize()
+                t = time.perf_counter() - t0
+                launches = plan.launch_count() - launches0
+            err = float(np.linalg.norm(Y.cpu().numpy() - exact))
+            out["runs"].append({"precision": prec, "rel_rmse": rel, "eps_abs": eps, "seconds": t,
+                                "error": err, "error_over_eps": err / eps, "rmse_pred": rep["rmse_pred"],
+                                "N_l": rep["N"], "V_l": rep["V"], "outer_products": rep["outer_products"],
+                                "outer_products_per_s": rep["outer_products"] / t, "gpu_launches": launches})
+        del ts
+    by = {(r["precision"], r["rel_rmse"]): r["seconds"] for r in out["runs"]}
+    out["fp32_over"] = {f"{p}@{rel:g}": by[("fp32", rel)] / by[(p, rel)]
+                        for p in precs for rel in rels if p != "fp32" and ("fp32", rel) in by}
+    return out
+
+
+def _measure_dedupe_bound(args, head, W, dev, stream):
+    """Index dedupe (merging the repeated draws of one sample, the note after Alg. 1) would save
+    at most the repeated slots' share of each level's work.  Measured on the draws themselves:
+    the fraction of a sample's c_l slots whose index already appeared earlier in the sample,
+    over 16 samples per level drawn by the library (mlmc_debug_indices), for the headline
+    workload and the 64 x 1024 x 64 workload; weighted by each level's measured share of the
+    headline's time (N_l t_l), and by the cost split C_l of the 64 x 1024 x 64 allocation."""
+    import torch
+
+    from paper_1904_00429_gb300 import binding
+    from paper_1904_00429_gb300.inputs import make_params
+
+    out = {}
+    for name, (m, n, p, c0, L) in {"mlmc_256x65536x256": (W["m"], W["n"], W["p"], W["c0"], W["L"]),
+                                   "mlmc_64x1024x64": (64, 1024, 64, 16, 5)}.items():
+        # the index draws depend only on n, the level and the sample: a one-row stand-in keeps the plan small
+        pp = make_params(1, n, 1, seed_A=0, seed_B=1, dtype=np.float32)
+        ts = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (pp.M, pp.S, pp.Mp, pp.Sp)]
+        with binding.Plan([binding.ProblemSpec(*ts, seed_A=0, seed_B=1, seed_idx=2)], c0=c0, L=L,
+                          precision="fp32", stream=stream) as plan:
+            frac = []
+            for l in range(L + 1):
+                c = c0 * 2 ** l
+                rep = 0
+                for smp in range(16):
+                    idx = plan.debug_indices(0, l, 10_000 + smp, 0, c).cpu().numpy()
+                    rep += c - len(np.unique(idx))
+                frac.append(rep / (16.0 * c))
+        if name == W["name"] and head is not None:
+            share = [nl * t for nl, t in zip(head["Nl"], head["t_l"])]
+        else:
+            share = [1.0] * (L + 1)   # equal cost per level (the allocation's sqrt(V_l C_l) is about level-free)
+        tot = sum(share)
+        bound = sum(f * sh for f, sh in zip(frac, share)) / tot
+        out[name] = {"repeated_slot_fraction_per_level": frac, "expected_c2_over_2n": [min(1.0, (c0 * 2**l) / (2.0 * n))
+                                                                                    for l in range(L + 1)],
+                     "time_saving_upper_bound": bound,
+                     "weights": "measured N_l t_l of the headline" if name == W["name"] else "equal per level"}
+    return out
+
+
 NONLINEAR = dict(name="abs_step_64x1024x64", m=64, n=1024, p=64, c0=16, R=2, Lmax=12, pilot=256, eps_entry=0.01,
                  precision="fp32")
 
@@ -521,11 +626,35 @@ def _nonlinear_params():
     return [x.astype(np.float32) for x in (pp.M * k + 2.0 / Nw["n"], pp.S * k, pp.Mp, pp.Sp)]
 
 
+def _mc_at_finest(spec, Nw, c, eps, sampling, stream):
+    """Standard MC at one level of c draws (Eq. Phigh) under the sampling law `sampling`: pilot,
+    allocation for the variance target eps^2 / 2, then a bounded timed batch projected to the
+    allocated N (seconds, N, seconds per sample)."""
+    import torch
+
+    from paper_1904_00429_gb300 import binding
+
+    with binding.Plan([spec], c0=c, L=0, ratio=2, precision=Nw["precision"], f="abs_step", sampling=sampling,
+                      pilot_n=Nw["pilot"], stream=stream) as mc:
+        mc.level_stats(0, 0, 0, Nw["pilot"])
+        N_mc = int(mc.allocate([eps])[0][0])
+        batch = max(64, min(N_mc, int(2e8 // c)))
+        mc.level_stats(0, 0, Nw["pilot"], 64)   # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mc.level_stats(0, 0, Nw["pilot"] + 64, batch)
+        torch.cuda.synchronize()
+        per_sample = (time.perf_counter() - t0) / batch
+    return N_mc * per_sample, N_mc, per_sample, batch
+
+
 def _measure_nonlinear(args, dev, stream):
     """E[f(AB)] with f(x) = |x| H(2 - x) (the paper's matrix example) on the CUDA cores (FP32):
     Alg. 2 with the adaptive choice of L, end to end through mlmc_estimate, against standard MC
     at the finest level MLMC chose (Eq. Phigh: one level of c_L draws, the same variance target
-    eps^2 / 2), whose time is measured on a bounded batch and projected to its allocated N."""
+    eps^2 / 2) under the uniform law and under xi** (Thm 3.1, the comparator of the paper's
+    Table 2), each timed on a bounded batch and projected to its allocated N; for level ratios
+    R = 2, 4 and 10 (the paper's experiments use 10)."""
     import torch
 
     from paper_1904_00429_gb300 import binding
@@ -534,44 +663,44 @@ def _measure_nonlinear(args, dev, stream):
     ts = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in _nonlinear_params()]
     eps = Nw["eps_entry"] * math.sqrt(Nw["m"] * Nw["p"])
     spec = binding.ProblemSpec(*ts, seed_A=7, seed_B=8, seed_idx=9, problem_id=0)
-    with binding.Plan([spec], c0=Nw["c0"], L=Nw["Lmax"], ratio=Nw["R"], precision=Nw["precision"], f="abs_step",
-                      adaptive_L=True, pilot_n=Nw["pilot"], stream=stream) as plan:
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        (Y,), (rep,) = plan.estimate([eps])
-        torch.cuda.synchronize()
-        t_mlmc = time.perf_counter() - t0
-    L = rep["L"]
-    cL = Nw["c0"] * Nw["R"] ** L
-    # standard MC at the finest level: pilot, allocation, then a bounded timed batch
-    with binding.Plan([spec], c0=cL, L=0, ratio=Nw["R"], precision=Nw["precision"], f="abs_step",
-                      pilot_n=Nw["pilot"], stream=stream) as mc:
-        mc.level_stats(0, 0, 0, Nw["pilot"])
-        N_mc = int(mc.allocate([eps])[0][0])
-        batch = max(64, min(N_mc, int(2e8 // cL)))
-        mc.level_stats(0, 0, Nw["pilot"], 64)   # warm-up
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        mc.level_stats(0, 0, Nw["pilot"] + 64, batch)
-        torch.cuda.synchronize()
-        per_sample = (time.perf_counter() - t0) / batch
-    t_mc = N_mc * per_sample
+    sweep = []
+    for R in (2, 4, 10):
+        Lmax = Nw["Lmax"]
+        while Nw["c0"] * R ** Lmax > (1 << 26):
+            Lmax -= 1
+        with binding.Plan([spec], c0=Nw["c0"], L=Lmax, ratio=R, precision=Nw["precision"], f="abs_step",
+                          adaptive_L=True, pilot_n=Nw["pilot"], stream=stream) as plan:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            (Y,), (rep,) = plan.estimate([eps])
+            torch.cuda.synchronize()
+            t_mlmc = time.perf_counter() - t0
+        L = rep["L"]
+        cL = Nw["c0"] * R ** L
+        t_u, N_u, _, batch_u = _mc_at_finest(spec, Nw, cL, eps, "uniform", stream)
+        t_x, N_x, _, batch_x = _mc_at_finest(spec, Nw, cL, eps, "optimal", stream)
+        sweep.append({"ratio": R, "L_max": Lmax,
+                      "mlmc": {"value": t_mlmc, "L": L, "bias_unmet": rep["bias_unmet"], "N_l": rep["N"],
+                               "outer_products": rep["outer_products"], "rmse_pred": rep["rmse_pred"],
+                               "level_mean_norms": rep["mean_norm"], "timing": "end to end through mlmc_estimate"},
+                      "mc_uniform": {"value": t_u, "c": cL, "N": N_u, "outer_products": float(N_u) * cL,
+                                     "timing": f"{batch_u} samples timed, projected to N"},
+                      "mc_xi_optimal": {"value": t_x, "c": cL, "N": N_x, "outer_products": float(N_x) * cL,
+                                        "timing": f"{batch_x} samples timed, projected to N"},
+                      "mc_uniform_over_mlmc": t_u / t_mlmc, "mc_xi_optimal_over_mlmc": t_x / t_mlmc})
+    head = sweep[0]
     # FMAs of the fine contraction (2 m p per outer product; the coarse slots add their own
     # contraction on top) over the end-to-end time, host rounds included
-    achieved = 2.0 * Nw["m"] * Nw["p"] * rep["outer_products"] / t_mlmc / 1e12
+    achieved = 2.0 * Nw["m"] * Nw["p"] * head["mlmc"]["outer_products"] / head["mlmc"]["value"] / 1e12
     return {"workload": Nw["name"], "metric": "time to RMSE eps for E[f(AB)], f(x) = |x| H(2 - x)", "unit": "s",
             "eps_abs": eps, "precision": Nw["precision"],
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": ALU_PEAKS["fp32"], "unit": "TFLOP/s",
+                         "frac": achieved / ALU_PEAKS["fp32"], "traffic": None,
+                         "peak_source": ALU_PEAKS["source"],
                          "kernel": "level_cuda_core_kernel<float, F = |x| H(2 - x)>",
-                         "note": "end to end (pilot and allocation rounds of Alg. 2 included)"},
-            "mlmc": {"value": t_mlmc, "L": L, "bias_unmet": rep["bias_unmet"], "N_l": rep["N"],
-                     "outer_products": rep["outer_products"], "rmse_pred": rep["rmse_pred"],
-                     "level_mean_norms": rep["mean_norm"], "timing": "end to end through mlmc_estimate"},
-            "mc_finest_level": {"value": t_mc, "c": cL, "N": N_mc, "outer_products": float(N_mc) * cL,
-                                "timing": f"{batch} samples timed, projected to N"},
-            "mc_over_mlmc": t_mc / t_mlmc}
+                         "note": "end to end (pilot and allocation rounds of Alg. 2 included), ratio 2"},
+            "mlmc": head["mlmc"], "mc_finest_level": head["mc_uniform"],
+            "mc_over_mlmc": head["mc_uniform_over_mlmc"], "sweep": sweep}
 
 
 XI = dict(name="sparse_rows_64x4096x64", m=64, n=4096, p=64, c0=16, R=2, L=5, pilot=256, rel_rmse=1e-2,
@@ -621,9 +750,9 @@ def _measure_xi(args, dev, stream):
     achieved = 2.0 * X["m"] * X["p"] * out["optimal"]["outer_products"] / out["optimal"]["value"] / 1e12
     return {"workload": X["name"], "metric": "time to rel. RMSE 1e-2 for E[AB] under xi^u and xi**", "unit": "s",
             "eps_abs": eps, "precision": X["precision"], "uniform": out["uniform"], "optimal": out["optimal"],
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": ALU_PEAKS["fp32"], "unit": "TFLOP/s",
+                         "frac": achieved / ALU_PEAKS["fp32"], "traffic": None,
+                         "peak_source": ALU_PEAKS["source"],
                          "kernel": "level_cuda_core_kernel<float, XI>",
                          "note": "xi** run end to end (plan creation, pilot and allocation included)"},
             "uniform_over_optimal": out["uniform"]["value"] / out["optimal"]["value"],
@@ -634,7 +763,7 @@ BATCHED = dict(name="batched_64_problems", count=64, shape_seed=7, c0=32, R=2, p
                step_outer=4.0e8, precision="bf16")
 
 
-def _measure_batched(args, dev, stream, peaks, peak_kind):
+def _measure_batched(args, dev, stream, peaks, peak_kind, precision="bf16", step_target=None, steps=None, warmup=None):
     """64 problems (m, p log-uniform on [32, 512], n log-uniform on [4096, 262144], L+1 uniform on
     3..9; M ~ N(0,1), S ~ U[0.05, 2]; c_l = 32 * 2^l; BF16) through mlmc_level_stats_batch: one
     persistent launch per wave, graph-replayed.  After the pilot (256 samples per level, which
@@ -660,8 +789,11 @@ def _measure_batched(args, dev, stream, peaks, peak_kind):
         del pp
     gen_s = time.perf_counter() - t0
     Lmax = max(L for *_, L in shapes)
-    plan = binding.Plan(specs, c0=Bc["c0"], L=Lmax, ratio=Bc["R"], precision=Bc["precision"], pilot_n=Bc["pilot"],
+    plan = binding.Plan(specs, c0=Bc["c0"], L=Lmax, ratio=Bc["R"], precision=precision, pilot_n=Bc["pilot"],
                         stream=stream)
+    step_target = Bc["step_outer"] if step_target is None else step_target
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
     levels = [L for *_, L in shapes]
     ranges = [(q, l) for q in range(len(shapes)) for l in range(levels[q] + 1)]
     torch.cuda.synchronize()
@@ -673,7 +805,7 @@ def _measure_batched(args, dev, stream, peaks, peak_kind):
     Nl = plan.allocate(eps)
     cl = [Bc["c0"] * Bc["R"]**l for l in range(Lmax + 1)]
     full_outer = sum(Nl[q][l] * cl[l] for q, l in ranges)
-    f = Bc["step_outer"] / full_outer
+    f = step_target / full_outer
     B = {(q, l): max(8, int(math.ceil(f * Nl[q][l]))) for q, l in ranges}
     step_outer = sum(B[r] * cl[r[1]] for r in ranges)
     next_id = {r: max(Bc["pilot"], 0) for r in ranges}
@@ -683,20 +815,20 @@ def _measure_batched(args, dev, stream, peaks, peak_kind):
         for r in ranges:
             next_id[r] += B[r]
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
     launches0 = plan.launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(torch.cuda.current_device()) as clocks:
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             step()
         e1.record(stream)
         torch.cuda.synchronize()
     plan.synchronize()
     launches = plan.launch_count() - launches0
-    t = e0.elapsed_time(e1) / 1e3 / args.steps
+    t = e0.elapsed_time(e1) / 1e3 / steps
     T = t * full_outer / step_outer
     flops = sum(2.0 * mpq[q][0] * mpq[q][1] * B[(q, l)] * cl[l] for q, l in ranges)
     bytes_alg = sum(2.0 * (mpq[q][0] + mpq[q][1]) * 4 * B[(q, l)] * cl[l] for q, l in ranges)
@@ -705,6 +837,18 @@ def _measure_batched(args, dev, stream, peaks, peak_kind):
     tpeak = peaks["bf16_tflops_sustained"]
     tfl = flops / t / 1e12
     bound_hbm = bytes_alg / (peaks["hbm_gbs"] * 1e9) >= flops / (tpeak * 1e12)
+    if precision in ("fp32", "fp64"):
+        # CUDA cores, one launch sequence per range: bound by FMA issue
+        peak = ALU_PEAKS[precision]
+        roof = {"bound": "alu", "achieved": tfl, "peak": peak, "unit": "TFLOP/s",
+                "frac": tfl / peak if peak else None, "traffic": None, "peak_source": ALU_PEAKS["source"],
+                "hbm_achieved_gbs": hbm, "kernel": f"level_cuda_core_kernel<{precision}> (one range at a time)"}
+        return {"workload": Bc["name"], "precision": precision,
+                "metric": "time-to-RMSE 1e-3 for every problem's E[A_q B_q] (projected)",
+                "value": T, "unit": "s", "ms_per_step": 1e3 * t, "step_fraction": f,
+                "outer_products_per_s": step_outer / t, "full_run_outer_products": full_outer,
+                "gpu_launches": launches, "pilot_s": pilot_s, "problems": len(shapes), "levels": len(ranges),
+                "roofline": roof, "clocks": clocks.summary()}
     roof = ({"bound": "hbm", "achieved": hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": hbm / peaks["hbm_gbs"],
              "tensor_achieved_tflops": tfl, "tensor_frac": tfl / tpeak}
             if bound_hbm else
@@ -738,6 +882,7 @@ def run_ours(args):
     W["eps"] = W["rel_rmse"] * float(np.linalg.norm(mu))
     stream = torch.cuda.current_stream(dev)
 
+    peaks_alu = measure_alu_peaks(stream) if rank == 0 else None
     head = _measure(args, args.precision, W, host, dev, rank, stream, world, with_e2e=True)
     others = []
     if not args.no_compare:
@@ -772,6 +917,10 @@ def run_ours(args):
         "per_level_us_per_sample": [1e6 * t for t in head["t_l"]],
         "gpu_launches": head["launches"],
         "roofline": _roofline(head, W, peaks, peak_kind, gen_rate),
+        "peaks_measured": {"fp32_tflops": peaks_alu["fp32_flops"] / 1e12, "fp64_tflops": peaks_alu["fp64_flops"] / 1e12,
+                           "int32_imad_per_s": peaks_alu["int32_imad_per_s"], "mufu_sin_per_s": peaks_alu["mufu_sin_per_s"],
+                           "generation_entries_per_s": gen_rate,
+                           "how": "mlmc_measure_peaks / mlmc_measure_generation_rate in this run"},
         "clocks": head["clocks"],
         "e2e": {"value": head["e2e_overhead_s"] + T, "unit": "s", "h2d_bytes_per_step": head["h2d"],
                 "d2h_bytes_per_step": head["d2h"], "overhead_s": head["e2e_overhead_s"]},
@@ -787,10 +936,21 @@ def run_ours(args):
         line["adjoint"] = _measure_adjoint(args, host, dev, stream, peaks, peak_kind)
     if not args.no_batched and world == 1:
         line["batched"] = _measure_batched(args, dev, stream, peaks, peak_kind)
+        if not args.no_compare:
+            # the plain FP32 comparator of the same 64 problems (CUDA cores), on a tenth of the step
+            fp32b = _measure_batched(args, dev, stream, peaks, peak_kind, precision="fp32",
+                                     step_target=BATCHED["step_outer"] / 10, steps=1, warmup=1)
+            line["batched"]["compare"] = {"fp32": fp32b, "fp32_over_bf16": fp32b["value"] / line["batched"]["value"]}
     if not args.no_nonlinear and world == 1:
         line["nonlinear"] = _measure_nonlinear(args, dev, stream)
     if not args.no_xi and world == 1:
         line["xi"] = _measure_xi(args, dev, stream)
+    if not args.no_dedupe and world == 1:
+        line["dedupe_bound"] = _measure_dedupe_bound(args, head, W, dev, stream)
+    ttr_rels = [float(x) for x in args.ttr.split(",") if x.strip("'\" ")]
+    if ttr_rels and world == 1:
+        line["ttr_64x1024x64"] = _measure_ttr(args, ttr_rels, [x for x in args.ttr_precisions.split(",") if x],
+                                              dev, stream)
     if args.ladder and world == 1:
         rels = [float(x) for x in args.ladder.split(",")]
         line["ladder"] = _measure_ladder(args, rels, W, host, mu, dev, stream, T)
@@ -815,7 +975,17 @@ PROFILE_CASES = {
     "tc_bf16_level8": ("bf16", 8, 2432),
     "tc_bf16_pair_level8": ("bf16", 8, 2432),
     "tc_e4m3_level0": ("fp8", 0, 16384),
+    "tc_e4m3_level8": ("fp8", 8, 2432),
     "cuda_core_f32_level0": ("fp32", 0, 4096),
+}
+
+
+SMALL_PROFILE_CASES = {
+    # name: (precision, level, samples per launch) on the 64x1024x64 workload (one launch each)
+    "small_bf16_level0": ("bf16", 0, 262144),
+    "small_bf16_level5": ("bf16", 5, 8192),
+    "small_f32_level0": ("fp32", 0, 262144),
+    "small_f32_level5": ("fp32", 5, 8192),
 }
 
 
@@ -857,6 +1027,18 @@ def run_profile_case(args):
         plan.close()
         print(json.dumps({"profile_case": args.profile_case, "status": "ok"}), flush=True)
         return
+    if args.profile_case in SMALL_PROFILE_CASES:
+        # one level of the 64 x 1024 x 64 workload (c_l = 16 * 2^l): three launches of one level kernel
+        prec, level, count = SMALL_PROFILE_CASES[args.profile_case]
+        ps = make_params(64, 1024, 64, seed_A=0, seed_B=1, dtype=np.float32)
+        st = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (ps.M, ps.S, ps.Mp, ps.Sp)]
+        plan = binding.Plan([binding.ProblemSpec(*st)], c0=16, L=5, precision=prec)
+        for i in range(3):
+            plan.level_stats(0, level, i * count, count)
+        plan.synchronize()
+        plan.close()
+        print(json.dumps({"profile_case": args.profile_case, "status": "ok"}), flush=True)
+        return
     pp = make_params(256, 65536, 256, seed_A=0, seed_B=1, dtype=np.float32)
     ts = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (pp.M, pp.S, pp.Mp, pp.Sp)]
     if args.profile_case == "adjoint":
@@ -886,15 +1068,20 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32", "fp64", "bf16", "fp8"], default="bf16")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP32 and FP8 comparison measurements")
+    ap.add_argument("--tile", type=int, default=0, help="tensor-core tile id of the headline workload (0: automatic)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the backward measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-problem batched measurement")
     ap.add_argument("--no-nonlinear", action="store_true", help="skip the E[f(AB)] adaptive-L measurement")
     ap.add_argument("--no-xi", action="store_true", help="skip the xi^u / xi** comparison")
+    ap.add_argument("--no-dedupe", action="store_true", help="skip the index-dedupe bound")
     ap.add_argument("--ladder", default="", help="comma-separated relative RMSE targets to run end to end "
                     "through mlmc_estimate (e.g. 3e-2; about a minute each at 3e-2)")
-    ap.add_argument("--profile-case", choices=sorted(list(PROFILE_CASES) + ["adjoint", "batched_8_problems",
-                                                                         "cuda_core_f32_xi_level3"]),
+    ap.add_argument("--ttr", default="1e-3", help="comma-separated relative RMSE targets of the end-to-end "
+                    "time-to-RMSE runs on the 64x1024x64 workload ('' to skip)")
+    ap.add_argument("--ttr-precisions", default="bf16,fp8,fp32", help="precisions of those runs")
+    ap.add_argument("--profile-case", choices=sorted(list(PROFILE_CASES) + list(SMALL_PROFILE_CASES) +
+                                                     ["adjoint", "batched_8_problems", "cuda_core_f32_xi_level3"]),
                     default=None,
                     help="run one small kernel invocation for ncu instead of the benchmark")
     args = ap.parse_args()
