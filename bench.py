@@ -295,7 +295,8 @@ def _measure(args, prec, W, host, dev, rank, stream, world, with_e2e):
     def make_plan(tensors):
         spec = binding.ProblemSpec(*tensors, seed_A=0, seed_B=1, seed_idx=2, problem_id=rank)
         return binding.Plan([spec], c0=W["c0"], L=W["L"], ratio=W["R"], precision=prec, pilot_n=W["pilot"],
-                            tile_override=args.tile if prec in ("bf16", "fp8") else 0, stream=stream)
+                            tile_override=args.tile if prec in ("bf16", "fp8") else
+                            args.fp32_tile if prec == "fp32" else 0, stream=stream)
 
     pdtype = torch.float64 if prec == "fp64" else torch.float32
     dev_params = [h.to(dev, pdtype, non_blocking=True) for h in host]
@@ -349,28 +350,32 @@ def _measure(args, prec, W, host, dev, rank, stream, world, with_e2e):
     del dev_params
 
     if with_e2e:
-        e2e_ms, e2e_sample_ms = [], []
+        # end to end through the C ABI with host buffers: mlmc_plan_host copies the four pinned
+        # parameter matrices to the device inside the call, the step's batches run, and
+        # mlmc_telescoping_sum_host writes the estimate back to host memory (synchronising);
+        # timed on the host around the whole step
+        e2e_s, e2e_sample_ms = [], []
         m, p = W["m"], W["p"]
         out_host = torch.empty(m * p, dtype=torch.float64).pin_memory()
+        host_p = [h if h.dtype == pdtype else h.to(pdtype).pin_memory() for h in host]
         for it in range(args.warmup + max(1, min(args.steps, 3))):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
-            e0.record(stream)
-            tensors = [h.to(dev, pdtype, non_blocking=True) for h in host]
-            p2 = make_plan(tensors)
+            t0 = time.perf_counter()
+            spec = binding.ProblemSpec(*host_p, seed_A=0, seed_B=1, seed_idx=2, problem_id=rank)
+            p2 = binding.Plan([spec], c0=W["c0"], L=W["L"], ratio=W["R"], precision=prec, pilot_n=W["pilot"],
+                              tile_override=args.tile if prec in ("bf16", "fp8") else 0, stream=stream, host=True)
             tm = []
             step(p2, tm)
-            y = p2.telescoping_sum()[0]
-            out_host.copy_(y.reshape(-1), non_blocking=True)
-            e1.record(stream)
-            torch.cuda.synchronize()
+            p2.telescoping_sum_host(out_host)
+            t1 = time.perf_counter()
             p2.close()
             if it >= args.warmup:
-                e2e_ms.append(e0.elapsed_time(e1))
+                e2e_s.append(t1 - t0)
                 e2e_sample_ms.append(sum(tm[0][i].elapsed_time(tm[0][i + 1]) for i in range(len(levels))))
-        res["e2e_overhead_s"] = (statistics.mean(e2e_ms) - statistics.mean(e2e_sample_ms)) / 1e3
-        res["h2d"] = sum(h.numel() * h.element_size() for h in host)
+        res["e2e_overhead_s"] = statistics.mean(e2e_s) - statistics.mean(e2e_sample_ms) / 1e3
+        res["h2d"] = sum(h.numel() * h.element_size() for h in host_p)
         res["d2h"] = m * p * 8
+        res["e2e_api"] = "mlmc_plan_host + mlmc_level_stats + mlmc_telescoping_sum_host (host buffers)"
     return res
 
 
@@ -626,7 +631,7 @@ def _nonlinear_params():
     return [x.astype(np.float32) for x in (pp.M * k + 2.0 / Nw["n"], pp.S * k, pp.Mp, pp.Sp)]
 
 
-def _mc_at_finest(spec, Nw, c, eps, sampling, stream):
+def _mc_at_finest(spec, Nw, c, eps, sampling, stream, precision=None):
     """Standard MC at one level of c draws (Eq. Phigh) under the sampling law `sampling`: pilot,
     allocation for the variance target eps^2 / 2, then a bounded timed batch projected to the
     allocated N (seconds, N, seconds per sample)."""
@@ -634,7 +639,8 @@ def _mc_at_finest(spec, Nw, c, eps, sampling, stream):
 
     from paper_1904_00429_gb300 import binding
 
-    with binding.Plan([spec], c0=c, L=0, ratio=2, precision=Nw["precision"], f="abs_step", sampling=sampling,
+    with binding.Plan([spec], c0=c, L=0, ratio=2, precision=precision or Nw["precision"], f="abs_step",
+                      sampling=sampling,
                       pilot_n=Nw["pilot"], stream=stream) as mc:
         mc.level_stats(0, 0, 0, Nw["pilot"])
         N_mc = int(mc.allocate([eps])[0][0])
@@ -675,6 +681,8 @@ def _measure_nonlinear(args, dev, stream):
             (Y,), (rep,) = plan.estimate([eps])
             torch.cuda.synchronize()
             t_mlmc = time.perf_counter() - t0
+        if R == 2:
+            Y_r2 = Y.cpu().numpy()
         L = rep["L"]
         cL = Nw["c0"] * R ** L
         t_u, N_u, _, batch_u = _mc_at_finest(spec, Nw, cL, eps, "uniform", stream)
@@ -688,6 +696,27 @@ def _measure_nonlinear(args, dev, stream):
                       "mc_xi_optimal": {"value": t_x, "c": cL, "N": N_x, "outer_products": float(N_x) * cL,
                                         "timing": f"{batch_x} samples timed, projected to N"},
                       "mc_uniform_over_mlmc": t_u / t_mlmc, "mc_xi_optimal_over_mlmc": t_x / t_mlmc})
+    # the tensor-core form of the targeted function (BF16 operands, ratio 2 only): the same
+    # problem and target, end to end, and MC at its finest level in BF16
+    bf16_spec = binding.ProblemSpec(*ts, seed_A=7, seed_B=8, seed_idx=9, problem_id=0)
+    with binding.Plan([bf16_spec], c0=Nw["c0"], L=Nw["Lmax"], ratio=2, precision="bf16", f="abs_step",
+                      adaptive_L=True, pilot_n=Nw["pilot"], stream=stream) as plan:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        (Yb,), (repb,) = plan.estimate([eps])
+        torch.cuda.synchronize()
+        t_bf16 = time.perf_counter() - t0
+    cLb = Nw["c0"] * 2 ** repb["L"]
+    t_ub, N_ub, _, batch_ub = _mc_at_finest(bf16_spec, Nw, cLb, eps, "uniform", stream, precision="bf16")
+    bf16 = {"mlmc": {"value": t_bf16, "L": repb["L"], "bias_unmet": repb["bias_unmet"], "N_l": repb["N"],
+                     "outer_products": repb["outer_products"], "rmse_pred": repb["rmse_pred"],
+                     "timing": "end to end through mlmc_estimate"},
+            "mc_uniform": {"value": t_ub, "c": cLb, "N": N_ub, "outer_products": float(N_ub) * cLb,
+                           "timing": f"{batch_ub} samples timed, projected to N"},
+            "mc_uniform_over_mlmc": t_ub / t_bf16,
+            "fp32_mlmc_over_bf16_mlmc": sweep[0]["mlmc"]["value"] / t_bf16,
+            "diff_to_fp32_estimate_over_eps": float(np.linalg.norm(Yb.cpu().numpy() - Y_r2)) / eps,
+            "kernel": "level_tc_bf16_kernel<F = |x| H(2 - x)>: fine and coarse sums in two TMEM accumulators"}
     head = sweep[0]
     # FMAs of the fine contraction (2 m p per outer product; the coarse slots add their own
     # contraction on top) over the end-to-end time, host rounds included
@@ -700,7 +729,7 @@ def _measure_nonlinear(args, dev, stream):
                          "kernel": "level_cuda_core_kernel<float, F = |x| H(2 - x)>",
                          "note": "end to end (pilot and allocation rounds of Alg. 2 included), ratio 2"},
             "mlmc": head["mlmc"], "mc_finest_level": head["mc_uniform"],
-            "mc_over_mlmc": head["mc_uniform_over_mlmc"], "sweep": sweep}
+            "mc_over_mlmc": head["mc_uniform_over_mlmc"], "sweep": sweep, "bf16": bf16}
 
 
 XI = dict(name="sparse_rows_64x4096x64", m=64, n=4096, p=64, c0=16, R=2, L=5, pilot=256, rel_rmse=1e-2,
@@ -763,6 +792,9 @@ BATCHED = dict(name="batched_64_problems", count=64, shape_seed=7, c0=32, R=2, p
                step_outer=4.0e8, precision="bf16")
 
 
+_BATCHED_INPUTS = {}
+
+
 def _measure_batched(args, dev, stream, peaks, peak_kind, precision="bf16", step_target=None, steps=None, warmup=None):
     """64 problems (m, p log-uniform on [32, 512], n log-uniform on [4096, 262144], L+1 uniform on
     3..9; M ~ N(0,1), S ~ U[0.05, 2]; c_l = 32 * 2^l; BF16) through mlmc_level_stats_batch: one
@@ -777,17 +809,21 @@ def _measure_batched(args, dev, stream, peaks, peak_kind, precision="bf16", step
 
     Bc = BATCHED
     shapes = batched_shapes(Bc["count"], Bc["shape_seed"])
-    specs, eps, mpq = [], [], []
-    t0 = time.perf_counter()
-    for q, (m, n, p, L) in enumerate(shapes):
-        pp = make_params(m, n, p, law="gauss", seed_A=2 * q, seed_B=2 * q + 1, seed_idx=2, problem_id=q,
-                         dtype=np.float32)
-        ts = [torch.from_numpy(x).to(dev) for x in (pp.M, pp.S, pp.Mp, pp.Sp)]
-        specs.append(binding.ProblemSpec(*ts, seed_A=2 * q, seed_B=2 * q + 1, seed_idx=2, problem_id=q, L=L))
-        eps.append(Bc["rel_rmse"] * float(np.linalg.norm(pp.exact_mean())))
-        mpq.append((m, p))
-        del pp
-    gen_s = time.perf_counter() - t0
+    key = (str(dev), Bc["count"], Bc["shape_seed"])
+    if key not in _BATCHED_INPUTS:
+        # drawn once per process: the BF16 run and its FP32 comparator use the same problems
+        specs, eps, mpq = [], [], []
+        t0 = time.perf_counter()
+        for q, (m, n, p, L) in enumerate(shapes):
+            pp = make_params(m, n, p, law="gauss", seed_A=2 * q, seed_B=2 * q + 1, seed_idx=2, problem_id=q,
+                             dtype=np.float32)
+            ts = [torch.from_numpy(x).to(dev) for x in (pp.M, pp.S, pp.Mp, pp.Sp)]
+            specs.append(binding.ProblemSpec(*ts, seed_A=2 * q, seed_B=2 * q + 1, seed_idx=2, problem_id=q, L=L))
+            eps.append(Bc["rel_rmse"] * float(np.linalg.norm(pp.exact_mean())))
+            mpq.append((m, p))
+            del pp
+        _BATCHED_INPUTS[key] = (specs, eps, mpq, time.perf_counter() - t0)
+    specs, eps, mpq, gen_s = _BATCHED_INPUTS[key]
     Lmax = max(L for *_, L in shapes)
     plan = binding.Plan(specs, c0=Bc["c0"], L=Lmax, ratio=Bc["R"], precision=precision, pilot_n=Bc["pilot"],
                         stream=stream)
@@ -923,7 +959,7 @@ def run_ours(args):
                            "how": "mlmc_measure_peaks / mlmc_measure_generation_rate in this run"},
         "clocks": head["clocks"],
         "e2e": {"value": head["e2e_overhead_s"] + T, "unit": "s", "h2d_bytes_per_step": head["h2d"],
-                "d2h_bytes_per_step": head["d2h"], "overhead_s": head["e2e_overhead_s"]},
+                "d2h_bytes_per_step": head["d2h"], "overhead_s": head["e2e_overhead_s"], "api": head["e2e_api"]},
     }
     if others:
         line["compare"] = {o["prec"]: {"value": o["T"], "unit": "s",
@@ -948,9 +984,17 @@ def run_ours(args):
     if not args.no_dedupe and world == 1:
         line["dedupe_bound"] = _measure_dedupe_bound(args, head, W, dev, stream)
     ttr_rels = [float(x) for x in args.ttr.split(",") if x.strip("'\" ")]
-    if ttr_rels and world == 1:
-        line["ttr_64x1024x64"] = _measure_ttr(args, ttr_rels, [x for x in args.ttr_precisions.split(",") if x],
-                                              dev, stream)
+    fp8_rels = [float(x) for x in args.ttr_fp8.split(",") if x.strip("'\" ")]
+    if (ttr_rels or fp8_rels) and world == 1:
+        out = _measure_ttr(args, ttr_rels, [x for x in args.ttr_precisions.split(",") if x], dev, stream) \
+            if ttr_rels else None
+        if fp8_rels:
+            o8 = _measure_ttr(args, fp8_rels, ["fp8"], dev, stream)
+            if out is None:
+                out = o8
+            else:
+                out["runs"] += o8["runs"]
+        line["ttr_64x1024x64"] = out
     if args.ladder and world == 1:
         rels = [float(x) for x in args.ladder.split(",")]
         line["ladder"] = _measure_ladder(args, rels, W, host, mu, dev, stream, T)
@@ -1069,6 +1113,8 @@ def main():
     ap.add_argument("--precision", choices=["fp32", "fp64", "bf16", "fp8"], default="bf16")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP32 and FP8 comparison measurements")
     ap.add_argument("--tile", type=int, default=0, help="tensor-core tile id of the headline workload (0: automatic)")
+    ap.add_argument("--fp32-tile", type=int, default=0,
+                    help="CUDA-core tile id of the FP32 comparator (0: automatic; 64064, 128064, 128128)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the backward measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-problem batched measurement")
@@ -1079,7 +1125,9 @@ def main():
                     "through mlmc_estimate (e.g. 3e-2; about a minute each at 3e-2)")
     ap.add_argument("--ttr", default="1e-3", help="comma-separated relative RMSE targets of the end-to-end "
                     "time-to-RMSE runs on the 64x1024x64 workload ('' to skip)")
-    ap.add_argument("--ttr-precisions", default="bf16,fp8,fp32", help="precisions of those runs")
+    ap.add_argument("--ttr-precisions", default="bf16,fp32", help="precisions of those runs")
+    ap.add_argument("--ttr-fp8", default="3e-3", help="relative targets of the E4M3 run on the same workload "
+                    "(its stochastic rounding makes 1e-3 take about 8 minutes; '' to skip)")
     ap.add_argument("--profile-case", choices=sorted(list(PROFILE_CASES) + list(SMALL_PROFILE_CASES) +
                                                      ["adjoint", "batched_8_problems", "cuda_core_f32_xi_level3"]),
                     default=None,

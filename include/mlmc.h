@@ -116,13 +116,20 @@ typedef struct {
                               one of 1032 1064 1128 1256 2032 2064 2128 2256 (e.g. 2128 = 256 x 128;
                               E4M3: 1032 1064 1128 2032 2064), or 3256: a cluster of two CTAs of
                               128 x 256 sharing one 256 x 256 tile (BF16 and E4M3, single-problem
-                              launches; the default for outputs above 128 x 128), or 4256: the
-                              same pair with 16 generator warps on 4-slot items */
+                              launches; the BF16 default for outputs above 128 x 128), or 4256: the
+                              same pair with 16 generator warps on 4-slot items (the E4M3 default
+                              for outputs above 128 x 128).  CUDA-core plans: 1000 * rows + columns
+                              of the output tile, 64064; FP32 with f = identity also 128064 (its
+                              default above 64 rows) and 128128 */
     int32_t adjoint_batch_log2; /* mlmc_backward replays at most 2^this sampled products per batch
                                    (0 = 26; at least c_L + 1 are always taken); scratch is 8 B each */
     int32_t f;           /* mlmc_function applied entrywise to each sketch (Sec. 3): the estimator then
                             targets E[f(AB)] with D = f(P_l) - f(P_{l-1}) (Alg. 1).  Anything but the
-                            identity needs MLMC_FP64 or MLMC_FP32 and has no mlmc_backward */
+                            identity needs MLMC_FP64, MLMC_FP32 or MLMC_BF16 (not E4M3) and has no
+                            mlmc_backward.  BF16 keeps the fine and coarse sums of a sample in two
+                            tensor-memory accumulators (FP32) and applies f to each in FP32; its
+                            tiles are 128 rows by 32, 64 or 128 columns (tile_override 1032, 1064,
+                            1128), and mlmc_level_stats_batch evaluates its ranges in turn */
     int32_t adaptive_L;  /* 0: mlmc_estimate uses the problem's L.  1: Alg. 2 chooses L: rounds on
                             levels 0..L for L = 0, 1, ... (the new finest level gets pilot_n samples,
                             every level is re-allocated from the variances of all samples held and
@@ -180,6 +187,15 @@ typedef struct mlmc_plan_s mlmc_plan_t;
  * (Alg. 1, Alg. 2). */
 MLMC_API mlmc_status mlmc_plan(const mlmc_problem* problems, int32_t nprob, const mlmc_options* options,
                       void* stream, mlmc_plan_t** plan_out);
+
+/* mlmc_plan_host: as mlmc_plan, for parameters in HOST memory (pinned or pageable): the
+ * problems' M_dev, S_dev, Mp_dev, Sp_dev fields point to host arrays with the same layout and
+ * leading dimensions.  The plan allocates device copies (owned by it until mlmc_plan_destroy),
+ * copies the parameters on `stream` and builds its layout from them; the host arrays may be
+ * reused once the stream has reached the layout copy (mlmc_synchronize).  Such a plan also owns
+ * a device buffer for mlmc_telescoping_sum_host.  Problem statement as for mlmc_plan. */
+MLMC_API mlmc_status mlmc_plan_host(const mlmc_problem* problems, int32_t nprob, const mlmc_options* options,
+                                    void* stream, mlmc_plan_t** plan_out);
 
 /* Release everything the plan owns (after draining its stream).  NULL is a no-op. */
 MLMC_API mlmc_status mlmc_plan_destroy(mlmc_plan_t* plan);
@@ -319,6 +335,10 @@ MLMC_API mlmc_status mlmc_bias_test(mlmc_plan_t* plan, int32_t prob, int32_t L, 
 
 /* Yhat of the current statistics without new samples: yhat_dev as above. */
 MLMC_API mlmc_status mlmc_telescoping_sum(mlmc_plan_t* plan, double* yhat_dev);
+
+/* The same written to HOST memory (every problem's m x p FP64 estimate back to back), for plans
+ * made by mlmc_plan_host (else MLMC_ERR_STATE); synchronises the plan's stream (Eq. hatY). */
+MLMC_API mlmc_status mlmc_telescoping_sum_host(mlmc_plan_t* plan, double* yhat_host);
 
 /* ---- level statistics without allocation ------------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers

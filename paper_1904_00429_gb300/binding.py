@@ -87,6 +87,8 @@ def lib() -> ctypes.CDLL:
         P, I32, I64, U64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
         sig = {
             "mlmc_plan": [P, I32, P, P, P],
+            "mlmc_plan_host": [P, I32, P, P, P],
+            "mlmc_telescoping_sum_host": [P, P],
             "mlmc_plan_destroy": [P],
             "mlmc_level_stats": [P, I32, I32, U64, U64],
             "mlmc_level_stats_batch": [P, P, I32],
@@ -159,24 +161,29 @@ class Plan:
     """A plan over one or more problems sharing the level schedule c_l = c0 * ratio**l.
 
     precision: "fp64", "fp32" (CUDA cores), "bf16" or "fp8" (tensor cores).  f: "identity"
-    (E[AB]) or "abs_step" (E[f(AB)] with f(x) = |x| H(2 - x); FP64/FP32).  adaptive_L: let
+    (E[AB]) or "abs_step" (E[f(AB)] with f(x) = |x| H(2 - x); FP64/FP32/BF16).  adaptive_L: let
     estimate() choose the finest level by Alg. 2's while loop, up to L.  sampling: "uniform"
     (xi^u) or "optimal" (xi** of Thm 3.1; FP64/FP32).  The fields mirror mlmc_options."""
 
     def __init__(self, problems: Sequence[ProblemSpec], *, c0: int, L: int, ratio: int = 2,
                  precision: str = "fp32", pilot_n: int = 256, nl_scale: float = 1.0,
                  timeout_ns: int = 0, tile_override: int = 0, adjoint_batch_log2: int = 0,
-                 f: str = "identity", adaptive_L: bool = False, sampling: str = "uniform", stream=None):
+                 f: str = "identity", adaptive_L: bool = False, sampling: str = "uniform", stream=None,
+                 host: bool = False):
+        """host=True: the parameters are CPU tensors (pinned for asynchronous copies); the plan is
+        made by mlmc_plan_host, which copies them to the current CUDA device itself."""
         self.problems = list(problems)
-        self.device = self.problems[0].M.device
+        self.host = host
+        self.device = torch.device("cuda", torch.cuda.current_device()) if host else self.problems[0].M.device
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         arr = (Problem * len(self.problems))()
         self.shapes = []
         self.levels = []
         for q, pr in enumerate(self.problems):
             for t in (pr.M, pr.S, pr.Mp, pr.Sp):
-                if not t.is_cuda or t.dim() != 2 or t.dtype not in DTYPE or t.stride(1) != 1:
-                    raise ValueError("parameters must be 2-D row-major float32/float64 CUDA tensors")
+                if t.is_cuda == host or t.dim() != 2 or t.dtype not in DTYPE or t.stride(1) != 1:
+                    raise ValueError("parameters must be 2-D row-major float32/float64 " +
+                                     ("CPU tensors (host=True)" if host else "CUDA tensors"))
             if pr.S.shape != pr.M.shape or pr.Sp.shape != pr.Mp.shape or pr.M.shape[1] != pr.Mp.shape[0]:
                 raise ValueError("inconsistent parameter shapes")
             dtypes = {pr.M.dtype, pr.S.dtype, pr.Mp.dtype, pr.Sp.dtype}
@@ -198,8 +205,9 @@ class Plan:
         self.nl_scale = nl_scale
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
-            _check(lib().mlmc_plan(arr, len(self.problems), ctypes.byref(self.options),
-                                   _stream_handle(self.stream), ctypes.byref(h)), "mlmc_plan")
+            make = lib().mlmc_plan_host if host else lib().mlmc_plan
+            _check(make(arr, len(self.problems), ctypes.byref(self.options), _stream_handle(self.stream),
+                        ctypes.byref(h)), "mlmc_plan_host" if host else "mlmc_plan")
         self._h = h
 
     # -- lifetime ---------------------------------------------------------------------------
@@ -332,6 +340,17 @@ class Plan:
         y = self._out(total)
         _check(lib().mlmc_telescoping_sum(self._h, _ptr(y)), "mlmc_telescoping_sum")
         return self._split(y)
+
+    def telescoping_sum_host(self, out: Optional[torch.Tensor] = None):
+        """Yhat written to host memory by mlmc_telescoping_sum_host (plans made with host=True);
+        ``out``: an optional (pinned) FP64 CPU tensor of sum m p elements."""
+        total = sum(m * p for m, _, p in self.shapes)
+        if out is None:
+            out = torch.empty(total, dtype=torch.float64)
+        if out.is_cuda or out.dtype != torch.float64 or out.numel() != total or not out.is_contiguous():
+            raise ValueError("out must be a contiguous FP64 CPU tensor of sum m p elements")
+        _check(lib().mlmc_telescoping_sum_host(self._h, _ptr(out)), "mlmc_telescoping_sum_host")
+        return self._split(out)
 
     def _split(self, flat: torch.Tensor):
         out, off = [], 0

@@ -74,6 +74,7 @@ struct ProblemState {
     TcMaps batch_maps{};    // ... and for the plan's batched tile
     int32_t batch_maps_tile = 0;
     int max_chunks = 1;
+    int cc_tile = 64064;      // CUDA-core output tile id (1000 rows + columns)
     double* xi_q = nullptr;   // xi** (MLMC_XI_OPTIMAL): weights q_k and their running sums Q_k (n each)
     double* xi_Q = nullptr;
     int* xi_G = nullptr;      // guide table of Q (n buckets)
@@ -115,6 +116,10 @@ struct mlmc_plan_s {
     cudaStream_t capture_stream = nullptr;
     cudaGraphExec_t batch_exec = nullptr;
     std::vector<int64_t> batch_key;
+    // plans made from host buffers (mlmc_plan_host): the device copies of the parameters, and the
+    // device buffer of mlmc_telescoping_sum_host
+    std::vector<void*> owned;
+    double* yhat_dev = nullptr;
 };
 
 namespace {
@@ -218,14 +223,22 @@ mlmc_status validate(const mlmc_problem* problems, int32_t nprob, const mlmc_opt
         return fail(MLMC_ERR_UNSUPPORTED, "the tensor-core precisions fold the coupling sign into B and need ratio 2");
     if (!(o->nl_scale > 0.0) || !std::isfinite(o->nl_scale)) return fail(MLMC_ERR_INVALID_ARG, "nl_scale must be > 0");
     if (o->timeout_ns < 0) return fail(MLMC_ERR_INVALID_ARG, "timeout_ns must be >= 0");
-    if (o->tile_override != 0 && !tc_tile_valid(decode_tile(o->tile_override), o->precision == MLMC_FP8_E4M3 ? 1 : 0))
+    const bool tc_prec = o->precision == MLMC_BF16 || o->precision == MLMC_FP8_E4M3;
+    if (!tc_prec && o->tile_override != 0 && !cuda_core_tile_valid(o->precision, o->f, o->tile_override))
+        return fail(MLMC_ERR_INVALID_ARG, "tile_override %d is not a CUDA-core tile of this plan (64064; FP32 with "
+                    "f = identity: 128064, 128128)", o->tile_override);
+    if (tc_prec && o->f == MLMC_F_IDENTITY && o->tile_override != 0 &&
+        !tc_tile_valid(decode_tile(o->tile_override), o->precision == MLMC_FP8_E4M3 ? 1 : 0))
         return fail(MLMC_ERR_INVALID_ARG, "tile_override %d is not a tile id of this precision (1032 .. 2256; "
                     "E4M3: 1032 1064 1128 2032 2064; pairs 3256, 4256)", o->tile_override);
+    if (tc_prec && o->f != MLMC_F_IDENTITY && o->tile_override != 0 && !tc_tile_valid_f(decode_tile(o->tile_override)))
+        return fail(MLMC_ERR_INVALID_ARG, "tile_override %d: a targeted function takes tiles 1032, 1064 or 1128",
+                    o->tile_override);
     if (o->adjoint_batch_log2 < 0 || o->adjoint_batch_log2 > 40)
         return fail(MLMC_ERR_INVALID_ARG, "adjoint_batch_log2 must be in [0, 40]");
     if (o->f != MLMC_F_IDENTITY && o->f != MLMC_F_ABS_STEP) return fail(MLMC_ERR_INVALID_ARG, "unknown f %d", o->f);
-    if (o->f != MLMC_F_IDENTITY && o->precision != MLMC_FP64 && o->precision != MLMC_FP32)
-        return fail(MLMC_ERR_UNSUPPORTED, "a targeted function other than the identity needs FP64 or FP32");
+    if (o->f != MLMC_F_IDENTITY && o->precision == MLMC_FP8_E4M3)
+        return fail(MLMC_ERR_UNSUPPORTED, "a targeted function other than the identity needs FP64, FP32 or BF16");
     if (o->adaptive_L != 0 && o->adaptive_L != 1) return fail(MLMC_ERR_INVALID_ARG, "adaptive_L must be 0 or 1");
     if (o->sampling != MLMC_XI_UNIFORM && o->sampling != MLMC_XI_OPTIMAL)
         return fail(MLMC_ERR_INVALID_ARG, "unknown sampling law %d", o->sampling);
@@ -271,6 +284,9 @@ void free_plan(mlmc_plan_t* plan)
     cudaFree(plan->batch_chan);
     cudaFree(plan->err_flag);
     cudaFree(plan->adj_buf);
+    for (void* q : plan->owned) cudaFree(q);
+    plan->owned.clear();
+    cudaFree(plan->yhat_dev);
     cudaFree(plan->batch_partial);
     cudaFree(plan->batch_q);
     cudaFree(plan->batch_dev);
@@ -336,6 +352,7 @@ mlmc_status run_level(mlmc_plan_t* plan, ProblemState& ps, int level, uint64_t s
     prm.rkB = philox_round_keys(prm.keyB);
     prm.tiles_m = ps.tiles_m;
     prm.tiles_p = ps.tiles_p;
+    prm.cc_tile = ps.cc_tile;
     prm.partial_sum = plan->partial_sum;
     prm.partial_q = plan->partial_q;
     prm.xi_q = ps.xi_q;
@@ -365,12 +382,19 @@ mlmc_status run_level(mlmc_plan_t* plan, ProblemState& ps, int level, uint64_t s
         cudaError_t err;
         if (tensor_core_precision(o.precision)) {
             prm.maps = ps.maps;
-            prm.pack = tc_pack(ps.tile, tc_format(o), ps.m, c) ? 1 : 0;
-            // f = identity (the only tensor-core f): for l >= 1 the fine and coarse estimates of one
-            // realisation have the same expectation, E[D_l] = 0, so only level 0 needs Welford
-            prm.welford = level == 0 ? 1 : 0;
             TcLaunch tl{plan->err_flag, plan->timeout_ns, static_cast<float>(double(ps.n) / double(c)), plan->num_sms};
-            err = launch_level_tc(prm, ps.tile, tc_format(o), tl, plan->stream);
+            if (o.f != MLMC_F_IDENTITY) {
+                // the targeted function: fine and coarse sums apart, Welford at every level
+                prm.pack = 0;
+                prm.welford = 1;
+                err = launch_level_tc_f(prm, ps.tile, o.f, tl, plan->stream);
+            } else {
+                prm.pack = tc_pack(ps.tile, tc_format(o), ps.m, c) ? 1 : 0;
+                // f = identity: for l >= 1 the fine and coarse estimates of one realisation have the
+                // same expectation, E[D_l] = 0, so only level 0 needs Welford
+                prm.welford = level == 0 ? 1 : 0;
+                err = launch_level_tc(prm, ps.tile, tc_format(o), tl, plan->stream);
+            }
         } else if (ps.m == 1 && ps.p == 1 && !ps.xi_Q) {
             err = launch_level_inner(prm, plan->f64, plan->opt.f, plan->stream);   // Sec. 2's inner product
         } else {
@@ -888,13 +912,16 @@ mlmc_status mlmc_plan(const mlmc_problem* problems, int32_t nprob, const mlmc_op
         ps.p_pad = (ps.p + 3) / 4 * 4;
         if (tensor_core_precision(options->precision)) {
             const TcTile tile = options->tile_override ? decode_tile(options->tile_override)
-                                                       : tc_tile_for(ps.m, ps.p, options->precision == MLMC_FP8_E4M3 ? 1 : 0,
-                                                                     true);
+                                : options->f != MLMC_F_IDENTITY
+                                    ? tc_tile_for_f(ps.p)
+                                    : tc_tile_for(ps.m, ps.p, options->precision == MLMC_FP8_E4M3 ? 1 : 0, true);
             ps.tile = tile;
             ps.tiles_m = int((ps.m + tile.rows - 1) / tile.rows);
             ps.tiles_p = int((ps.p + tile.bn - 1) / tile.bn);
         } else {
-            const CudaCoreTile tile = cuda_core_tile(options->precision);
+            ps.cc_tile = options->tile_override ? options->tile_override
+                                                : cuda_core_default_tile(options->precision, options->f, ps.m);
+            const CudaCoreTile tile = cuda_core_tile(ps.cc_tile);
             ps.tiles_m = int((ps.m + tile.tm - 1) / tile.tm);
             ps.tiles_p = int((ps.p + tile.tp - 1) / tile.tp);
         }
@@ -1029,7 +1056,8 @@ mlmc_status mlmc_level_stats_batch(mlmc_plan_t* plan, const mlmc_range* ranges, 
     }
     if (rs.empty()) return MLMC_OK;
     DeviceGuard g(plan->device);
-    if (!tensor_core_precision(plan->opt.precision)) {
+    // the batched persistent launch is the identity's; other forms evaluate the ranges in turn
+    if (!tensor_core_precision(plan->opt.precision) || plan->opt.f != MLMC_F_IDENTITY) {
         for (const BatchRange& r : rs) {
             ProblemState& ps = plan->probs[size_t(r.prob)];
             const int64_t mp = ps.m * ps.p;
@@ -1172,6 +1200,81 @@ mlmc_status mlmc_reset_level_stats(mlmc_plan_t* plan, int32_t prob, int32_t leve
     }
     ps.has_estimate = false;
     return MLMC_OK;
+}
+
+mlmc_status mlmc_plan_host(const mlmc_problem* problems, int32_t nprob, const mlmc_options* options, void* stream,
+                           mlmc_plan_t** plan_out)
+{
+    if (!plan_out) return fail(MLMC_ERR_INVALID_ARG, "null plan_out");
+    *plan_out = nullptr;
+    mlmc_status st = validate(problems, nprob, options);
+    if (st != MLMC_OK) return st;
+    if (fault_is("alloc")) return fail(MLMC_ERR_OOM, "injected fault: device allocation of the plan failed");
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    std::vector<mlmc_problem> dev(problems, problems + nprob);
+    std::vector<void*> owned;
+    auto release = [&]() {
+        cudaStreamSynchronize(cs);
+        for (void* q : owned) cudaFree(q);
+    };
+    for (int32_t q = 0; q < nprob; ++q) {
+        const mlmc_problem& pr = problems[q];
+        const size_t elem = pr.dtype == MLMC_DTYPE_F64 ? 8 : 4;
+        // row-major with the caller's leading dimensions: m rows of ldA, n rows of ldB
+        const size_t bytes_a = size_t(pr.m - 1) * size_t(pr.ldA) * elem + size_t(pr.n) * elem;
+        const size_t bytes_b = size_t(pr.n - 1) * size_t(pr.ldB) * elem + size_t(pr.p) * elem;
+        const void* src[4] = {pr.M_dev, pr.S_dev, pr.Mp_dev, pr.Sp_dev};
+        void* dst[4] = {nullptr, nullptr, nullptr, nullptr};
+        for (int i = 0; i < 4; ++i) {
+            const size_t b = i < 2 ? bytes_a : bytes_b;
+            if (cudaMalloc(&dst[i], b) != cudaSuccess) {
+                release();
+                return fail(MLMC_ERR_OOM, "cudaMalloc of the device copy of problem %d's parameters failed", q);
+            }
+            owned.push_back(dst[i]);
+            if (cudaMemcpyAsync(dst[i], src[i], b, cudaMemcpyHostToDevice, cs) != cudaSuccess) {
+                release();
+                return fail(MLMC_ERR_CUDA, "copy of problem %d's parameters to the device failed", q);
+            }
+        }
+        dev[size_t(q)].M_dev = dst[0];
+        dev[size_t(q)].S_dev = dst[1];
+        dev[size_t(q)].Mp_dev = dst[2];
+        dev[size_t(q)].Sp_dev = dst[3];
+    }
+    mlmc_plan_t* plan = nullptr;
+    st = mlmc_plan(dev.data(), nprob, options, stream, &plan);
+    if (st != MLMC_OK) {
+        release();
+        return st;
+    }
+    size_t total = 0;
+    for (int32_t q = 0; q < nprob; ++q) total += size_t(problems[q].m) * size_t(problems[q].p);
+    if (cudaMalloc(reinterpret_cast<void**>(&plan->yhat_dev), sizeof(double) * total) != cudaSuccess) {
+        release();
+        mlmc_plan_destroy(plan);
+        return fail(MLMC_ERR_OOM, "cudaMalloc of the estimate buffer failed");
+    }
+    plan->owned = std::move(owned);
+    *plan_out = plan;
+    return MLMC_OK;
+}
+
+mlmc_status mlmc_telescoping_sum_host(mlmc_plan_t* plan, double* yhat_host)
+{
+    mlmc_status st = enter(plan);
+    if (st != MLMC_OK) return st;
+    if (!yhat_host) return fail(MLMC_ERR_INVALID_ARG, "null yhat_host");
+    if (!plan->yhat_dev) return fail(MLMC_ERR_STATE, "the plan was not made by mlmc_plan_host");
+    if ((st = mlmc_telescoping_sum(plan, plan->yhat_dev)) != MLMC_OK) return st;
+    DeviceGuard g(plan->device);
+    size_t total = 0;
+    for (const auto& ps : plan->probs) total += size_t(ps.m) * size_t(ps.p);
+    cudaError_t err = cudaMemcpyAsync(yhat_host, plan->yhat_dev, sizeof(double) * total, cudaMemcpyDeviceToHost,
+                                      plan->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(plan->stream);
+    if (check_cuda(plan, err, "copy of the estimate to the host") != MLMC_OK) return plan->sticky;
+    return check_device_flag(plan);
 }
 
 mlmc_status mlmc_telescoping_sum(mlmc_plan_t* plan, double* yhat_dev)

@@ -61,6 +61,7 @@ struct LevelParams {
     const double* xi_Q;   // their running sums (n)
     double xi_Qtot;       // Q[n-1]
     const int* xi_G;      // guide table of the running sums (n buckets)
+    int cc_tile;          // CUDA-core kernel: output tile id 1000 rows + columns (0 or 64064: 64 x 64)
     int pack;             // tensor-core kernel, 128-row tiles: two samples per accumulator (m <= 64, c % 16 == 0)
     int welford;          // tensor-core kernel: grow each chunk's M2 sample by sample (Welford); 0: levels whose
                           // mean is zero by construction keep the raw sum of ||D||^2 and subtract ||S||^2 / n
@@ -77,7 +78,9 @@ struct CudaCoreTile {
 // f: the targeted function (mlmc_function), applied to the fine and coarse estimates apart.
 cudaError_t launch_level_cuda_core_f64(const LevelParams& prm, int f, cudaStream_t st);
 cudaError_t launch_level_cuda_core_f32(const LevelParams& prm, int f, cudaStream_t st);
-CudaCoreTile cuda_core_tile(int precision);
+bool cuda_core_tile_valid(int precision, int f, int id);   // id = 1000 rows + columns: 64064, 128064, 128128
+int cuda_core_default_tile(int precision, int f, int64_t m);
+CudaCoreTile cuda_core_tile(int id);
 // The inner-product case m = p = 1 (uniform law): one warp per sample, FP64 or FP32.
 cudaError_t launch_level_inner(const LevelParams& prm, bool f64, int f, cudaStream_t st);
 
@@ -118,6 +121,11 @@ int tc_stage_width_b(const TcTile& t);
 TcTile tc_tile_for(int64_t m, int64_t p, int q, bool allow_pair);
 bool tc_tile_valid(const TcTile& t, int q);
 cudaError_t launch_level_tc(const LevelParams& prm, const TcTile& tile, int q, const TcLaunch& tl, cudaStream_t st);
+// BF16 with a targeted function (f = 1): fine and coarse sums in two accumulators, tiles of 128
+// rows and 32, 64 or 128 columns
+TcTile tc_tile_for_f(int64_t p);
+bool tc_tile_valid_f(const TcTile& t);
+cudaError_t launch_level_tc_f(const LevelParams& prm, const TcTile& tile, int f, const TcLaunch& tl, cudaStream_t st);
 // Whether a launch of `tile` over a level with c slots packs two samples per accumulator.
 bool tc_pack(const TcTile& tile, int q, int64_t m, int64_t c);
 // CTAs of a batched launch for this tile (resident CTAs per SM x SMs); 0 on error.  Also sets

@@ -317,25 +317,55 @@ level_cuda_core_kernel(const LevelParams prm)
     }
 }
 
-template <typename T, int TM, int TP, int TK, int RM, int RP>
+template <typename T, int TM, int TP, int TK, int RM, int RP, bool kIdentityOnly = false>
 cudaError_t launch(const LevelParams& prm, int f, cudaStream_t st)
 {
     constexpr int NT = (TM / RM) * (TP / RP);
     dim3 grid(prm.tiles_m * prm.tiles_p, prm.nchunks);
     const bool xi = prm.xi_Q != nullptr;
-    switch (f * 2 + (xi ? 1 : 0)) {
-    case 0: level_cuda_core_kernel<T, TM, TP, TK, RM, RP, 0, false><<<grid, NT, 0, st>>>(prm); break;
-    case 1: level_cuda_core_kernel<T, TM, TP, TK, RM, RP, 0, true><<<grid, NT, 0, st>>>(prm); break;
-    case 2: level_cuda_core_kernel<T, TM, TP, TK, RM, RP, 1, false><<<grid, NT, 0, st>>>(prm); break;
-    case 3: level_cuda_core_kernel<T, TM, TP, TK, RM, RP, 1, true><<<grid, NT, 0, st>>>(prm); break;
-    default: return cudaErrorInvalidValue;
+    if constexpr (kIdentityOnly) {
+        if (f != 0) return cudaErrorInvalidValue;
+        if (xi)
+            level_cuda_core_kernel<T, TM, TP, TK, RM, RP, 0, true><<<grid, NT, 0, st>>>(prm);
+        else
+            level_cuda_core_kernel<T, TM, TP, TK, RM, RP, 0, false><<<grid, NT, 0, st>>>(prm);
+        return cudaGetLastError();
+    } else {
+        switch (f * 2 + (xi ? 1 : 0)) {
+        case 0: level_cuda_core_kernel<T, TM, TP, TK, RM, RP, 0, false><<<grid, NT, 0, st>>>(prm); break;
+        case 1: level_cuda_core_kernel<T, TM, TP, TK, RM, RP, 0, true><<<grid, NT, 0, st>>>(prm); break;
+        case 2: level_cuda_core_kernel<T, TM, TP, TK, RM, RP, 1, false><<<grid, NT, 0, st>>>(prm); break;
+        case 3: level_cuda_core_kernel<T, TM, TP, TK, RM, RP, 1, true><<<grid, NT, 0, st>>>(prm); break;
+        default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
     }
-    return cudaGetLastError();
 }
 
 }  // namespace
 
-CudaCoreTile cuda_core_tile(int /*precision*/) { return CudaCoreTile{64, 64}; }
+// Output tiles (id 1000 rows + columns): 64 x 64 (4 x 4 registers per thread); FP32 with
+// f = identity also 128 x 64 (8 x 4) and 128 x 128 (8 x 8), which generate each sampled entry of
+// A for fewer output tiles at the price of occupancy.  Measured on a GB300 at 256 x 65536 x 256:
+// 128 x 64 (two CTAs per SM) 8 % faster than 64 x 64 (three), 128 x 128 (one) 11 % slower; so FP32
+// outputs of more than 64 rows take 128 x 64.
+int cuda_core_default_tile(int precision, int f, int64_t m)
+{
+    return (precision == MLMC_FP32 && f == MLMC_F_IDENTITY && m > 64) ? 128064 : 64064;
+}
+
+bool cuda_core_tile_valid(int precision, int f, int id)
+{
+    if (id == 64064) return true;
+    return precision == MLMC_FP32 && f == MLMC_F_IDENTITY && (id == 128064 || id == 128128);
+}
+
+CudaCoreTile cuda_core_tile(int id)
+{
+    if (id == 128064) return CudaCoreTile{128, 64};
+    if (id == 128128) return CudaCoreTile{128, 128};
+    return CudaCoreTile{64, 64};
+}
 
 cudaError_t launch_level_cuda_core_f64(const LevelParams& prm, int f, cudaStream_t st)
 {
@@ -344,6 +374,8 @@ cudaError_t launch_level_cuda_core_f64(const LevelParams& prm, int f, cudaStream
 
 cudaError_t launch_level_cuda_core_f32(const LevelParams& prm, int f, cudaStream_t st)
 {
+    if (prm.cc_tile == 128128) return launch<float, 128, 128, 32, 8, 8, true>(prm, f, st);
+    if (prm.cc_tile == 128064) return launch<float, 128, 64, 32, 8, 4, true>(prm, f, st);
     return launch<float, 64, 64, 32, 4, 4>(prm, f, st);
 }
 

@@ -58,7 +58,11 @@ constexpr uint64_t kDrainNs = 100000000ull;   // bound on waiting for own copies
 // the peer has three sub-blocks of slack before a slice is reused.
 // W: generator warps, 8 (with 8-slot items) or 16 (pairs only, tile 4256: 4-slot items, so that
 // every one of the 512 generator threads takes one item of a 32-slot sub-block); plus the producer.
-template <int MH, int BN, int Q, int P = 0, int W = 8>
+// F: the targeted function (0: identity; 1: |x| H(2 - x)).  F != 0 keeps the fine and the coarse
+// sums apart: each 32-slot sub-block holds the even slots at K positions 0-15 and the odd (coarse)
+// slots at 16-31, the first K step accumulates into E and the second into O, and the drain forms
+// D = f(n/c_l (E + O)) - f(n/c_{l-1} O) and keeps the chunk's running sum S in tensor memory.
+template <int MH, int BN, int Q, int P = 0, int W = 8, int F = 0>
 struct TcCfg {
     static constexpr int kGW = W;                         // generator warps
     static constexpr int kGT = 32 * W;                    // generator threads
@@ -82,7 +86,8 @@ struct TcCfg {
     // Tiles of at most 256 accumulator columns also keep the chunk's running sum of D in tensor
     // memory (a second accumulator S after D); the 256 x 256 tile adds each D to global memory.
     static constexpr bool kAccS = kTileCols <= 256;
-    static constexpr int kAccCols = kAccS ? 2 * kTileCols : kTileCols;
+    static constexpr int kSOff = F ? 2 * kTileCols : kTileCols;   // tensor-memory column of S
+    static constexpr int kAccCols = F ? 3 * kTileCols : kAccS ? 2 * kTileCols : kTileCols;
     static constexpr int kTmemCols = kAccCols <= 32 ? 32 : kAccCols <= 64 ? 64 : kAccCols <= 128 ? 128
                                      : kAccCols <= 256 ? 256 : 512;
     // barriers: full[2], empty[2], slice[kSlices], done, and for pairs peer[kSlices] (the peer's B half landed)
@@ -98,7 +103,8 @@ struct TcCfg {
     static_assert(kKSteps * 16 == kSub, "a sub-block is a whole number of K = 16 MMA steps");
     static_assert(BN % 16 == 0 && BN >= 32 && BN <= 256, "N of the MMA");
     static constexpr bool kFits = kSmemBytes <= 227 * 1024 &&   // E4M3's 32-slot staging rules out wide tiles
-                                  (!P || (MH == 1 && BN == 256)) && (W == 8 || (W == 16 && P));
+                                  (!P || (MH == 1 && BN == 256)) && (W == 8 || (W == 16 && P)) &&
+                                  (F == 0 || (MH == 1 && BN <= 128 && Q == 0 && P == 0 && W == 8 && kSub == 32));
 
 };
 
@@ -108,6 +114,14 @@ struct TcExtra {
     int total_items;  // nchunks * tiles
     float scale;      // n / c_l
 };
+
+// The targeted function in FP32: F = 1 is |x| H(2 - x) with H(0) = 1; F = 0 the identity.
+template <int F>
+__device__ __forceinline__ float tc_targeted(float x)
+{
+    if constexpr (F == 1) return (2.0f - x >= 0.0f) ? fabsf(x) : 0.0f;
+    return x;
+}
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
 {
@@ -297,11 +311,11 @@ __device__ __forceinline__ void gen_block_e4m3(const int* idx, int slot0, bool v
 // sample's positions, so one MMA chain forms both samples' D.  Each half keeps its own running
 // sum (rows of S) and Welford M2; at the end of a chunk the halves are combined by Chan's update.
 // Needs c_l % 16 == 0 (a group of 8 slots, and an E4M3 block, never straddles two samples).
-template <int MH, int BN, int Q, bool kBatch, int P = 0, int W = 8>
-__global__ void __launch_bounds__(TcCfg<MH, BN, Q, P, W>::kThr, 1)
+template <int MH, int BN, int Q, bool kBatch, int P = 0, int W = 8, int F = 0>
+__global__ void __launch_bounds__(TcCfg<MH, BN, Q, P, W, F>::kThr, 1)
 level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra ex, const TcBatch bt)
 {
-    using C = TcCfg<MH, BN, Q, P, W>;
+    using C = TcCfg<MH, BN, Q, P, W, F>;
     constexpr int kGenWarps = C::kGW;
     constexpr int kGenThreads = C::kGT;
     constexpr int kNS = C::kNS;
@@ -464,7 +478,7 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
             const uint64_t chunk = prm.chunk0 + static_cast<uint64_t>(cy);
             const uint64_t sa = max(prm.s_begin, chunk * static_cast<uint64_t>(prm.chunk));
             const uint64_t sb = min(prm.s_end, (chunk + 1) * static_cast<uint64_t>(prm.chunk));
-            const bool PK = MH == 1 && P == 0 && prm.pack != 0;   // packed samples (uniform per item)
+            const bool PK = MH == 1 && P == 0 && F == 0 && prm.pack != 0;   // packed samples (uniform per item)
             const uint64_t kG = PK ? 2 : 1;                        // samples per accumulator
             for (uint64_t s = sa; s < sb && !aborted; s += kG) {
                 const uint32_t lsw = level_sample_word(prm.l, s);
@@ -510,8 +524,10 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                         const int t = t0 + 2 * lane;
                         int64_t r0 = -1, r1 = -1;
                         if (t < prm.c) index_pair(prm.keyI, lsw, s_lo, t >> 1, static_cast<uint64_t>(prm.n), r0, r1);
-                        idx[2 * lane] = t < prm.c ? static_cast<int>(r0) : -1;
-                        idx[2 * lane + 1] = t + 1 < prm.c ? static_cast<int>(r1) : -1;
+                        // F != 0: even slot t at K position lane, odd slot t + 1 at 16 + lane
+                        const int p0 = F ? lane : 2 * lane, p1 = F ? kSub / 2 + lane : 2 * lane + 1;
+                        idx[p0] = t < prm.c ? static_cast<int>(r0) : -1;
+                        idx[p1] = t + 1 < prm.c ? static_cast<int>(r1) : -1;
                     }
                     __syncwarp();
                     const int nvalid = min(kSub, nK - t0);
@@ -520,25 +536,28 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                     const uint32_t a_region = tc::smem_addr(stg);
                     const uint32_t b_region = a_region + static_cast<uint32_t>(kSub * C::kRows * 8);
                     if (gather) {
-                        // TMA row gathers, four slots per instruction (boxes of kRows and kBGen pairs)
-                        const int groups = (nvalid + 3) / 4;
+                        // TMA row gathers, four slots per instruction (boxes of kRows and kBGen pairs);
+                        // F != 0: the valid K positions are a prefix of each 16-position half
+                        const int ga = F ? (min(kSub / 2, (nvalid + 1) / 2) + 3) / 4 : (nvalid + 3) / 4;
+                        const int groups = F ? ga + (min(kSub / 2, nvalid / 2) + 3) / 4 : ga;
                         if (lane == 0)
                             tc::mbar_arrive_expect_tx(bar_full(b),
                                                       static_cast<uint32_t>(groups * 4 * (C::kRows + C::kBGen) * 8));
                         __syncwarp();
                         if (lane < groups) {
-                            const int r0 = max(idx[4 * lane], 0), r1 = max(idx[4 * lane + 1], 0);
-                            const int r2 = max(idx[4 * lane + 2], 0), r3 = max(idx[4 * lane + 3], 0);
-                            tc::tma_gather4(a_region + static_cast<uint32_t>(4 * lane * C::kRows * 8), &maps->a, tm0,
+                            const int gq = (F && lane >= ga) ? kSub / 8 + (lane - ga) : lane;   // group of 4 positions
+                            const int r0 = max(idx[4 * gq], 0), r1 = max(idx[4 * gq + 1], 0);
+                            const int r2 = max(idx[4 * gq + 2], 0), r3 = max(idx[4 * gq + 3], 0);
+                            tc::tma_gather4(a_region + static_cast<uint32_t>(4 * gq * C::kRows * 8), &maps->a, tm0,
                                             r0, r1, r2, r3, bar_full(b));
-                            tc::tma_gather4(b_region + static_cast<uint32_t>(4 * lane * C::kBGen * 8), &maps->b,
+                            tc::tma_gather4(b_region + static_cast<uint32_t>(4 * gq * C::kBGen * 8), &maps->b,
                                             prm.m_pad + geo.bcol0, r0, r1, r2, r3, bar_full(b));
                         }
                     } else {
                         if (lane == 0)
                             tc::mbar_arrive_expect_tx(bar_full(b), static_cast<uint32_t>(nvalid) * (a_bytes + b_bytes));
                         __syncwarp();
-                        if (lane < nvalid) {
+                        if (F ? (lane < kSub && idx[lane] >= 0) : lane < nvalid) {
                             const int k = idx[lane];
                             const float* row = PA + static_cast<int64_t>(k) * prm.ldPA;
                             if (a_bytes)
@@ -576,7 +595,7 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
         for_each_item(job_gen, [&](const LevelParams& prm, int cy, int tile, const TcMaps*) -> bool {
             const int tiles_n = prm.tiles_m * prm.tiles_p;
             const int nsub = (prm.c + kSub - 1) / kSub;
-            const bool coarse_sign = prm.l > 0;
+            const bool coarse_sign = F == 0 && prm.l > 0;   // F != 0 keeps the coarse sum apart instead
             const float scale = static_cast<float>(prm.w_fine);
             const Geo geo = geometry(prm, tile);
             const int tm0 = geo.tm0;
@@ -608,7 +627,7 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                 dr.ncols = MH == 2 ? BN : (split ? BN / kSplit : (hgrp == 0 ? BN : 0));
                 dr.gi = tm0 + (MH == 2 ? hgrp * 128 : 0) + dr.quarter * 32 + lane;
             }
-            const bool PK = MH == 1 && P == 0 && prm.pack != 0;   // packed samples (uniform per item)
+            const bool PK = MH == 1 && P == 0 && F == 0 && prm.pack != 0;   // packed samples (uniform per item)
             const uint64_t kG = PK ? 2 : 1;
             if (PK) dr.gi = (dr.quarter & 1) * 32 + lane;          // rows 64-127: the second sample
             const int pk_half = PK ? (warp & 3) >> 1 : 0;           // the sample of this warp's drained rows
@@ -808,6 +827,13 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
 #pragma unroll
                         for (int ks = 0; ks < C::kKSteps; ++ks) {
                             const int koff = 32 * (kj * C::kKSteps + ks);   // bytes into the swizzle atom
+                            if constexpr (F != 0) {
+                                // even slots (K step 0) into E, odd (coarse) slots (K step 1) into O
+                                tc::mma_bf16(tmem + ks * C::kTileCols, tc::sw128_kmajor_desc(tc::smem_addr(a_tile) + koff),
+                                             tc::sw128_kmajor_desc(tc::smem_addr(b_tile) + koff), idesc,
+                                             jj > 0 ? 1u : 0u);
+                                continue;
+                            }
                             const bool acc = jj > 0 || ks > 0;
 #pragma unroll
                             for (int h = 0; h < MH; ++h) {
@@ -885,7 +911,39 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                 const int kbefore = static_cast<int>((s - sa) / kG);
                 // FP32 throughout (FP64 runs at 1/64 of the FP32 rate here); exact for k (k + 1) <= 2^24
                 const float wk = kbefore > 0 ? 1.0f / static_cast<float>(kbefore * (kbefore + 1)) : 0.0f;
-                if constexpr (C::kAccS) {
+                if constexpr (F != 0) {
+                    // fine = n/c_l (E + O), coarse = n/c_{l-1} O (the odd slots t = 1 mod 2 are the
+                    // coarse ones), D = f(fine) - f(coarse) (level 0: f(fine)); the chunk's running sum
+                    // S of D is read, grown by Welford's update and written back in tensor memory
+                    const float sc = 2.0f * scale;
+                    const float kf = static_cast<float>(kbefore);
+                    const bool coarse = prm.l > 0;
+                    float qsamp = 0.0f;
+                    for (int cb = 0; cb < dr.ncols; cb += 16) {   // ncols is a multiple of 32
+                        float ve[16], vo[16], vs[16];
+                        tc::tmem_ld_32x32b_x16_nowait(dr.taddr(tmem, cb), ve);
+                        tc::tmem_ld_32x32b_x16_nowait(dr.taddr(tmem + C::kTileCols, cb), vo);
+                        if (kbefore > 0) tc::tmem_ld_32x32b_x16_nowait(dr.taddr(tmem + C::kSOff, cb), vs);
+                        tc::tmem_ld_wait();
+                        float qs = 0.0f;
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) {
+                            float d = tc_targeted<F>(scale * (ve[e] + vo[e]));
+                            if (coarse) d -= tc_targeted<F>(sc * vo[e]);
+                            if (kbefore > 0) {
+                                const float dk = fmaf(kf, d, -vs[e]);
+                                qs = fmaf(dk, dk, qs);
+                                vs[e] += d;
+                            } else {
+                                vs[e] = d;
+                            }
+                        }
+                        tc::tmem_st_32x32b_x16(dr.taddr(tmem + C::kSOff, cb), vs);
+                        qsamp += qs;
+                    }
+                    tc::tmem_st_wait();
+                    qw = fmaf(qsamp, wk, qw);
+                } else if constexpr (C::kAccS) {
                     // the running sum S (after this sample) sits beside D in tensor memory:
                     // k D - sum_k = (k + 1) D - S, one fused rounding per element (PK: per half,
                     // and a group without a second sample has nothing in rows 64-127).  Levels
@@ -1029,9 +1087,10 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                 // the chunk's sum of D: one store per element of the tile (raw form: also ||S||^2)
                 tc::tc_fence_after_sync();
                 float ssq = 0.0f;
+                const float sscale = F ? 1.0f : scale;   // F != 0: S holds scaled values already
                 for (int cb = 0; cb < dr.ncols; cb += kCW) {
                     float v[64];   // store_cols reads up to 64; the 16-warp form fills the first 32
-                    const uint32_t ta = dr.taddr(tmem + C::kTileCols, cb);
+                    const uint32_t ta = dr.taddr(tmem + C::kSOff, cb);
                     tc::tmem_ld_32x32b_x32_nowait(ta, v);
                     if (kCW == 64 && cb + 32 < dr.ncols) tc::tmem_ld_32x32b_x32_nowait(ta + 32, v + 32);
                     tc::tmem_ld_wait();
@@ -1040,7 +1099,7 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
 #pragma unroll
                     for (int e = 0; e < kCW; ++e) {
                         if (e < nv) qs = fmaf(v[e], v[e], qs);
-                        v[e] *= scale;
+                        v[e] *= sscale;
                     }
                     ssq += qs;
                     store_cols(v, cb, nv, 0);
@@ -1050,7 +1109,7 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
             }
             if (aborted) return false;
             // the Welford terms in FP64 (tiles that keep S drained unscaled values)
-            q += static_cast<double>(qw) * (C::kAccS ? scale_sq : 1.0);
+            q += static_cast<double>(qw) * (C::kAccS && F == 0 ? scale_sq : 1.0);
             // work-item epilogue: the chunk's M2 over this tile, fixed-order reduction
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) q += __shfl_xor_sync(0xffffffffu, q, off);
@@ -1188,6 +1247,25 @@ cudaError_t launch_pair(const LevelParams& prm, const TcLaunch& tl, cudaStream_t
     return cudaGetLastError();
 }
 
+// The targeted-function form (F = 1): one CTA per 128 x BN tile, BF16 operands.
+template <int BN>
+cudaError_t launch_single_f(const LevelParams& prm, const TcLaunch& tl, cudaStream_t st)
+{
+    using C = TcCfg<1, BN, 0, 0, 8, 1>;
+    auto kern = level_tc_bf16_kernel<1, BN, 0, false, 0, 8, 1>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, C::kThr, C::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    const int per_sm = max(1, min(occ, 512 / C::kTmemCols));
+    const int items = prm.nchunks * prm.tiles_m * prm.tiles_p;
+    const int grid = max(1, min(items, per_sm * tl.num_sms));
+    TcExtra ex{tl.err_flag, tl.timeout_ns, items, tl.scale};
+    kern<<<grid, C::kThr, C::kSmemBytes, st>>>(prm, ex, TcBatch{});
+    return cudaGetLastError();
+}
+
 template <int MH, int BN, int Q>
 struct FitsF {
     static bool run() { return TcCfg<MH, BN, Q>::kFits; }
@@ -1303,7 +1381,9 @@ bool tc_tile_valid(const TcTile& t, int q)
 TcTile tc_tile_for(int64_t m, int64_t p, int q, bool allow_pair)
 {
     TcTile t{};
-    if (allow_pair && m > 128 && p > 128) return TcTile{1, 256, 128, 1};   // cluster pair (8 generator warps)
+    // cluster pair; E4M3 (the heavier generation of stochastic rounding) with 16 generator warps,
+    // measured 10 % faster than 8 on the 256 x 65536 x 256 workload, BF16 with 8 (7 % faster)
+    if (allow_pair && m > 128 && p > 128) return TcTile{1, 256, 128, q == 1 ? 2 : 1};
     t.mh = m <= 128 ? 1 : 2;
     t.bn = p <= 32 ? 32 : p <= 64 ? 64 : p <= 128 ? 128 : 256;
     while (!tc_tile_valid(t, q) && t.bn > 32) t.bn /= 2;   // E4M3: narrower column tiles
@@ -1318,6 +1398,24 @@ cudaError_t launch_level_tc(const LevelParams& prm, const TcTile& tile, int q, c
     if (tile.pair == 2) return q ? launch_pair<1, 16>(prm, tl, st) : launch_pair<0, 16>(prm, tl, st);
     if (tile.pair) return q ? launch_pair<1, 8>(prm, tl, st) : launch_pair<0, 8>(prm, tl, st);
     return dispatch_tile<SingleF>(tile, q, prm, tl, st);
+}
+
+TcTile tc_tile_for_f(int64_t p)
+{
+    const int bn = p <= 32 ? 32 : p <= 64 ? 64 : 128;
+    return TcTile{1, bn, 128, 0};
+}
+
+bool tc_tile_valid_f(const TcTile& t) { return t.mh == 1 && !t.pair && (t.bn == 32 || t.bn == 64 || t.bn == 128); }
+
+cudaError_t launch_level_tc_f(const LevelParams& prm, const TcTile& tile, int f, const TcLaunch& tl, cudaStream_t st)
+{
+    if (f != 1 || !tc_tile_valid_f(tile)) return cudaErrorInvalidValue;
+    switch (tile.bn) {
+    case 32: return launch_single_f<32>(prm, tl, st);
+    case 64: return launch_single_f<64>(prm, tl, st);
+    default: return launch_single_f<128>(prm, tl, st);
+    }
 }
 
 int tc_batch_grid(const TcTile& tile, int q, int num_sms)

@@ -257,6 +257,22 @@ __device__ __forceinline__ void tmem_ld_32x32b_x16_nowait(uint32_t taddr, float*
 
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// Store 16 consecutive 32-bit columns of this warp's 32 lanes (one per thread) into tensor memory;
+// tmem_st_wait() orders the stores before later tensor-memory reads of the same columns.
+__device__ __forceinline__ void tmem_st_32x32b_x16(uint32_t taddr, const float* v)
+{
+    const uint32_t* r = reinterpret_cast<const uint32_t*>(v);
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};"
+        :
+        : "r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+          "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // Shared-memory descriptor of a K-major operand tile in the 128-byte swizzled layout: rows of
 // 64 bf16 (128 bytes), 8-row groups 1024 bytes apart, tile base 1024-byte aligned.  Advancing
 // the start address by 32 bytes selects the next 16-element K step inside the swizzle atom.

@@ -152,6 +152,28 @@ def test_fp32_level_statistics_match_oracle_small():
             assert abs(M2 - M2ref) <= 4 * tau32(lv.cl(l)) * M2ref
 
 
+@pytest.mark.parametrize("tile", [128064, 128128])
+@pytest.mark.parametrize("m,n,p", [(200, 3000, 130), (129, 500, 257)])
+def test_fp32_wide_tiles_ragged(m, n, p, tile):
+    """The FP32 128 x 64 and 128 x 128 tiles (f = identity): several tiles with ragged edges in
+    both directions, sampled D and level statistics over several chunks."""
+    pp = make_params(m, n, p, seed_A=31, seed_B=32, seed_idx=33, problem_id=1, dtype=np.float32)
+    orc = _orc(pp)
+    lv = oracle.Levels(16, 2, 3)
+    with _plan(pp, "fp32", 16, 3, dtype=torch.float32, tile_override=tile) as plan:
+        for l, s in [(0, 0), (1, 70), (3, 5)]:
+            D = plan.debug_sample(0, l, s).cpu().numpy()
+            Dref, _, _, mag = oracle.sample(orc, lv, l, s)
+            assert np.all(np.abs(D - Dref) <= tau32(lv.cl(l)) * mag), (l, s)
+        for l in range(4):
+            plan.level_stats(0, l, 10, 150)
+            n_got, mean, M2 = plan.get_level_stats(0, l)
+            mref, M2ref, magm = oracle.level_stats(orc, lv, l, 10, 150)
+            assert n_got == 150
+            assert np.all(np.abs(mean.cpu().numpy() - mref) <= tau32(lv.cl(l)) * magm), l
+            assert abs(M2 - M2ref) <= 4 * tau32(lv.cl(l)) * M2ref, (l, M2, M2ref)
+
+
 @pytest.mark.parametrize("m,n,p,c0,R,L", [(37, 1000, 53, 3, 3, 3), (1, 50, 1, 1, 2, 4), (130, 17, 5, 5, 2, 2)])
 def test_fp64_ragged_shapes_and_ratios(m, n, p, c0, R, L):
     pp = make_params(m, n, p, seed_A=11, seed_B=12, seed_idx=13, problem_id=4)

@@ -135,3 +135,20 @@ def test_e4m3_rejects_wide_tiles_and_backward():
         with pytest.raises(binding.MLMCError) as e:
             plan.backward([torch.zeros(16, 16, device=DEV, dtype=torch.float64)])
         assert e.value.status == 6
+
+
+def test_e4m3_pair_tiles_agree():
+    """The two cluster-pair forms (3256: 8 generator warps on 8-slot items; 4256, the E4M3
+    default: 16 warps on 4-slot items, the block maximum over 8 lanes) quantise every entry
+    alike (same block maxima, same dithers), so their level sums of D agree bit for bit and
+    their M2 up to the FP32 grouping of the drains."""
+    pp = make_params(200, 3000, 300, seed_A=13, seed_B=14, seed_idx=15, problem_id=0, dtype=np.float32)
+    with binding.Plan([_spec(pp)], c0=32, L=2, precision="fp8", tile_override=3256) as a, \
+            binding.Plan([_spec(pp)], c0=32, L=2, precision="fp8", tile_override=4256) as b:
+        for l in range(3):
+            a.level_stats(0, l, 0, 40)
+            b.level_stats(0, l, 0, 40)
+            na, sa, qa = a.get_level_state(0, l)
+            nb, sb, qb = b.get_level_state(0, l)
+            assert na == nb == 40 and torch.equal(sa, sb)
+            assert abs(qa - qb) <= 2e-5 * qb

@@ -143,22 +143,24 @@ PAIR_CASES = [
 ]
 
 
+@pytest.mark.parametrize("pair_tile", [3256, 4256])
 @pytest.mark.parametrize("m,n,p,c0,L,picks", PAIR_CASES)
-def test_bf16_cta_pair_tile_matches_oracle_and_single_cta_tile(m, n, p, c0, L, picks):
-    """Tile 3256 (two CTAs of a cluster share a 256 x 256 tile, each generating half of B for both)
-    against the FP64 oracle, and its level sums against the 128 x 256 single-CTA tile (the same
-    MMA chain per element, so the sums of D agree bit for bit; the M2 are grouped by the drain's
-    column split, so they agree up to FP32 rounding)."""
+def test_bf16_cta_pair_tile_matches_oracle_and_single_cta_tile(m, n, p, c0, L, picks, pair_tile):
+    """Tiles 3256 and 4256 (two CTAs of a cluster share a 256 x 256 tile, each generating half of B
+    for both; 4256 with 16 generator warps on 4-slot items) against the FP64 oracle, and their
+    level sums against the 128 x 256 single-CTA tile (the same MMA chain per element, so the sums
+    of D agree bit for bit; the M2 are grouped by the drain's column split, so they agree up to
+    FP32 rounding)."""
     pp = make_params(m, n, p, seed_A=3, seed_B=4, seed_idx=5, problem_id=1, dtype=np.float32)
     orc = _orc(pp)
     lv = oracle.Levels(c0, 2, L)
-    with _plan(pp, c0, L, tile_override=3256) as plan:
+    with _plan(pp, c0, L, tile_override=pair_tile) as plan:
         for l, s in picks:
             c = lv.cl(l)
             D = plan.debug_sample(0, l, s).cpu().numpy()
             Dref, _, _, mag = oracle.sample(orc, lv, l, s)
             assert np.all(np.abs(D - Dref) / mag <= tau_bf16(c)), (l, s)
-    with _plan(pp, c0, L, tile_override=3256) as a, _plan(pp, c0, L, tile_override=1256) as b:
+    with _plan(pp, c0, L, tile_override=pair_tile) as a, _plan(pp, c0, L, tile_override=1256) as b:
         for l in range(min(L, 3) + 1):
             a.level_stats(0, l, 0, 96)
             b.level_stats(0, l, 0, 96)
