@@ -58,19 +58,19 @@ def measure_alu_peaks(stream):
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel from one ncu capture
 # (profiles/); None once the kernel changed after the capture
 TRAFFIC = {
-    # DRAM bytes per sampled outer product of the 64 x 64 tile kernel (level-0 capture of 262144
+    # DRAM bytes per sampled outer product of the 128 x 64 tile kernel (level-0 capture of 262144
     # outer products), used for every level
-    "fp32": {"dram_bytes_per_outer_product": {0: 790.9e6 / 262144, 8: 790.9e6 / 262144},
+    "fp32": {"dram_bytes_per_outer_product": {0: (745842432 + 13862912) / 262144, 8: (745842432 + 13862912) / 262144},
              "source": "profiles/level_cuda_core_f32_mlmc_256x65536x256.md"},
     # DRAM bytes (read + write) per sampled outer product of the CTA-pair kernel (tile 3256) at
     # levels 0 and 8, each from one ncu pass over one launch of the bench's profile case
     # (16384 level-0 samples, 2432 level-8 samples of this workload); levels between are
     # interpolated, and bench.py scales them by the outer products of its own launches
-    "bf16": {"dram_bytes_per_outer_product": {0: (2902364416 + 62743296) / 1048576,
-                                              8: (108993357568 + 76798720) / 39845888},
+    "bf16": {"dram_bytes_per_outer_product": {0: (2901958400 + 62803200) / 1048576,
+                                              8: (108988471808 + 78316800) / 39845888},
              "source": "profiles/level_tc_bf16_mlmc_256x65536x256.md"},
-    "fp8": {"dram_bytes_per_outer_product": {0: (2901204224 + 62871296) / 1048576,
-                                             8: (108976157440 + 83111680) / 39845888},
+    "fp8": {"dram_bytes_per_outer_product": {0: (2902601984 + 62838272) / 1048576,
+                                             8: (109010083328 + 77853952) / 39845888},
             "source": "profiles/level_tc_bf16_mlmc_256x65536x256.md"},
 }
 

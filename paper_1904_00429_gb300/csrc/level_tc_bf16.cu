@@ -67,7 +67,9 @@ struct TcCfg {
     static constexpr int kGW = W;                         // generator warps
     static constexpr int kGT = 32 * W;                    // generator threads
     static constexpr int kThr = kGT + 32;                  // + the producer warp
-    static constexpr int kNS = W == 16 ? 4 : 8;           // slots per generator item
+    // slots per generator item: 4 where 8 would leave too few items per sub-block to keep the
+    // generator warps busy (the 16-warp pair; BF16 single-CTA tiles of at most 64 columns)
+    static constexpr int kNS = (W == 16 || (Q == 0 && P == 0 && MH == 1 && BN <= 64)) ? 4 : 8;
     // Slots per sub-block: 32 for E4M3 (one scale block), pairs, and small tiles whose 16-slot
     // sub-block would leave generator threads idle ((rows + BN) / 4 x 2 items for 256 threads)
     static constexpr int kSub = (Q || P || 128 * MH + BN <= 256) ? 32 : 16;
@@ -159,14 +161,30 @@ __device__ __forceinline__ void gen_block(const int* idx, int slot0, bool valid_
         return;
     }
     // Branch-free: the Philox blocks are independent dependency chains, computed for every slot
-    // (a missing slot uses k = 0) and zeroed afterwards, so they can interleave.
+    // (a missing slot uses k = 0) and zeroed afterwards, so they can interleave.  An item without
+    // any slot (a packed half's K positions of the other sample, the tail of the last sub-block)
+    // only writes zeros.
     int ks[NS];
-    uint4 w[NS];
+    bool any = false;
 #pragma unroll
     for (int u = 0; u < NS; ++u) {
         ks[u] = idx[slot0 + u];
-        w[u] = philox4x32_10_rk(make_uint4(rowgrp, static_cast<uint32_t>(max(ks[u], 0)), s_lo, lsw), rk);
+        any |= ks[u] >= 0;
     }
+    if (!any) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            if constexpr (NS == 8)
+                *reinterpret_cast<uint4*>(tile + tile_offset<kSw>(row0 + r, chunk)) = make_uint4(0, 0, 0, 0);
+            else
+                *reinterpret_cast<uint2*>(tile + tile_offset<kSw>(row0 + r, chunk) + sub) = make_uint2(0, 0);
+        }
+        return;
+    }
+    uint4 w[NS];
+#pragma unroll
+    for (int u = 0; u < NS; ++u)
+        w[u] = philox4x32_10_rk(make_uint4(rowgrp, static_cast<uint32_t>(max(ks[u], 0)), s_lo, lsw), rk);
     float v[4][NS];
 #pragma unroll
     for (int u = 0; u < NS; ++u) {
@@ -704,18 +722,22 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                                 // packed samples: A rows 0-63 belong to sample s, rows 64-127 to s + 1 (zero
                                 // on the other sample's K positions); B's K positions to whichever owns them
                                 if (it < kItemsA) {
-                                    const int g4 = Q == 0 ? it % (C::kRows / 4) : it / kGroups;
-                                    const int sg = Q == 0 ? it / (C::kRows / 4) : it % kGroups;
+                                    // BF16: items ordered (half, slot group, row group), so a warp's items
+                                    // belong to one half and skip the other sample's positions together
+                                    const int rest = it >> 4;
+                                    const int g4 = Q == 0 ? (rest / kGroups) * 16 + (it & 15) : it / kGroups;
+                                    const int sg = Q == 0 ? rest % kGroups : it % kGroups;
                                     const int h = g4 >> 4;
                                     const int i = 4 * (g4 & 15);
                                     const uint64_t sh = s + static_cast<uint64_t>(h);
                                     const bool vr = i < prm.m && h < ngrp;
                                     const int* ih = idxh_s + b * 2 * kSub + h * kSub;
-                                    const unsigned char* src = st + (sg * 8) * (C::kRows * 8) + (g4 & 15) * 32;
+                                    const unsigned char* src = st + (sg * kNS) * (C::kRows * 8) + (g4 & 15) * 32;
                                     if constexpr (Q == 0)
-                                        gen_block(ih, sg * 8, vr, static_cast<uint32_t>(i >> 2), static_cast<uint32_t>(sh),
-                                                  level_sample_word(prm.l, sh), prm.rkA, src, C::kRows * 8, false,
-                                                  a_tile, 4 * g4, kGroups * kk + sg);
+                                        gen_block<128, kNS>(ih, sg * kNS, vr, static_cast<uint32_t>(i >> 2),
+                                                            static_cast<uint32_t>(sh), level_sample_word(prm.l, sh),
+                                                            prm.rkA, src, C::kRows * 8, false, a_tile, 4 * g4,
+                                                            (kSub / 8) * kk + (sg * kNS) / 8, ((sg * kNS) % 8) * 2);
                                     else
                                         gen_block_e4m3(ih, sg * 8, vr, static_cast<uint32_t>(i >> 2),
                                                        static_cast<uint32_t>(sh), level_sample_word(prm.l, sh), prm.rkA,
@@ -726,14 +748,15 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                                     const int g4 = Q == 0 ? it2 % (C::kBGen / 4) : it2 / kGroups;
                                     const int sg = Q == 0 ? it2 / (C::kBGen / 4) : it2 % kGroups;
                                     const int jc = geo.bcol0 + 4 * g4;
-                                    const int kp0 = j * kSub + sg * 8;   // first K position of the 8 slots
+                                    const int kp0 = j * kSub + sg * kNS;   // first K position of the item's slots
                                     const int h = kp0 < nK ? kp0 / prm.c : 0;
                                     const uint64_t sh = s + static_cast<uint64_t>(h);
-                                    const unsigned char* src = stB + (sg * 8) * (C::kBGen * 8) + g4 * 32;
+                                    const unsigned char* src = stB + (sg * kNS) * (C::kBGen * 8) + g4 * 32;
                                     if constexpr (Q == 0)
-                                        gen_block(idx, sg * 8, jc < prm.p, static_cast<uint32_t>(jc >> 2),
-                                                  static_cast<uint32_t>(sh), level_sample_word(prm.l, sh), prm.rkB, src,
-                                                  C::kBGen * 8, coarse_sign, b_tile, brow0 + 4 * g4, kGroups * kk + sg);
+                                        gen_block<128, kNS>(idx, sg * kNS, jc < prm.p, static_cast<uint32_t>(jc >> 2),
+                                                            static_cast<uint32_t>(sh), level_sample_word(prm.l, sh),
+                                                            prm.rkB, src, C::kBGen * 8, coarse_sign, b_tile, brow0 + 4 * g4,
+                                                            (kSub / 8) * kk + (sg * kNS) / 8, ((sg * kNS) % 8) * 2);
                                     else
                                         gen_block_e4m3(idx, sg * 8, jc < prm.p, static_cast<uint32_t>(jc >> 2),
                                                        static_cast<uint32_t>(sh), level_sample_word(prm.l, sh), prm.rkB,
@@ -743,7 +766,7 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                             } else if constexpr (Q == 0) {
                                 // consecutive threads take consecutive row groups
                                 if (it < kItemsA) {
-                                    // 4 rows of A x 8 slots
+                                    // 4 rows of A x kNS slots
                                     const int g4 = it % (C::kRows / 4);
                                     const int sg = it / (C::kRows / 4);
                                     const int i = tm0 + 4 * g4;
@@ -753,11 +776,12 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                                                            C::kRows * 8, false, a_tile + kk * C::kASliceBytes, 4 * g4,
                                                            (sg * kNS) / 8, ((sg * kNS) % 8) * 2);
                                     else
-                                        gen_block(idx, sg * 8, i < prm.m, static_cast<uint32_t>(i >> 2), s_lo, lsw,
-                                                  prm.rkA, st + (sg * 8) * (C::kRows * 8) + g4 * 32, C::kRows * 8,
-                                                  false, a_tile, 4 * g4, kGroups * kk + sg);
+                                        gen_block<128, kNS>(idx, sg * kNS, i < prm.m, static_cast<uint32_t>(i >> 2), s_lo,
+                                                            lsw, prm.rkA, st + (sg * kNS) * (C::kRows * 8) + g4 * 32,
+                                                            C::kRows * 8, false, a_tile, 4 * g4,
+                                                            (kSub / 8) * kk + (sg * kNS) / 8, ((sg * kNS) % 8) * 2);
                                 } else {
-                                    // 4 columns of B (rows of the transposed tile) x 8 slots, sign folded in;
+                                    // 4 columns of B (rows of the transposed tile) x kNS slots, sign folded in;
                                     // a pair also writes them into the peer's B tile
                                     const int it2 = it - kItemsA;
                                     const int g4 = it2 % (C::kBGen / 4);
@@ -769,10 +793,10 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                                                            C::kBGen * 8, coarse_sign, b_tile + kk * C::kBSliceBytes,
                                                            brow0 + 4 * g4, (sg * kNS) / 8, ((sg * kNS) % 8) * 2);
                                     else
-                                        gen_block(idx, sg * 8, jc < prm.p, static_cast<uint32_t>(jc >> 2), s_lo, lsw,
-                                                  prm.rkB, stB + (sg * 8) * (C::kBGen * 8) + g4 * 32,
-                                                  C::kBGen * 8, coarse_sign, b_tile, brow0 + 4 * g4,
-                                                  kGroups * kk + sg);
+                                        gen_block<128, kNS>(idx, sg * kNS, jc < prm.p, static_cast<uint32_t>(jc >> 2), s_lo,
+                                                            lsw, prm.rkB, stB + (sg * kNS) * (C::kBGen * 8) + g4 * 32,
+                                                            C::kBGen * 8, coarse_sign, b_tile, brow0 + 4 * g4,
+                                                            (kSub / 8) * kk + (sg * kNS) / 8, ((sg * kNS) % 8) * 2);
                                 }
                             } else {
                                 // E4M3: the kGroups threads of one row group are adjacent lanes, so the
