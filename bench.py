@@ -15,6 +15,10 @@ estimator has no bias for f = identity, so the time of the full run is
 with t_l the measured device time of level l's batches (CUDA events on the plan's stream).
 ``value`` is that projected time in seconds (lower is better).
 
+Measured end to end as well (default legs): the headline workload at rel. RMSE 3e-2 through
+mlmc_estimate (``ladder``: extrapolated to 1e-3 by eps^-2 and set beside the projection), and
+the 64 x 1024 x 64 workload at 1e-3 (BF16) and 3e-3 (BF16, FP32, E4M3) (``ttr_64x1024x64``).
+
 e2e: the same metric through the C ABI from pinned host buffers: each e2e step copies the
 four parameter matrices host->device, builds a plan (layout copy), runs the step's batches
 and reads the estimate back; T_e2e = (e2e step time - its sampling time) + sum_l N_l t_l / B_l.
@@ -442,7 +446,7 @@ def _roofline(res, W, peaks, peak_kind, gen_rate=None):
 ADJOINT = dict(name="adjoint_256x65536x256", m=256, n=65536, p=256, c0=64, R=2, L=8, N=256, precision="bf16")
 
 
-def _measure_adjoint(args, host, dev, stream, peaks, peak_kind):
+def _measure_adjoint(args, host, dev, stream, peaks, peak_kind, gen_rate=None):
     """Backward of the loss ||Yhat - T||_F^2 through mlmc_backward: A 256 x 65536, B 65536 x 256,
     c_l = 64 * 2^l for l = 0..8, N_l = 256 samples per level, BF16 forward (straight-through
     adjoint).  Times exactly ``args.steps`` backward calls after ``args.warmup`` untimed ones."""
@@ -491,7 +495,13 @@ def _measure_adjoint(args, host, dev, stream, peaks, peak_kind):
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None, "peak_source": src,
                          "flops": "useful: 4 m p per record (the hi/lo split of G issues twice that)",
-                         "kernel": "segment_tc_kernel"}}
+                         "kernel": "segment_tc_kernel",
+                         # the bound that binds: regenerating the replayed vectors, 2 (m + p) normals
+                         # per record against the measured generation rate (the same arithmetic)
+                         "generation": None if not gen_rate else
+                         {"bound": "alu", "achieved": normals / t, "peak": gen_rate, "unit": "entries/s",
+                          "frac": normals / t / gen_rate,
+                          "peak_source": "mlmc_measure_generation_rate in this run"}}}
 
 
 def _measure_ladder(args, rels, W, host, exact, dev, stream, projected):
@@ -762,18 +772,20 @@ def _measure_xi(args, dev, stream):
     mu = params[0].astype(np.float64) @ params[2].astype(np.float64)
     eps = X["rel_rmse"] * float(np.linalg.norm(mu))
     out = {}
-    for law in ("uniform", "optimal"):
+    # FP32 (CUDA cores) under both laws, then BF16 (tensor cores, the slot weights folded into B)
+    for key, law, prec in (("uniform", "uniform", X["precision"]), ("optimal", "optimal", X["precision"]),
+                           ("bf16_uniform", "uniform", "bf16"), ("bf16_optimal", "optimal", "bf16")):
         spec = binding.ProblemSpec(*ts, seed_A=3, seed_B=4, seed_idx=5, problem_id=0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        with binding.Plan([spec], c0=X["c0"], L=X["L"], ratio=X["R"], precision=X["precision"], pilot_n=X["pilot"],
+        with binding.Plan([spec], c0=X["c0"], L=X["L"], ratio=X["R"], precision=prec, pilot_n=X["pilot"],
                           sampling=law, stream=stream) as plan:
             (Y,), (rep,) = plan.estimate([eps])
             torch.cuda.synchronize()
             t = time.perf_counter() - t0
         err = float(np.linalg.norm(Y.cpu().numpy() - mu))
-        out[law] = {"value": t, "N_l": rep["N"], "V_l": rep["V"], "outer_products": rep["outer_products"],
-                    "rmse_pred": rep["rmse_pred"], "error": err,
+        out[key] = {"value": t, "N_l": rep["N"], "V_l": rep["V"], "outer_products": rep["outer_products"],
+                    "rmse_pred": rep["rmse_pred"], "error": err, "precision": prec,
                     "timing": "end to end through mlmc_estimate, plan creation included"}
     # FMAs of the contraction (2 m p per sampled outer product) over the end-to-end time of xi**
     achieved = 2.0 * X["m"] * X["p"] * out["optimal"]["outer_products"] / out["optimal"]["value"] / 1e12
@@ -785,7 +797,11 @@ def _measure_xi(args, dev, stream):
                          "kernel": "level_cuda_core_kernel<float, XI>",
                          "note": "xi** run end to end (plan creation, pilot and allocation included)"},
             "uniform_over_optimal": out["uniform"]["value"] / out["optimal"]["value"],
-            "V0_uniform_over_optimal": out["uniform"]["V_l"][0] / out["optimal"]["V_l"][0]}
+            "V0_uniform_over_optimal": out["uniform"]["V_l"][0] / out["optimal"]["V_l"][0],
+            "bf16": {"uniform": out["bf16_uniform"], "optimal": out["bf16_optimal"],
+                     "uniform_over_optimal": out["bf16_uniform"]["value"] / out["bf16_optimal"]["value"],
+                     "fp32_optimal_over_bf16_optimal": out["optimal"]["value"] / out["bf16_optimal"]["value"],
+                     "kernel": "level_tc_bf16_kernel (xi** weights folded into B before rounding)"}}
 
 
 BATCHED = dict(name="batched_64_problems", count=64, shape_seed=7, c0=32, R=2, pilot=256, rel_rmse=1e-3,
@@ -969,13 +985,14 @@ def run_ours(args):
                                        "clocks": o["clocks"]}
                            for o in others}
     if not args.no_adjoint and world == 1:
-        line["adjoint"] = _measure_adjoint(args, host, dev, stream, peaks, peak_kind)
+        line["adjoint"] = _measure_adjoint(args, host, dev, stream, peaks, peak_kind, gen_rate)
     if not args.no_batched and world == 1:
         line["batched"] = _measure_batched(args, dev, stream, peaks, peak_kind)
         if not args.no_compare:
-            # the plain FP32 comparator of the same 64 problems (CUDA cores), on a tenth of the step
+            # the plain FP32 comparator of the same 64 problems (CUDA cores, the ranges in turn), on
+            # steps of the same size (one timed step)
             fp32b = _measure_batched(args, dev, stream, peaks, peak_kind, precision="fp32",
-                                     step_target=BATCHED["step_outer"] / 10, steps=1, warmup=1)
+                                     step_target=BATCHED["step_outer"], steps=1, warmup=1)
             line["batched"]["compare"] = {"fp32": fp32b, "fp32_over_bf16": fp32b["value"] / line["batched"]["value"]}
     if not args.no_nonlinear and world == 1:
         line["nonlinear"] = _measure_nonlinear(args, dev, stream)
@@ -983,17 +1000,26 @@ def run_ours(args):
         line["xi"] = _measure_xi(args, dev, stream)
     if not args.no_dedupe and world == 1:
         line["dedupe_bound"] = _measure_dedupe_bound(args, head, W, dev, stream)
-    ttr_rels = [float(x) for x in args.ttr.split(",") if x.strip("'\" ")]
-    fp8_rels = [float(x) for x in args.ttr_fp8.split(",") if x.strip("'\" ")]
-    if (ttr_rels or fp8_rels) and world == 1:
-        out = _measure_ttr(args, ttr_rels, [x for x in args.ttr_precisions.split(",") if x], dev, stream) \
-            if ttr_rels else None
-        if fp8_rels:
-            o8 = _measure_ttr(args, fp8_rels, ["fp8"], dev, stream)
+    def _floats(text):
+        return [float(x) for x in text.split(",") if x.strip("'\" ")]
+
+    def _words(text):
+        return [x for x in text.split(",") if x.strip("'\" ")]
+
+    ttr_sets = [(_floats(args.ttr), _words(args.ttr_precisions)),
+                (_floats(args.ttr_side), _words(args.ttr_side_precisions))]
+    ttr_sets = [(r, p) for r, p in ttr_sets if r and p]
+    if ttr_sets and world == 1:
+        out = None
+        for rels, precs in ttr_sets:
+            o = _measure_ttr(args, rels, precs, dev, stream)
             if out is None:
-                out = o8
+                out = o
             else:
-                out["runs"] += o8["runs"]
+                out["runs"] += o["runs"]
+        by = {(r["precision"], r["rel_rmse"]): r["seconds"] for r in out["runs"]}
+        out["fp32_over"] = {f"{p}@{rel:g}": by[("fp32", rel)] / t for (p, rel), t in by.items()
+                            if p != "fp32" and ("fp32", rel) in by}
         line["ttr_64x1024x64"] = out
     if args.ladder and world == 1:
         rels = [float(x) for x in args.ladder.split(",")]
@@ -1054,11 +1080,17 @@ def run_profile_case(args):
                                              seed_A=2 * q, seed_B=2 * q + 1, seed_idx=2, problem_id=q, L=L))
             ranges += [(q, l) for l in range(L + 1)]
         plan = binding.Plan(specs, c0=BATCHED["c0"], L=8, precision="bf16", tile_override=1128)
+        waves = []
         for i in range(3):
+            c0 = plan.launch_count()
             plan.level_stats_batch([(q, l, 256 * i, 256) for q, l in ranges])
+            waves.append((plan.launch_count() - c0) // 3)   # a wave: the level kernel and two merges
         plan.synchronize()
         plan.close()
-        print(json.dumps({"profile_case": args.profile_case, "status": "ok"}), flush=True)
+        shapes = batched_shapes(BATCHED["count"], BATCHED["shape_seed"])[:8]
+        alg = sum(256 * BATCHED["c0"] * BATCHED["R"]**l * 2 * (shapes[q][0] + shapes[q][2]) * 4 for q, l in ranges)
+        print(json.dumps({"profile_case": args.profile_case, "status": "ok", "level_launches_per_call": waves,
+                          "algorithmic_bytes_per_call": alg}), flush=True)
         return
     if args.profile_case == "cuda_core_f32_xi_level3":
         # the xi** variant of the CUDA-core kernel on the sparse-row workload, level 3 (c = 128)
@@ -1121,13 +1153,15 @@ def main():
     ap.add_argument("--no-nonlinear", action="store_true", help="skip the E[f(AB)] adaptive-L measurement")
     ap.add_argument("--no-xi", action="store_true", help="skip the xi^u / xi** comparison")
     ap.add_argument("--no-dedupe", action="store_true", help="skip the index-dedupe bound")
-    ap.add_argument("--ladder", default="", help="comma-separated relative RMSE targets to run end to end "
-                    "through mlmc_estimate (e.g. 3e-2; about a minute each at 3e-2)")
+    ap.add_argument("--ladder", default="3e-2", help="comma-separated relative RMSE targets to run end to end "
+                    "through mlmc_estimate on the headline workload (about a minute at 3e-2; '' to skip)")
     ap.add_argument("--ttr", default="1e-3", help="comma-separated relative RMSE targets of the end-to-end "
                     "time-to-RMSE runs on the 64x1024x64 workload ('' to skip)")
-    ap.add_argument("--ttr-precisions", default="bf16,fp32", help="precisions of those runs")
-    ap.add_argument("--ttr-fp8", default="3e-3", help="relative targets of the E4M3 run on the same workload "
-                    "(its stochastic rounding makes 1e-3 take about 8 minutes; '' to skip)")
+    ap.add_argument("--ttr-precisions", default="bf16", help="precisions of those runs (each about 3 minutes "
+                    "at 1e-3)")
+    ap.add_argument("--ttr-side", default="3e-3", help="relative targets of the shorter runs of every "
+                    "precision in --ttr-side-precisions ('' to skip)")
+    ap.add_argument("--ttr-side-precisions", default="bf16,fp32,fp8", help="precisions of the shorter runs")
     ap.add_argument("--profile-case", choices=sorted(list(PROFILE_CASES) + list(SMALL_PROFILE_CASES) +
                                                      ["adjoint", "batched_8_problems", "cuda_core_f32_xi_level3"]),
                     default=None,

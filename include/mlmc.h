@@ -137,7 +137,10 @@ typedef struct {
                             whose finest mean satisfies ||Y_L||_F < (sqrt(R) + 1) eps / sqrt(2)
                             (Remark 3.5, Eq. L_num_bound_matrix), or at the problem's L */
     int32_t sampling;    /* mlmc_sampling: the law of the sampled indices.  MLMC_XI_OPTIMAL needs
-                            MLMC_FP64 or MLMC_FP32 and has no mlmc_backward */
+                            MLMC_FP64, MLMC_FP32 or MLMC_BF16 (not E4M3) and has no mlmc_backward;
+                            BF16 multiplies each entry of B by its slot's weight Q_{n-1} / q_k (FP32)
+                            before rounding, applies 1 / c_l to the accumulator, and evaluates
+                            mlmc_level_stats_batch ranges in turn */
 } mlmc_options;
 
 /* Index laws (mlmc_options.sampling). */

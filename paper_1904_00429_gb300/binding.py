@@ -163,7 +163,7 @@ class Plan:
     precision: "fp64", "fp32" (CUDA cores), "bf16" or "fp8" (tensor cores).  f: "identity"
     (E[AB]) or "abs_step" (E[f(AB)] with f(x) = |x| H(2 - x); FP64/FP32/BF16).  adaptive_L: let
     estimate() choose the finest level by Alg. 2's while loop, up to L.  sampling: "uniform"
-    (xi^u) or "optimal" (xi** of Thm 3.1; FP64/FP32).  The fields mirror mlmc_options."""
+    (xi^u) or "optimal" (xi** of Thm 3.1; FP64/FP32/BF16).  The fields mirror mlmc_options."""
 
     def __init__(self, problems: Sequence[ProblemSpec], *, c0: int, L: int, ratio: int = 2,
                  precision: str = "fp32", pilot_n: int = 256, nl_scale: float = 1.0,

@@ -231,6 +231,10 @@ mlmc_status validate(const mlmc_problem* problems, int32_t nprob, const mlmc_opt
         !tc_tile_valid(decode_tile(o->tile_override), o->precision == MLMC_FP8_E4M3 ? 1 : 0))
         return fail(MLMC_ERR_INVALID_ARG, "tile_override %d is not a tile id of this precision (1032 .. 2256; "
                     "E4M3: 1032 1064 1128 2032 2064; pairs 3256, 4256)", o->tile_override);
+    if (tc_prec && o->f == MLMC_F_IDENTITY && o->sampling == MLMC_XI_OPTIMAL && o->tile_override != 0 &&
+        !tc_tile_valid_xi(decode_tile(o->tile_override)))
+        return fail(MLMC_ERR_INVALID_ARG, "tile_override %d: xi** takes tiles 1032, 1064, 1128 or 3256",
+                    o->tile_override);
     if (tc_prec && o->f != MLMC_F_IDENTITY && o->tile_override != 0 && !tc_tile_valid_f(decode_tile(o->tile_override)))
         return fail(MLMC_ERR_INVALID_ARG, "tile_override %d: a targeted function takes tiles 1032, 1064 or 1128",
                     o->tile_override);
@@ -242,8 +246,8 @@ mlmc_status validate(const mlmc_problem* problems, int32_t nprob, const mlmc_opt
     if (o->adaptive_L != 0 && o->adaptive_L != 1) return fail(MLMC_ERR_INVALID_ARG, "adaptive_L must be 0 or 1");
     if (o->sampling != MLMC_XI_UNIFORM && o->sampling != MLMC_XI_OPTIMAL)
         return fail(MLMC_ERR_INVALID_ARG, "unknown sampling law %d", o->sampling);
-    if (o->sampling != MLMC_XI_UNIFORM && o->precision != MLMC_FP64 && o->precision != MLMC_FP32)
-        return fail(MLMC_ERR_UNSUPPORTED, "the xi** sampling law needs FP64 or FP32");
+    if (o->sampling != MLMC_XI_UNIFORM && o->precision == MLMC_FP8_E4M3)
+        return fail(MLMC_ERR_UNSUPPORTED, "the xi** sampling law needs FP64, FP32 or BF16");
     for (int32_t q = 0; q < nprob; ++q) {
         const mlmc_problem& pr = problems[q];
         const int L = pr.L >= 0 ? pr.L : o->L;
@@ -388,6 +392,11 @@ mlmc_status run_level(mlmc_plan_t* plan, ProblemState& ps, int level, uint64_t s
                 prm.pack = 0;
                 prm.welford = 1;
                 err = launch_level_tc_f(prm, ps.tile, o.f, tl, plan->stream);
+            } else if (ps.xi_Q) {
+                // xi**: per-slot weights, no packed samples; the level means are zero for l >= 1 too
+                prm.pack = 0;
+                prm.welford = level == 0 ? 1 : 0;
+                err = launch_level_tc(prm, ps.tile, tc_format(o), tl, plan->stream);
             } else {
                 prm.pack = tc_pack(ps.tile, tc_format(o), ps.m, c) ? 1 : 0;
                 // f = identity: for l >= 1 the fine and coarse estimates of one realisation have the
@@ -912,8 +921,8 @@ mlmc_status mlmc_plan(const mlmc_problem* problems, int32_t nprob, const mlmc_op
         ps.p_pad = (ps.p + 3) / 4 * 4;
         if (tensor_core_precision(options->precision)) {
             const TcTile tile = options->tile_override ? decode_tile(options->tile_override)
-                                : options->f != MLMC_F_IDENTITY
-                                    ? tc_tile_for_f(ps.p)
+                                : options->f != MLMC_F_IDENTITY      ? tc_tile_for_f(ps.p)
+                                : options->sampling == MLMC_XI_OPTIMAL ? tc_tile_for_xi(ps.m, ps.p)
                                     : tc_tile_for(ps.m, ps.p, options->precision == MLMC_FP8_E4M3 ? 1 : 0, true);
             ps.tile = tile;
             ps.tiles_m = int((ps.m + tile.rows - 1) / tile.rows);
@@ -1056,8 +1065,10 @@ mlmc_status mlmc_level_stats_batch(mlmc_plan_t* plan, const mlmc_range* ranges, 
     }
     if (rs.empty()) return MLMC_OK;
     DeviceGuard g(plan->device);
-    // the batched persistent launch is the identity's; other forms evaluate the ranges in turn
-    if (!tensor_core_precision(plan->opt.precision) || plan->opt.f != MLMC_F_IDENTITY) {
+    // the batched persistent launch is the identity's under the uniform law; other forms evaluate
+    // the ranges in turn
+    if (!tensor_core_precision(plan->opt.precision) || plan->opt.f != MLMC_F_IDENTITY ||
+        plan->opt.sampling != MLMC_XI_UNIFORM) {
         for (const BatchRange& r : rs) {
             ProblemState& ps = plan->probs[size_t(r.prob)];
             const int64_t mp = ps.m * ps.p;

@@ -125,6 +125,9 @@ cudaError_t launch_level_tc(const LevelParams& prm, const TcTile& tile, int q, c
 // rows and 32, 64 or 128 columns
 TcTile tc_tile_for_f(int64_t p);
 bool tc_tile_valid_f(const TcTile& t);
+// BF16 under xi**: the CTA pair above 128 x 128, else tiles of 128 rows and at most 128 columns
+TcTile tc_tile_for_xi(int64_t m, int64_t p);
+bool tc_tile_valid_xi(const TcTile& t);
 cudaError_t launch_level_tc_f(const LevelParams& prm, const TcTile& tile, int f, const TcLaunch& tl, cudaStream_t st);
 // Whether a launch of `tile` over a level with c slots packs two samples per accumulator.
 bool tc_pack(const TcTile& tile, int q, int64_t m, int64_t c);

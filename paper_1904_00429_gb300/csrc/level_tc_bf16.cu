@@ -95,6 +95,7 @@ struct TcCfg {
     // barriers: full[2], empty[2], slice[kSlices], done, and for pairs peer[kSlices] (the peer's B half landed)
     static constexpr int kNumBars = 2 + 2 + kSlices + 1 + (P ? kSlices : 0) + 1 /*abort drain*/;
     static constexpr int kBookBytes = 2 * kSub * 4 /*idx*/ + 2 * 2 * kSub * 4 /*idx per packed half*/ +
+                                      2 * kSub * 4 /*xi** slot weights*/ +
                                       kNumBars * 8 + 16 /*tmem, abort*/ + kGW * 8 +
                                       (P ? 0 : 2 * static_cast<int>(sizeof(LevelParams)) +
                                                    static_cast<int>(alignof(LevelParams)))
@@ -141,12 +142,14 @@ __device__ __forceinline__ uint32_t tile_offset(int row, int chunk)
     return kSw == 128 ? tc::sw128_offset(row, chunk) : tc::sw64_offset(row, chunk);
 }
 
-template <int kSw = 128, int NS = 8>
+// kWt: each slot's entries are also multiplied by its weight gw[slot] (xi**: Q_{n-1} / q_k) before
+// rounding.  kSkip: an item without any slot writes zeros without drawing (tiles that pack samples).
+template <int kSw = 128, int NS = 8, bool kWt = false, bool kSkip = false>
 __device__ __forceinline__ void gen_block(const int* idx, int slot0, bool valid_rows, uint32_t rowgrp,
                                           uint32_t s_lo, uint32_t lsw, const PhiloxRoundKeys& rk,
                                           const unsigned char* stage,
                                           int stride, bool odd_negative, unsigned char* tile, int row0, int chunk,
-                                          int sub = 0)
+                                          int sub = 0, const float* gw = nullptr)
 {
     static_assert(NS == 8 || NS == 4, "slots per item");
     if (!valid_rows) {
@@ -161,30 +164,38 @@ __device__ __forceinline__ void gen_block(const int* idx, int slot0, bool valid_
         return;
     }
     // Branch-free: the Philox blocks are independent dependency chains, computed for every slot
-    // (a missing slot uses k = 0) and zeroed afterwards, so they can interleave.  An item without
-    // any slot (a packed half's K positions of the other sample, the tail of the last sub-block)
-    // only writes zeros.
+    // (a missing slot uses k = 0) and zeroed afterwards, so they can interleave.  With kSkip, an
+    // item without any slot (a packed half's K positions of the other sample, the tail of the last
+    // sub-block) only writes zeros.
     int ks[NS];
-    bool any = false;
-#pragma unroll
-    for (int u = 0; u < NS; ++u) {
-        ks[u] = idx[slot0 + u];
-        any |= ks[u] >= 0;
-    }
-    if (!any) {
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            if constexpr (NS == 8)
-                *reinterpret_cast<uint4*>(tile + tile_offset<kSw>(row0 + r, chunk)) = make_uint4(0, 0, 0, 0);
-            else
-                *reinterpret_cast<uint2*>(tile + tile_offset<kSw>(row0 + r, chunk) + sub) = make_uint2(0, 0);
-        }
-        return;
-    }
     uint4 w[NS];
+    if constexpr (kSkip) {
+        bool any = false;
 #pragma unroll
-    for (int u = 0; u < NS; ++u)
-        w[u] = philox4x32_10_rk(make_uint4(rowgrp, static_cast<uint32_t>(max(ks[u], 0)), s_lo, lsw), rk);
+        for (int u = 0; u < NS; ++u) {
+            ks[u] = idx[slot0 + u];
+            any |= ks[u] >= 0;
+        }
+        if (!any) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                if constexpr (NS == 8)
+                    *reinterpret_cast<uint4*>(tile + tile_offset<kSw>(row0 + r, chunk)) = make_uint4(0, 0, 0, 0);
+                else
+                    *reinterpret_cast<uint2*>(tile + tile_offset<kSw>(row0 + r, chunk) + sub) = make_uint2(0, 0);
+            }
+            return;
+        }
+#pragma unroll
+        for (int u = 0; u < NS; ++u)
+            w[u] = philox4x32_10_rk(make_uint4(rowgrp, static_cast<uint32_t>(max(ks[u], 0)), s_lo, lsw), rk);
+    } else {
+#pragma unroll
+        for (int u = 0; u < NS; ++u) {
+            ks[u] = idx[slot0 + u];
+            w[u] = philox4x32_10_rk(make_uint4(rowgrp, static_cast<uint32_t>(max(ks[u], 0)), s_lo, lsw), rk);
+        }
+    }
     float v[4][NS];
 #pragma unroll
     for (int u = 0; u < NS; ++u) {
@@ -194,7 +205,8 @@ __device__ __forceinline__ void gen_block(const int* idx, int slot0, bool valid_
         const float4 p0 = src[0];
         const float4 p1 = src[1];
         const bool use = ks[u] >= 0;
-        const float sg = (odd_negative && (u & 1)) ? -1.0f : 1.0f;
+        float sg = (odd_negative && (u & 1)) ? -1.0f : 1.0f;
+        if constexpr (kWt) sg *= gw[slot0 + u];
         v[0][u] = use ? sg * fmaf(p0.y, z[0], p0.x) : 0.0f;
         v[1][u] = use ? sg * fmaf(p0.w, z[1], p0.z) : 0.0f;
         v[2][u] = use ? sg * fmaf(p1.y, z[2], p1.x) : 0.0f;
@@ -329,11 +341,16 @@ __device__ __forceinline__ void gen_block_e4m3(const int* idx, int slot0, bool v
 // sample's positions, so one MMA chain forms both samples' D.  Each half keeps its own running
 // sum (rows of S) and Welford M2; at the end of a chunk the halves are combined by Chan's update.
 // Needs c_l % 16 == 0 (a group of 8 slots, and an E4M3 block, never straddles two samples).
-template <int MH, int BN, int Q, bool kBatch, int P = 0, int W = 8, int F = 0>
+// XI: the xi** law (Thm 3.1): the producer draws each slot by inverse CDF and stores its weight
+// Q_{n-1} / q_k, which the generators fold into B; the accumulator is scaled by 1 / c_l.
+template <int MH, int BN, int Q, bool kBatch, int P = 0, int W = 8, int F = 0, bool XI = false>
 __global__ void __launch_bounds__(TcCfg<MH, BN, Q, P, W, F>::kThr, 1)
 level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra ex, const TcBatch bt)
 {
     using C = TcCfg<MH, BN, Q, P, W, F>;
+    static_assert(!XI || (Q == 0 && !kBatch), "xi** runs BF16 single-problem launches");
+    // tiles that pack two samples per accumulator skip the items of the other sample's positions
+    constexpr bool kSkip = P == 0 && MH == 1 && BN <= 64;
     constexpr int kGenWarps = C::kGW;
     constexpr int kGenThreads = C::kGT;
     constexpr int kNS = C::kNS;
@@ -355,10 +372,11 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
     uint32_t* tmem_s = reinterpret_cast<uint32_t*>(bars + C::kNumBars);
     volatile int* abort_s = reinterpret_cast<volatile int*>(tmem_s + 1);
     double* red_s = reinterpret_cast<double*>(tmem_s + 4);
+    float* gw_s = reinterpret_cast<float*>(red_s + kGenWarps);   // xi**: [2][kSub] slot weights Q_{n-1} / q_k
     // batched launches: each role keeps its own copy of the current job's parameters (aligned as
     // the type requires: it embeds tensor maps)
     LevelParams* job_prod = reinterpret_cast<LevelParams*>(
-        (reinterpret_cast<uintptr_t>(red_s + kGenWarps) + alignof(LevelParams) - 1) &
+        (reinterpret_cast<uintptr_t>(gw_s + 2 * kSub) + alignof(LevelParams) - 1) &
         ~static_cast<uintptr_t>(alignof(LevelParams) - 1));
     LevelParams* job_gen = job_prod + 1;
 
@@ -541,11 +559,30 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                     } else if (lane < kSub / 2) {
                         const int t = t0 + 2 * lane;
                         int64_t r0 = -1, r1 = -1;
-                        if (t < prm.c) index_pair(prm.keyI, lsw, s_lo, t >> 1, static_cast<uint64_t>(prm.n), r0, r1);
+                        float g0 = 0.0f, g1 = 0.0f;
+                        if (t < prm.c) {
+                            if constexpr (XI) {
+                                // xi** (Thm 3.1): inverse-CDF draws and the weights Q_{n-1} / q_k
+                                uint64_t w0, w1;
+                                index_words(prm.keyI, lsw, s_lo, t >> 1, w0, w1);
+                                r0 = index_from_cdf(w0, prm.xi_Q, prm.xi_q, prm.xi_G, prm.n);
+                                g0 = static_cast<float>(__ddiv_rn(prm.xi_Qtot, prm.xi_q[r0]));
+                                if (t + 1 < prm.c) {
+                                    r1 = index_from_cdf(w1, prm.xi_Q, prm.xi_q, prm.xi_G, prm.n);
+                                    g1 = static_cast<float>(__ddiv_rn(prm.xi_Qtot, prm.xi_q[r1]));
+                                }
+                            } else {
+                                index_pair(prm.keyI, lsw, s_lo, t >> 1, static_cast<uint64_t>(prm.n), r0, r1);
+                            }
+                        }
                         // F != 0: even slot t at K position lane, odd slot t + 1 at 16 + lane
                         const int p0 = F ? lane : 2 * lane, p1 = F ? kSub / 2 + lane : 2 * lane + 1;
                         idx[p0] = t < prm.c ? static_cast<int>(r0) : -1;
                         idx[p1] = t + 1 < prm.c ? static_cast<int>(r1) : -1;
+                        if constexpr (XI) {
+                            gw_s[b * kSub + p0] = g0;
+                            gw_s[b * kSub + p1] = g1;
+                        }
                     }
                     __syncwarp();
                     const int nvalid = min(kSub, nK - t0);
@@ -614,7 +651,9 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
             const int tiles_n = prm.tiles_m * prm.tiles_p;
             const int nsub = (prm.c + kSub - 1) / kSub;
             const bool coarse_sign = F == 0 && prm.l > 0;   // F != 0 keeps the coarse sum apart instead
-            const float scale = static_cast<float>(prm.w_fine);
+            // n / c_l; xi** folds Q_{n-1} / q_k into B and leaves 1 / c_l
+            const float scale = XI ? static_cast<float>(1.0 / static_cast<double>(prm.c))
+                                         : static_cast<float>(prm.w_fine);
             const Geo geo = geometry(prm, tile);
             const int tm0 = geo.tm0;
             const int tp0 = geo.tp0;
@@ -734,7 +773,7 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                                     const int* ih = idxh_s + b * 2 * kSub + h * kSub;
                                     const unsigned char* src = st + (sg * kNS) * (C::kRows * 8) + (g4 & 15) * 32;
                                     if constexpr (Q == 0)
-                                        gen_block<128, kNS>(ih, sg * kNS, vr, static_cast<uint32_t>(i >> 2),
+                                        gen_block<128, kNS, false, kSkip>(ih, sg * kNS, vr, static_cast<uint32_t>(i >> 2),
                                                             static_cast<uint32_t>(sh), level_sample_word(prm.l, sh),
                                                             prm.rkA, src, C::kRows * 8, false, a_tile, 4 * g4,
                                                             (kSub / 8) * kk + (sg * kNS) / 8, ((sg * kNS) % 8) * 2);
@@ -753,7 +792,7 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                                     const uint64_t sh = s + static_cast<uint64_t>(h);
                                     const unsigned char* src = stB + (sg * kNS) * (C::kBGen * 8) + g4 * 32;
                                     if constexpr (Q == 0)
-                                        gen_block<128, kNS>(idx, sg * kNS, jc < prm.p, static_cast<uint32_t>(jc >> 2),
+                                        gen_block<128, kNS, false, kSkip>(idx, sg * kNS, jc < prm.p, static_cast<uint32_t>(jc >> 2),
                                                             static_cast<uint32_t>(sh), level_sample_word(prm.l, sh),
                                                             prm.rkB, src, C::kBGen * 8, coarse_sign, b_tile, brow0 + 4 * g4,
                                                             (kSub / 8) * kk + (sg * kNS) / 8, ((sg * kNS) % 8) * 2);
@@ -776,7 +815,7 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                                                            C::kRows * 8, false, a_tile + kk * C::kASliceBytes, 4 * g4,
                                                            (sg * kNS) / 8, ((sg * kNS) % 8) * 2);
                                     else
-                                        gen_block<128, kNS>(idx, sg * kNS, i < prm.m, static_cast<uint32_t>(i >> 2), s_lo,
+                                        gen_block<128, kNS, false, kSkip>(idx, sg * kNS, i < prm.m, static_cast<uint32_t>(i >> 2), s_lo,
                                                             lsw, prm.rkA, st + (sg * kNS) * (C::kRows * 8) + g4 * 32,
                                                             C::kRows * 8, false, a_tile, 4 * g4,
                                                             (kSub / 8) * kk + (sg * kNS) / 8, ((sg * kNS) % 8) * 2);
@@ -787,16 +826,34 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                                     const int g4 = it2 % (C::kBGen / 4);
                                     const int sg = it2 / (C::kBGen / 4);
                                     const int jc = geo.bcol0 + 4 * g4;
-                                    if constexpr (P)
-                                        gen_block<64, kNS>(idx, sg * kNS, jc < prm.p, static_cast<uint32_t>(jc >> 2), s_lo,
-                                                           lsw, prm.rkB, stB + (sg * kNS) * (C::kBGen * 8) + g4 * 32,
-                                                           C::kBGen * 8, coarse_sign, b_tile + kk * C::kBSliceBytes,
-                                                           brow0 + 4 * g4, (sg * kNS) / 8, ((sg * kNS) % 8) * 2);
-                                    else
-                                        gen_block<128, kNS>(idx, sg * kNS, jc < prm.p, static_cast<uint32_t>(jc >> 2), s_lo,
-                                                            lsw, prm.rkB, stB + (sg * kNS) * (C::kBGen * 8) + g4 * 32,
-                                                            C::kBGen * 8, coarse_sign, b_tile, brow0 + 4 * g4,
-                                                            (kSub / 8) * kk + (sg * kNS) / 8, ((sg * kNS) % 8) * 2);
+                                    const unsigned char* srcB = stB + (sg * kNS) * (C::kBGen * 8) + g4 * 32;
+                                    const float* gw = gw_s + b * kSub;
+                                    // xi**: the slot weights are folded in too
+                                    if constexpr (P) {
+                                        if constexpr (XI)
+                                            gen_block<64, kNS, true>(idx, sg * kNS, jc < prm.p, static_cast<uint32_t>(jc >> 2),
+                                                                     s_lo, lsw, prm.rkB, srcB, C::kBGen * 8, coarse_sign,
+                                                                     b_tile + kk * C::kBSliceBytes, brow0 + 4 * g4,
+                                                                     (sg * kNS) / 8, ((sg * kNS) % 8) * 2, gw);
+                                        else
+                                            gen_block<64, kNS>(idx, sg * kNS, jc < prm.p, static_cast<uint32_t>(jc >> 2), s_lo,
+                                                               lsw, prm.rkB, srcB, C::kBGen * 8, coarse_sign,
+                                                               b_tile + kk * C::kBSliceBytes, brow0 + 4 * g4,
+                                                               (sg * kNS) / 8, ((sg * kNS) % 8) * 2);
+                                    } else {
+                                        if constexpr (XI)
+                                            gen_block<128, kNS, true, kSkip>(idx, sg * kNS, jc < prm.p, static_cast<uint32_t>(jc >> 2),
+                                                                      s_lo, lsw, prm.rkB, srcB, C::kBGen * 8, coarse_sign,
+                                                                      b_tile, brow0 + 4 * g4,
+                                                                      (kSub / 8) * kk + (sg * kNS) / 8,
+                                                                      ((sg * kNS) % 8) * 2, gw);
+                                        else
+                                            gen_block<128, kNS, false, kSkip>(idx, sg * kNS, jc < prm.p,
+                                                                static_cast<uint32_t>(jc >> 2), s_lo,
+                                                                lsw, prm.rkB, srcB, C::kBGen * 8, coarse_sign, b_tile,
+                                                                brow0 + 4 * g4, (kSub / 8) * kk + (sg * kNS) / 8,
+                                                                ((sg * kNS) % 8) * 2);
+                                    }
                                 }
                             } else {
                                 // E4M3: the kGroups threads of one row group are adjacent lanes, so the
@@ -1188,23 +1245,34 @@ cudaError_t prepare(int* per_sm)
     return cudaSuccess;
 }
 
+// One single-problem launch of the single-CTA kernel (F: targeted function, XI: xi** law).
+template <int MH, int BN, int Q, int F, bool XI>
+cudaError_t launch_single(const LevelParams& prm, const TcLaunch& tl, cudaStream_t st)
+{
+    using C = TcCfg<MH, BN, Q, 0, 8, F>;
+    if constexpr (!C::kFits) {
+        return cudaErrorInvalidValue;
+    } else {
+        auto kern = level_tc_bf16_kernel<MH, BN, Q, false, 0, 8, F, XI>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+        if (e != cudaSuccess) return e;
+        int occ = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, C::kThr, C::kSmemBytes);
+        if (e != cudaSuccess) return e;
+        const int per_sm = max(1, min(occ, 512 / C::kTmemCols));
+        const int items = prm.nchunks * prm.tiles_m * prm.tiles_p;
+        const int grid = max(1, min(items, per_sm * tl.num_sms));
+        TcExtra ex{tl.err_flag, tl.timeout_ns, items, tl.scale};
+        kern<<<grid, C::kThr, C::kSmemBytes, st>>>(prm, ex, TcBatch{});
+        return cudaGetLastError();
+    }
+}
+
 template <int MH, int BN, int Q>
 struct SingleF {
     static cudaError_t run(const LevelParams& prm, const TcLaunch& tl, cudaStream_t st)
     {
-        using C = TcCfg<MH, BN, Q>;
-        if constexpr (!C::kFits) {
-            return cudaErrorInvalidValue;
-        } else {
-            int per_sm = 1;
-            cudaError_t e = prepare<MH, BN, Q, false>(&per_sm);
-            if (e != cudaSuccess) return e;
-            const int items = prm.nchunks * prm.tiles_m * prm.tiles_p;
-            const int grid = max(1, min(items, per_sm * tl.num_sms));
-            TcExtra ex{tl.err_flag, tl.timeout_ns, items, tl.scale};
-            level_tc_bf16_kernel<MH, BN, Q, false><<<grid, C::kThr, C::kSmemBytes, st>>>(prm, ex, TcBatch{});
-            return cudaGetLastError();
-        }
+        return launch_single<MH, BN, Q, 0, false>(prm, tl, st);
     }
 };
 
@@ -1240,11 +1308,11 @@ struct GridF {
 };
 
 // A cluster pair (two CTAs, 128 rows each) on one 256 x 256 output tile; W generator warps.
-template <int Q, int W>
+template <int Q, int W, bool XI = false>
 cudaError_t launch_pair(const LevelParams& prm, const TcLaunch& tl, cudaStream_t st)
 {
     using C = TcCfg<1, 256, Q, 1, W>;
-    auto kern = level_tc_bf16_kernel<1, 256, Q, false, 1, W>;
+    auto kern = level_tc_bf16_kernel<1, 256, Q, false, 1, W, 0, XI>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
     if (e != cudaSuccess) return e;
     cudaLaunchAttribute attr[1];
@@ -1268,25 +1336,6 @@ cudaError_t launch_pair(const LevelParams& prm, const TcLaunch& tl, cudaStream_t
     TcExtra ex{tl.err_flag, tl.timeout_ns, pair_items, tl.scale};
     e = cudaLaunchKernelEx(&cfg, kern, prm, ex, TcBatch{});
     if (e != cudaSuccess) return e;
-    return cudaGetLastError();
-}
-
-// The targeted-function form (F = 1): one CTA per 128 x BN tile, BF16 operands.
-template <int BN>
-cudaError_t launch_single_f(const LevelParams& prm, const TcLaunch& tl, cudaStream_t st)
-{
-    using C = TcCfg<1, BN, 0, 0, 8, 1>;
-    auto kern = level_tc_bf16_kernel<1, BN, 0, false, 0, 8, 1>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
-    if (e != cudaSuccess) return e;
-    int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, C::kThr, C::kSmemBytes);
-    if (e != cudaSuccess) return e;
-    const int per_sm = max(1, min(occ, 512 / C::kTmemCols));
-    const int items = prm.nchunks * prm.tiles_m * prm.tiles_p;
-    const int grid = max(1, min(items, per_sm * tl.num_sms));
-    TcExtra ex{tl.err_flag, tl.timeout_ns, items, tl.scale};
-    kern<<<grid, C::kThr, C::kSmemBytes, st>>>(prm, ex, TcBatch{});
     return cudaGetLastError();
 }
 
@@ -1419,6 +1468,16 @@ TcTile tc_tile_for(int64_t m, int64_t p, int q, bool allow_pair)
 cudaError_t launch_level_tc(const LevelParams& prm, const TcTile& tile, int q, const TcLaunch& tl, cudaStream_t st)
 {
     if (!tc_tile_valid(tile, q)) return cudaErrorInvalidValue;
+    if (prm.xi_Q) {
+        // xi**: BF16, the CTA pair or single-CTA tiles of 128 rows and at most 128 columns
+        if (q != 0 || !tc_tile_valid_xi(tile)) return cudaErrorInvalidValue;
+        if (tile.pair) return launch_pair<0, 8, true>(prm, tl, st);
+        switch (tile.bn) {
+        case 32: return launch_single<1, 32, 0, 0, true>(prm, tl, st);
+        case 64: return launch_single<1, 64, 0, 0, true>(prm, tl, st);
+        default: return launch_single<1, 128, 0, 0, true>(prm, tl, st);
+        }
+    }
     if (tile.pair == 2) return q ? launch_pair<1, 16>(prm, tl, st) : launch_pair<0, 16>(prm, tl, st);
     if (tile.pair) return q ? launch_pair<1, 8>(prm, tl, st) : launch_pair<0, 8>(prm, tl, st);
     return dispatch_tile<SingleF>(tile, q, prm, tl, st);
@@ -1432,13 +1491,23 @@ TcTile tc_tile_for_f(int64_t p)
 
 bool tc_tile_valid_f(const TcTile& t) { return t.mh == 1 && !t.pair && (t.bn == 32 || t.bn == 64 || t.bn == 128); }
 
+TcTile tc_tile_for_xi(int64_t m, int64_t p)
+{
+    if (m > 128 && p > 128) return TcTile{1, 256, 128, 1};
+    return tc_tile_for_f(p);
+}
+
+bool tc_tile_valid_xi(const TcTile& t) { return (t.pair == 1 && t.mh == 1 && t.bn == 256) || tc_tile_valid_f(t); }
+
 cudaError_t launch_level_tc_f(const LevelParams& prm, const TcTile& tile, int f, const TcLaunch& tl, cudaStream_t st)
 {
     if (f != 1 || !tc_tile_valid_f(tile)) return cudaErrorInvalidValue;
+    const bool xi = prm.xi_Q != nullptr;
     switch (tile.bn) {
-    case 32: return launch_single_f<32>(prm, tl, st);
-    case 64: return launch_single_f<64>(prm, tl, st);
-    default: return launch_single_f<128>(prm, tl, st);
+    case 32: return xi ? launch_single<1, 32, 0, 1, true>(prm, tl, st) : launch_single<1, 32, 0, 1, false>(prm, tl, st);
+    case 64: return xi ? launch_single<1, 64, 0, 1, true>(prm, tl, st) : launch_single<1, 64, 0, 1, false>(prm, tl, st);
+    default:
+        return xi ? launch_single<1, 128, 0, 1, true>(prm, tl, st) : launch_single<1, 128, 0, 1, false>(prm, tl, st);
     }
 }
 

@@ -63,7 +63,7 @@ def test_invalid_arguments_are_reported_before_anything_else(monkeypatch):
     (("fp32", 0, 2, 0), 1, "adaptive_L"),
     (("fp32", 0, 0, 5), 1, "sampling"),
     (("fp8", 1, 0, 0), 6, "FP64, FP32 or BF16"),   # f has no E4M3 form
-    (("fp8", 0, 0, 1), 6, "FP64 or FP32"),    # so does xi**
+    (("fp8", 0, 0, 1), 6, "FP64, FP32 or BF16"),   # xi** has no E4M3 form
 ])
 def test_option_combinations_are_validated_on_the_host(monkeypatch, fields, status, word):
     """Targeted function, adaptive L and sampling law are checked before any device work (the

@@ -9,7 +9,10 @@ Bars:
     cumulative sum would be the only way to differ);
   * FP64 samples: |D - D_oracle| <= 1e-12 * mag (mag includes the 1 / xi weights); level means
     within 1e-12 of the mean magnitude, M2 within 1e-11 relative; the estimate's N_l equal;
-  * FP32 samples: tau_32(c) = (c + 8) 2^-24 + 2^-16 of mag, plus 2^-24 for the FP32 weights.
+  * FP32 samples: tau_32(c) = (c + 8) 2^-24 + 2^-16 of mag, plus 2^-24 for the FP32 weights;
+  * BF16 (tensor cores; the weight Q_{n-1} / q_k, rounded to FP32, multiplies each entry of B before
+    its bfloat16 rounding): tau_bf16(c) = 2^-7 + 2^-15 + (c + 8) 2^-23 of mag plus 2^-22 for the
+    FP32 weight and its product, per sample and for level means over the same samples.
 """
 import numpy as np
 import pytest
@@ -142,7 +145,7 @@ def test_unsupported_combinations():
     params = _params(8, 64, 8, np.float32)
     ts = [torch.from_numpy(x).to(DEV) for x in params]
     with pytest.raises(binding.MLMCError) as e:
-        binding.Plan([binding.ProblemSpec(*ts)], c0=4, L=2, precision="bf16", sampling="optimal")
+        binding.Plan([binding.ProblemSpec(*ts)], c0=4, L=2, precision="fp8", sampling="optimal")
     assert e.value.status == 6
     with binding.Plan([binding.ProblemSpec(*ts)], c0=4, L=2, precision="fp32", sampling="optimal") as plan:
         for l in range(3):
@@ -151,3 +154,67 @@ def test_unsupported_combinations():
         with pytest.raises(binding.MLMCError) as e:
             plan.backward([torch.zeros(8, 8, device=DEV, dtype=torch.float64)])
         assert e.value.status == 6
+
+
+def tau_bf16(c):
+    return 2.0**-7 + 2.0**-15 + (c + 8) * 2.0**-23 + 2.0**-22
+
+
+BF16_CASES = [
+    # m, n, p, c0, L, f, (level, sample) pairs
+    (24, 700, 16, 4, 3, "identity", [(0, 0), (1, 3), (3, 9)]),        # c_l < 32: partial sub-blocks
+    (70, 300, 130, 1, 4, "identity", [(0, 1), (2, 8), (4, 2)]),       # two column tiles, odd slot counts
+    (200, 2000, 300, 32, 2, "identity", [(0, 4), (2, 11)]),           # the CTA pair (256 x 256 tiles)
+    (64, 1024, 64, 16, 3, "abs_step", [(0, 2), (1, 5), (3, 1)]),      # the targeted-function form
+]
+
+
+@pytest.mark.parametrize("m,n,p,c0,L,f,picks", BF16_CASES)
+def test_bf16_samples_and_levels_match_oracle(m, n, p, c0, L, f, picks):
+    params = _params(m, n, p, np.float32)
+    if f != "identity":
+        # entries of AB of order one around the jump of f at 2
+        k = 2.0 / np.sqrt(n)
+        params = [(params[0] * k + 2.0 / n).astype(np.float32), (params[1] * k).astype(np.float32),
+                  params[2], params[3]]
+    orc = _orc(params)
+    lv = oracle.Levels(c0, 2, L)
+    fkind = oracle.F_ABS_STEP if f != "identity" else oracle.F_IDENTITY
+    near = 0
+    with _plan(params, "bf16", c0, L, f=f) as plan:
+        for l, s in picks:
+            c = lv.cl(l)
+            D = plan.debug_sample(0, l, s).cpu().numpy().astype(np.float64)
+            Dref, Pf, Pc, mag = oracle.sample(orc, lv, l, s, fkind=fkind)
+            ok = np.ones(D.shape, dtype=bool)
+            if f != "identity":
+                band = tau_bf16(c) * mag
+                ok = (np.abs(Pf - 2.0) > band) & ((np.abs(Pc - 2.0) > band) | (l == 0))
+                near += int((~ok).sum())
+            err = np.abs(D - Dref)[ok] / mag[ok]
+            assert np.all(err <= tau_bf16(c)), (l, s, err.max(), tau_bf16(c))
+        if f == "identity":
+            for l in range(min(L, 2) + 1):
+                plan.level_stats(0, l, 0, 40)
+                n_got, mean, _ = plan.get_level_stats(0, l)
+                mref, _, magm = oracle.level_stats(orc, lv, l, 0, 40)
+                assert n_got == 40
+                assert np.all(np.abs(mean.cpu().numpy() - mref) <= tau_bf16(lv.cl(l)) * magm), l
+    assert near <= 0.25 * m * p * len(picks)
+
+
+def test_bf16_xi_lowers_variance_and_estimates():
+    """BF16 under xi** against BF16 under the uniform law on the same problem: a smaller level-0
+    variance, and an estimate within five predicted RMSEs of M M'."""
+    params = _params(48, 2048, 40, np.float32)
+    ts = [torch.from_numpy(x).to(DEV) for x in params]
+    mu = params[0].astype(np.float64) @ params[2].astype(np.float64)
+    eps = 0.02 * float(np.linalg.norm(mu))
+    V0 = {}
+    for law in ("uniform", "optimal"):
+        with binding.Plan([binding.ProblemSpec(*ts, **SEEDS)], c0=16, L=3, precision="bf16", sampling=law,
+                          pilot_n=128) as plan:
+            (Y,), (rep,) = plan.estimate([eps])
+            V0[law] = rep["V"][0]
+            assert np.linalg.norm(Y.cpu().numpy() - mu) <= 5 * rep["rmse_pred"]
+    assert V0["optimal"] < V0["uniform"], V0

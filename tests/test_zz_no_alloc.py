@@ -8,7 +8,8 @@ call reuses the scratch the first one left behind) and compares each result (the
 the level's M2) with what the plan-based entry points (mlmc_level_stats + mlmc_get_level_state)
 give for the same samples, within the FP64 parity tolerance of the other tests (1e-12 of the
 summed term magnitudes); a problem near the size limit makes one call run several launches,
-each folding its chunks into the outputs left by the one before.
+each folding its chunks into the outputs left by the one before; and a call captured into a
+CUDA graph is replayed.
 
 The file is named so that pytest collects it last.
 """
@@ -37,7 +38,7 @@ def built():
     assert torch.cuda.is_available()
 
 
-def _noalloc(tensors, pp, c0, level, begin, count, precision, dtype_code, stream):
+def _args(tensors, pp, c0, level, precision, dtype_code):
     M, S, Mp, Sp = tensors
     m, n = M.shape
     p = Mp.shape[1]
@@ -46,8 +47,17 @@ def _noalloc(tensors, pp, c0, level, begin, count, precision, dtype_code, stream
     opts = binding.Options(c0, 2, level, binding.PRECISION[precision], 2, 1.0, 0, 0, 0)
     out_sum = torch.full((m, p), float("nan"), dtype=torch.float64, device=M.device)
     out_q = torch.full((1,), float("nan"), dtype=torch.float64, device=M.device)
-    rc = binding.lib().mlmc_level_stats_noalloc(ctypes.byref(prob), ctypes.byref(opts), level, begin, count,
-                                                out_sum.data_ptr(), out_q.data_ptr(), stream.cuda_stream)
+    return prob, opts, out_sum, out_q
+
+
+def _call(prob, opts, level, begin, count, out_sum, out_q, stream):
+    return binding.lib().mlmc_level_stats_noalloc(ctypes.byref(prob), ctypes.byref(opts), level, begin, count,
+                                                  out_sum.data_ptr(), out_q.data_ptr(), stream.cuda_stream)
+
+
+def _noalloc(tensors, pp, c0, level, begin, count, precision, dtype_code, stream):
+    prob, opts, out_sum, out_q = _args(tensors, pp, c0, level, precision, dtype_code)
+    rc = _call(prob, opts, level, begin, count, out_sum, out_q, stream)
     return rc, out_sum, out_q
 
 
@@ -105,6 +115,37 @@ def test_noalloc_near_its_size_limit_runs_several_launches():
         diff = np.abs(s_na.cpu().numpy() - s_plan.cpu().numpy())
         assert np.all(diff <= 1e-12 * count * 4.0 * mag), diff.max()
         assert abs(float(q_na.item()) - q_plan) <= 1e-11 * q_plan
+
+
+def test_noalloc_inside_cuda_graph_capture():
+    """A warm-up call (it looks the scratch up), then a call captured into a CUDA graph on a side
+    stream and replayed twice: each replay writes the plan path's result into the outputs."""
+    dev = torch.device("cuda:0")
+    m, n, p, c0, L = 70, 900, 45, 8, 3
+    pp = make_params(m, n, p, seed_A=41, seed_B=42, seed_idx=43, problem_id=6)
+    tensors = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (pp.M, pp.S, pp.Mp, pp.Sp)]
+    level, begin, count = 3, 5, 40
+    prob, opts, out_sum, out_q = _args(tensors, pp, c0, level, "fp64", 0)
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(side):
+        assert _call(prob, opts, level, 0, 16, out_sum, out_q, side) == 0   # warm-up
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        rc = _call(prob, opts, level, begin, count, out_sum, out_q, side)
+    assert rc == 0, binding.lib().mlmc_last_error()
+    s_plan, q_plan = _plan_state(tensors, pp, c0, L, level, begin, count, "fp64")
+    orc = oracle.Problem(*pp.f64(), seed_A=41, seed_B=42, seed_idx=43, problem_id=6)
+    _, _, magm = oracle.level_stats(orc, oracle.Levels(c0, 2, L), level, begin, count)
+    for _ in range(2):
+        out_sum.fill_(float("nan"))
+        out_q.fill_(float("nan"))
+        graph.replay()
+        torch.cuda.synchronize()
+        diff = np.abs(out_sum.cpu().numpy() - s_plan.cpu().numpy())
+        assert np.all(diff <= 1e-12 * count * magm), diff.max()
+        assert abs(float(out_q.item()) - q_plan) <= 1e-11 * q_plan
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
