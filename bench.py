@@ -810,6 +810,11 @@ BATCHED = dict(name="batched_64_problems", count=64, shape_seed=7, c0=32, R=2, p
 
 _BATCHED_INPUTS = {}
 
+# DRAM bytes (read + write) per algorithmic gathered byte of the batched kernel, by tile, from one
+# ncu pass over one launch of the batched_8_problems profile case (29.995 GB algorithmic)
+BATCHED_TRAFFIC = {1128: {"dram_over_algorithmic": (36247647744 + 71866112) / 29995171840,
+                          "source": "profiles/level_tc_bf16_batched_64_problems.md"}}
+
 
 def _measure_batched(args, dev, stream, peaks, peak_kind, precision="bf16", step_target=None, steps=None, warmup=None):
     """64 problems (m, p log-uniform on [32, 512], n log-uniform on [4096, 262144], L+1 uniform on
@@ -906,7 +911,16 @@ def _measure_batched(args, dev, stream, peaks, peak_kind, precision="bf16", step
             if bound_hbm else
             {"bound": "tensor", "achieved": tfl, "peak": tpeak, "unit": "TFLOP/s", "frac": tfl / tpeak,
              "hbm_achieved_gbs": hbm})
-    roof.update({"traffic": None, "peak_source": f"{'hbm_gbs' if bound_hbm else 'bf16_tflops_sustained'} ({peak_kind})",
+    # DRAM traffic per level launch: the DRAM bytes per algorithmic byte of one captured launch of
+    # the 128 x 128 batched kernel (8 of the problems, 256 samples per level) times this step's
+    # algorithmic bytes per launch; null for another tile
+    waves = max(1, launches // (3 * steps))
+    bt = BATCHED_TRAFFIC.get(tile)
+    traffic = None if bt is None else {
+        "value": bt["dram_over_algorithmic"] * bytes_alg / waves, "unit": "bytes per launch", "launches": waves * steps,
+        "algorithmic_bytes_per_launch": bytes_alg / waves, "source": bt["source"]}
+    roof.update({"traffic": traffic,
+                 "peak_source": f"{'hbm_gbs' if bound_hbm else 'bf16_tflops_sustained'} ({peak_kind})",
                  "kernel": "level_tc_bf16_kernel<batched>"})
     return {"workload": Bc["name"], "metric": "time-to-RMSE 1e-3 for every problem's E[A_q B_q] (projected)",
             "value": T, "unit": "s", "ms_per_step": 1e3 * t, "step_fraction": f,

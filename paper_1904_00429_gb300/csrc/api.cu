@@ -393,8 +393,8 @@ mlmc_status run_level(mlmc_plan_t* plan, ProblemState& ps, int level, uint64_t s
                 prm.welford = 1;
                 err = launch_level_tc_f(prm, ps.tile, o.f, tl, plan->stream);
             } else if (ps.xi_Q) {
-                // xi**: per-slot weights, no packed samples; the level means are zero for l >= 1 too
-                prm.pack = 0;
+                // xi**: per-slot weights; the level means are zero for l >= 1 too
+                prm.pack = tc_pack(ps.tile, tc_format(o), ps.m, c) ? 1 : 0;
                 prm.welford = level == 0 ? 1 : 0;
                 err = launch_level_tc(prm, ps.tile, tc_format(o), tl, plan->stream);
             } else {

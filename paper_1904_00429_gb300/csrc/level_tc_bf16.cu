@@ -535,7 +535,36 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                     }
                     int* idx = idx_s + b * kSub;
                     const int t0 = j * kSub;
-                    if (PK) {
+                    if (XI) {
+                        // xi** (Thm 3.1): one slot per lane (a draw walks the tables with dependent
+                        // loads: 32 walks in parallel), inverse-CDF index and weight Q_{n-1} / q_k.
+                        // K position kp holds slot kp (PK: sample s + kp / c_l, slot kp mod c_l;
+                        // F != 0: even slots at positions 0-15, odd slots at 16-31)
+                        if (lane < kSub) {
+                            const int kp = t0 + lane;
+                            const int h = (PK && kp < nK) ? kp / prm.c : 0;
+                            const int t = kp - h * prm.c;
+                            int r = -1;
+                            float g = 0.0f;
+                            if (kp < nK) {
+                                const uint64_t sh = s + static_cast<uint64_t>(h);
+                                uint64_t w0, w1;
+                                index_words(prm.keyI, level_sample_word(prm.l, sh), static_cast<uint32_t>(sh), t >> 1,
+                                            w0, w1);
+                                r = static_cast<int>(index_from_cdf((t & 1) ? w1 : w0, prm.xi_Q, prm.xi_q, prm.xi_G,
+                                                                    prm.n));
+                                g = static_cast<float>(__ddiv_rn(prm.xi_Qtot, prm.xi_q[r]));
+                            }
+                            const int pos = F ? ((lane & 1) ? kSub / 2 + (lane >> 1) : (lane >> 1)) : lane;
+                            idx[pos] = r;
+                            gw_s[b * kSub + pos] = g;
+                            if (PK) {
+                                int* ih = idxh_s + b * 2 * kSub;
+                                ih[lane] = h == 0 ? r : -1;
+                                ih[kSub + lane] = h == 1 ? r : -1;
+                            }
+                        }
+                    } else if (PK) {
                         // K position kp -> sample s + h (h = kp / c_l), slot kp - h c_l; c_l is even, so a
                         // slot pair never straddles the two samples
                         if (lane < kSub / 2) {
@@ -559,30 +588,11 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                     } else if (lane < kSub / 2) {
                         const int t = t0 + 2 * lane;
                         int64_t r0 = -1, r1 = -1;
-                        float g0 = 0.0f, g1 = 0.0f;
-                        if (t < prm.c) {
-                            if constexpr (XI) {
-                                // xi** (Thm 3.1): inverse-CDF draws and the weights Q_{n-1} / q_k
-                                uint64_t w0, w1;
-                                index_words(prm.keyI, lsw, s_lo, t >> 1, w0, w1);
-                                r0 = index_from_cdf(w0, prm.xi_Q, prm.xi_q, prm.xi_G, prm.n);
-                                g0 = static_cast<float>(__ddiv_rn(prm.xi_Qtot, prm.xi_q[r0]));
-                                if (t + 1 < prm.c) {
-                                    r1 = index_from_cdf(w1, prm.xi_Q, prm.xi_q, prm.xi_G, prm.n);
-                                    g1 = static_cast<float>(__ddiv_rn(prm.xi_Qtot, prm.xi_q[r1]));
-                                }
-                            } else {
-                                index_pair(prm.keyI, lsw, s_lo, t >> 1, static_cast<uint64_t>(prm.n), r0, r1);
-                            }
-                        }
+                        if (t < prm.c) index_pair(prm.keyI, lsw, s_lo, t >> 1, static_cast<uint64_t>(prm.n), r0, r1);
                         // F != 0: even slot t at K position lane, odd slot t + 1 at 16 + lane
                         const int p0 = F ? lane : 2 * lane, p1 = F ? kSub / 2 + lane : 2 * lane + 1;
                         idx[p0] = t < prm.c ? static_cast<int>(r0) : -1;
                         idx[p1] = t + 1 < prm.c ? static_cast<int>(r1) : -1;
-                        if constexpr (XI) {
-                            gw_s[b * kSub + p0] = g0;
-                            gw_s[b * kSub + p1] = g1;
-                        }
                     }
                     __syncwarp();
                     const int nvalid = min(kSub, nK - t0);
@@ -792,10 +802,11 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                                     const uint64_t sh = s + static_cast<uint64_t>(h);
                                     const unsigned char* src = stB + (sg * kNS) * (C::kBGen * 8) + g4 * 32;
                                     if constexpr (Q == 0)
-                                        gen_block<128, kNS, false, kSkip>(idx, sg * kNS, jc < prm.p, static_cast<uint32_t>(jc >> 2),
+                                        gen_block<128, kNS, XI, kSkip>(idx, sg * kNS, jc < prm.p, static_cast<uint32_t>(jc >> 2),
                                                             static_cast<uint32_t>(sh), level_sample_word(prm.l, sh),
                                                             prm.rkB, src, C::kBGen * 8, coarse_sign, b_tile, brow0 + 4 * g4,
-                                                            (kSub / 8) * kk + (sg * kNS) / 8, ((sg * kNS) % 8) * 2);
+                                                            (kSub / 8) * kk + (sg * kNS) / 8, ((sg * kNS) % 8) * 2,
+                                                            gw_s + b * kSub);
                                     else
                                         gen_block_e4m3(idx, sg * 8, jc < prm.p, static_cast<uint32_t>(jc >> 2),
                                                        static_cast<uint32_t>(sh), level_sample_word(prm.l, sh), prm.rkB,
