@@ -116,9 +116,9 @@ typedef struct {
                               one of 1032 1064 1128 1256 2032 2064 2128 2256 (e.g. 2128 = 256 x 128;
                               E4M3: 1032 1064 1128 2032 2064), or 3256: a cluster of two CTAs of
                               128 x 256 sharing one 256 x 256 tile (BF16 and E4M3, single-problem
-                              launches; the BF16 default for outputs above 128 x 128), or 4256: the
-                              same pair with 16 generator warps on 4-slot items (the E4M3 default
-                              for outputs above 128 x 128).  CUDA-core plans: 1000 * rows + columns
+                              and batched launches; the BF16 default for outputs above 128 x 128),
+                              or 4256: the same pair with 16 generator warps on 4-slot items (the
+                              E4M3 default for outputs above 128 x 128; single-problem launches).  CUDA-core plans: 1000 * rows + columns
                               of the output tile, 64064; FP32 with f = identity also 128064 (its
                               default above 64 rows) and 128128 */
     int32_t adjoint_batch_log2; /* mlmc_backward replays at most 2^this sampled products per batch
@@ -276,10 +276,12 @@ typedef struct {
  * autotuner's: the first call times every candidate tile on the first chunk
  * of each range and keeps the fastest for the plan (mlmc_get_batch_tile).
  * Tiles of at most 256 accumulator columns per CTA (all but 2256, including
- * the pair 3256 of single-problem launches) keep each chunk's running sum of
- * D in tensor memory, so with any of them the per-level sums of D are the same
- * bit for bit; the 2256 tile adds scaled samples in global memory and agrees
- * with them up to FP32 rounding.  Batched launches do not use 3256.  The M2
+ * the pair 3256) keep each chunk's running sum of D in tensor memory, so with
+ * any of them the per-level sums of D are the same bit for bit; the 2256 tile
+ * adds scaled samples in global memory and agrees with them up to FP32
+ * rounding.  The CTA pair 3256 runs batched launches as clusters of two CTAs,
+ * each cluster walking its own list of (job, chunks, 256 x 256 tile) items;
+ * the 16-warp pair 4256 serves single-problem launches only.  The M2
  * are grouped by output tile, so they agree across tiles up to rounding; with
  * the same tile a batched call and the same ranges run one by one give the
  * same bits.  Other
@@ -290,9 +292,9 @@ typedef struct {
 MLMC_API mlmc_status mlmc_level_stats_batch(mlmc_plan_t* plan, const mlmc_range* ranges, int32_t count);
 
 /* Tile of the batched BF16 launches as a tile id (see mlmc_options), 0 before
- * the first batched call.  timings_ms (host array of 8, may be NULL) receives
+ * the first batched call.  timings_ms (host array of 9, may be NULL) receives
  * the autotuner's time in ms of each candidate in the order 1032 1064 1128
- * 1256 2032 2064 2128 2256 (negative: not tried). */
+ * 1256 2032 2064 2128 2256 3256 (negative: not tried). */
 MLMC_API mlmc_status mlmc_get_batch_tile(const mlmc_plan_t* plan, int32_t* tile_id, double* timings_ms);
 
 /* ---- estimator (Alg. 2) ------------------------------------------------------------- */

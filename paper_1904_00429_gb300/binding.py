@@ -251,9 +251,9 @@ class Plan:
     def batch_tile(self):
         """(tile id of the batched launches, autotuner ms per candidate tile id)."""
         tid = ctypes.c_int32()
-        ms = (ctypes.c_double * 8)()
+        ms = (ctypes.c_double * 9)()
         _check(lib().mlmc_get_batch_tile(self._h, ctypes.byref(tid), ms), "mlmc_get_batch_tile")
-        ids = (1032, 1064, 1128, 1256, 2032, 2064, 2128, 2256)
+        ids = (1032, 1064, 1128, 1256, 2032, 2064, 2128, 2256, 3256)
         return tid.value, {i: ms[k] for k, i in enumerate(ids) if ms[k] >= 0}
 
     def get_level_stats(self, prob: int, level: int):

@@ -105,7 +105,7 @@ struct mlmc_plan_s {
     size_t adj_bytes = 0;
     // batched launches (created on the first mlmc_level_stats_batch)
     TcTile batch_tile{0, 0, 0};
-    double tune_ms[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
+    double tune_ms[9] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
     int batch_grid = 0;
     float* batch_partial = nullptr;
     double* batch_q = nullptr;
@@ -208,7 +208,7 @@ int32_t encode_tile(const TcTile& t)
     return t.pair ? (t.pair == 2 ? 4000 : 3000) + t.bn : 1000 * t.mh + t.bn;
 }
 
-const int32_t kTileIds[8] = {1032, 1064, 1128, 1256, 2032, 2064, 2128, 2256};
+const int32_t kTileIds[9] = {1032, 1064, 1128, 1256, 2032, 2064, 2128, 2256, 3256};
 
 mlmc_status validate(const mlmc_problem* problems, int32_t nprob, const mlmc_options* o)
 {
@@ -517,6 +517,8 @@ mlmc_status build_waves(mlmc_plan_t* plan, const std::vector<BatchRange>& ranges
         const int64_t mp = ps.m * ps.p;
         const int tm = int((ps.m + tile.rows - 1) / tile.rows), tp = int((ps.p + tile.bn - 1) / tile.bn);
         const int tiles = tm * tp;
+        // the CTA pair's items cover two row tiles of 128 (a row tile beyond m holds no outputs)
+        const int item_tiles = tile.pair ? ((tm + 1) / 2) * tp : tiles;
         if (size_t(mp) * 4 > kBatchPartialBytes || tiles > 65535)
             return fail(MLMC_ERR_UNSUPPORTED, "problem %d is too large for the batched launch", r.prob);
         LevelParams base = base_params(plan, ps, r.level);
@@ -582,7 +584,7 @@ mlmc_status build_waves(mlmc_plan_t* plan, const std::vector<BatchRange>& ranges
                 const uint64_t a = std::max<uint64_t>(prm.s_begin, (cb + cy) * ch);
                 const uint64_t b = std::min<uint64_t>(prm.s_end, (cb + cy + len) * ch);
                 const double cost = double(b - a) * per_sample;
-                for (int t = 0; t < tiles; ++t)
+                for (int t = 0; t < item_tiles; ++t)
                     w->items.emplace_back(cost, uint64_t(job) | (cy << 16) | (len << 40) | (uint64_t(t) << 48));
             }
             w->units += int64_t(nb) * tiles;
@@ -719,11 +721,11 @@ mlmc_status autotune_batch_tile(mlmc_plan_t* plan, const std::vector<BatchRange>
     double best = 1e300;
     TcTile best_tile = tc_tile_for(mmax, pmax, tc_format(plan->opt), false);
     mlmc_status st = MLMC_OK;
-    for (int c = 0; c < 8 && st == MLMC_OK; ++c) {
+    for (int c = 0; c < 9 && st == MLMC_OK; ++c) {
         const TcTile t = decode_tile(kTileIds[c]);
         plan->tune_ms[c] = -1.0;
-        // skip tiles far wider or taller than every problem
-        if ((t.mh == 2 && mmax <= 128) || (t.bn > 32 && pmax <= t.bn / 2)) continue;
+        // skip tiles far wider or taller than every problem (the pair: 256 x 256 per cluster)
+        if ((t.mh == 2 && mmax <= 128) || (t.bn > 32 && pmax <= t.bn / 2) || (t.pair && mmax <= 128)) continue;
         if (!tc_tile_valid(t, tc_format(plan->opt))) continue;
         const int grid = std::min(tc_batch_grid(t, tc_format(plan->opt), plan->num_sms), kBatchMaxGrid);
         if (grid <= 0) continue;
@@ -769,8 +771,8 @@ mlmc_status run_batch(mlmc_plan_t* plan, const std::vector<BatchRange>& ranges)
     if (st != MLMC_OK) return st;
     if (plan->batch_tile.mh == 0) {
         if (plan->opt.tile_override) {
-            if (decode_tile(plan->opt.tile_override).pair)
-                return fail(MLMC_ERR_UNSUPPORTED, "tile 3256 (CTA pairs) serves single-problem launches only");
+            if (decode_tile(plan->opt.tile_override).pair == 2)
+                return fail(MLMC_ERR_UNSUPPORTED, "tile 4256 (16-warp CTA pairs) serves single-problem launches only");
             plan->batch_tile = decode_tile(plan->opt.tile_override);
             plan->batch_grid =
                 std::min(tc_batch_grid(plan->batch_tile, tc_format(plan->opt), plan->num_sms), kBatchMaxGrid);
@@ -1089,7 +1091,7 @@ mlmc_status mlmc_get_batch_tile(const mlmc_plan_t* plan, int32_t* tile_id, doubl
     if (!plan || !tile_id) return fail(MLMC_ERR_INVALID_ARG, "null argument");
     *tile_id = encode_tile(plan->batch_tile);
     if (timings_ms)
-        for (int c = 0; c < 8; ++c) timings_ms[c] = plan->tune_ms[c];
+        for (int c = 0; c < 9; ++c) timings_ms[c] = plan->tune_ms[c];
     return MLMC_OK;
 }
 

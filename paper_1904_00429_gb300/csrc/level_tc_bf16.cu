@@ -99,7 +99,7 @@ struct TcCfg {
                                       kNumBars * 8 + 16 /*tmem, abort*/ + kGW * 8 +
                                       (P ? 0 : 2 * static_cast<int>(sizeof(LevelParams)) +
                                                    static_cast<int>(alignof(LevelParams)))
-                                      /*job copies of batched launches (pairs run single-problem launches)*/;
+                                      /*job copies of batched launches (pairs read the job table)*/;
     static constexpr int kSmemBytes = 1024 /*align slack*/ + kTileBytes + 2 * kStageBytes + kBookBytes;
     static_assert(kAccCols <= 512, "tile exceeds tensor memory");
     static_assert(kTmemCols >= kAccCols, "the allocation holds the accumulators");
@@ -357,7 +357,6 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
     // columns per TMEM read in the drains: the 16-warp form has fewer registers a thread
     constexpr int kCW = W == 16 ? 32 : 64;
     static_assert(C::kFits, "shared memory");
-    static_assert(!(P && kBatch), "pairs run single-problem launches");
     constexpr int kSub = C::kSub;
     constexpr int kSlices = C::kSlices;
     extern __shared__ unsigned char smem_raw[];
@@ -421,11 +420,14 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
     auto for_each_item = [&](LevelParams* copy, auto&& body_fn, bool whole_cta) {
         if constexpr (kBatch) {
             int cur = -1;
-            const int i0 = bt.cta_begin[blockIdx.x], i1 = bt.cta_begin[blockIdx.x + 1];
+            // pairs: both CTAs of a cluster walk the cluster's list (the same items in the same
+            // order); an item's tile is then a pair of row tiles and a column tile
+            const int unit = P ? static_cast<int>(blockIdx.x >> 1) : static_cast<int>(blockIdx.x);
+            const int i0 = bt.cta_begin[unit], i1 = bt.cta_begin[unit + 1];
             for (int i = i0; i < i1; ++i) {
                 const uint64_t it = bt.items[i];
                 const int job = static_cast<int>(it & 0xFFFFu);
-                if (job != cur) {
+                if (!P && job != cur) {
                     const uint32_t* src = reinterpret_cast<const uint32_t*>(bt.jobs + job);
                     uint32_t* dst = reinterpret_cast<uint32_t*>(copy);
                     const int nthr = whole_cta ? kGenThreads : 32;
@@ -444,7 +446,10 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                 bool go = true;
                 // tensor maps are read from the job table in global memory (not the shared copy)
                 const TcMaps* maps = &bt.jobs[job].maps;
-                for (int cy = cy0; cy < cy0 + ncy && go; ++cy) go = body_fn(*copy, cy, tile, maps);
+                // pairs keep no shared copy (their shared memory is full): they read the job's
+                // parameters from the table in global memory
+                const LevelParams& jp = P ? bt.jobs[job] : *copy;
+                for (int cy = cy0; cy < cy0 + ncy && go; ++cy) go = body_fn(jp, cy, tile, maps);
                 if (!go) break;
             }
         } else if constexpr (P) {
@@ -1350,6 +1355,58 @@ cudaError_t launch_pair(const LevelParams& prm, const TcLaunch& tl, cudaStream_t
     return cudaGetLastError();
 }
 
+// Batched launches of the CTA pair (tile 3256): `clusters` clusters of two CTAs, each cluster
+// walking its own item list.  The function attributes were set by pair_batch_grid (no attribute
+// calls while a graph is captured).
+template <int Q>
+cudaError_t launch_pair_batch(const TcBatch& bt, int clusters, const TcLaunch& tl, cudaStream_t st)
+{
+    using C = TcCfg<1, 256, Q, 1, 8>;
+    auto kern = level_tc_bf16_kernel<1, 256, Q, true, 1, 8>;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(C::kThr);
+    cfg.dynamicSmemBytes = C::kSmemBytes;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3(2 * static_cast<unsigned>(max(1, clusters)));
+    TcExtra ex{tl.err_flag, tl.timeout_ns, 0, 0.0f};
+    LevelParams none{};
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, none, ex, bt);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+// Clusters of the batched CTA pair that fit on the GPU at once (the units its item lists are cut
+// into); sets the kernel's shared-memory attribute.
+template <int Q>
+int pair_batch_grid(int num_sms)
+{
+    using C = TcCfg<1, 256, Q, 1, 8>;
+    auto kern = level_tc_bf16_kernel<1, 256, Q, true, 1, 8>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes) != cudaSuccess)
+        return 0;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(C::kThr);
+    cfg.dynamicSmemBytes = C::kSmemBytes;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3(2 * static_cast<unsigned>(num_sms / 2));
+    int max_clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&max_clusters, kern, &cfg) != cudaSuccess) return 0;
+    return max(0, max_clusters);
+}
+
 template <int MH, int BN, int Q>
 struct FitsF {
     static bool run() { return TcCfg<MH, BN, Q>::kFits; }
@@ -1524,14 +1581,16 @@ cudaError_t launch_level_tc_f(const LevelParams& prm, const TcTile& tile, int f,
 
 int tc_batch_grid(const TcTile& tile, int q, int num_sms)
 {
-    if (!tc_tile_valid(tile, q) || tile.pair) return 0;
+    if (!tc_tile_valid(tile, q) || tile.pair == 2) return 0;
+    if (tile.pair) return q ? pair_batch_grid<1>(num_sms) : pair_batch_grid<0>(num_sms);
     return dispatch_tile<GridF>(tile, q, num_sms);
 }
 
 cudaError_t launch_level_tc_batch(const TcBatch& bt, const TcTile& tile, int q, int grid, const TcLaunch& tl,
                                   cudaStream_t st)
 {
-    if (!tc_tile_valid(tile, q) || tile.pair) return cudaErrorInvalidValue;
+    if (!tc_tile_valid(tile, q) || tile.pair == 2) return cudaErrorInvalidValue;
+    if (tile.pair) return q ? launch_pair_batch<1>(bt, grid, tl, st) : launch_pair_batch<0>(bt, grid, tl, st);
     return dispatch_tile<BatchF>(tile, q, bt, grid, tl, st);
 }
 

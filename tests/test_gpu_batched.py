@@ -66,8 +66,10 @@ def _ranges(nprob, L, begin, count):
     return [(q, l, begin, count) for q in range(nprob) for l in range(L + 1)]
 
 
-@pytest.mark.parametrize("tile", [1064, 2128, 1256])
+@pytest.mark.parametrize("tile", [1064, 2128, 1256, 3256])
 def test_batched_matches_one_by_one_same_tile(tile):
+    """With the same tile (3256: clusters of two CTAs walking per-cluster item lists) a batched
+    call and the same ranges run one by one give the same bits."""
     specs, _ = _specs(SHAPES)
     L = 3
     with binding.Plan(specs, c0=16, L=L, precision="bf16", tile_override=tile) as a, \
@@ -133,13 +135,15 @@ def test_batched_many_waves_and_graph_replay():
             assert na == nb and torch.equal(sa, sb) and qa == qb
 
 
-def test_batched_levels_match_fp64_oracle():
-    """Level means of two batched problems against the FP64 oracle (BF16 bound of the level kernel)."""
-    shapes = [(37, 1000, 53), (64, 1024, 64)]
+@pytest.mark.parametrize("tile", [0, 3256])
+def test_batched_levels_match_fp64_oracle(tile):
+    """Level means of batched problems against the FP64 oracle (BF16 bound of the level kernel),
+    with the autotuned tile and with the CTA pair (whose second CTA holds no rows when m <= 128)."""
+    shapes = [(37, 1000, 53), (64, 1024, 64)] + ([(200, 3000, 300)] if tile else [])
     specs, pps = _specs(shapes, seed0=30)
     L, N = 3, 40
     lv = oracle.Levels(16, 2, L)
-    with binding.Plan(specs, c0=16, L=L, precision="bf16") as plan:
+    with binding.Plan(specs, c0=16, L=L, precision="bf16", tile_override=tile) as plan:
         plan.level_stats_batch(_ranges(len(shapes), L, 0, N))
         for q, pp in enumerate(pps):
             orc = oracle.Problem(*pp.f64(), seed_A=pp.seed_A, seed_B=pp.seed_B, seed_idx=pp.seed_idx,
@@ -176,6 +180,10 @@ def test_batched_rejects_bad_ranges():
         assert e.value.status == 1
         plan.level_stats_batch([])
         plan.level_stats_batch([(0, 0, 0, 0)])
+    with binding.Plan(specs, c0=16, L=2, precision="bf16", tile_override=4256) as plan:
+        with pytest.raises(binding.MLMCError) as e:   # the 16-warp pair serves single-problem launches
+            plan.level_stats_batch([(0, 0, 0, 8)])
+        assert e.value.status == 6
 
 
 def test_batched_fp32_runs_one_by_one():

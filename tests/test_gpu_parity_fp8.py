@@ -106,15 +106,16 @@ def test_e4m3_level_means_against_fp64_oracle_precision_workload():
           f"{np.linalg.norm(Y - Yref) / np.linalg.norm(Yref):.3e}")
 
 
-def test_e4m3_batched_matches_one_by_one():
+@pytest.mark.parametrize("tile", [1064, 3256])
+def test_e4m3_batched_matches_one_by_one(tile):
     shapes = [(37, 1000, 53), (64, 1024, 64), (200, 3000, 300)]
     specs = []
     for q, (m, n, p) in enumerate(shapes):
         pp = make_params(m, n, p, seed_A=2 * q, seed_B=2 * q + 1, seed_idx=2, problem_id=q, dtype=np.float32)
         specs.append(_spec(pp))
     ranges = [(q, l, 0, 50) for q in range(3) for l in range(3)]
-    with binding.Plan(specs, c0=16, L=2, precision="fp8", tile_override=1064) as a, \
-            binding.Plan(specs, c0=16, L=2, precision="fp8", tile_override=1064) as b:
+    with binding.Plan(specs, c0=16, L=2, precision="fp8", tile_override=tile) as a, \
+            binding.Plan(specs, c0=16, L=2, precision="fp8", tile_override=tile) as b:
         a.level_stats_batch(ranges)
         for r in ranges:
             b.level_stats(*r)
