@@ -811,8 +811,14 @@ BATCHED = dict(name="batched_64_problems", count=64, shape_seed=7, c0=32, R=2, p
 _BATCHED_INPUTS = {}
 
 # DRAM bytes (read + write) per algorithmic gathered byte of the batched kernel, by tile, from one
-# ncu pass over one launch of the batched_8_problems profile case (29.995 GB algorithmic)
+# ncu pass over one launch of a profile case: 1128 on the workload's first 8 problems (29.995 GB
+# algorithmic), the CTA pair 3256 on its first 8 problems of more than 128 rows and columns
+# (21.937 GB), which carry most of the gathered bytes
 BATCHED_TRAFFIC = {1128: {"dram_over_algorithmic": (36247647744 + 71866112) / 29995171840,
+                          "captured_on": "batched_8_problems",
+                          "source": "profiles/level_tc_bf16_batched_64_problems.md"},
+                   3256: {"dram_over_algorithmic": (22977974784 + 119399936) / 21936668672,
+                          "captured_on": "batched_8_large_problems",
                           "source": "profiles/level_tc_bf16_batched_64_problems.md"}}
 
 
@@ -912,13 +918,13 @@ def _measure_batched(args, dev, stream, peaks, peak_kind, precision="bf16", step
             {"bound": "tensor", "achieved": tfl, "peak": tpeak, "unit": "TFLOP/s", "frac": tfl / tpeak,
              "hbm_achieved_gbs": hbm})
     # DRAM traffic per level launch: the DRAM bytes per algorithmic byte of one captured launch of
-    # the 128 x 128 batched kernel (8 of the problems, 256 samples per level) times this step's
-    # algorithmic bytes per launch; null for another tile
+    # the batched kernel on this tile times this step's algorithmic bytes per launch; null for a
+    # tile without a capture
     waves = max(1, launches // (3 * steps))
     bt = BATCHED_TRAFFIC.get(tile)
     traffic = None if bt is None else {
         "value": bt["dram_over_algorithmic"] * bytes_alg / waves, "unit": "bytes per launch", "launches": waves * steps,
-        "algorithmic_bytes_per_launch": bytes_alg / waves, "source": bt["source"]}
+        "algorithmic_bytes_per_launch": bytes_alg / waves, "captured_on": bt["captured_on"], "source": bt["source"]}
     roof.update({"traffic": traffic,
                  "peak_source": f"{'hbm_gbs' if bound_hbm else 'bf16_tflops_sustained'} ({peak_kind})",
                  "kernel": "level_tc_bf16_kernel<batched>"})
@@ -1083,17 +1089,21 @@ def run_profile_case(args):
     from paper_1904_00429_gb300.inputs import make_params, make_target
 
     dev = torch.device("cuda:0")
-    if args.profile_case == "batched_8_problems":
-        # the first 8 problems of the batched workload, 128 x 128 tile, 256 samples per level
+    if args.profile_case in ("batched_8_problems", "batched_8_large_problems"):
+        # the first 8 problems of the batched workload on the 128 x 128 tile, or the first 8 of more
+        # than 128 rows and columns on the CTA pair; 256 samples per level
         from paper_1904_00429_gb300.inputs import batched_shapes
+        large = args.profile_case == "batched_8_large_problems"
+        all_shapes = list(enumerate(batched_shapes(BATCHED["count"], BATCHED["shape_seed"])))
+        picked = [(q0, sh) for q0, sh in all_shapes if not large or (sh[0] > 128 and sh[2] > 128)][:8]
         specs, ranges = [], []
-        for q, (m, n, p, L) in enumerate(batched_shapes(BATCHED["count"], BATCHED["shape_seed"])[:8]):
-            pq = make_params(m, n, p, law="gauss", seed_A=2 * q, seed_B=2 * q + 1, seed_idx=2, problem_id=q,
+        for q, (q0, (m, n, p, L)) in enumerate(picked):
+            pq = make_params(m, n, p, law="gauss", seed_A=2 * q0, seed_B=2 * q0 + 1, seed_idx=2, problem_id=q0,
                              dtype=np.float32)
             specs.append(binding.ProblemSpec(*[torch.from_numpy(x).to(dev) for x in (pq.M, pq.S, pq.Mp, pq.Sp)],
-                                             seed_A=2 * q, seed_B=2 * q + 1, seed_idx=2, problem_id=q, L=L))
+                                             seed_A=2 * q0, seed_B=2 * q0 + 1, seed_idx=2, problem_id=q0, L=L))
             ranges += [(q, l) for l in range(L + 1)]
-        plan = binding.Plan(specs, c0=BATCHED["c0"], L=8, precision="bf16", tile_override=1128)
+        plan = binding.Plan(specs, c0=BATCHED["c0"], L=8, precision="bf16", tile_override=3256 if large else 1128)
         waves = []
         for i in range(3):
             c0 = plan.launch_count()
@@ -1101,7 +1111,7 @@ def run_profile_case(args):
             waves.append((plan.launch_count() - c0) // 3)   # a wave: the level kernel and two merges
         plan.synchronize()
         plan.close()
-        shapes = batched_shapes(BATCHED["count"], BATCHED["shape_seed"])[:8]
+        shapes = [sh for _, sh in picked]
         alg = sum(256 * BATCHED["c0"] * BATCHED["R"]**l * 2 * (shapes[q][0] + shapes[q][2]) * 4 for q, l in ranges)
         print(json.dumps({"profile_case": args.profile_case, "status": "ok", "level_launches_per_call": waves,
                           "algorithmic_bytes_per_call": alg}), flush=True)
@@ -1177,7 +1187,8 @@ def main():
                     "precision in --ttr-side-precisions ('' to skip)")
     ap.add_argument("--ttr-side-precisions", default="bf16,fp32,fp8", help="precisions of the shorter runs")
     ap.add_argument("--profile-case", choices=sorted(list(PROFILE_CASES) + list(SMALL_PROFILE_CASES) +
-                                                     ["adjoint", "batched_8_problems", "cuda_core_f32_xi_level3"]),
+                                                     ["adjoint", "batched_8_problems", "batched_8_large_problems",
+                                                      "cuda_core_f32_xi_level3"]),
                     default=None,
                     help="run one small kernel invocation for ncu instead of the benchmark")
     args = ap.parse_args()
