@@ -68,8 +68,8 @@ struct TcCfg {
     static constexpr int kGT = 32 * W;                    // generator threads
     static constexpr int kThr = kGT + 32;                  // + the producer warp
     // slots per generator item: 4 where 8 would leave too few items per sub-block to keep the
-    // generator warps busy (the 16-warp pair; BF16 single-CTA tiles of at most 64 columns)
-    static constexpr int kNS = (W == 16 || (Q == 0 && P == 0 && MH == 1 && BN <= 64)) ? 4 : 8;
+    // generator warps busy (the 16-warp pair; single-CTA tiles of at most 64 columns)
+    static constexpr int kNS = (W == 16 || (P == 0 && MH == 1 && BN <= 64)) ? 4 : 8;
     // Slots per sub-block: 32 for E4M3 (one scale block), pairs, and small tiles whose 16-slot
     // sub-block would leave generator threads idle ((rows + BN) / 4 x 2 items for 256 threads)
     static constexpr int kSub = (Q || P || 128 * MH + BN <= 256) ? 32 : 16;
@@ -793,10 +793,11 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                                                             prm.rkA, src, C::kRows * 8, false, a_tile, 4 * g4,
                                                             (kSub / 8) * kk + (sg * kNS) / 8, ((sg * kNS) % 8) * 2);
                                     else
-                                        gen_block_e4m3(ih, sg * 8, vr, static_cast<uint32_t>(i >> 2),
-                                                       static_cast<uint32_t>(sh), level_sample_word(prm.l, sh), prm.rkA,
-                                                       src, C::kRows * 8, false, a_tile, 4 * g4, kGroups * kk + sg,
-                                                       j * kSub + sg * 8 - h * prm.c);
+                                        gen_block_e4m3<128, kNS>(ih, sg * kNS, vr, static_cast<uint32_t>(i >> 2),
+                                                                 static_cast<uint32_t>(sh), level_sample_word(prm.l, sh),
+                                                                 prm.rkA, src, C::kRows * 8, false, a_tile, 4 * g4,
+                                                                 (kSub / 8) * kk + (sg * kNS) / 8,
+                                                                 j * kSub + sg * kNS - h * prm.c, false, ((sg * kNS) % 8) * 2);
                                 } else {
                                     const int it2 = it - kItemsA;
                                     const int g4 = Q == 0 ? it2 % (C::kBGen / 4) : it2 / kGroups;
@@ -813,10 +814,11 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                                                             (kSub / 8) * kk + (sg * kNS) / 8, ((sg * kNS) % 8) * 2,
                                                             gw_s + b * kSub);
                                     else
-                                        gen_block_e4m3(idx, sg * 8, jc < prm.p, static_cast<uint32_t>(jc >> 2),
-                                                       static_cast<uint32_t>(sh), level_sample_word(prm.l, sh), prm.rkB,
-                                                       src, C::kBGen * 8, coarse_sign, b_tile, brow0 + 4 * g4,
-                                                       kGroups * kk + sg, kp0 - h * prm.c, prm.c == 16);
+                                        gen_block_e4m3<128, kNS>(idx, sg * kNS, jc < prm.p, static_cast<uint32_t>(jc >> 2),
+                                                                 static_cast<uint32_t>(sh), level_sample_word(prm.l, sh),
+                                                                 prm.rkB, src, C::kBGen * 8, coarse_sign, b_tile,
+                                                                 brow0 + 4 * g4, (kSub / 8) * kk + (sg * kNS) / 8,
+                                                                 kp0 - h * prm.c, prm.c == 16, ((sg * kNS) % 8) * 2);
                                 }
                             } else if constexpr (Q == 0) {
                                 // consecutive threads take consecutive row groups
@@ -886,9 +888,11 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                                                                 (sg * kNS) / 8, j * kSub + sg * kNS, false,
                                                                 ((sg * kNS) % 8) * 2);
                                     else
-                                        gen_block_e4m3(idx, sg * 8, i < prm.m, static_cast<uint32_t>(i >> 2), s_lo, lsw,
-                                                       prm.rkA, st + (sg * 8) * (C::kRows * 8) + g4 * 32, C::kRows * 8,
-                                                       false, a_tile, 4 * g4, kGroups * kk + sg, j * kSub + sg * 8);
+                                        gen_block_e4m3<128, kNS>(idx, sg * kNS, i < prm.m, static_cast<uint32_t>(i >> 2),
+                                                                 s_lo, lsw, prm.rkA,
+                                                                 st + (sg * kNS) * (C::kRows * 8) + g4 * 32, C::kRows * 8,
+                                                                 false, a_tile, 4 * g4, (kSub / 8) * kk + (sg * kNS) / 8,
+                                                                 j * kSub + sg * kNS, false, ((sg * kNS) % 8) * 2);
                                 } else {
                                     const int it2 = it - kItemsA;
                                     const int g4 = it2 / kGroups, sg = it2 % kGroups;
@@ -901,10 +905,12 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                                                                 (sg * kNS) / 8, j * kSub + sg * kNS, false,
                                                                 ((sg * kNS) % 8) * 2);
                                     else
-                                        gen_block_e4m3(idx, sg * 8, jc < prm.p, static_cast<uint32_t>(jc >> 2), s_lo, lsw,
-                                                       prm.rkB, stB + (sg * 8) * (C::kBGen * 8) + g4 * 32,
-                                                       C::kBGen * 8, coarse_sign, b_tile, brow0 + 4 * g4,
-                                                       kGroups * kk + sg, j * kSub + sg * 8);
+                                        gen_block_e4m3<128, kNS>(idx, sg * kNS, jc < prm.p, static_cast<uint32_t>(jc >> 2),
+                                                                 s_lo, lsw, prm.rkB,
+                                                                 stB + (sg * kNS) * (C::kBGen * 8) + g4 * 32, C::kBGen * 8,
+                                                                 coarse_sign, b_tile, brow0 + 4 * g4,
+                                                                 (kSub / 8) * kk + (sg * kNS) / 8, j * kSub + sg * kNS,
+                                                                 false, ((sg * kNS) % 8) * 2);
                                 }
                             }
                         }
