@@ -775,13 +775,32 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                         for (int it = tid; it < kItemsA + kItemsB; it += kGenThreads) {
                             if (PK) {
                                 // packed samples: A rows 0-63 belong to sample s, rows 64-127 to s + 1 (zero
-                                // on the other sample's K positions); B's K positions to whichever owns them
-                                if (it < kItemsA) {
+                                // on the other sample's K positions); B's K positions to whichever owns them.
+                                // BF16 takes the A items of half 0, then the B items, then the A items of
+                                // half 1, so that a thread's items (it, it + 256) hold one of the active
+                                // half's A items or one B item, not both
+                                // (4-slot tiles: there the items outnumber the threads)
+                                int itA = -1, itB = -1;
+                                if constexpr (Q == 0 && kNS == 4) {
+                                    constexpr int kAH = kItemsA / 2;
+                                    if (it < kAH)
+                                        itA = it;
+                                    else if (it < kAH + kItemsB)
+                                        itB = it - kAH;
+                                    else
+                                        itA = it - kItemsB;
+                                } else {
+                                    if (it < kItemsA)
+                                        itA = it;
+                                    else
+                                        itB = it - kItemsA;
+                                }
+                                if (itA >= 0) {
                                     // BF16: items ordered (half, slot group, row group), so a warp's items
                                     // belong to one half and skip the other sample's positions together
-                                    const int rest = it >> 4;
-                                    const int g4 = Q == 0 ? (rest / kGroups) * 16 + (it & 15) : it / kGroups;
-                                    const int sg = Q == 0 ? rest % kGroups : it % kGroups;
+                                    const int rest = itA >> 4;
+                                    const int g4 = Q == 0 ? (rest / kGroups) * 16 + (itA & 15) : itA / kGroups;
+                                    const int sg = Q == 0 ? rest % kGroups : itA % kGroups;
                                     const int h = g4 >> 4;
                                     const int i = 4 * (g4 & 15);
                                     const uint64_t sh = s + static_cast<uint64_t>(h);
@@ -800,7 +819,7 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                                                                  (kSub / 8) * kk + (sg * kNS) / 8,
                                                                  j * kSub + sg * kNS - h * prm.c, false, ((sg * kNS) % 8) * 2);
                                 } else {
-                                    const int it2 = it - kItemsA;
+                                    const int it2 = itB;
                                     const int g4 = Q == 0 ? it2 % (C::kBGen / 4) : it2 / kGroups;
                                     const int sg = Q == 0 ? it2 / (C::kBGen / 4) : it2 % kGroups;
                                     const int jc = geo.bcol0 + 4 * g4;
@@ -822,11 +841,19 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                                                                  kp0 - h * prm.c, prm.c == 16, ((sg * kNS) % 8) * 2);
                                 }
                             } else if constexpr (Q == 0) {
-                                // consecutive threads take consecutive row groups
-                                if (it < kItemsA) {
+                                // consecutive threads take consecutive row groups.  Single-CTA 4-slot tiles
+                                // (more items than threads) take the A items of rows 0-63, then the B
+                                // items, then the A items of rows 64-127, so that with at most 64 rows
+                                // (64-127 are padding, drawn for nothing) no thread holds two drawn items
+                                constexpr bool kSplitA = P == 0 && MH == 1 && kNS == 4;
+                                constexpr int kAH = kItemsA / 2;
+                                const bool isA = kSplitA ? (it < kAH || it >= kAH + kItemsB) : it < kItemsA;
+                                const int itA = kSplitA ? (it < kAH ? it : it - kItemsB) : it;
+                                const int itB = kSplitA ? it - kAH : it - kItemsA;
+                                if (isA) {
                                     // 4 rows of A x kNS slots
-                                    const int g4 = it % (C::kRows / 4);
-                                    const int sg = it / (C::kRows / 4);
+                                    const int g4 = kSplitA ? (itA / kAH) * 16 + itA % 16 : itA % (C::kRows / 4);
+                                    const int sg = kSplitA ? (itA % kAH) / 16 : itA / (C::kRows / 4);
                                     const int i = tm0 + 4 * g4;
                                     if constexpr (P)
                                         gen_block<64, kNS>(idx, sg * kNS, i < prm.m, static_cast<uint32_t>(i >> 2), s_lo,
@@ -841,7 +868,7 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                                 } else {
                                     // 4 columns of B (rows of the transposed tile) x kNS slots, sign folded in;
                                     // a pair also writes them into the peer's B tile
-                                    const int it2 = it - kItemsA;
+                                    const int it2 = itB;
                                     const int g4 = it2 % (C::kBGen / 4);
                                     const int sg = it2 / (C::kBGen / 4);
                                     const int jc = geo.bcol0 + 4 * g4;
