@@ -530,6 +530,54 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                 const int nsubg = PK ? (nK + kSub - 1) / kSub : nsub;
                 for (int j = 0; j < nsubg; ++j, ++g) {
                     const int b = static_cast<int>(g & 1);
+                    const int t0 = j * kSub;
+                    // this sub-block's draws, made before waiting for staging buffer b (they do not
+                    // touch it): the table walks of xi** and the Philox blocks of the indices run
+                    // while the generators still use the buffer
+                    int dr0 = -1, dr1 = -1, dh = 0;
+                    float dg = 0.0f;
+                    if (XI) {
+                        // xi** (Thm 3.1): one slot per lane (a draw walks the tables with dependent
+                        // loads: 32 walks in parallel), inverse-CDF index and weight Q_{n-1} / q_k.
+                        // K position kp holds slot kp (PK: sample s + kp / c_l, slot kp mod c_l)
+                        if (lane < kSub) {
+                            const int kp = t0 + lane;
+                            dh = (PK && kp < nK) ? kp / prm.c : 0;
+                            const int t = kp - dh * prm.c;
+                            if (kp < nK) {
+                                const uint64_t sh = s + static_cast<uint64_t>(dh);
+                                uint64_t w0, w1;
+                                index_words(prm.keyI, level_sample_word(prm.l, sh), static_cast<uint32_t>(sh), t >> 1,
+                                            w0, w1);
+                                dr0 = static_cast<int>(index_from_cdf((t & 1) ? w1 : w0, prm.xi_Q, prm.xi_q, prm.xi_G,
+                                                                      prm.n));
+                                dg = static_cast<float>(__ddiv_rn(prm.xi_Qtot, prm.xi_q[dr0]));
+                            }
+                        }
+                    } else if (PK) {
+                        // K position kp -> sample s + h (h = kp / c_l), slot kp - h c_l; c_l is even, so a
+                        // slot pair never straddles the two samples
+                        if (lane < kSub / 2) {
+                            const int kp = t0 + 2 * lane;
+                            dh = kp < nK ? kp / prm.c : 0;
+                            if (kp < nK) {
+                                const uint64_t sh = s + static_cast<uint64_t>(dh);
+                                int64_t r0, r1;
+                                index_pair(prm.keyI, level_sample_word(prm.l, sh), static_cast<uint32_t>(sh),
+                                           (kp - dh * prm.c) >> 1, static_cast<uint64_t>(prm.n), r0, r1);
+                                dr0 = static_cast<int>(r0);
+                                dr1 = static_cast<int>(r1);
+                            }
+                        }
+                    } else if (lane < kSub / 2) {
+                        const int t = t0 + 2 * lane;
+                        if (t < prm.c) {
+                            int64_t r0, r1;
+                            index_pair(prm.keyI, lsw, s_lo, t >> 1, static_cast<uint64_t>(prm.n), r0, r1);
+                            dr0 = static_cast<int>(r0);
+                            dr1 = t + 1 < prm.c ? static_cast<int>(r1) : -1;
+                        }
+                    }
                     if (g >= 2 && !tc::mbar_wait_bounded(bar_empty(b), ((g >> 1) - 1) & 1,
                                                          tc::globaltimer() + ex.timeout_ns)) {
                         *abort_s = 1;
@@ -540,65 +588,33 @@ level_tc_bf16_kernel(const __grid_constant__ LevelParams prm_arg, const TcExtra 
                         break;
                     }
                     int* idx = idx_s + b * kSub;
-                    const int t0 = j * kSub;
                     if (XI) {
-                        // xi** (Thm 3.1): one slot per lane (a draw walks the tables with dependent
-                        // loads: 32 walks in parallel), inverse-CDF index and weight Q_{n-1} / q_k.
-                        // K position kp holds slot kp (PK: sample s + kp / c_l, slot kp mod c_l;
-                        // F != 0: even slots at positions 0-15, odd slots at 16-31)
+                        // F != 0: even slots at positions 0-15, odd slots at 16-31
                         if (lane < kSub) {
-                            const int kp = t0 + lane;
-                            const int h = (PK && kp < nK) ? kp / prm.c : 0;
-                            const int t = kp - h * prm.c;
-                            int r = -1;
-                            float g = 0.0f;
-                            if (kp < nK) {
-                                const uint64_t sh = s + static_cast<uint64_t>(h);
-                                uint64_t w0, w1;
-                                index_words(prm.keyI, level_sample_word(prm.l, sh), static_cast<uint32_t>(sh), t >> 1,
-                                            w0, w1);
-                                r = static_cast<int>(index_from_cdf((t & 1) ? w1 : w0, prm.xi_Q, prm.xi_q, prm.xi_G,
-                                                                    prm.n));
-                                g = static_cast<float>(__ddiv_rn(prm.xi_Qtot, prm.xi_q[r]));
-                            }
                             const int pos = F ? ((lane & 1) ? kSub / 2 + (lane >> 1) : (lane >> 1)) : lane;
-                            idx[pos] = r;
-                            gw_s[b * kSub + pos] = g;
+                            idx[pos] = dr0;
+                            gw_s[b * kSub + pos] = dg;
                             if (PK) {
                                 int* ih = idxh_s + b * 2 * kSub;
-                                ih[lane] = h == 0 ? r : -1;
-                                ih[kSub + lane] = h == 1 ? r : -1;
+                                ih[lane] = dh == 0 ? dr0 : -1;
+                                ih[kSub + lane] = dh == 1 ? dr0 : -1;
                             }
                         }
                     } else if (PK) {
-                        // K position kp -> sample s + h (h = kp / c_l), slot kp - h c_l; c_l is even, so a
-                        // slot pair never straddles the two samples
                         if (lane < kSub / 2) {
-                            const int kp = t0 + 2 * lane;
-                            int64_t r0 = -1, r1 = -1;
-                            const int h = kp < nK ? kp / prm.c : 0;
-                            if (kp < nK) {
-                                const uint64_t sh = s + static_cast<uint64_t>(h);
-                                index_pair(prm.keyI, level_sample_word(prm.l, sh), static_cast<uint32_t>(sh),
-                                           (kp - h * prm.c) >> 1, static_cast<uint64_t>(prm.n), r0, r1);
-                            }
-                            const int v0 = kp < nK ? static_cast<int>(r0) : -1, v1 = kp < nK ? static_cast<int>(r1) : -1;
-                            idx[2 * lane] = v0;
-                            idx[2 * lane + 1] = v1;
+                            idx[2 * lane] = dr0;
+                            idx[2 * lane + 1] = dr1;
                             int* ih = idxh_s + b * 2 * kSub;
-                            ih[2 * lane] = h == 0 ? v0 : -1;
-                            ih[2 * lane + 1] = h == 0 ? v1 : -1;
-                            ih[kSub + 2 * lane] = h == 1 ? v0 : -1;
-                            ih[kSub + 2 * lane + 1] = h == 1 ? v1 : -1;
+                            ih[2 * lane] = dh == 0 ? dr0 : -1;
+                            ih[2 * lane + 1] = dh == 0 ? dr1 : -1;
+                            ih[kSub + 2 * lane] = dh == 1 ? dr0 : -1;
+                            ih[kSub + 2 * lane + 1] = dh == 1 ? dr1 : -1;
                         }
                     } else if (lane < kSub / 2) {
-                        const int t = t0 + 2 * lane;
-                        int64_t r0 = -1, r1 = -1;
-                        if (t < prm.c) index_pair(prm.keyI, lsw, s_lo, t >> 1, static_cast<uint64_t>(prm.n), r0, r1);
                         // F != 0: even slot t at K position lane, odd slot t + 1 at 16 + lane
                         const int p0 = F ? lane : 2 * lane, p1 = F ? kSub / 2 + lane : 2 * lane + 1;
-                        idx[p0] = t < prm.c ? static_cast<int>(r0) : -1;
-                        idx[p1] = t + 1 < prm.c ? static_cast<int>(r1) : -1;
+                        idx[p0] = dr0;
+                        idx[p1] = dr1;
                     }
                     __syncwarp();
                     const int nvalid = min(kSub, nK - t0);
