@@ -72,6 +72,8 @@ TRAFFIC = {
     # interpolated, and bench.py scales them by the outer products of its own launches
     "bf16": {"dram_bytes_per_outer_product": {0: (2901958400 + 62803200) / 1048576,
                                               8: (108988471808 + 78316800) / 39845888},
+             # levels with c_l >= 4096 run on the single-CTA 256 x 256 tile: its level-8 capture
+             "wide": {"from_c": 4096, "dram_bytes_per_outer_product": (109698142208 + 624583168) / 39845888},
              "source": "profiles/level_tc_bf16_mlmc_256x65536x256.md"},
     "fp8": {"dram_bytes_per_outer_product": {0: (2902601984 + 62838272) / 1048576,
                                              8: (109010083328 + 77853952) / 39845888},
@@ -79,7 +81,10 @@ TRAFFIC = {
 }
 
 
-def dram_per_outer(prec, level):
+def dram_per_outer(prec, level, c=None):
+    w = TRAFFIC[prec].get("wide")
+    if w is not None and c is not None and c >= w["from_c"]:
+        return w["dram_bytes_per_outer_product"]   # levels on the single-CTA 256 x 256 tile
     t = TRAFFIC[prec]["dram_bytes_per_outer_product"]
     if level in t:
         return t[level]
@@ -395,7 +400,8 @@ def _roofline(res, W, peaks, peak_kind, gen_rate=None):
         # estimated DRAM bytes per level-kernel launch, averaged over the timed launches
         # (each level_stats call is one level-kernel launch and two merges; one telescoping sum per step)
         level_launches = max(1, (res["launches"] - res["steps"]) // 3)
-        dram = sum(res["steps"] * b * (W["c0"] * W["R"]**l) * dram_per_outer(prec, l) for l, b in enumerate(res["B"]))
+        dram = sum(res["steps"] * b * (W["c0"] * W["R"]**l) * dram_per_outer(prec, l, W["c0"] * W["R"]**l)
+                   for l, b in enumerate(res["B"]))
         traffic = {"value": dram / level_launches, "unit": "bytes per launch", "launches": level_launches,
                    "algorithmic_bytes_per_launch": bytes_alg / level_launches, "source": TRAFFIC[prec]["source"]}
     if prec in ("fp32", "fp64"):

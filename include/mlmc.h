@@ -116,7 +116,8 @@ typedef struct {
                               one of 1032 1064 1128 1256 2032 2064 2128 2256 (e.g. 2128 = 256 x 128;
                               E4M3: 1032 1064 1128 2032 2064), or 3256: a cluster of two CTAs of
                               128 x 256 sharing one 256 x 256 tile (BF16 and E4M3, single-problem
-                              and batched launches; the BF16 default for outputs above 128 x 128),
+                              and batched launches; the BF16 default for outputs above 128 x 128,
+                              whose levels with c_l >= 4096 then run on 2256, measured faster there),
                               or 4256: the same pair with 16 generator warps on 4-slot items (the
                               E4M3 default for outputs above 128 x 128; single-problem launches).  CUDA-core plans: 1000 * rows + columns
                               of the output tile, 64064; FP32 with f = identity also 128064 (its

@@ -71,6 +71,13 @@ struct ProblemState {
     int tiles_m = 1, tiles_p = 1;
     TcTile tile{0, 0, 0};   // tensor-core tile of the single-problem launches
     TcMaps maps{};          // row-gather maps of PAB for `tile`
+    // BF16 problems on the CTA pair: levels with c_l >= c_wide run on the single-CTA 256 x 256
+    // tile instead, which measured faster there (the pair's per-sub-block exchange outweighs its
+    // cheaper per-sample drain once a sample has hundreds of sub-blocks)
+    TcTile tile_wide{0, 0, 0};
+    TcMaps maps_wide{};
+    int tiles_m_wide = 1, tiles_p_wide = 1;
+    int64_t c_wide = INT64_MAX;
     TcMaps batch_maps{};    // ... and for the plan's batched tile
     int32_t batch_maps_tile = 0;
     int max_chunks = 1;
@@ -209,6 +216,10 @@ int32_t encode_tile(const TcTile& t)
 }
 
 const int32_t kTileIds[9] = {1032, 1064, 1128, 1256, 2032, 2064, 2128, 2256, 3256};
+// BF16 single-problem launches on the CTA pair switch to the 256 x 256 single-CTA tile from this
+// many slots per sample on (measured on 256 x 65536 x 256: at c_l = 4096, 8192, 16384 the single
+// CTA took 4 %, 8 %, 10 % less time than the pair; at 2048 and below it took more)
+constexpr int64_t kWideTileFromC = 4096;
 
 mlmc_status validate(const mlmc_problem* problems, int32_t nprob, const mlmc_options* o)
 {
@@ -354,8 +365,11 @@ mlmc_status run_level(mlmc_plan_t* plan, ProblemState& ps, int level, uint64_t s
     prm.keyI = key(ps.desc.seed_idx, ps.desc.problem_id);
     prm.rkA = philox_round_keys(prm.keyA);
     prm.rkB = philox_round_keys(prm.keyB);
-    prm.tiles_m = ps.tiles_m;
-    prm.tiles_p = ps.tiles_p;
+    // the tile of this level (BF16 pairs: the single-CTA 256 x 256 tile from c_wide on)
+    const bool wide = ps.tile_wide.mh != 0 && c >= ps.c_wide;
+    const TcTile& tile = wide ? ps.tile_wide : ps.tile;
+    prm.tiles_m = wide ? ps.tiles_m_wide : ps.tiles_m;
+    prm.tiles_p = wide ? ps.tiles_p_wide : ps.tiles_p;
     prm.cc_tile = ps.cc_tile;
     prm.partial_sum = plan->partial_sum;
     prm.partial_q = plan->partial_q;
@@ -385,24 +399,24 @@ mlmc_status run_level(mlmc_plan_t* plan, ProblemState& ps, int level, uint64_t s
         prm.s_end = std::min<uint64_t>(s_end, (cb + nb) * ch);
         cudaError_t err;
         if (tensor_core_precision(o.precision)) {
-            prm.maps = ps.maps;
+            prm.maps = wide ? ps.maps_wide : ps.maps;
             TcLaunch tl{plan->err_flag, plan->timeout_ns, static_cast<float>(double(ps.n) / double(c)), plan->num_sms};
             if (o.f != MLMC_F_IDENTITY) {
                 // the targeted function: fine and coarse sums apart, Welford at every level
                 prm.pack = 0;
                 prm.welford = 1;
-                err = launch_level_tc_f(prm, ps.tile, o.f, tl, plan->stream);
+                err = launch_level_tc_f(prm, tile, o.f, tl, plan->stream);
             } else if (ps.xi_Q) {
                 // xi**: per-slot weights; the level means are zero for l >= 1 too
-                prm.pack = tc_pack(ps.tile, tc_format(o), ps.m, c) ? 1 : 0;
+                prm.pack = tc_pack(tile, tc_format(o), ps.m, c) ? 1 : 0;
                 prm.welford = level == 0 ? 1 : 0;
-                err = launch_level_tc(prm, ps.tile, tc_format(o), tl, plan->stream);
+                err = launch_level_tc(prm, tile, tc_format(o), tl, plan->stream);
             } else {
-                prm.pack = tc_pack(ps.tile, tc_format(o), ps.m, c) ? 1 : 0;
+                prm.pack = tc_pack(tile, tc_format(o), ps.m, c) ? 1 : 0;
                 // f = identity: for l >= 1 the fine and coarse estimates of one realisation have the
                 // same expectation, E[D_l] = 0, so only level 0 needs Welford
                 prm.welford = level == 0 ? 1 : 0;
-                err = launch_level_tc(prm, ps.tile, tc_format(o), tl, plan->stream);
+                err = launch_level_tc(prm, tile, tc_format(o), tl, plan->stream);
             }
         } else if (ps.m == 1 && ps.p == 1 && !ps.xi_Q) {
             err = launch_level_inner(prm, plan->f64, plan->opt.f, plan->stream);   // Sec. 2's inner product
@@ -413,7 +427,7 @@ mlmc_status run_level(mlmc_plan_t* plan, ProblemState& ps, int level, uint64_t s
         if (check_cuda(plan, err, "level kernel launch") != MLMC_OK) return plan->sticky;
         plan->launches += 3;  // level kernel, merge of the sums, merge of the M2
         const ChunkRun run{prm.s_begin, prm.s_end, cb, ch, n_before, nb};
-        err = launch_merge_partials(plan->partial_sum, plan->f64, plan->partial_q, ps.tiles_m * ps.tiles_p,
+        err = launch_merge_partials(plan->partial_sum, plan->f64, plan->partial_q, prm.tiles_m * prm.tiles_p,
                                     ps.m * ps.p, run, sum, M2, plan->chan, plan->stream);
         if (check_cuda(plan, err, "merge kernel launch") != MLMC_OK) return plan->sticky;
         n_before += prm.s_end - prm.s_begin;
@@ -929,6 +943,14 @@ mlmc_status mlmc_plan(const mlmc_problem* problems, int32_t nprob, const mlmc_op
             ps.tile = tile;
             ps.tiles_m = int((ps.m + tile.rows - 1) / tile.rows);
             ps.tiles_p = int((ps.p + tile.bn - 1) / tile.bn);
+            const TcTile wide = decode_tile(2256);
+            if (!options->tile_override && options->precision == MLMC_BF16 && options->f == MLMC_F_IDENTITY &&
+                options->sampling == MLMC_XI_UNIFORM && tile.pair == 1 && tc_tile_valid(wide, 0)) {
+                ps.tile_wide = wide;
+                ps.tiles_m_wide = int((ps.m + wide.rows - 1) / wide.rows);
+                ps.tiles_p_wide = int((ps.p + wide.bn - 1) / wide.bn);
+                ps.c_wide = kWideTileFromC;
+            }
         } else {
             ps.cc_tile = options->tile_override ? options->tile_override
                                                 : cuda_core_default_tile(options->precision, options->f, ps.m);
@@ -941,7 +963,8 @@ mlmc_status mlmc_plan(const mlmc_problem* problems, int32_t nprob, const mlmc_op
         const size_t budget = tensor_core_precision(options->precision) ? kPartialBudgetTc : kPartialBudget;
         ps.max_chunks = int(std::clamp<size_t>(budget / per_chunk, 1, kMaxChunksPerLaunch));
         max_partial = std::max(max_partial, per_chunk * size_t(ps.max_chunks));
-        max_q = std::max(max_q, size_t(ps.max_chunks) * size_t(ps.tiles_m * ps.tiles_p));
+        max_q = std::max(max_q, size_t(ps.max_chunks) *
+                                    size_t(std::max(ps.tiles_m * ps.tiles_p, ps.tiles_m_wide * ps.tiles_p_wide)));
         max_mp = std::max(max_mp, mp);
         // one row per inner index k holds both gathered vectors, so a sampled index is one
         // contiguous read of 2 (m_pad + p_pad) elements
@@ -964,6 +987,9 @@ mlmc_status mlmc_plan(const mlmc_problem* problems, int32_t nprob, const mlmc_op
         }
         if (tensor_core_precision(options->precision))
             tc_encode_maps(&ps.maps, ps.PAB, ps.n, ps.ld, tc_stage_width_a(ps.tile), tc_stage_width_b(ps.tile));
+        if (ps.tile_wide.mh)
+            tc_encode_maps(&ps.maps_wide, ps.PAB, ps.n, ps.ld, tc_stage_width_a(ps.tile_wide),
+                           tc_stage_width_b(ps.tile_wide));
         if (options->sampling == MLMC_XI_OPTIMAL) {
             // xi** (Thm 3.1) from the laid-out parameters; its total must be a positive number
             if (cudaMalloc(reinterpret_cast<void**>(&ps.xi_q), sizeof(double) * size_t(ps.n)) != cudaSuccess ||
