@@ -65,7 +65,7 @@ typedef enum {
     MLMC_ERR_OOM = 3,          /* device allocation of the plan's scratch failed */
     MLMC_ERR_TIMEOUT = 4,      /* a bounded device wait gave up */
     MLMC_ERR_NUMERIC = 5,      /* a statistic became NaN or infinite */
-    MLMC_ERR_UNSUPPORTED = 6,  /* valid request this build does not implement */
+    MLMC_ERR_UNSUPPORTED = 6,  /* valid request the library does not implement */
     MLMC_ERR_STATE = 7         /* call out of order (e.g. backward before estimate) */
 } mlmc_status;
 
