@@ -26,8 +26,13 @@
 //     chunk partial.  The 256 x 256 single-CTA tile keeps only D in tensor memory and folds each
 //     sample into the chunk partial in global memory (one owner thread per element, read back
 //     and rewritten in sample order).
-// CTA pairs (tile 3256): a cluster of two CTAs shares one 256 x 256 tile, each generating its
-// 128 rows of A and half of B and sending that half to the peer with a shared-to-shared bulk copy.
+// CTA pairs (tiles 3256, 4256): a cluster of two CTAs shares one 256 x 256 tile, each generating
+// its 128 rows of A and half of B and sending that half to the peer with a shared-to-shared bulk
+// copy; in batched launches each cluster walks its own item list.
+// Forms selected by template parameters: Q (bfloat16 or block-scaled E4M3 with stochastic
+// rounding), F (the targeted function: fine and coarse sums in two accumulators, f applied in the
+// drain), XI (the xi** law: inverse-CDF draws, per-slot weights folded into B), W (8 or 16
+// generator warps), kBatch (a batched launch over many problems and levels).
 // Every mbarrier wait is bounded by a %globaltimer deadline; on timeout the kernel records
 // MLMC_ERR_TIMEOUT, waits (bounded) for its own copies and MMAs in flight and frees its tensor
 // memory before leaving.
