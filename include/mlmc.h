@@ -38,7 +38,10 @@
  *     the first error seen by a plan sticks and is returned by every later
  *     call on that plan.  mlmc_last_error() gives a thread-local message.
  *   - Work is enqueued on the plan's stream and is asynchronous unless the
- *     function says otherwise.
+ *     function says otherwise.  (mlmc_level_stats runs its chunk merges on a
+ *     stream the plan owns, forked from the plan's stream after each level
+ *     kernel and joined back into it before the call returns, so every later
+ *     work on the plan's stream sees the merged statistics.)
  */
 #ifndef MLMC_H
 #define MLMC_H

@@ -95,8 +95,14 @@ struct mlmc_plan_s {
     bool f64 = false;
     size_t elem = 4;
     std::vector<ProblemState> probs;
-    void* partial_sum = nullptr;
-    double* partial_q = nullptr;
+    // Chunk partials of a level call, two sets: the level kernel of one batch of chunks writes one
+    // set while the merges of the batch before read the other, on merge_stream (forked from the
+    // plan's stream by `produced`, joined back by `merged` before the call returns).
+    void* partial_sum[2] = {nullptr, nullptr};
+    double* partial_q[2] = {nullptr, nullptr};
+    cudaStream_t merge_stream = nullptr;
+    cudaEvent_t produced[2] = {nullptr, nullptr};   // a batch's partials are written (plan's stream)
+    cudaEvent_t merged[2] = {nullptr, nullptr};     // a batch's partials are folded (merge_stream)
     double* dbg_sum = nullptr;    // one level's state for debug_sample
     double* dbg_M2 = nullptr;
     double* chan = nullptr;       // between-chunk terms of a merge (merge_groups(m p) of the largest problem)
@@ -290,8 +296,16 @@ void free_plan(mlmc_plan_t* plan)
         cudaFree(ps.xi_Q);
         cudaFree(ps.xi_G);
     }
-    cudaFree(plan->partial_sum);
-    cudaFree(plan->partial_q);
+    if (plan->merge_stream) {
+        cudaStreamSynchronize(plan->merge_stream);
+        cudaStreamDestroy(plan->merge_stream);
+    }
+    for (int set = 0; set < 2; ++set) {
+        cudaFree(plan->partial_sum[set]);
+        cudaFree(plan->partial_q[set]);
+        if (plan->produced[set]) cudaEventDestroy(plan->produced[set]);
+        if (plan->merged[set]) cudaEventDestroy(plan->merged[set]);
+    }
     cudaFree(plan->dbg_sum);
     cudaFree(plan->dbg_M2);
     cudaFree(plan->chan);
@@ -371,8 +385,6 @@ mlmc_status run_level(mlmc_plan_t* plan, ProblemState& ps, int level, uint64_t s
     prm.tiles_m = wide ? ps.tiles_m_wide : ps.tiles_m;
     prm.tiles_p = wide ? ps.tiles_p_wide : ps.tiles_p;
     prm.cc_tile = ps.cc_tile;
-    prm.partial_sum = plan->partial_sum;
-    prm.partial_q = plan->partial_q;
     prm.xi_q = ps.xi_q;
     prm.xi_Q = ps.xi_Q;
     prm.xi_Qtot = ps.xi_Qtot;
@@ -391,8 +403,26 @@ mlmc_status run_level(mlmc_plan_t* plan, ProblemState& ps, int level, uint64_t s
     } pop_range;
     const uint64_t chunk_first = s0 / ch;
     const uint64_t chunk_last = (s_end - 1) / ch;
-    for (uint64_t cb = chunk_first; cb <= chunk_last; cb += uint64_t(ps.max_chunks)) {
+    // Batches alternate between the two sets of partials; the merges of batch i (in order on
+    // merge_stream) overlap the level kernel of batch i + 1, and batch i + 2 waits for them.
+    int batch = 0;
+    struct JoinOnExit {   // an early return still orders the plan's stream after every merge enqueued
+        mlmc_plan_t* plan;
+        const int& batch;
+        bool armed = true;
+        ~JoinOnExit()
+        {
+            if (armed && batch > 0) cudaStreamWaitEvent(plan->stream, plan->merged[(batch - 1) & 1], 0);
+        }
+    } join_on_exit{plan, batch};
+    for (uint64_t cb = chunk_first; cb <= chunk_last; cb += uint64_t(ps.max_chunks), ++batch) {
         const int nb = int(std::min<uint64_t>(uint64_t(ps.max_chunks), chunk_last - cb + 1));
+        const int set = batch & 1;
+        if (batch >= 2 &&
+            check_cuda(plan, cudaStreamWaitEvent(plan->stream, plan->merged[set], 0), "merge wait") != MLMC_OK)
+            return plan->sticky;
+        prm.partial_sum = plan->partial_sum[set];
+        prm.partial_q = plan->partial_q[set];
         prm.chunk0 = cb;
         prm.nchunks = nb;
         prm.s_begin = std::max<uint64_t>(s0, cb * ch);
@@ -427,11 +457,21 @@ mlmc_status run_level(mlmc_plan_t* plan, ProblemState& ps, int level, uint64_t s
         if (check_cuda(plan, err, "level kernel launch") != MLMC_OK) return plan->sticky;
         plan->launches += 3;  // level kernel, merge of the sums, merge of the M2
         const ChunkRun run{prm.s_begin, prm.s_end, cb, ch, n_before, nb};
-        err = launch_merge_partials(plan->partial_sum, plan->f64, plan->partial_q, prm.tiles_m * prm.tiles_p,
-                                    ps.m * ps.p, run, sum, M2, plan->chan, plan->stream);
+        err = cudaEventRecord(plan->produced[set], plan->stream);
+        if (err == cudaSuccess) err = cudaStreamWaitEvent(plan->merge_stream, plan->produced[set], 0);
+        if (err == cudaSuccess)
+            err = launch_merge_partials(plan->partial_sum[set], plan->f64, plan->partial_q[set],
+                                        prm.tiles_m * prm.tiles_p, ps.m * ps.p, run, sum, M2, plan->chan,
+                                        plan->merge_stream);
+        if (err == cudaSuccess) err = cudaEventRecord(plan->merged[set], plan->merge_stream);
         if (check_cuda(plan, err, "merge kernel launch") != MLMC_OK) return plan->sticky;
         n_before += prm.s_end - prm.s_begin;
     }
+    // join: later work on the plan's stream sees the merged level state
+    join_on_exit.armed = false;
+    if (batch > 0 &&
+        check_cuda(plan, cudaStreamWaitEvent(plan->stream, plan->merged[(batch - 1) & 1], 0), "merge join") != MLMC_OK)
+        return plan->sticky;
     return MLMC_OK;
 }
 
@@ -443,9 +483,9 @@ constexpr int kBatchMaxItems = 1 << 20;                 // (job, chunk, tile) un
 constexpr int kBatchMaxWaves = 4;                       // waves per graph launch
 constexpr int kBatchMaxGrid = 4096;
 constexpr int kMergeMaxChunks = 4096;
-// between-chunk terms of one wave's merges: one per 256 entries of each job (the partials of a
-// wave hold at most kBatchPartialBytes / 4 entries), plus one per job for the rounding up
-constexpr size_t kBatchChanEntries = kBatchPartialBytes / 4 / 256 + kBatchMaxJobs;
+// between-chunk terms of one wave's merges: one per kMergeGroup entries of each job (the partials
+// of a wave hold at most kBatchPartialBytes / 4 entries), plus one per job for the rounding up
+constexpr size_t kBatchChanEntries = kBatchPartialBytes / 4 / kMergeGroup + kBatchMaxJobs;
 
 struct BatchRange {
     int prob, level;
@@ -1014,9 +1054,22 @@ mlmc_status mlmc_plan(const mlmc_problem* problems, int32_t nprob, const mlmc_op
             }
         }
     }
-    if (cudaMalloc(&plan->partial_sum, max_partial) != cudaSuccess) return oom("chunk partials");
-    if (cudaMalloc(reinterpret_cast<void**>(&plan->partial_q), sizeof(double) * max_q) != cudaSuccess)
-        return oom("chunk sums of squares");
+    for (int set = 0; set < 2; ++set) {
+        if (cudaMalloc(&plan->partial_sum[set], max_partial) != cudaSuccess) return oom("chunk partials");
+        if (cudaMalloc(reinterpret_cast<void**>(&plan->partial_q[set]), sizeof(double) * max_q) != cudaSuccess)
+            return oom("chunk sums of squares");
+        if (cudaEventCreateWithFlags(&plan->produced[set], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&plan->merged[set], cudaEventDisableTiming) != cudaSuccess)
+            return oom("merge events");
+    }
+    {
+        // the merges run beside the next batch's level kernel: the highest priority, so that
+        // their few small blocks start as soon as an SM has room
+        int lo = 0, hi = 0;
+        cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        if (cudaStreamCreateWithPriority(&plan->merge_stream, cudaStreamNonBlocking, hi) != cudaSuccess)
+            return oom("merge stream");
+    }
     if (cudaMalloc(reinterpret_cast<void**>(&plan->dbg_sum), sizeof(double) * max_mp) != cudaSuccess)
         return oom("debug state");
     if (cudaMalloc(reinterpret_cast<void**>(&plan->dbg_M2), sizeof(double)) != cudaSuccess) return oom("debug state");

@@ -153,8 +153,9 @@ __host__ __device__ inline uint64_t chunk_count(const ChunkRun& r, int c)
     return b - a;
 }
 
-// Entry groups of the merge (one per kMergeThreads entries): the length of its scratch of
+// Entry groups of the merge (one per kMergeGroup entries): the length of its scratch of
 // between-chunk terms.
+constexpr int kMergeGroup = 64;
 int merge_groups(int64_t mp);
 
 // One job of a batched merge: the FP32 chunk partials of an m x p level (mp entries) and their

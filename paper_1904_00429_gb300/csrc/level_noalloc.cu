@@ -291,7 +291,7 @@ extern "C" mlmc_status mlmc_level_stats_noalloc(const mlmc_problem* problem, con
     const size_t elem = f64 ? 8 : 4;
     const int64_t mp = pr.m * pr.p;
     const size_t tiles = size_t(tiles_m) * size_t(tiles_p);
-    // scratch of `ch` chunks: the merge's between-chunk terms (one double per 256 entries), the
+    // scratch of `ch` chunks: the merge's between-chunk terms (one double per kMergeGroup entries), the
     // chunks' M2 per tile, then their partial sums, each part starting on a 256-byte boundary
     const size_t chan_bytes = (size_t(merge_groups(mp)) * 8 + 255) / 256 * 256;
     auto need = [&](size_t ch) { return chan_bytes + (ch * tiles * 8 + 255) / 256 * 256 + ch * size_t(mp) * elem; };

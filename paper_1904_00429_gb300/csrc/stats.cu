@@ -6,8 +6,9 @@
 // (accumulated sample by sample with Welford's update).  The merge folds the chunks into the
 // level strictly in chunk order with Chan's pairwise update
 //     M2 <- M2 + M2_c + N n_c / (N + n_c) ||mean_c - mean||_F^2,   sum <- sum + sum_c,
-// one thread per entry for the sums, so the state is a deterministic function of the samples
-// folded in.  Y_l = sum / N and V_l = M2 / (N - 1).
+// one thread per entry for the sums (blocks of kMergeGroup entries, so that the few thousand
+// entries of a small problem still spread over most SMs), so the state is a deterministic
+// function of the samples folded in.  Y_l = sum / N and V_l = M2 / (N - 1).
 #include <algorithm>
 
 #include <cuda_runtime.h>
@@ -19,6 +20,9 @@ namespace mlmc {
 namespace {
 
 constexpr int kMergeThreads = 256;
+// kMergeGroup (internal.h) entries per block of the chunk folds and per share of the
+// between-chunk term: the fold is a chain over the chunks in order, so its parallelism is the
+// number of entries.
 constexpr int kMaxMergeChunks = 4096;
 
 // Per-chunk coefficients of Chan's update, the same for every entry: computed once per block
@@ -89,16 +93,17 @@ __device__ __forceinline__ double chan_fold(const T* __restrict__ partial, int64
             inv_N = T(1) / static_cast<T>(before);
         }
         if (!active) continue;
-        // eight independent loads in flight, then the folds in chunk order
-        for (int i = 0; i < cnt; i += 8) {
-            const int k = min(8, cnt - i);
-            T v[8];
+        // kLoads independent loads in flight, then the folds in chunk order
+        constexpr int kLoads = 16;
+        for (int i = 0; i < cnt; i += kLoads) {
+            const int k = min(kLoads, cnt - i);
+            T v[kLoads];
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
+            for (int u = 0; u < kLoads; ++u)
                 v[u] = u < k ? partial[static_cast<int64_t>(t0 + i + u) * mp + e] : T(0);
             T grp = T(0);
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
+            for (int u = 0; u < kLoads; ++u) {
                 if (u < k) {
                     const ChanCoef<T> cf = coef[i + u];
                     const T t = fma(-cf.nc, K, v[u]);            // sum_c - n_c K
@@ -116,8 +121,9 @@ __device__ __forceinline__ double chan_fold(const T* __restrict__ partial, int64
     return chan;
 }
 
-// Sum of `v` over a block of kMergeThreads threads in a fixed shape; the result is valid in
-// thread 0.  `red` holds kMergeThreads / 32 doubles.
+// Sum of `v` over a block of kThreads threads in a fixed shape; the result is valid in
+// thread 0.  `red` holds kThreads / 32 doubles.
+template <int kThreads>
 __device__ __forceinline__ double block_sum(double v, double* red)
 {
 #pragma unroll
@@ -127,85 +133,92 @@ __device__ __forceinline__ double block_sum(double v, double* red)
     __syncthreads();
     double t = 0.0;
     if (threadIdx.x == 0)
-        for (int w = 0; w < kMergeThreads / 32; ++w) t += red[w];
+        for (int w = 0; w < kThreads / 32; ++w) t += red[w];
     return t;
 }
 
-// One thread per entry, one block per group of kMergeThreads entries: the sums, and each
+// One thread per entry, one block per group of kMergeGroup entries: the sums, and each
 // group's share of the between-chunk term in chan_out[group].
 template <typename T>
-__global__ void __launch_bounds__(kMergeThreads)
+__global__ void __launch_bounds__(kMergeGroup)
 merge_chan_kernel(const T* __restrict__ partial, const ChunkRun run, int64_t mp, double* level_sum,
                   double* chan_out)
 {
-    __shared__ double red[kMergeThreads / 32];
+    __shared__ double red[kMergeGroup / 32];
     __shared__ ChanCoef<T> coef[kCoefTile];
-    const int64_t e = static_cast<int64_t>(blockIdx.x) * kMergeThreads + threadIdx.x;
+    const int64_t e = static_cast<int64_t>(blockIdx.x) * kMergeGroup + threadIdx.x;
     const double chan = chan_fold<T>(partial, mp, e, e < mp, run, level_sum + e, coef);
-    const double t = block_sum(chan, red);
+    const double t = block_sum<kMergeGroup>(chan, red);
     if (threadIdx.x == 0) chan_out[blockIdx.x] = t;
 }
 
-// M2 <- M2 + sum_c M2_c (chunk order; M2_c the sum over the chunk's tiles) + sum of the groups'
-// between-chunk terms (group order).  One block.
+// M2 <- M2 + sum_c M2_c (chunk order; M2_c the sum over the chunk's tiles) + the sum of the
+// groups' between-chunk terms (a fixed shape over the groups).  One block of kMergeThreads.
+// The chunk order keeps a run split at a chunk boundary into two calls bit-identical to one
+// call (the first call's between-chunk terms are zero).
 __device__ __forceinline__ void fold_m2(const double* __restrict__ partial_q, int nchunks, int tiles,
                                         const double* __restrict__ chan, int groups, double* level_M2,
-                                        double* chunk_q)
+                                        double* chunk_q, double* red)
 {
     for (int c = threadIdx.x; c < nchunks; c += blockDim.x) {
         double t = 0.0;
         for (int x = 0; x < tiles; ++x) t += partial_q[static_cast<int64_t>(c) * tiles + x];
         chunk_q[c] = t;
     }
-    __syncthreads();
+    double cg = 0.0;
+    for (int g = threadIdx.x; g < groups; g += blockDim.x) cg += chan[g];
+    const double chan_sum = block_sum<kMergeThreads>(cg, red);   // ends with a block barrier
     if (threadIdx.x == 0) {
         double acc = *level_M2;
         for (int c = 0; c < nchunks; ++c) acc += chunk_q[c];
-        for (int g = 0; g < groups; ++g) acc += chan[g];
-        *level_M2 = acc;
+        *level_M2 = acc + chan_sum;
     }
     __syncthreads();
 }
 
-__global__ void merge_m2_kernel(const double* __restrict__ partial_q, int nchunks, int tiles,
-                                const double* __restrict__ chan, int groups, double* level_M2)
+__global__ void __launch_bounds__(kMergeThreads)
+merge_m2_kernel(const double* __restrict__ partial_q, int nchunks, int tiles, const double* __restrict__ chan,
+                int groups, double* level_M2)
 {
     __shared__ double chunk_q[kMaxMergeChunks];
-    fold_m2(partial_q, nchunks, tiles, chan, groups, level_M2, chunk_q);
+    __shared__ double red[kMergeThreads / 32];
+    fold_m2(partial_q, nchunks, tiles, chan, groups, level_M2, chunk_q, red);
 }
 
 // Batched merge: the jobs of one wave (count read from the device), each folded into its
 // level's FP64 state exactly as merge_chan_kernel / merge_m2_kernel do (the same per-entry fold,
-// the same groups of kMergeThreads entries, the same orders), so a batched call and the same
+// the same groups of kMergeGroup entries, the same orders), so a batched call and the same
 // ranges run one by one give the same bits.  The grid is fixed (grid-stride over jobs in y and
 // entry groups in x) so that a captured graph stays valid when the wave's contents change; a
 // wave holds at most one job per (problem, level).
-__global__ void __launch_bounds__(kMergeThreads) merge_batch_kernel(const MergeJob* __restrict__ jobs,
-                                                                    const int* __restrict__ njobs_dev)
+__global__ void __launch_bounds__(kMergeGroup) merge_batch_kernel(const MergeJob* __restrict__ jobs,
+                                                                  const int* __restrict__ njobs_dev)
 {
-    __shared__ double red[kMergeThreads / 32];
+    __shared__ double red[kMergeGroup / 32];
     __shared__ ChanCoef<float> coef[kCoefTile];
     const int njobs = *njobs_dev;
     for (int j = blockIdx.y; j < njobs; j += gridDim.y) {
         const MergeJob jb = jobs[j];
-        const int64_t groups = (jb.mp + kMergeThreads - 1) / kMergeThreads;
+        const int64_t groups = (jb.mp + kMergeGroup - 1) / kMergeGroup;
         for (int64_t g = blockIdx.x; g < groups; g += gridDim.x) {
-            const int64_t e = g * kMergeThreads + threadIdx.x;
+            const int64_t e = g * kMergeGroup + threadIdx.x;
             const double chan = chan_fold<float>(jb.partial, jb.mp, e, e < jb.mp, jb.run, jb.sum + e, coef);
-            const double t = block_sum(chan, red);
+            const double t = block_sum<kMergeGroup>(chan, red);
             if (threadIdx.x == 0) jb.chan[g] = t;
         }
     }
 }
 
-__global__ void merge_batch_m2_kernel(const MergeJob* __restrict__ jobs, const int* __restrict__ njobs_dev)
+__global__ void __launch_bounds__(kMergeThreads)
+merge_batch_m2_kernel(const MergeJob* __restrict__ jobs, const int* __restrict__ njobs_dev)
 {
     __shared__ double chunk_q[kMaxMergeChunks];
+    __shared__ double red[kMergeThreads / 32];
     const int njobs = *njobs_dev;
     for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
         const MergeJob jb = jobs[j];
-        const int groups = static_cast<int>((jb.mp + kMergeThreads - 1) / kMergeThreads);
-        fold_m2(jb.partial_q, jb.run.nchunks, jb.tiles, jb.chan, groups, jb.M2, chunk_q);
+        const int groups = static_cast<int>((jb.mp + kMergeGroup - 1) / kMergeGroup);
+        fold_m2(jb.partial_q, jb.run.nchunks, jb.tiles, jb.chan, groups, jb.M2, chunk_q, red);
     }
 }
 
@@ -383,7 +396,7 @@ inline unsigned blocks_for(int64_t n, int threads) { return static_cast<unsigned
 
 }  // namespace
 
-int merge_groups(int64_t mp) { return static_cast<int>((mp + kMergeThreads - 1) / kMergeThreads); }
+int merge_groups(int64_t mp) { return static_cast<int>((mp + kMergeGroup - 1) / kMergeGroup); }
 
 cudaError_t launch_merge_partials(const void* partial_sum, bool partial_f64, const double* partial_q, int tiles,
                                   int64_t mp, const ChunkRun& run, double* level_sum, double* level_M2,
@@ -392,10 +405,10 @@ cudaError_t launch_merge_partials(const void* partial_sum, bool partial_f64, con
     if (run.nchunks < 1 || run.nchunks > kMaxMergeChunks) return cudaErrorInvalidValue;
     const unsigned g = static_cast<unsigned>(merge_groups(mp));
     if (partial_f64)
-        merge_chan_kernel<double><<<g, kMergeThreads, 0, st>>>(static_cast<const double*>(partial_sum), run, mp,
+        merge_chan_kernel<double><<<g, kMergeGroup, 0, st>>>(static_cast<const double*>(partial_sum), run, mp,
                                                                level_sum, chan_scratch);
     else
-        merge_chan_kernel<float><<<g, kMergeThreads, 0, st>>>(static_cast<const float*>(partial_sum), run, mp,
+        merge_chan_kernel<float><<<g, kMergeGroup, 0, st>>>(static_cast<const float*>(partial_sum), run, mp,
                                                               level_sum, chan_scratch);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
@@ -406,7 +419,7 @@ cudaError_t launch_merge_partials(const void* partial_sum, bool partial_f64, con
 
 cudaError_t launch_merge_batch(const MergeJob* jobs, const int* njobs_dev, cudaStream_t st)
 {
-    merge_batch_kernel<<<dim3(64, 256), kMergeThreads, 0, st>>>(jobs, njobs_dev);
+    merge_batch_kernel<<<dim3(128, 256), kMergeGroup, 0, st>>>(jobs, njobs_dev);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     merge_batch_m2_kernel<<<256, kMergeThreads, 0, st>>>(jobs, njobs_dev);
