@@ -372,8 +372,8 @@ MLMC_API mlmc_status mlmc_telescoping_sum_host(mlmc_plan_t* plan, double* yhat_h
  * scratch is a fixed 4 MiB array in the library's device image, present on
  * every GPU that loads the library until the process exits.  A problem is
  * accepted only if one chunk of partials fits: m*p*(8 for FP64, 4 for FP32)
- * + 8*ceil(m/64)*ceil(p/64) + 8*ceil(m*p/256), each part rounded up to 256
- * bytes, <= 4 MiB (for FP64, about m*p <= 500000); larger sizes return
+ * + 8*ceil(m/64)*ceil(p/64) + 8*ceil(m*p/64), each part rounded up to 256
+ * bytes, <= 4 MiB (for FP64, about m*p <= 515000); larger sizes return
  * MLMC_ERR_INVALID_ARG with a message.
  * Set-up: the first call on each device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current); make that first call

@@ -301,7 +301,7 @@ extern "C" mlmc_status mlmc_level_stats_noalloc(const mlmc_problem* problem, con
     if (chunks == 0)
         return noalloc_fail(MLMC_ERR_INVALID_ARG,
                             "m*p = %lld too large for the %zu-byte no-alloc scratch (needs m*p*%zu + 8*tiles + "
-                            "8*ceil(m*p/256), each rounded up to 256, <= %zu bytes)",
+                            "8*ceil(m*p/64), each rounded up to 256, <= %zu bytes)",
                             (long long)mp, kNoallocScratchBytes, elem, kNoallocScratchBytes);
     const size_t q_bytes = (chunks * tiles * 8 + 255) / 256 * 256;
 
