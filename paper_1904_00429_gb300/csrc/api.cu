@@ -13,6 +13,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <numeric>
 #include <string>
 #include <vector>
 
@@ -329,6 +330,44 @@ bool tensor_core_precision(int precision) { return precision == MLMC_BF16 || pre
 
 // Operand format of the tensor-core kernel: 0 = bfloat16, 1 = FP8 E4M3 block-scaled.
 int tc_format(const mlmc_options& o) { return o.precision == MLMC_FP8_E4M3 ? 1 : 0; }
+
+// Chunks per launch of the persistent tensor-core kernels in whole rounds.  A launch's items
+// (chunks x output tiles, or x tile pairs) are dealt round-robin to the CTAs (or CTA pairs) that
+// fit on the GPU at once, so a count that is not a multiple of those units leaves some idle in
+// the last round: 1024 chunks of one tile pair on 76 pairs take 14 rounds for 13.5 rounds of
+// work (4 % idle).  Where the budget's count loses more than 1 %, it is rounded (up while the
+// merge's limit allows, else down) to a multiple of the units of every tile the problem's levels
+// use, so full launches keep every unit busy.
+void round_to_waves(ProblemState& ps, int q, int num_sms)
+{
+    auto tiles_per_chunk = [](const TcTile& t, int tiles_m, int tiles_p) {
+        return t.pair ? int64_t((tiles_m + 1) / 2) * tiles_p : int64_t(tiles_m) * tiles_p;
+    };
+    // chunk-count step that makes the items a multiple of the units, and the busy fraction now
+    auto fit = [&](const TcTile& t, int tiles_m, int tiles_p, int64_t* step, double* busy) {
+        const int64_t units = tc_batch_grid(t, q, num_sms);
+        const int64_t per_chunk = tiles_per_chunk(t, tiles_m, tiles_p);
+        if (units <= 0 || per_chunk <= 0) return false;
+        *step = units / std::gcd(units, per_chunk);
+        const int64_t items = int64_t(ps.max_chunks) * per_chunk;
+        *busy = double(items) / double((items + units - 1) / units * units);
+        return true;
+    };
+    int64_t step = 1;
+    double busy = 1.0;
+    if (!fit(ps.tile, ps.tiles_m, ps.tiles_p, &step, &busy)) return;
+    if (ps.tile_wide.mh) {
+        int64_t sw = 1;
+        double bw = 1.0;
+        if (fit(ps.tile_wide, ps.tiles_m_wide, ps.tiles_p_wide, &sw, &bw)) {
+            step = std::lcm(step, sw);
+            busy = std::min(busy, bw);
+        }
+    }
+    if (busy >= 0.99 || step > ps.max_chunks) return;
+    const int64_t up = (int64_t(ps.max_chunks) + step - 1) / step * step;
+    ps.max_chunks = int(up <= kMaxChunksPerLaunch ? up : int64_t(ps.max_chunks) / step * step);
+}
 
 // Read the kernels' error word (synchronises the stream).
 mlmc_status check_device_flag(mlmc_plan_t* plan)
@@ -960,6 +999,8 @@ mlmc_status mlmc_plan(const mlmc_problem* problems, int32_t nprob, const mlmc_op
     plan->elem = plan->f64 ? 8 : 4;
     plan->probs.resize(size_t(nprob));
 
+    if (cudaDeviceGetAttribute(&plan->num_sms, cudaDevAttrMultiProcessorCount, plan->device) != cudaSuccess)
+        plan->num_sms = 1;
     size_t max_partial = 0, max_q = 0, max_mp = 0;
     auto oom = [&](const char* what) {
         free_plan(plan);
@@ -1002,6 +1043,7 @@ mlmc_status mlmc_plan(const mlmc_problem* problems, int32_t nprob, const mlmc_op
         const size_t per_chunk = mp * plan->elem;
         const size_t budget = tensor_core_precision(options->precision) ? kPartialBudgetTc : kPartialBudget;
         ps.max_chunks = int(std::clamp<size_t>(budget / per_chunk, 1, kMaxChunksPerLaunch));
+        if (tensor_core_precision(options->precision)) round_to_waves(ps, tc_format(*options), plan->num_sms);
         max_partial = std::max(max_partial, per_chunk * size_t(ps.max_chunks));
         max_q = std::max(max_q, size_t(ps.max_chunks) *
                                     size_t(std::max(ps.tiles_m * ps.tiles_p, ps.tiles_m_wide * ps.tiles_p_wide)));
@@ -1079,8 +1121,6 @@ mlmc_status mlmc_plan(const mlmc_problem* problems, int32_t nprob, const mlmc_op
     if (cudaMalloc(reinterpret_cast<void**>(&plan->ext_q), sizeof(double)) != cudaSuccess) return oom("merge scratch");
     if (cudaMalloc(reinterpret_cast<void**>(&plan->err_flag), sizeof(int)) != cudaSuccess) return oom("error flag");
     cudaMemsetAsync(plan->err_flag, 0, sizeof(int), plan->stream);
-    if (cudaDeviceGetAttribute(&plan->num_sms, cudaDevAttrMultiProcessorCount, plan->device) != cudaSuccess)
-        plan->num_sms = 1;
     if (options->timeout_ns > 0) plan->timeout_ns = uint64_t(options->timeout_ns);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) {
