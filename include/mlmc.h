@@ -217,9 +217,12 @@ MLMC_API mlmc_status mlmc_plan_destroy(mlmc_plan_t* plan);
  * chunks are folded into the level in chunk order by Chan's pairwise update
  * (the variance of Remark 3.6 without the cancellation of a one-pass formula).
  * Samples are pure functions of their ids, so disjoint ranges may be
- * evaluated in any order and split across calls; the statistics are
- * bit-identical for any split at multiples of 64 sample ids and in any case
- * equal up to rounding.  count = 0 is a no-op. */
+ * evaluated in any order and split across calls: for any split at multiples
+ * of 64 sample ids N and the per-entry sums are bit-identical (one chain of
+ * FP64 additions per entry in chunk order) and M2 equal up to the rounding of
+ * its between-chunk terms, which are summed per launch of chunks (bit-identical
+ * too where the launches coincide, e.g. a first call of one chunk); any split
+ * gives the same statistics up to rounding.  count = 0 is a no-op. */
 MLMC_API mlmc_status mlmc_level_stats(mlmc_plan_t* plan, int32_t prob, int32_t level, uint64_t sample_begin,
                              uint64_t count);
 

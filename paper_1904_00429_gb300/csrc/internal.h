@@ -13,7 +13,8 @@ namespace mlmc {
 // Samples are grouped into fixed chunks of consecutive sample ids (chunk c of a
 // level holds ids c*chunk .. c*chunk+chunk-1).  Partial statistics are produced
 // per chunk and folded into a level in chunk order, so the result does not
-// depend on grid shapes or on how sample ranges are split at chunk boundaries.
+// depend on grid shapes, and a split of sample ranges at chunk boundaries
+// changes only the rounding of M2's between-chunk terms (summed per launch).
 // The plan's kernels use chunk_samples(c_l) (8 to 64, a power of two: cheap
 // samples get longer chunks: the longest with at most 8192 sampled products, or 8
 // samples; this bounds the FP32 accumulation of a chunk sum); the no-allocation

@@ -154,8 +154,9 @@ merge_chan_kernel(const T* __restrict__ partial, const ChunkRun run, int64_t mp,
 
 // M2 <- M2 + sum_c M2_c (chunk order; M2_c the sum over the chunk's tiles) + the sum of the
 // groups' between-chunk terms (a fixed shape over the groups).  One block of kMergeThreads.
-// The chunk order keeps a run split at a chunk boundary into two calls bit-identical to one
-// call (the first call's between-chunk terms are zero).
+// The chunk order keeps a run split into two calls, the first of one chunk, bit-identical to
+// one call (the first call's between-chunk terms are zero); other splits move the launches'
+// between-chunk sums by rounding.
 __device__ __forceinline__ void fold_m2(const double* __restrict__ partial_q, int nchunks, int tiles,
                                         const double* __restrict__ chan, int groups, double* level_M2,
                                         double* chunk_q, double* red)
